@@ -1,0 +1,160 @@
+/*
+ * symft.h -- C ABI of the B300 SymFT per-shot sampling engine.
+ *
+ * The engine samples noisy, adaptive, Clifford-dominated circuits with Pauli
+ * rotations exactly, following SymFT (arxiv 2607.28600):
+ *   - symft_compile runs the one-time compile step on the host: symbolic
+ *     Clifford-Pauli frame factorization (Sec. 3, Eqs. factorization-invariant
+ *     and factorized-circuit), adaptive stabilizer-coordinate planning over the
+ *     stabilizer-destabilizer tableau (Sec. 4, seven instruction kinds), and
+ *     lowering of the affine sign expressions into a flat device plan (Sec. 6,
+ *     "Precompiled sampling instructions").
+ *   - symft_sample runs the per-shot sampler (Sec. 5, single-shot algorithm)
+ *     on the GPU for many shots at once: counter-based noise and random bits,
+ *     bit-packed sign evaluation (64 shots per word), and the dense
+ *     active-state executor for PromoteRot / ActiveDiagRot / ActivePairRot /
+ *     ActiveDiagMeas / ActivePairMeas.
+ *
+ * Output layout (every column output): column j occupies words
+ * out[j*W .. j*W + W-1] with W = ceil(shots / 64); bit (r & 63) of word r >> 6
+ * is shot r (relative to shot_offset).  Padding bits past `shots` are 0.
+ * Columns: meas_out has one column per recorded measurement (record order),
+ * det_out one per DETECTOR, obs_out one per observable index, discard_out a
+ * single column.
+ *
+ * Randomness: shot r (absolute index shot_offset + r) of seed s draws from a
+ * fixed Philox4x32-10 stream keyed by (s, channel ordinal, measurement
+ * ordinal, shot block), so outputs do not depend on launch shapes, on how
+ * shots are split across calls, or on the precision of the dense executor
+ * (up to outcome flips where an FP32 branch probability sits within rounding
+ * of the measurement uniform).
+ *
+ * Errors: every int-returning call returns SYMFT_OK (0) or a negative
+ * symft_status; symft_last_error() returns a message for the calling thread.
+ * Device code never traps: errors it detects are written to a status word
+ * that symft_sample_ex reads back when args->check is set.
+ */
+#ifndef SYMFT_H
+#define SYMFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SYMFT_OK = 0,
+  SYMFT_E_PARSE = -1,        /* malformed circuit text */
+  SYMFT_E_UNSUPPORTED = -2,  /* instruction outside the supported model */
+  SYMFT_E_ARG = -3,          /* invalid argument (null plan, bad sizes, ...) */
+  SYMFT_E_CAPACITY = -4,     /* plan exceeds a build limit (active width, ...) */
+  SYMFT_E_NOMEM = -5,        /* host or device allocation failed */
+  SYMFT_E_CUDA = -6,         /* CUDA runtime error */
+  SYMFT_E_TIMEOUT = -7,      /* a bounded device wait expired */
+  SYMFT_E_DEVICE = -8        /* device-side check failed (status word) */
+} symft_status;
+
+enum { SYMFT_POSTSELECT_NONE = 0, SYMFT_POSTSELECT_ALL = 1 };
+enum { SYMFT_FP32 = 0, SYMFT_FP64 = 1 };
+enum { SYMFT_OUT_DEVICE = 0, SYMFT_OUT_HOST = 1 };
+
+typedef struct symft_plan symft_plan;   /* opaque; immutable after compile */
+
+typedef struct {
+  int postselect;   /* SYMFT_POSTSELECT_*: reject a shot at the first fired
+                       detector (Sec. 6, "Detector postselection") */
+  int reserved[7];
+} symft_options;
+
+/* Counts of a compiled plan (Sec. 5, "Sampling complexity"). */
+typedef struct {
+  uint32_t n_qubits;
+  uint32_t n_meas_events;     /* all measurements, recorded and hidden (resets) */
+  uint32_t n_records;         /* recorded measurements: columns of meas_out */
+  uint32_t n_dets;            /* columns of det_out */
+  uint32_t n_obs;             /* columns of obs_out */
+  uint32_t n_channels;        /* stochastic Pauli noise locations n_e */
+  uint32_t k_max;             /* peak active width k_max^S */
+  uint32_t n_instr[7];        /* PromoteRot, ActiveDiagRot, ActivePairRot,
+                                 RandomMeas, DetMeas, ActiveDiagMeas,
+                                 ActivePairMeas */
+  uint32_t max_expr_weight;   /* d - 1 = max weight of an evaluated sign */
+  uint32_t n_noise_components;/* symplectic noise bits carried by the plan */
+  uint32_t n_targets;         /* bit-packed outputs the sign kernel computes */
+  uint32_t n_causal;          /* active-measurement outcomes (m3 symbols) */
+  uint64_t sign_xor_terms;    /* total (symbol, target) incidences */
+} symft_info;
+
+/* One sampling request.  All pointers may be NULL to skip that output. */
+typedef struct {
+  uint64_t shots;          /* number of shots (>= 1) */
+  uint64_t seed;           /* Philox key */
+  uint64_t shot_offset;    /* absolute index of the first shot; multiple of 128 */
+  uint64_t* meas_out;      /* n_records * W words */
+  uint64_t* det_out;       /* n_dets * W words */
+  uint64_t* obs_out;       /* n_obs * W words */
+  uint64_t* discard_out;   /* W words: 1 = shot rejected by postselection */
+  int precision;           /* SYMFT_FP32 (default) or SYMFT_FP64 dense vectors */
+  int out_location;        /* SYMFT_OUT_DEVICE (default) or SYMFT_OUT_HOST */
+  int check;               /* non-zero: synchronise and read the device status */
+  int reserved;
+  void* stream;            /* cudaStream_t (NULL: legacy default stream) */
+} symft_sample_args;
+
+/* Compile circuit text (grammar below) with default options.
+ * circuit_text: NUL-terminated, caller-owned, only read during the call.
+ * *out receives a plan owned by the library; free with symft_plan_free.
+ * Returns SYMFT_E_PARSE / SYMFT_E_UNSUPPORTED / SYMFT_E_CAPACITY on bad input.
+ *
+ * Grammar (Stim-like, one instruction per line, '#' comments):
+ *   H S S_DAG SQRT_X SQRT_X_DAG X Y Z I  q...        single-qubit Cliffords
+ *   CX|CNOT CY CZ SWAP  a b ...                      two-qubit Cliffords
+ *   CX|CY|CZ rec[-k] q                               record-controlled Pauli
+ *   R_X(t) R_Y(t) R_Z(t) T T_DAG q...; R_PAULI(t) X0*Z3*...  rotations
+ *       R_P(t) = exp(-i t P / 2)  (Sec. 2)
+ *   M MX MY MR MRX R RX q...; MPP X0*Z1 ...          Pauli measurements
+ *       (R = hidden Z measurement + X feedback, RX likewise in X)
+ *   X_ERROR(p) Y_ERROR(p) Z_ERROR(p) DEPOLARIZE1(p) DEPOLARIZE2(p)
+ *   PAULI_CHANNEL_1(px,py,pz)                        stochastic Pauli noise
+ *   DETECTOR rec[-k]...  OBSERVABLE_INCLUDE(i) rec[-k]...  REPEAT n { }
+ *   TICK QUBIT_COORDS SHIFT_COORDS                    ignored
+ */
+int symft_compile(const char* circuit_text, symft_plan** out);
+
+/* As symft_compile with options (NULL = defaults). */
+int symft_compile_ex(const char* circuit_text, const symft_options* opt, symft_plan** out);
+
+/* Fill *info with the plan's counts.  Host only, no GPU needed. */
+int symft_plan_info(const symft_plan* plan, symft_info* info);
+
+/* Release a plan and its device workspace.  NULL is a no-op.  The caller must
+ * make sure no sampling call on the plan is still running. */
+void symft_plan_free(symft_plan* plan);
+
+/* Sample `shots` shots with seed `seed` into caller-owned DEVICE buffers
+ * (layout above), asynchronously on `cuda_stream` (a cudaStream_t or NULL).
+ * Results are valid once the stream has been synchronised.  The first call
+ * on a plan uploads it and allocates its workspace (cudaMalloc); later calls
+ * reuse both.  Calls on one plan must not overlap (one stream at a time). */
+int symft_sample(const symft_plan* plan, uint64_t shots, uint64_t seed,
+                 uint64_t* meas_out, uint64_t* det_out, uint64_t* obs_out,
+                 void* cuda_stream);
+
+/* General form: shot offset, discard column, precision, host outputs
+ * (out_location = SYMFT_OUT_HOST: the pointers are host memory, preferably
+ * pinned; the call copies results back and returns after the copy). */
+int symft_sample_ex(const symft_plan* plan, const symft_sample_args* args);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char* symft_last_error(void);
+
+/* Number of kernel launches the last sampling call on this thread issued. */
+int symft_last_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SYMFT_H */

@@ -1,0 +1,191 @@
+"""B300-native SymFT per-shot sampling engine: thin Python binding of libsymft.so.
+
+Every step of the sampler runs in the library (C++ compile step, CUDA kernels);
+this module only marshals arguments through ctypes.  Device buffers are passed
+as raw pointers (``torch.Tensor.data_ptr()``), host buffers as numpy arrays.
+There is no CPU fallback: if the shared library is missing the import of
+:func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsymft.so")
+
+SYMFT_OK = 0
+POSTSELECT_NONE, POSTSELECT_ALL = 0, 1
+FP32, FP64 = 0, 1
+OUT_DEVICE, OUT_HOST = 0, 1
+INSTR_NAMES = ("PromoteRot", "ActiveDiagRot", "ActivePairRot", "RandomMeas", "DetMeas",
+               "ActiveDiagMeas", "ActivePairMeas")
+
+EXPORTS = ("symft_compile", "symft_compile_ex", "symft_plan_info", "symft_plan_free",
+           "symft_sample", "symft_sample_ex", "symft_last_error", "symft_last_launch_count")
+
+
+class SymftError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"symft error {code}: {msg}")
+        self.code = code
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("postselect", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_uint32), ("n_meas_events", ctypes.c_uint32),
+                ("n_records", ctypes.c_uint32), ("n_dets", ctypes.c_uint32),
+                ("n_obs", ctypes.c_uint32), ("n_channels", ctypes.c_uint32),
+                ("k_max", ctypes.c_uint32), ("n_instr", ctypes.c_uint32 * 7),
+                ("max_expr_weight", ctypes.c_uint32), ("n_noise_components", ctypes.c_uint32),
+                ("n_targets", ctypes.c_uint32), ("n_causal", ctypes.c_uint32),
+                ("sign_xor_terms", ctypes.c_uint64)]
+
+
+class _SampleArgs(ctypes.Structure):
+    _fields_ = [("shots", ctypes.c_uint64), ("seed", ctypes.c_uint64),
+                ("shot_offset", ctypes.c_uint64), ("meas_out", ctypes.c_void_p),
+                ("det_out", ctypes.c_void_p), ("obs_out", ctypes.c_void_p),
+                ("discard_out", ctypes.c_void_p), ("precision", ctypes.c_int),
+                ("out_location", ctypes.c_int), ("check", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+_LIB = None
+
+
+def lib():
+    """Load libsymft.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_2607_28600_b300.build` "
+                          "(there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    L.symft_compile.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]
+    L.symft_compile.restype = ctypes.c_int
+    L.symft_compile_ex.argtypes = [ctypes.c_char_p, ctypes.POINTER(_Options), ctypes.POINTER(ctypes.c_void_p)]
+    L.symft_compile_ex.restype = ctypes.c_int
+    L.symft_plan_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Info)]
+    L.symft_plan_info.restype = ctypes.c_int
+    L.symft_plan_free.argtypes = [ctypes.c_void_p]
+    L.symft_plan_free.restype = None
+    L.symft_sample.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
+                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.symft_sample.restype = ctypes.c_int
+    L.symft_sample_ex.argtypes = [ctypes.c_void_p, ctypes.POINTER(_SampleArgs)]
+    L.symft_sample_ex.restype = ctypes.c_int
+    L.symft_last_error.argtypes = []
+    L.symft_last_error.restype = ctypes.c_char_p
+    L.symft_last_launch_count.argtypes = []
+    L.symft_last_launch_count.restype = ctypes.c_int
+    _LIB = L
+    return L
+
+
+def _check(rc):
+    if rc != SYMFT_OK:
+        raise SymftError(rc, lib().symft_last_error().decode(errors="replace"))
+
+
+def _ptr(x):
+    """Raw address of a torch tensor, numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream  # torch.cuda.Stream
+
+
+class Plan:
+    """Owned handle of a compiled plan (frees it on garbage collection)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self._info = None
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _LIB is not None:
+            _LIB.symft_plan_free(h)
+
+    @property
+    def info(self) -> dict:
+        if self._info is None:
+            self._info = symft_plan_info(self)
+        return self._info
+
+    def words(self, shots: int) -> int:
+        return (shots + 63) // 64
+
+
+def symft_compile(circuit_text: str, postselect: int = POSTSELECT_NONE) -> Plan:
+    h = ctypes.c_void_p()
+    opt = _Options()
+    opt.postselect = postselect
+    _check(lib().symft_compile_ex(circuit_text.encode(), ctypes.byref(opt), ctypes.byref(h)))
+    return Plan(h.value)
+
+
+def symft_plan_info(plan: Plan) -> dict:
+    info = _Info()
+    _check(lib().symft_plan_info(plan.handle, ctypes.byref(info)))
+    d = {name: getattr(info, name) for name, _ in _Info._fields_ if name != "n_instr"}
+    d["n_instr"] = {INSTR_NAMES[i]: int(info.n_instr[i]) for i in range(7)}
+    return d
+
+
+def symft_sample(plan: Plan, shots: int, seed: int, meas_out=None, det_out=None, obs_out=None,
+                 stream=None) -> None:
+    _check(lib().symft_sample(plan.handle, shots, seed, _ptr(meas_out), _ptr(det_out),
+                              _ptr(obs_out), _stream(stream)))
+
+
+def symft_sample_ex(plan: Plan, shots: int, seed: int, shot_offset: int = 0, meas_out=None,
+                    det_out=None, obs_out=None, discard_out=None, precision: int = FP32,
+                    out_location: int = OUT_DEVICE, check: bool = False, stream=None) -> None:
+    a = _SampleArgs()
+    a.shots, a.seed, a.shot_offset = shots, seed, shot_offset
+    a.meas_out, a.det_out = _ptr(meas_out), _ptr(det_out)
+    a.obs_out, a.discard_out = _ptr(obs_out), _ptr(discard_out)
+    a.precision, a.out_location, a.check = precision, out_location, int(bool(check))
+    a.stream = _stream(stream)
+    _check(lib().symft_sample_ex(plan.handle, ctypes.byref(a)))
+
+
+def symft_last_launch_count() -> int:
+    return lib().symft_last_launch_count()
+
+
+def sample_to_tensors(plan: Plan, shots: int, seed: int, shot_offset: int = 0,
+                      precision: int = FP32, stream=None, device="cuda"):
+    """Allocate device output columns (torch int64 holding the uint64 words) and sample."""
+    import torch
+    W = plan.words(shots)
+    info = plan.info
+    meas = torch.empty((info["n_records"], W), dtype=torch.int64, device=device)
+    det = torch.empty((info["n_dets"], W), dtype=torch.int64, device=device)
+    obs = torch.empty((info["n_obs"], W), dtype=torch.int64, device=device)
+    disc = torch.empty((W,), dtype=torch.int64, device=device)
+    symft_sample_ex(plan, shots, seed, shot_offset=shot_offset,
+                    meas_out=meas if meas.numel() else None,
+                    det_out=det if det.numel() else None,
+                    obs_out=obs if obs.numel() else None,
+                    discard_out=disc, precision=precision, stream=stream)
+    return meas, det, obs, disc

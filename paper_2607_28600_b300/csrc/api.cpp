@@ -1,0 +1,399 @@
+// C ABI (include/symft.h): compile, plan info, sampling, errors.
+//
+// The plan owns its host description, its device copy (uploaded by the first
+// sampling call) and a workspace that grows to the largest request seen and
+// is reused by later calls (Sec. 6, "Reusing the prepared state").
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "plan_dev.hpp"
+#include "internal.hpp"
+#include "symft.h"
+
+namespace symft {
+cudaError_t launch_sign(const SignArgs& a, int warps_per_block, int grid, cudaStream_t st);
+cudaError_t launch_dense(const DenseArgs& a, bool fp64, int warps_per_block, int grid, size_t smem,
+                         cudaStream_t st);
+cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t st);
+}  // namespace symft
+
+
+
+using namespace symft;
+
+namespace {
+thread_local std::string g_last_error;
+thread_local int g_last_launches = 0;
+
+int set_error(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t need) {
+    if (need <= bytes) return cudaSuccess;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&ptr, need);
+    if (e == cudaSuccess) bytes = need;
+    return e;
+  }
+  void release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+  }
+};
+}  // namespace
+
+struct symft_plan {
+  HostPlan hp;
+  std::mutex mu;
+  bool uploaded = false;
+  int device = -1;
+  DevBuf plan_buf;
+  DevPlan dp{};
+  DevBuf signs, m3, det_scratch, gvec, status;
+  DevBuf h_meas, h_det, h_obs, h_disc;   // staging for host outputs
+  int sm_count = 0;
+};
+
+namespace {
+
+template <class T>
+size_t push(std::vector<unsigned char>& blob, const std::vector<T>& v) {
+  size_t off = (blob.size() + 15) & ~size_t(15);
+  blob.resize(off + v.size() * sizeof(T) + 16);
+  if (!v.empty()) std::memcpy(blob.data() + off, v.data(), v.size() * sizeof(T));
+  return off;
+}
+
+cudaError_t upload(symft_plan* P) {
+  const HostPlan& h = P->hp;
+  std::vector<ChannelDev> ch(h.n_channels);
+  for (uint32_t c = 0; c < h.n_channels; ++c)
+    ch[c] = ChannelDev{h.ch_theta_last[c], h.ch_qtab[c], h.ch_ctab[c], h.ch_comp0[c], h.ch_ncomp[c]};
+  std::vector<uint32_t> qtheta;
+  for (auto& q : h.qtabs) qtheta.insert(qtheta.end(), q.theta, q.theta + kNoiseBlock);
+  std::vector<CellTableDev> ct(h.ctabs.size());
+  for (size_t i = 0; i < h.ctabs.size(); ++i) {
+    ct[i].ncell = h.ctabs[i].ncell;
+    std::memcpy(ct[i].phi, h.ctabs[i].phi, sizeof(ct[i].phi));
+    std::memcpy(ct[i].mask, h.ctabs[i].mask, sizeof(ct[i].mask));
+  }
+  std::vector<DenseInstrDev> dn(h.dense.size());
+  for (size_t g = 0; g < h.dense.size(); ++g) {
+    const DenseInstr& d = h.dense[g];
+    DenseInstrDev& o = dn[g];
+    o.kind = d.kind;
+    o.k = d.k;
+    o.h = d.h;
+    o.mu = d.mu;
+    o.a = d.a;
+    o.b = d.b;
+    o.eta = d.eta;
+    o.m3 = d.m3;
+    o.c = d.c;
+    o.s = d.s;
+    o.sign_target_col = d.sign_target - h.tgt_sign0;
+    o.causal_off = d.causal_off;
+    o.causal_n = d.causal_n;
+    o.t = d.t;
+  }
+  std::vector<unsigned char> blob;
+  size_t o_ch = push(blob, ch), o_q = push(blob, qtheta), o_ct = push(blob, ct);
+  size_t o_co = push(blob, h.comp_off), o_ctg = push(blob, h.comp_tgt);
+  size_t o_m1t = push(blob, h.m1_t), o_m1o = push(blob, h.m1_off), o_m1g = push(blob, h.m1_tgt);
+  size_t o_tc = push(blob, h.tgt_const), o_tco = push(blob, h.tgt_causal_off), o_tca = push(blob, h.tgt_causal);
+  size_t o_pe = push(blob, h.post_events), o_dn = push(blob, dn), o_dc = push(blob, h.dense_causal);
+  cudaError_t e = P->plan_buf.ensure(blob.size());
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(P->plan_buf.ptr, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  auto at = [&](size_t off) { return static_cast<unsigned char*>(P->plan_buf.ptr) + off; };
+  DevPlan& d = P->dp;
+  d.n_channels = h.n_channels;
+  d.ch = reinterpret_cast<const ChannelDev*>(at(o_ch));
+  d.qtheta = reinterpret_cast<const uint32_t*>(at(o_q));
+  d.ctabs = reinterpret_cast<const CellTableDev*>(at(o_ct));
+  d.comp_off = reinterpret_cast<const uint32_t*>(at(o_co));
+  d.comp_tgt = reinterpret_cast<const uint32_t*>(at(o_ctg));
+  d.n_m1 = static_cast<uint32_t>(h.m1_t.size());
+  d.m1_t = reinterpret_cast<const uint32_t*>(at(o_m1t));
+  d.m1_off = reinterpret_cast<const uint32_t*>(at(o_m1o));
+  d.m1_tgt = reinterpret_cast<const uint32_t*>(at(o_m1g));
+  d.n_targets = h.n_targets;
+  d.tgt_det0 = h.tgt_det0;
+  d.tgt_obs0 = h.tgt_obs0;
+  d.tgt_sign0 = h.tgt_sign0;
+  d.tgt_const = reinterpret_cast<const uint8_t*>(at(o_tc));
+  d.tgt_causal_off = reinterpret_cast<const uint32_t*>(at(o_tco));
+  d.tgt_causal = reinterpret_cast<const uint32_t*>(at(o_tca));
+  d.n_post_events = static_cast<uint32_t>(h.post_events.size());
+  d.post_events = reinterpret_cast<const int32_t*>(at(o_pe));
+  d.n_dense = static_cast<uint32_t>(h.dense.size());
+  d.dense = reinterpret_cast<const DenseInstrDev*>(at(o_dn));
+  d.dense_causal = reinterpret_cast<const uint32_t*>(at(o_dc));
+  d.n_m3 = h.n_m3;
+  d.n_records = h.n_records;
+  d.n_dets = h.n_dets;
+  d.n_obs = h.n_obs;
+  d.postselect = h.postselect;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  P->device = dev;
+  cudaDeviceGetAttribute(&P->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  P->uploaded = true;
+  return cudaSuccess;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t _e = (expr);                                                             \
+    if (_e != cudaSuccess)                                                               \
+      return set_error(_e == cudaErrorMemoryAllocation ? SYMFT_E_NOMEM : SYMFT_E_CUDA,   \
+                       std::string(#expr) + ": " + cudaGetErrorString(_e));              \
+  } while (0)
+
+int sample_impl(symft_plan* P, const symft_sample_args* a) {
+  const HostPlan& h = P->hp;
+  if (a->shots == 0) return set_error(SYMFT_E_ARG, "shots must be >= 1");
+  if (a->shot_offset % kNoiseBlock) return set_error(SYMFT_E_ARG, "shot_offset must be a multiple of 128");
+  if (a->shots + a->shot_offset > (1ull << 39)) return set_error(SYMFT_E_ARG, "shot index beyond 2^39");
+  if (a->precision != SYMFT_FP32 && a->precision != SYMFT_FP64) return set_error(SYMFT_E_ARG, "bad precision");
+  if (a->out_location != SYMFT_OUT_DEVICE && a->out_location != SYMFT_OUT_HOST)
+    return set_error(SYMFT_E_ARG, "bad out_location");
+  cudaStream_t st = static_cast<cudaStream_t>(a->stream);
+  if (!P->uploaded) CUDA_TRY(upload(P));
+  int launches = 0;
+  const uint64_t W = (a->shots + 63) / 64;
+  const uint64_t nblk = (a->shots + kNoiseBlock - 1) / kNoiseBlock;
+  const bool host = a->out_location == SYMFT_OUT_HOST;
+
+  uint64_t *meas = a->meas_out, *det = a->det_out, *obs = a->obs_out, *disc = a->discard_out;
+  if (host) {
+    if (meas) { CUDA_TRY(P->h_meas.ensure(std::max<uint64_t>(1, h.n_records * W) * 8)); meas = (uint64_t*)P->h_meas.ptr; }
+    if (det) { CUDA_TRY(P->h_det.ensure(std::max<uint64_t>(1, h.n_dets * W) * 8)); det = (uint64_t*)P->h_det.ptr; }
+    if (obs) { CUDA_TRY(P->h_obs.ensure(std::max<uint64_t>(1, h.n_obs * W) * 8)); obs = (uint64_t*)P->h_obs.ptr; }
+    if (disc) { CUDA_TRY(P->h_disc.ensure(W * 8)); disc = (uint64_t*)P->h_disc.ptr; }
+  }
+  if (h.n_records == 0) meas = nullptr;
+  if (h.n_dets == 0) det = nullptr;
+  if (h.n_obs == 0) obs = nullptr;
+  const bool need_final = h.n_m3 > 0 || h.postselect || disc != nullptr;
+  if (h.postselect && det == nullptr && h.n_dets > 0) {
+    CUDA_TRY(P->det_scratch.ensure(h.n_dets * W * 8));
+    det = static_cast<uint64_t*>(P->det_scratch.ptr);
+  }
+  const uint32_t G = static_cast<uint32_t>(h.dense.size());
+  uint64_t* signs = nullptr;
+  if (G) {
+    CUDA_TRY(P->signs.ensure(G * W * 8));
+    signs = static_cast<uint64_t*>(P->signs.ptr);
+  }
+  CUDA_TRY(P->status.ensure(16));
+  int* status = static_cast<int*>(P->status.ptr);
+  if (a->check) CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+
+  // --- sign kernel ---------------------------------------------------------
+  if (h.n_targets > 0) {
+    SignArgs s{};
+    s.p = P->dp;
+    s.seed = a->seed;
+    s.block0 = a->shot_offset / kNoiseBlock;
+    s.n_blocks = nblk;
+    s.W = W;
+    s.shots = a->shots;
+    s.meas = meas;
+    s.det = det;
+    s.obs = obs;
+    s.signs = signs;
+    s.status = status;
+    size_t per_warp = static_cast<size_t>(h.n_targets) * 16;
+    if (per_warp > 200 * 1024)
+      return set_error(SYMFT_E_CAPACITY, "too many bit-packed targets for shared memory (" +
+                                             std::to_string(h.n_targets) + ")");
+    int wpb = static_cast<int>(std::min<size_t>(8, std::max<size_t>(1, (96 * 1024) / per_warp)));
+    uint64_t want = (nblk + wpb - 1) / wpb;
+    uint64_t cap = static_cast<uint64_t>(P->sm_count) * 16;
+    int grid = static_cast<int>(std::max<uint64_t>(1, std::min(want, cap)));
+    CUDA_TRY(launch_sign(s, wpb, grid, st));
+    ++launches;
+  }
+  // --- dense kernel --------------------------------------------------------
+  if (G) {
+    const bool fp64 = a->precision == SYMFT_FP64;
+    CUDA_TRY(P->m3.ensure(std::max<uint64_t>(1, h.n_m3 * W) * 8));
+    if (h.n_m3) CUDA_TRY(cudaMemsetAsync(P->m3.ptr, 0, h.n_m3 * W * 8, st));
+    DenseArgs d{};
+    d.p = P->dp;
+    d.seed = a->seed;
+    d.shot0 = a->shot_offset;
+    d.shots = a->shots;
+    d.W = W;
+    d.signs = signs;
+    d.m3_out = static_cast<uint64_t*>(P->m3.ptr);
+    d.kmax = h.k_max;
+    d.status = status;
+    const size_t amp = fp64 ? 16 : 8;
+    const size_t m3bytes = ((h.n_m3 + 31) / 32) * 4;
+    const size_t vec_bytes = (static_cast<size_t>(1) << h.k_max) * amp;
+    int wpb = 4;
+    size_t smem;
+    if (vec_bytes + m3bytes <= 48 * 1024) {
+      wpb = static_cast<int>(std::min<size_t>(8, std::max<size_t>(1, (160 * 1024) / (vec_bytes + m3bytes + 16))));
+      d.use_smem = 1;
+      smem = ((wpb * m3bytes + 15) & ~size_t(15)) + wpb * vec_bytes;
+    } else {
+      d.use_smem = 0;
+      smem = wpb * m3bytes + 16;
+    }
+    uint64_t want = (a->shots + wpb - 1) / wpb;
+    uint64_t cap = static_cast<uint64_t>(P->sm_count) * (d.use_smem ? 16 : 8);
+    if (!d.use_smem) {
+      // bound the global-memory vectors to ~8 GB of resident warp slots
+      uint64_t max_warps = std::max<uint64_t>(1, (8ull << 30) / vec_bytes);
+      cap = std::min<uint64_t>(cap, std::max<uint64_t>(1, max_warps / wpb));
+    }
+    int grid = static_cast<int>(std::max<uint64_t>(1, std::min(want, cap)));
+    if (!d.use_smem) {
+      d.gvec_stride = static_cast<uint64_t>(1) << h.k_max;
+      CUDA_TRY(P->gvec.ensure(static_cast<size_t>(grid) * wpb * vec_bytes));
+      d.gvec = P->gvec.ptr;
+    }
+    CUDA_TRY(launch_dense(d, fp64, wpb, grid, smem, st));
+    ++launches;
+  }
+  // --- finalize ------------------------------------------------------------
+  if (need_final) {
+    FinalArgs f{};
+    f.p = P->dp;
+    f.W = W;
+    f.shots = a->shots;
+    f.m3 = h.n_m3 ? static_cast<const uint64_t*>(P->m3.ptr) : nullptr;
+    f.meas = meas;
+    f.det = det;
+    f.obs = obs;
+    f.discard = disc;
+    CUDA_TRY(launch_finalize(f, st));
+    ++launches;
+  }
+  if (host) {
+    if (a->meas_out && meas) CUDA_TRY(cudaMemcpyAsync(a->meas_out, meas, h.n_records * W * 8, cudaMemcpyDeviceToHost, st));
+    if (a->det_out && det) CUDA_TRY(cudaMemcpyAsync(a->det_out, det, h.n_dets * W * 8, cudaMemcpyDeviceToHost, st));
+    if (a->obs_out && obs) CUDA_TRY(cudaMemcpyAsync(a->obs_out, obs, h.n_obs * W * 8, cudaMemcpyDeviceToHost, st));
+    if (a->discard_out && disc) CUDA_TRY(cudaMemcpyAsync(a->discard_out, disc, W * 8, cudaMemcpyDeviceToHost, st));
+  }
+  g_last_launches = launches;
+  if (host || a->check) CUDA_TRY(cudaStreamSynchronize(st));
+  if (a->check) {
+    int hs = 0;
+    CUDA_TRY(cudaMemcpy(&hs, status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (hs != 0) return set_error(SYMFT_E_DEVICE, "device status " + std::to_string(hs));
+  }
+  return SYMFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int symft_compile_ex(const char* text, const symft_options* opt, symft_plan** out) {
+  g_last_error.clear();
+  if (!text || !out) return set_error(SYMFT_E_ARG, "null argument");
+  *out = nullptr;
+  symft_options o{};
+  if (opt) o = *opt;
+  if (o.postselect != SYMFT_POSTSELECT_NONE && o.postselect != SYMFT_POSTSELECT_ALL)
+    return set_error(SYMFT_E_ARG, "bad postselect mode");
+  try {
+    Circuit c = parse_circuit(text);
+    symft_plan* p = new symft_plan();
+    p->hp = compile_plan(c, o);
+    *out = p;
+    return SYMFT_OK;
+  } catch (const Error& e) {
+    return set_error(e.code, e.what());
+  } catch (const std::bad_alloc&) {
+    return set_error(SYMFT_E_NOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return set_error(SYMFT_E_PARSE, e.what());
+  }
+}
+
+int symft_compile(const char* text, symft_plan** out) { return symft_compile_ex(text, nullptr, out); }
+
+int symft_plan_info(const symft_plan* p, symft_info* info) {
+  if (!p || !info) return set_error(SYMFT_E_ARG, "null argument");
+  const HostPlan& h = p->hp;
+  std::memset(info, 0, sizeof(*info));
+  info->n_qubits = h.n_qubits;
+  info->n_meas_events = h.n_meas;
+  info->n_records = h.n_records;
+  info->n_dets = h.n_dets;
+  info->n_obs = h.n_obs;
+  info->n_channels = h.n_channels;
+  info->k_max = h.k_max;
+  for (int i = 0; i < 7; ++i) info->n_instr[i] = h.hist[i];
+  info->max_expr_weight = h.max_expr_weight;
+  info->n_noise_components = h.n_comp;
+  info->n_targets = h.n_targets;
+  info->n_causal = h.n_m3;
+  info->sign_xor_terms = h.sign_xor_terms;
+  return SYMFT_OK;
+}
+
+void symft_plan_free(symft_plan* p) {
+  if (!p) return;
+  p->plan_buf.release();
+  p->signs.release();
+  p->m3.release();
+  p->det_scratch.release();
+  p->gvec.release();
+  p->status.release();
+  p->h_meas.release();
+  p->h_det.release();
+  p->h_obs.release();
+  p->h_disc.release();
+  delete p;
+}
+
+int symft_sample_ex(const symft_plan* plan, const symft_sample_args* args) {
+  g_last_error.clear();
+  g_last_launches = 0;
+  if (!plan || !args) return set_error(SYMFT_E_ARG, "null argument");
+  symft_plan* P = const_cast<symft_plan*>(plan);
+  std::lock_guard<std::mutex> lk(P->mu);
+  try {
+    return sample_impl(P, args);
+  } catch (const std::bad_alloc&) {
+    return set_error(SYMFT_E_NOMEM, "host allocation failed");
+  }
+}
+
+int symft_sample(const symft_plan* plan, uint64_t shots, uint64_t seed, uint64_t* meas_out,
+                 uint64_t* det_out, uint64_t* obs_out, void* stream) {
+  symft_sample_args a{};
+  a.shots = shots;
+  a.seed = seed;
+  a.meas_out = meas_out;
+  a.det_out = det_out;
+  a.obs_out = obs_out;
+  a.stream = stream;
+  return symft_sample_ex(plan, &a);
+}
+
+const char* symft_last_error(void) { return g_last_error.c_str(); }
+
+int symft_last_launch_count(void) { return g_last_launches; }
+
+}  // extern "C"

@@ -1,0 +1,477 @@
+// Sampling kernels (Sec. 5, single-shot algorithm, run for many shots at once).
+//
+//  sign_kernel      one warp per 128-shot block: draws the noise components and
+//                   the random-measurement bits from the counter-based streams,
+//                   scatters them into the bit-packed sign/record/detector
+//                   accumulators held in shared memory (64 shots per word,
+//                   2 words per block), and writes the columns out.  This is
+//                   the exogenous part of every affine sign (Sec. 6, "Sampling
+//                   independent symbols").
+//  dense_kernel     one warp per shot: runs the dense-state instructions
+//                   (PromoteRot, ActiveDiagRot, ActivePairRot, ActiveDiagMeas,
+//                   ActivePairMeas, Sec. 4) on the shot's active vector,
+//                   completing each sign with the causal residual of the
+//                   active outcomes sampled earlier in the same shot.
+//  finalize_kernel  one thread per 64-shot word: folds the active outcomes
+//                   into records / detectors / observables and applies the
+//                   postselection rule.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "device.cuh"
+
+namespace symft {
+
+namespace {
+
+__device__ __forceinline__ uint32_t tail_draw(uint32_t c, uint32_t gb, uint32_t i, uint32_t k0,
+                                              uint32_t k1, uint4& cache, uint32_t& cache_i) {
+  uint32_t blk = i >> 2;
+  if (blk != cache_i) {
+    cache = philox(make_uint4(c, gb, blk, kTagTail), k0, k1);
+    cache_i = blk;
+  }
+  uint32_t s = i & 3;
+  return s == 0 ? cache.x : (s == 1 ? cache.y : (s == 2 ? cache.z : cache.w));
+}
+
+// smallest j in [0,128) with u < theta[j]  (128 if none)
+__device__ __forceinline__ int first_above(const uint32_t* __restrict__ th, uint32_t u) {
+  int lo = 0, hi = 128;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (u < __ldg(th + mid)) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void xor_bit(unsigned long long* slots, uint32_t target, int lane_bit) {
+  atomicXor(slots + 2 * target + (lane_bit >> 6), 1ull << (lane_bit & 63));
+}
+
+}  // namespace
+
+
+
+// Shared memory per warp: n_targets * 16 bytes.
+__global__ void __launch_bounds__(256) sign_kernel(SignArgs A) {
+  extern __shared__ unsigned long long smem[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  const uint32_t NT = A.p.n_targets;
+  unsigned long long* slots = smem + (size_t)wib * 2 * NT;
+  const uint32_t k0 = (uint32_t)A.seed, k1 = (uint32_t)(A.seed >> 32);
+
+  for (uint64_t lb = (uint64_t)blockIdx.x * wpb + wib; lb < A.n_blocks; lb += (uint64_t)gridDim.x * wpb) {
+    const uint32_t gb = (uint32_t)(A.block0 + lb);
+    // 1. constants
+    for (uint32_t i = lane; i < NT; i += 32) {
+      unsigned long long v = A.p.tgt_const[i] ? ~0ull : 0ull;
+      slots[2 * i] = v;
+      slots[2 * i + 1] = v;
+    }
+    __syncwarp();
+    // 2. random-measurement bits m1: one Philox block = the 128 bits of this block
+    for (uint32_t j = lane; j < A.p.n_m1; j += 32) {
+      uint4 o = philox(make_uint4(__ldg(A.p.m1_t + j), gb, 0u, kTagMbit), k0, k1);
+      unsigned long long w0 = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
+      unsigned long long w1 = (unsigned long long)o.z | ((unsigned long long)o.w << 32);
+      const uint32_t e = __ldg(A.p.m1_off + j + 1);
+      for (uint32_t q = __ldg(A.p.m1_off + j); q < e; ++q) {
+        uint32_t tg = __ldg(A.p.m1_tgt + q);
+        atomicXor(slots + 2 * tg, w0);
+        atomicXor(slots + 2 * tg + 1, w1);
+      }
+    }
+    // 3. noise: channel groups of 4 share one head Philox block
+    const uint32_t n_groups = (A.p.n_channels + 3) >> 2;
+    for (uint32_t g = lane; g < n_groups; g += 32) {
+      uint4 head = philox(make_uint4(g, gb, 0u, kTagHead), k0, k1);
+      uint32_t hv[4] = {head.x, head.y, head.z, head.w};
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        uint32_t c = 4 * g + s;
+        if (c >= A.p.n_channels) break;
+        uint4 raw = __ldg(reinterpret_cast<const uint4*>(A.p.ch) + c);
+        uint32_t theta_last = raw.x;
+        uint32_t u = hv[s];
+        if (u >= theta_last) continue;   // common case: no fire in 128 shots
+        const uint32_t qtab = raw.y & 0xFFFFu, ctab = raw.y >> 16;
+        const uint32_t comp0 = raw.z;
+        const uint32_t* th = A.p.qtheta + (size_t)qtab * 128;
+        const CellTableDev* ct = A.p.ctabs + ctab;
+        const uint32_t ncell = __ldg(&ct->ncell);
+        uint4 cache = make_uint4(0, 0, 0, 0);
+        uint32_t cache_i = 0xFFFFFFFFu;
+        uint32_t ti = 0;
+        int L = 0;
+        for (int guard = 0; guard < 129; ++guard) {
+          int j = first_above(th, u);
+          if (j > 127 - L) break;
+          int lanebit = L + j;
+          uint32_t cell = 0;
+          if (ncell > 1) {
+            uint32_t v = tail_draw(c, gb, ti++, k0, k1, cache, cache_i);
+            cell = ncell - 1;
+            for (uint32_t kk = 0; kk + 1 < ncell; ++kk)
+              if (v < __ldg(&ct->phi[kk])) { cell = kk; break; }
+          }
+          uint32_t mask = __ldg(&ct->mask[cell]);
+          while (mask) {
+            uint32_t b = __ffs(mask) - 1;
+            mask &= mask - 1;
+            uint32_t comp = comp0 + b;
+            const uint32_t e = __ldg(A.p.comp_off + comp + 1);
+            for (uint32_t q = __ldg(A.p.comp_off + comp); q < e; ++q)
+              xor_bit(slots, __ldg(A.p.comp_tgt + q), lanebit);
+          }
+          L = lanebit + 1;
+          if (L >= 128) break;
+          u = tail_draw(c, gb, ti++, k0, k1, cache, cache_i);
+        }
+      }
+    }
+    __syncwarp();
+    // 4. write the columns (padding bits cleared)
+    const uint64_t w0 = 2 * lb, w1 = 2 * lb + 1;
+    const bool has1 = w1 < A.W;
+    uint64_t m0 = ~0ull, m1 = ~0ull;
+    {
+      uint64_t base = lb * 128;
+      uint64_t left = A.shots - base;
+      if (left < 64) { m0 = (left == 0) ? 0ull : ((1ull << left) - 1); m1 = 0; }
+      else if (left < 128) { m1 = (left == 64) ? 0ull : ((1ull << (left - 64)) - 1); }
+    }
+    for (uint32_t i = lane; i < NT; i += 32) {
+      uint64_t* col;
+      uint64_t idx;
+      if (i < A.p.tgt_det0) { col = A.meas; idx = i; }
+      else if (i < A.p.tgt_obs0) { col = A.det; idx = i - A.p.tgt_det0; }
+      else if (i < A.p.tgt_sign0) { col = A.obs; idx = i - A.p.tgt_obs0; }
+      else { col = A.signs; idx = i - A.p.tgt_sign0; }
+      if (col == nullptr) continue;
+      uint64_t v0 = slots[2 * i] & m0, v1 = slots[2 * i + 1] & m1;
+      uint64_t* dst = col + idx * A.W + w0;
+      if (has1 && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+        *reinterpret_cast<ulonglong2*>(dst) = make_ulonglong2(v0, v1);
+      } else {
+        dst[0] = v0;
+        if (has1) dst[1] = v1;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Dense executor: one warp per shot, active vector in shared or global memory.
+// ---------------------------------------------------------------------------
+template <typename Real>
+struct Cplx {
+  Real re, im;
+};
+
+
+
+__device__ __forceinline__ uint32_t insert_bit(uint32_t z, int h, uint32_t d) {
+  uint32_t low = z & ((1u << h) - 1u);
+  return low | (d << h) | ((z >> h) << (h + 1));
+}
+
+__device__ __forceinline__ double meas_uniform(uint64_t seed, uint32_t t, uint64_t r) {
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  uint64_t w = r >> 6;
+  uint4 ob = philox(make_uint4(t, (uint32_t)(w >> 1), (uint32_t)(w >> 33), kTagMbit), k0, k1);
+  uint64_t word = (w & 1) ? ((uint64_t)ob.z | ((uint64_t)ob.w << 32)) : ((uint64_t)ob.x | ((uint64_t)ob.y << 32));
+  uint64_t bit = (word >> (r & 63)) & 1ull;
+  uint4 of = philox(make_uint4(t, (uint32_t)(r >> 1), (uint32_t)(r >> 33), kTagMfrac), k0, k1);
+  uint64_t fw = (r & 1) ? ((uint64_t)of.z | ((uint64_t)of.w << 32)) : ((uint64_t)of.x | ((uint64_t)of.y << 32));
+  uint64_t f = fw >> 12;
+  return (double)((bit << 52) + f) * 0x1p-53;
+}
+
+template <typename Real>
+__device__ __forceinline__ double norm2(Cplx<Real> v) {
+  return (double)v.re * (double)v.re + (double)v.im * (double)v.im;
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
+  extern __shared__ unsigned char dsm[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  const uint32_t S = 1u << A.kmax;
+  const uint32_t m3w = (A.p.n_m3 + 31) / 32;
+  uint32_t* m3bits = reinterpret_cast<uint32_t*>(dsm) + (size_t)wib * m3w;
+  Cplx<Real>* vec;
+  const uint64_t warp_global = (uint64_t)blockIdx.x * wpb + wib;
+  if (A.use_smem) {
+    size_t off = ((size_t)wpb * m3w * 4 + 15) & ~(size_t)15;
+    vec = reinterpret_cast<Cplx<Real>*>(dsm + off) + (size_t)wib * S;
+  } else {
+    vec = reinterpret_cast<Cplx<Real>*>(A.gvec) + warp_global * A.gvec_stride;
+  }
+
+  for (uint64_t r = warp_global; r < A.shots; r += (uint64_t)gridDim.x * wpb) {
+    const uint64_t rg = A.shot0 + r;     // absolute shot index
+    const uint64_t w = r >> 6;
+    const uint64_t bitmask = 1ull << (r & 63);
+    for (uint32_t i = lane; i < m3w; i += 32) m3bits[i] = 0u;
+    if (lane == 0) {
+      vec[0].re = (Real)1;
+      vec[0].im = (Real)0;
+    }
+    __syncwarp();
+    uint32_t k = 0;
+    for (uint32_t g = 0; g < A.p.n_dense; ++g) {
+      const DenseInstrDev I = A.p.dense[g];
+      // sign: exogenous bit xor causal residual over m3 bits of this shot
+      uint32_t lam = 0;
+      if (lane == 0) {
+        lam = (uint32_t)((__ldg(A.signs + (uint64_t)I.sign_target_col * A.W + w) & bitmask) != 0);
+        for (uint32_t q = 0; q < I.causal_n; ++q) {
+          uint32_t j = __ldg(A.p.dense_causal + I.causal_off + q);
+          lam ^= (m3bits[j >> 5] >> (j & 31)) & 1u;
+        }
+      }
+      lam = __shfl_sync(0xffffffffu, lam, 0);
+      const Real sg = lam ? (Real)-1 : (Real)1;
+      const Real c = (Real)I.c, s = (Real)I.s;
+      const uint32_t n = 1u << k;
+      switch (I.kind) {
+        case 0: {  // PromoteRot: a'_{x} = c a_x, a'_{x+2^k} = -i sg s a_x
+          for (uint32_t x = lane; x < n; x += 32) {
+            Cplx<Real> v = vec[x];
+            Cplx<Real> hi;
+            hi.re = sg * s * v.im;
+            hi.im = -sg * s * v.re;
+            vec[x + n] = hi;
+            v.re *= c;
+            v.im *= c;
+            vec[x] = v;
+          }
+          ++k;
+          break;
+        }
+        case 1: {  // ActiveDiagRot: a_x *= c - i sg mu (-1)^{b.x} s
+          const Real mu = I.mu == 0 ? (Real)1 : (Real)-1;
+          for (uint32_t x = lane; x < n; x += 32) {
+            Real f = sg * mu * s * ((__popc(x & I.b) & 1) ? (Real)-1 : (Real)1);
+            Cplx<Real> v = vec[x];
+            Cplx<Real> o;
+            o.re = c * v.re + f * v.im;
+            o.im = c * v.im - f * v.re;
+            vec[x] = o;
+          }
+          break;
+        }
+        case 2: {  // ActivePairRot on pairs (x0, x0 ^ a)
+          const int p = 31 - __clz(I.a);
+          // coefficient -i mu sg s (-1)^{b.x} for mu = i^mu
+          Real cr, ci;  // -i * i^mu
+          switch (I.mu & 3) {
+            case 0: cr = 0; ci = -1; break;
+            case 1: cr = 1; ci = 0; break;
+            case 2: cr = 0; ci = 1; break;
+            default: cr = -1; ci = 0; break;
+          }
+          cr *= sg * s;
+          ci *= sg * s;
+          for (uint32_t z = lane; z < (n >> 1); z += 32) {
+            uint32_t x0 = insert_bit(z, p, 0u);
+            uint32_t x1 = x0 ^ I.a;
+            Cplx<Real> v0 = vec[x0], v1 = vec[x1];
+            Real s1 = (__popc(x1 & I.b) & 1) ? (Real)-1 : (Real)1;   // applied to a_{x1} in a'_{x0}
+            Real s0 = (__popc(x0 & I.b) & 1) ? (Real)-1 : (Real)1;
+            Cplx<Real> o0, o1;
+            o0.re = c * v0.re + s1 * (cr * v1.re - ci * v1.im);
+            o0.im = c * v0.im + s1 * (cr * v1.im + ci * v1.re);
+            o1.re = c * v1.re + s0 * (cr * v0.re - ci * v0.im);
+            o1.im = c * v1.im + s0 * (cr * v0.im + ci * v0.re);
+            vec[x0] = o0;
+            vec[x1] = o1;
+          }
+          break;
+        }
+        case 5:
+        case 6: {  // active measurements
+          const int h = I.h;
+          double S0 = 0.0, S1 = 0.0;   // by effective label y (pair) / parity (diag)
+          const Real inv_sqrt2 = (Real)0.70710678118654752440;
+          Real mcr = 0, mci = 0;       // conj(mu)
+          if (I.kind == 6) {
+            switch (I.mu & 3) {
+              case 0: mcr = 1; mci = 0; break;
+              case 1: mcr = 0; mci = -1; break;
+              case 2: mcr = -1; mci = 0; break;
+              default: mcr = 0; mci = 1; break;
+            }
+          }
+          if (I.kind == 5) {
+            for (uint32_t x = lane; x < n; x += 32) {
+              double v = norm2(vec[x]);
+              if (__popc(x & I.b) & 1) S1 += v; else S0 += v;
+            }
+          } else {
+            for (uint32_t z = lane; z < (n >> 1); z += 32) {
+              uint32_t u0 = insert_bit(z, h, 0u);
+              Cplx<Real> a0 = vec[u0], a1 = vec[u0 ^ I.a];
+              Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
+              // t = conj(mu) (-1)^{b.u0} a1 ; beta(y) = (a0 + (-1)^y t)/sqrt2
+              Real tr = sb * (mcr * a1.re - mci * a1.im), ti = sb * (mcr * a1.im + mci * a1.re);
+              Cplx<Real> b0, b1;
+              b0.re = (a0.re + tr) * inv_sqrt2; b0.im = (a0.im + ti) * inv_sqrt2;
+              b1.re = (a0.re - tr) * inv_sqrt2; b1.im = (a0.im - ti) * inv_sqrt2;
+              S0 += norm2(b0);
+              S1 += norm2(b1);
+            }
+          }
+#pragma unroll
+          for (int off = 16; off; off >>= 1) {
+            S0 += __shfl_xor_sync(0xffffffffu, S0, off);
+            S1 += __shfl_xor_sync(0xffffffffu, S1, off);
+          }
+          // label for m = 0: diag -> parity lam^eta ; pair -> y = lam
+          const uint32_t l0 = I.kind == 5 ? (lam ^ (uint32_t)I.eta) : lam;
+          const double Sl0 = l0 ? S1 : S0;
+          const double p0 = Sl0 / (S0 + S1);
+          uint32_t m = 0;
+          if (lane == 0) m = meas_uniform(A.seed, I.t, rg) < p0 ? 0u : 1u;
+          m = __shfl_sync(0xffffffffu, m, 0);
+          const uint32_t lab = l0 ^ m;
+          const double Sm = lab ? S1 : S0;
+          const Real scale = (Real)(1.0 / sqrt(Sm));
+          // in-place compaction in increasing z order (sources are never below z)
+          const uint32_t half = n >> 1;
+          for (uint32_t z0 = 0; z0 < half; z0 += 32) {
+            uint32_t z = z0 + lane;
+            Cplx<Real> val;
+            val.re = 0; val.im = 0;
+            if (z < half) {
+              if (I.kind == 5) {
+                uint32_t u = insert_bit(z, h, lab);
+                uint32_t x = u ^ ((uint32_t)(__popc(u & I.b & ~(1u << h)) & 1) << h);
+                // x(b,u): bit h = u_h xor parity of b over the other bits
+                val = vec[x];
+              } else {
+                uint32_t u0 = insert_bit(z, h, 0u);
+                Cplx<Real> a0 = vec[u0], a1 = vec[u0 ^ I.a];
+                Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
+                if (lab) sb = -sb;
+                Real tr = sb * (mcr * a1.re - mci * a1.im), ti = sb * (mcr * a1.im + mci * a1.re);
+                val.re = (a0.re + tr) * inv_sqrt2;
+                val.im = (a0.im + ti) * inv_sqrt2;
+              }
+              val.re *= scale;
+              val.im *= scale;
+            }
+            __syncwarp();
+            if (z < half) vec[z] = val;
+            __syncwarp();
+          }
+          --k;
+          if (m) {
+            if (lane == 0) {
+              m3bits[I.m3 >> 5] |= 1u << (I.m3 & 31);
+              atomicOr(reinterpret_cast<unsigned long long*>(A.m3_out) + (uint64_t)I.m3 * A.W + w,
+                       (unsigned long long)bitmask);
+            }
+          }
+          break;
+        }
+        default:
+          if (lane == 0 && A.status) atomicExch(A.status, 1);
+          break;
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Finalize: causal residuals of records/detectors/observables and postselection.
+// ---------------------------------------------------------------------------
+
+
+__global__ void finalize_kernel(FinalArgs A) {
+  for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < A.W; w += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t pad = ~0ull;
+    if (w == A.W - 1 && (A.shots & 63)) pad = (1ull << (A.shots & 63)) - 1;
+    if (A.m3) {
+      for (uint32_t i = 0; i < A.p.tgt_sign0; ++i) {
+        uint32_t b = __ldg(A.p.tgt_causal_off + i), e = __ldg(A.p.tgt_causal_off + i + 1);
+        if (b == e) continue;
+        uint64_t acc = 0;
+        for (uint32_t q = b; q < e; ++q) acc ^= A.m3[(uint64_t)__ldg(A.p.tgt_causal + q) * A.W + w];
+        uint64_t* col;
+        uint64_t idx;
+        if (i < A.p.tgt_det0) { col = A.meas; idx = i; }
+        else if (i < A.p.tgt_obs0) { col = A.det; idx = i - A.p.tgt_det0; }
+        else { col = A.obs; idx = i - A.p.tgt_obs0; }
+        if (col) col[idx * A.W + w] ^= acc & pad;
+      }
+    }
+    if (A.p.postselect) {
+      uint64_t cut = 0;
+      for (uint32_t e = 0; e < A.p.n_post_events; ++e) {
+        int32_t ev = __ldg(A.p.post_events + e);
+        if (ev >= 0) {
+          if (A.meas) A.meas[(uint64_t)ev * A.W + w] &= ~cut;
+        } else {
+          uint64_t* d = A.det + (uint64_t)(-1 - ev) * A.W + w;
+          uint64_t v = *d & ~cut;
+          *d = v;
+          cut |= v;
+        }
+      }
+      if (A.obs)
+        for (uint32_t j = 0; j < A.p.n_obs; ++j) A.obs[(uint64_t)j * A.W + w] &= ~cut;
+      if (A.discard) A.discard[w] = cut & pad;
+    } else if (A.discard) {
+      A.discard[w] = 0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launch wrappers (host)
+// ---------------------------------------------------------------------------
+cudaError_t launch_sign(const SignArgs& a, int warps_per_block, int grid, cudaStream_t st) {
+  size_t smem = (size_t)warps_per_block * a.p.n_targets * 16;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(sign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  sign_kernel<<<grid, warps_per_block * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_dense_t(const DenseArgs& a, int warps_per_block, int grid, size_t smem, cudaStream_t st) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(dense_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dense_kernel<Real><<<grid, warps_per_block * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense(const DenseArgs& a, bool fp64, int warps_per_block, int grid, size_t smem, cudaStream_t st) {
+  return fp64 ? launch_dense_t<double>(a, warps_per_block, grid, smem, st)
+              : launch_dense_t<float>(a, warps_per_block, grid, smem, st);
+}
+
+cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t st) {
+  int threads = 256;
+  uint64_t blocks = (a.W + threads - 1) / threads;
+  if (blocks > 65535) blocks = 65535;
+  if (blocks == 0) blocks = 1;
+  finalize_kernel<<<(unsigned)blocks, threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace symft

@@ -1,0 +1,100 @@
+// Device plan layout and kernel argument blocks (host- and device-visible PODs).
+#pragma once
+
+#include <cstdint>
+
+namespace symft {
+
+// stream tags (counter word 3)
+constexpr uint32_t kTagHead = 1, kTagTail = 2, kTagMbit = 3, kTagMfrac = 4;
+
+struct ChannelDev {        // 16 bytes, one per noise channel
+  uint32_t theta_last;     // THETA_127: u >= this means no fire in the block
+  uint16_t qtab, ctab;
+  uint32_t comp0;
+  uint32_t ncomp;
+};
+
+struct CellTableDev {
+  uint32_t ncell;
+  uint32_t phi[15];
+  uint8_t mask[16];
+};
+
+struct DenseInstrDev {
+  int32_t kind, k, h, mu;
+  uint32_t a, b;
+  int32_t eta, m3;
+  double c, s;
+  uint32_t sign_target_col;   // column of the exogenous sign in the scratch
+  uint32_t causal_off, causal_n;
+  uint32_t t;
+};
+
+struct DevPlan {
+  uint32_t n_channels;
+  const ChannelDev* ch;
+  const uint32_t* qtheta;       // [n_qtab][128]
+  const CellTableDev* ctabs;
+  const uint32_t* comp_off;
+  const uint32_t* comp_tgt;
+  uint32_t n_m1;
+  const uint32_t* m1_t;
+  const uint32_t* m1_off;
+  const uint32_t* m1_tgt;
+  uint32_t n_targets, tgt_det0, tgt_obs0, tgt_sign0;
+  const uint8_t* tgt_const;
+  const uint32_t* tgt_causal_off;
+  const uint32_t* tgt_causal;
+  uint32_t n_post_events;
+  const int32_t* post_events;
+  uint32_t n_dense;
+  const DenseInstrDev* dense;
+  const uint32_t* dense_causal;
+  uint32_t n_m3;
+  uint32_t n_records, n_dets, n_obs;
+  int postselect;
+};
+
+
+struct SignArgs {
+  DevPlan p;
+  uint64_t seed;
+  uint64_t block0;        // global index of the first 128-shot block
+  uint64_t n_blocks;      // local blocks
+  uint64_t W;             // words per column
+  uint64_t shots;
+  uint64_t* meas;         // may be null
+  uint64_t* det;
+  uint64_t* obs;
+  uint64_t* signs;        // dense sign scratch (n_dense columns) or null
+  int* status;
+};
+
+struct DenseArgs {
+  DevPlan p;
+  uint64_t seed;
+  uint64_t shot0;         // absolute index of local shot 0
+  uint64_t shots;
+  uint64_t W;
+  const uint64_t* signs;  // exogenous sign columns (n_dense x W)
+  uint64_t* m3_out;       // active outcomes (n_m3 x W), zeroed before launch
+  void* gvec;             // global vector scratch (per resident warp) or null
+  uint64_t gvec_stride;   // amplitudes per warp slot in gvec
+  uint32_t kmax;
+  int use_smem;
+  int* status;
+};
+
+struct FinalArgs {
+  DevPlan p;
+  uint64_t W;
+  uint64_t shots;
+  const uint64_t* m3;     // may be null when n_m3 == 0
+  uint64_t* meas;
+  uint64_t* det;          // required when postselecting
+  uint64_t* obs;
+  uint64_t* discard;
+};
+
+}  // namespace symft

@@ -1,0 +1,103 @@
+"""C-ABI checks that need no GPU: the library loads, exports every declared
+symbol, compiles circuits on the host, and validates arguments."""
+import ctypes
+import os
+import random
+import re
+
+import pytest
+
+import paper_2607_28600_b300 as S
+from oracle import symft as osymft
+from oracle.circuit import parse as oparse
+from paper_2607_28600_b300.workloads import random_near_clifford, rotated_surface_code_memory
+from tests.circuits_for_tests import random_clifford_text
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_library_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "symft.h")).read()
+    declared = set(re.findall(r"^\s*(?:int|void|const char\*)\s+(symft_\w+)\s*\(", hdr, re.M))
+    assert declared == set(S.EXPORTS)
+    L = S.lib()
+    for name in declared:
+        assert hasattr(L, name), name
+
+
+def test_plan_info_matches_oracle_planner():
+    """The C++ compile step and the oracle's plain SymFT plan the same instruction stream."""
+    for trial in range(25):
+        rng = random.Random(900 + trial)
+        n = rng.randint(2, 7)
+        txt = random_clifford_text(rng, n, 60, rot=0.25)
+        p = S.symft_compile(txt)
+        o = osymft.Plan(oparse(txt))
+        info = p.info
+        assert info["k_max"] == o.stats["k_max"]
+        for name, cnt in info["n_instr"].items():
+            assert cnt == o.stats["hist"].get(name, 0), (trial, name)
+
+
+@pytest.mark.parametrize("d", [3, 5, 7])
+def test_surface_code_plan_counts(d):
+    p = S.symft_compile(rotated_surface_code_memory(d, d, 1e-3))
+    info = p.info
+    c = oparse(rotated_surface_code_memory(d, d, 1e-3))
+    assert info["n_qubits"] == c.num_qubits
+    assert info["n_records"] == c.num_records and info["n_dets"] == c.num_dets
+    assert info["n_channels"] == c.num_channels and info["k_max"] == 0
+    # first-round X checks and half of the final data measurements are random
+    assert info["n_instr"]["RandomMeas"] == d * d - 1
+
+
+@pytest.mark.parametrize("text,code", [
+    ("H 0\nFOO 1\n", -2),
+    ("H 0\nCX 0\n", -1),
+    ("M 0\nDETECTOR rec[-2]\n", -1),
+    ("X_ERROR(1.5) 0\n", -1),
+    ("REPEAT 2 {\nH 0\n", -1),
+    ("R_PAULI(0.1) X0*Z0\n", -1),
+    ("MPP X0*Q1\n", -1),
+])
+def test_compile_errors(text, code):
+    with pytest.raises(S.SymftError) as ei:
+        S.symft_compile(text)
+    assert ei.value.code == code
+
+
+def test_sample_argument_errors_before_any_device_work():
+    p = S.symft_compile("H 0\nM 0\n")
+    with pytest.raises(S.SymftError) as ei:
+        S.symft_sample_ex(p, 0, 1)
+    assert ei.value.code == -3
+    with pytest.raises(S.SymftError) as ei:
+        S.symft_sample_ex(p, 10, 1, shot_offset=64)
+    assert ei.value.code == -3
+    with pytest.raises(S.SymftError) as ei:
+        S.symft_sample_ex(p, 10, 1, precision=7)
+    assert ei.value.code == -3
+
+
+def test_null_arguments():
+    L = S.lib()
+    assert L.symft_compile(None, None) == -3
+    assert L.symft_plan_info(None, None) == -3
+    L.symft_plan_free(None)
+    assert L.symft_sample(None, 1, 1, None, None, None, None) == -3
+
+
+def test_capacity_error_for_wide_active_state():
+    # 26 independent T rotations on |+> promote 26 coordinates
+    txt = "H " + " ".join(map(str, range(26))) + "\n" + "T " + " ".join(map(str, range(26))) + "\nM 0\n"
+    with pytest.raises(S.SymftError) as ei:
+        S.symft_compile(txt)
+    assert ei.value.code == -4
+
+
+def test_repeat_and_generators_compile():
+    txt = "R 0 1\nREPEAT 3 {\nH 0\nCX 0 1\nMR 1\nDETECTOR rec[-1]\n}\nM 0\n"
+    p = S.symft_compile(txt)
+    assert p.info["n_records"] == 4 and p.info["n_dets"] == 3
+    p2 = S.symft_compile(random_near_clifford(20, 30, 6, seed=3))
+    assert p2.info["n_qubits"] == 20
