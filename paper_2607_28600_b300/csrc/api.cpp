@@ -17,6 +17,7 @@
 
 namespace symft {
 cudaError_t launch_sign(const SignArgs& a, int warps_per_block, int grid, cudaStream_t st);
+size_t sign_smem_bytes(uint32_t n_targets, int warps_per_block);
 cudaError_t launch_dense(const DenseArgs& a, bool fp64, int warps_per_block, int grid, size_t smem,
                          cudaStream_t st);
 cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t st);
@@ -82,6 +83,8 @@ cudaError_t upload(symft_plan* P) {
   std::vector<ChannelDev> ch(h.n_channels);
   for (uint32_t c = 0; c < h.n_channels; ++c)
     ch[c] = ChannelDev{h.ch_theta_last[c], h.ch_qtab[c], h.ch_ctab[c], h.ch_comp0[c], h.ch_ncomp[c]};
+  std::vector<uint32_t> theta4(((h.n_channels + 3) / 4) * 4, 0u);
+  for (uint32_t c = 0; c < h.n_channels; ++c) theta4[c] = h.ch_theta_last[c];
   std::vector<uint32_t> qtheta;
   for (auto& q : h.qtabs) qtheta.insert(qtheta.end(), q.theta, q.theta + kNoiseBlock);
   std::vector<CellTableDev> ct(h.ctabs.size());
@@ -111,6 +114,7 @@ cudaError_t upload(symft_plan* P) {
   }
   std::vector<unsigned char> blob;
   size_t o_ch = push(blob, ch), o_q = push(blob, qtheta), o_ct = push(blob, ct);
+  size_t o_t4 = push(blob, theta4);
   size_t o_co = push(blob, h.comp_off), o_ctg = push(blob, h.comp_tgt);
   size_t o_m1t = push(blob, h.m1_t), o_m1o = push(blob, h.m1_off), o_m1g = push(blob, h.m1_tgt);
   size_t o_tc = push(blob, h.tgt_const), o_tco = push(blob, h.tgt_causal_off), o_tca = push(blob, h.tgt_causal);
@@ -123,6 +127,9 @@ cudaError_t upload(symft_plan* P) {
   DevPlan& d = P->dp;
   d.n_channels = h.n_channels;
   d.ch = reinterpret_cast<const ChannelDev*>(at(o_ch));
+  d.theta4 = reinterpret_cast<const uint4*>(at(o_t4));
+  d.n_qtab = static_cast<uint32_t>(h.qtabs.size());
+  d.n_ctab = static_cast<uint32_t>(h.ctabs.size());
   d.qtheta = reinterpret_cast<const uint32_t*>(at(o_q));
   d.ctabs = reinterpret_cast<const CellTableDev*>(at(o_ct));
   d.comp_off = reinterpret_cast<const uint32_t*>(at(o_co));
@@ -218,11 +225,12 @@ int sample_impl(symft_plan* P, const symft_sample_args* a) {
     s.obs = obs;
     s.signs = signs;
     s.status = status;
-    size_t per_warp = static_cast<size_t>(h.n_targets) * 16;
-    if (per_warp > 200 * 1024)
+    const size_t fixed = sign_smem_bytes(h.n_targets, 0);
+    const size_t per_warp = sign_smem_bytes(h.n_targets, 1) - fixed;
+    if (fixed + per_warp > 220 * 1024)
       return set_error(SYMFT_E_CAPACITY, "too many bit-packed targets for shared memory (" +
                                              std::to_string(h.n_targets) + ")");
-    int wpb = static_cast<int>(std::min<size_t>(8, std::max<size_t>(1, (96 * 1024) / per_warp)));
+    int wpb = static_cast<int>(std::min<size_t>(8, std::max<size_t>(1, (100 * 1024 - fixed) / per_warp)));
     uint64_t want = (nblk + wpb - 1) / wpb;
     uint64_t cap = static_cast<uint64_t>(P->sm_count) * 16;
     int grid = static_cast<int>(std::max<uint64_t>(1, std::min(want, cap)));

@@ -25,124 +25,168 @@ namespace symft {
 
 namespace {
 
-__device__ __forceinline__ uint32_t tail_draw(uint32_t c, uint32_t gb, uint32_t i, uint32_t k0,
-                                              uint32_t k1, uint4& cache, uint32_t& cache_i) {
-  uint32_t blk = i >> 2;
-  if (blk != cache_i) {
-    cache = philox(make_uint4(c, gb, blk, kTagTail), k0, k1);
-    cache_i = blk;
-  }
-  uint32_t s = i & 3;
-  return s == 0 ? cache.x : (s == 1 ? cache.y : (s == 2 ? cache.z : cache.w));
+constexpr int kQueue = 64;          // per-warp queue of channels that fire in the block
+constexpr int kMaxSmemQ = 8;        // q tables staged in shared memory
+constexpr int kMaxSmemC = 16;       // cell tables staged in shared memory
+
+__device__ __forceinline__ uint32_t pick(uint4 v, uint32_t s) {
+  return s == 0 ? v.x : (s == 1 ? v.y : (s == 2 ? v.z : v.w));
 }
 
-// smallest j in [0,128) with u < theta[j]  (128 if none)
-__device__ __forceinline__ int first_above(const uint32_t* __restrict__ th, uint32_t u) {
-  int lo = 0, hi = 128;
-  while (lo < hi) {
-    int mid = (lo + hi) >> 1;
-    if (u < __ldg(th + mid)) hi = mid;
-    else lo = mid + 1;
-  }
+// smallest j in [0,128) with u < theta[j]  (128 if none); theta in shared memory
+__device__ __forceinline__ int first_above(const uint32_t* th, uint32_t u) {
+  int lo = 0;
+#pragma unroll
+  for (int step = 64; step; step >>= 1)
+    if (u >= th[lo + step - 1]) lo += step;
+  if (lo == 127 && u >= th[127]) lo = 128;
   return lo;
-}
-
-__device__ __forceinline__ void xor_bit(unsigned long long* slots, uint32_t target, int lane_bit) {
-  atomicXor(slots + 2 * target + (lane_bit >> 6), 1ull << (lane_bit & 63));
 }
 
 }  // namespace
 
-
-
-// Shared memory per warp: n_targets * 16 bytes.
+// Shared memory layout: [q tables][cell tables] then per warp
+//   slots  n_targets x 4 uint32 (128 lanes of one block, bit l&31 of word l>>5)
+//   queue  kQueue x uint2 (channel, head draw)
 __global__ void __launch_bounds__(256) sign_kernel(SignArgs A) {
-  extern __shared__ unsigned long long smem[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
   const uint32_t NT = A.p.n_targets;
-  unsigned long long* slots = smem + (size_t)wib * 2 * NT;
   const uint32_t k0 = (uint32_t)A.seed, k1 = (uint32_t)(A.seed >> 32);
+
+  // stage the noise tables (shared by all warps of the block)
+  const bool q_in_smem = A.p.n_qtab <= kMaxSmemQ, c_in_smem = A.p.n_ctab <= kMaxSmemC;
+  uint32_t* sq = reinterpret_cast<uint32_t*>(smem_raw);
+  CellTableDev* sc = reinterpret_cast<CellTableDev*>(smem_raw + kMaxSmemQ * 128 * 4);
+  if (q_in_smem)
+    for (uint32_t i = threadIdx.x; i < A.p.n_qtab * 128; i += blockDim.x) sq[i] = __ldg(A.p.qtheta + i);
+  if (c_in_smem)
+    for (uint32_t i = threadIdx.x; i < A.p.n_ctab; i += blockDim.x) sc[i] = A.p.ctabs[i];
+  __syncthreads();
+  const uint32_t* qtab_base = q_in_smem ? sq : A.p.qtheta;
+  const CellTableDev* ctab_base = c_in_smem ? sc : A.p.ctabs;
+
+  const size_t table_bytes = kMaxSmemQ * 128 * 4 + kMaxSmemC * sizeof(CellTableDev);
+  const size_t per_warp = (size_t)NT * 16 + kQueue * 8;
+  unsigned char* wbase = smem_raw + table_bytes + (size_t)wib * per_warp;
+  uint32_t* slots = reinterpret_cast<uint32_t*>(wbase);
+  uint2* queue = reinterpret_cast<uint2*>(wbase + (size_t)NT * 16);
+
+  const uint32_t n_groups = (A.p.n_channels + 3) >> 2;
+  const uint32_t lt_mask = (1u << lane) - 1u;
 
   for (uint64_t lb = (uint64_t)blockIdx.x * wpb + wib; lb < A.n_blocks; lb += (uint64_t)gridDim.x * wpb) {
     const uint32_t gb = (uint32_t)(A.block0 + lb);
     // 1. constants
     for (uint32_t i = lane; i < NT; i += 32) {
-      unsigned long long v = A.p.tgt_const[i] ? ~0ull : 0ull;
-      slots[2 * i] = v;
-      slots[2 * i + 1] = v;
+      uint32_t v = A.p.tgt_const[i] ? ~0u : 0u;
+      reinterpret_cast<uint4*>(slots)[i] = make_uint4(v, v, v, v);
     }
     __syncwarp();
     // 2. random-measurement bits m1: one Philox block = the 128 bits of this block
     for (uint32_t j = lane; j < A.p.n_m1; j += 32) {
       uint4 o = philox(make_uint4(__ldg(A.p.m1_t + j), gb, 0u, kTagMbit), k0, k1);
-      unsigned long long w0 = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
-      unsigned long long w1 = (unsigned long long)o.z | ((unsigned long long)o.w << 32);
       const uint32_t e = __ldg(A.p.m1_off + j + 1);
       for (uint32_t q = __ldg(A.p.m1_off + j); q < e; ++q) {
-        uint32_t tg = __ldg(A.p.m1_tgt + q);
-        atomicXor(slots + 2 * tg, w0);
-        atomicXor(slots + 2 * tg + 1, w1);
+        uint32_t* t = slots + 4 * __ldg(A.p.m1_tgt + q);
+        atomicXor(t + 0, o.x);
+        atomicXor(t + 1, o.y);
+        atomicXor(t + 2, o.z);
+        atomicXor(t + 3, o.w);
       }
     }
-    // 3. noise: channel groups of 4 share one head Philox block
-    const uint32_t n_groups = (A.p.n_channels + 3) >> 2;
-    for (uint32_t g = lane; g < n_groups; g += 32) {
-      uint4 head = philox(make_uint4(g, gb, 0u, kTagHead), k0, k1);
-      uint32_t hv[4] = {head.x, head.y, head.z, head.w};
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        uint32_t c = 4 * g + s;
-        if (c >= A.p.n_channels) break;
-        uint4 raw = __ldg(reinterpret_cast<const uint4*>(A.p.ch) + c);
-        uint32_t theta_last = raw.x;
-        uint32_t u = hv[s];
-        if (u >= theta_last) continue;   // common case: no fire in 128 shots
-        const uint32_t qtab = raw.y & 0xFFFFu, ctab = raw.y >> 16;
-        const uint32_t comp0 = raw.z;
-        const uint32_t* th = A.p.qtheta + (size_t)qtab * 128;
-        const CellTableDev* ct = A.p.ctabs + ctab;
-        const uint32_t ncell = __ldg(&ct->ncell);
-        uint4 cache = make_uint4(0, 0, 0, 0);
-        uint32_t cache_i = 0xFFFFFFFFu;
-        uint32_t ti = 0;
+    // 3. noise.  Phase A: every lane draws the head uniform of four channels
+    //    (one Philox block); channels that fire somewhere in the block are
+    //    queued.  Phase B: each lane runs the rest of one queued channel's
+    //    word-geometric process and scatters its fired lanes into the targets.
+    uint32_t qn = 0;
+    auto drain = [&](uint32_t count) {
+      uint2 ent = make_uint2(0u, 0u);
+      if ((uint32_t)lane < count) ent = queue[lane];
+      __syncwarp();
+      if ((uint32_t)lane < count) {
+        const uint32_t c = ent.x;
+        uint32_t u = ent.y;
+        const uint4 raw = __ldg(reinterpret_cast<const uint4*>(A.p.ch) + c);
+        const uint32_t qt = raw.y & 0xFFFFu, ctb = raw.y >> 16, comp0 = raw.z;
+        const uint32_t* th = qtab_base + (size_t)qt * 128;
+        const CellTableDev* ct = ctab_base + ctb;
+        const uint32_t ncell = ct->ncell;
+        uint4 cache = make_uint4(0u, 0u, 0u, 0u);
+        uint32_t cache_i = 0xFFFFFFFFu, ti = 0;
         int L = 0;
         for (int guard = 0; guard < 129; ++guard) {
           int j = first_above(th, u);
           if (j > 127 - L) break;
-          int lanebit = L + j;
+          const int lanebit = L + j;
           uint32_t cell = 0;
           if (ncell > 1) {
-            uint32_t v = tail_draw(c, gb, ti++, k0, k1, cache, cache_i);
+            if ((ti >> 2) != cache_i) {
+              cache_i = ti >> 2;
+              cache = philox(make_uint4(c, gb, cache_i, kTagTail), k0, k1);
+            }
+            const uint32_t v = pick(cache, ti & 3);
+            ++ti;
             cell = ncell - 1;
             for (uint32_t kk = 0; kk + 1 < ncell; ++kk)
-              if (v < __ldg(&ct->phi[kk])) { cell = kk; break; }
+              if (v < ct->phi[kk]) { cell = kk; break; }
           }
-          uint32_t mask = __ldg(&ct->mask[cell]);
+          uint32_t mask = ct->mask[cell];
+          const uint32_t wsel = (uint32_t)lanebit >> 5, bit = 1u << (lanebit & 31);
           while (mask) {
-            uint32_t b = __ffs(mask) - 1;
+            const uint32_t comp = comp0 + (__ffs(mask) - 1);
             mask &= mask - 1;
-            uint32_t comp = comp0 + b;
             const uint32_t e = __ldg(A.p.comp_off + comp + 1);
             for (uint32_t q = __ldg(A.p.comp_off + comp); q < e; ++q)
-              xor_bit(slots, __ldg(A.p.comp_tgt + q), lanebit);
+              atomicXor(slots + 4 * __ldg(A.p.comp_tgt + q) + wsel, bit);
           }
           L = lanebit + 1;
           if (L >= 128) break;
-          u = tail_draw(c, gb, ti++, k0, k1, cache, cache_i);
+          if ((ti >> 2) != cache_i) {
+            cache_i = ti >> 2;
+            cache = philox(make_uint4(c, gb, cache_i, kTagTail), k0, k1);
+          }
+          u = pick(cache, ti & 3);
+          ++ti;
+        }
+      }
+      __syncwarp();
+    };
+    const uint32_t iters = (n_groups + 31) >> 5;
+    for (uint32_t it = 0; it < iters; ++it) {
+      const uint32_t g = it * 32 + lane;
+      const bool valid = g < n_groups;
+      uint4 head = make_uint4(0u, 0u, 0u, 0u), th4 = make_uint4(0u, 0u, 0u, 0u);
+      if (valid) {
+        th4 = __ldg(A.p.theta4 + g);
+        if (th4.x | th4.y | th4.z | th4.w) head = philox(make_uint4(g, gb, 0u, kTagHead), k0, k1);
+      }
+#pragma unroll
+      for (uint32_t s = 0; s < 4; ++s) {
+        const uint32_t u = pick(head, s);
+        const bool fire = valid && u < pick(th4, s);
+        const uint32_t bal = __ballot_sync(0xffffffffu, fire);
+        if (fire) queue[qn + __popc(bal & lt_mask)] = make_uint2(4 * g + s, u);
+        qn += __popc(bal);
+        __syncwarp();
+        if (qn >= 32) {
+          drain(32);
+          qn -= 32;
+          if ((uint32_t)lane < qn) queue[lane] = queue[32 + lane];
+          __syncwarp();
         }
       }
     }
-    __syncwarp();
+    if (qn) drain(qn);
     // 4. write the columns (padding bits cleared)
     const uint64_t w0 = 2 * lb, w1 = 2 * lb + 1;
     const bool has1 = w1 < A.W;
     uint64_t m0 = ~0ull, m1 = ~0ull;
     {
-      uint64_t base = lb * 128;
-      uint64_t left = A.shots - base;
-      if (left < 64) { m0 = (left == 0) ? 0ull : ((1ull << left) - 1); m1 = 0; }
+      const uint64_t left = A.shots - lb * 128;
+      if (left < 64) { m0 = (1ull << left) - 1; m1 = 0; }
       else if (left < 128) { m1 = (left == 64) ? 0ull : ((1ull << (left - 64)) - 1); }
     }
     for (uint32_t i = lane; i < NT; i += 32) {
@@ -153,7 +197,8 @@ __global__ void __launch_bounds__(256) sign_kernel(SignArgs A) {
       else if (i < A.p.tgt_sign0) { col = A.obs; idx = i - A.p.tgt_obs0; }
       else { col = A.signs; idx = i - A.p.tgt_sign0; }
       if (col == nullptr) continue;
-      uint64_t v0 = slots[2 * i] & m0, v1 = slots[2 * i + 1] & m1;
+      const uint4 v = reinterpret_cast<const uint4*>(slots)[i];
+      const uint64_t v0 = (((uint64_t)v.y << 32) | v.x) & m0, v1 = (((uint64_t)v.w << 32) | v.z) & m1;
       uint64_t* dst = col + idx * A.W + w0;
       if (has1 && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
         *reinterpret_cast<ulonglong2*>(dst) = make_ulonglong2(v0, v1);
@@ -440,8 +485,13 @@ __global__ void finalize_kernel(FinalArgs A) {
 // ---------------------------------------------------------------------------
 // launch wrappers (host)
 // ---------------------------------------------------------------------------
+size_t sign_smem_bytes(uint32_t n_targets, int warps_per_block) {
+  return kMaxSmemQ * 128 * 4 + kMaxSmemC * sizeof(CellTableDev) +
+         (size_t)warps_per_block * ((size_t)n_targets * 16 + kQueue * 8);
+}
+
 cudaError_t launch_sign(const SignArgs& a, int warps_per_block, int grid, cudaStream_t st) {
-  size_t smem = (size_t)warps_per_block * a.p.n_targets * 16;
+  size_t smem = sign_smem_bytes(a.p.n_targets, warps_per_block);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(sign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

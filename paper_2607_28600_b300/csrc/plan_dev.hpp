@@ -3,6 +3,8 @@
 
 #include <cstdint>
 
+#include <vector_types.h>
+
 namespace symft {
 
 // stream tags (counter word 3)
@@ -34,6 +36,8 @@ struct DenseInstrDev {
 struct DevPlan {
   uint32_t n_channels;
   const ChannelDev* ch;
+  const uint4* theta4;          // THETA_127 of channels 4g..4g+3 (0 = never fires)
+  uint32_t n_qtab, n_ctab;
   const uint32_t* qtheta;       // [n_qtab][128]
   const CellTableDev* ctabs;
   const uint32_t* comp_off;
