@@ -16,8 +16,10 @@
 #include "symft.h"
 
 namespace symft {
-cudaError_t launch_sign(const SignArgs& a, int warps_per_block, int grid, cudaStream_t st);
-size_t sign_smem_bytes(uint32_t n_targets, int warps_per_block);
+constexpr int kSignBlocksPerCta = 2;   // 128-shot noise blocks per CTA (256 shots)
+cudaError_t launch_sign(const SignArgs& a, int grid, cudaStream_t st);
+size_t sign_smem_bytes(const DevPlan& p);
+cudaError_t sign_occupancy(const DevPlan& p, int* ctas_per_sm);
 cudaError_t launch_dense(const DenseArgs& a, bool fp64, int warps_per_block, int grid, size_t smem,
                          cudaStream_t st);
 cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t st);
@@ -115,7 +117,18 @@ cudaError_t upload(symft_plan* P) {
   std::vector<unsigned char> blob;
   size_t o_ch = push(blob, ch), o_q = push(blob, qtheta), o_ct = push(blob, ct);
   size_t o_t4 = push(blob, theta4);
-  size_t o_co = push(blob, h.comp_off), o_ctg = push(blob, h.comp_tgt);
+  // packed incidence lists (16-bit targets, 24-bit offsets, 8-bit counts)
+  if (h.n_targets >= 65536) throw Error(SYMFT_E_CAPACITY, "more than 65535 bit-packed targets");
+  if (h.comp_tgt.size() >= (1u << 24)) throw Error(SYMFT_E_CAPACITY, "too many sign incidences");
+  if (h.n_channels >= (1u << 28)) throw Error(SYMFT_E_CAPACITY, "too many noise channels");
+  std::vector<uint32_t> comp_rng(h.n_comp);
+  for (uint32_t k = 0; k < h.n_comp; ++k) {
+    uint32_t n = h.comp_off[k + 1] - h.comp_off[k];
+    if (n >= 256) throw Error(SYMFT_E_CAPACITY, "a noise component reaches more than 255 targets");
+    comp_rng[k] = (h.comp_off[k] << 8) | n;
+  }
+  std::vector<uint16_t> comp_tgt(h.comp_tgt.begin(), h.comp_tgt.end());
+  size_t o_co = push(blob, comp_rng), o_ctg = push(blob, comp_tgt);
   size_t o_m1t = push(blob, h.m1_t), o_m1o = push(blob, h.m1_off), o_m1g = push(blob, h.m1_tgt);
   size_t o_tc = push(blob, h.tgt_const), o_tco = push(blob, h.tgt_causal_off), o_tca = push(blob, h.tgt_causal);
   size_t o_pe = push(blob, h.post_events), o_dn = push(blob, dn), o_dc = push(blob, h.dense_causal);
@@ -132,8 +145,8 @@ cudaError_t upload(symft_plan* P) {
   d.n_ctab = static_cast<uint32_t>(h.ctabs.size());
   d.qtheta = reinterpret_cast<const uint32_t*>(at(o_q));
   d.ctabs = reinterpret_cast<const CellTableDev*>(at(o_ct));
-  d.comp_off = reinterpret_cast<const uint32_t*>(at(o_co));
-  d.comp_tgt = reinterpret_cast<const uint32_t*>(at(o_ctg));
+  d.comp_rng = reinterpret_cast<const uint32_t*>(at(o_co));
+  d.comp_tgt = reinterpret_cast<const uint16_t*>(at(o_ctg));
   d.n_m1 = static_cast<uint32_t>(h.m1_t.size());
   d.m1_t = reinterpret_cast<const uint32_t*>(at(o_m1t));
   d.m1_off = reinterpret_cast<const uint32_t*>(at(o_m1o));
@@ -180,7 +193,13 @@ int sample_impl(symft_plan* P, const symft_sample_args* a) {
   if (a->out_location != SYMFT_OUT_DEVICE && a->out_location != SYMFT_OUT_HOST)
     return set_error(SYMFT_E_ARG, "bad out_location");
   cudaStream_t st = static_cast<cudaStream_t>(a->stream);
-  if (!P->uploaded) CUDA_TRY(upload(P));
+  if (!P->uploaded) {
+    try {
+      CUDA_TRY(upload(P));
+    } catch (const Error& e) {
+      return set_error(e.code, e.what());
+    }
+  }
   int launches = 0;
   const uint64_t W = (a->shots + 63) / 64;
   const uint64_t nblk = (a->shots + kNoiseBlock - 1) / kNoiseBlock;
@@ -225,16 +244,16 @@ int sample_impl(symft_plan* P, const symft_sample_args* a) {
     s.obs = obs;
     s.signs = signs;
     s.status = status;
-    const size_t fixed = sign_smem_bytes(h.n_targets, 0);
-    const size_t per_warp = sign_smem_bytes(h.n_targets, 1) - fixed;
-    if (fixed + per_warp > 220 * 1024)
+    const size_t smem = sign_smem_bytes(P->dp);
+    if (smem > 220 * 1024)
       return set_error(SYMFT_E_CAPACITY, "too many bit-packed targets for shared memory (" +
                                              std::to_string(h.n_targets) + ")");
-    int wpb = static_cast<int>(std::min<size_t>(8, std::max<size_t>(1, (100 * 1024 - fixed) / per_warp)));
-    uint64_t want = (nblk + wpb - 1) / wpb;
-    uint64_t cap = static_cast<uint64_t>(P->sm_count) * 16;
-    int grid = static_cast<int>(std::max<uint64_t>(1, std::min(want, cap)));
-    CUDA_TRY(launch_sign(s, wpb, grid, st));
+    const uint64_t chunks = (nblk + kSignBlocksPerCta - 1) / kSignBlocksPerCta;
+    int per_sm = 1;
+    CUDA_TRY(sign_occupancy(P->dp, &per_sm));
+    uint64_t cap = static_cast<uint64_t>(P->sm_count) * std::max(1, per_sm);
+    int grid = static_cast<int>(std::max<uint64_t>(1, std::min(chunks, cap)));
+    CUDA_TRY(launch_sign(s, grid, st));
     ++launches;
   }
   // --- dense kernel --------------------------------------------------------

@@ -26,8 +26,6 @@ namespace symft {
 namespace {
 
 constexpr int kQueue = 64;          // per-warp queue of channels that fire in the block
-constexpr int kMaxSmemQ = 8;        // q tables staged in shared memory
-constexpr int kMaxSmemC = 16;       // cell tables staged in shared memory
 
 __device__ __forceinline__ uint32_t pick(uint4 v, uint32_t s) {
   return s == 0 ? v.x : (s == 1 ? v.y : (s == 2 ? v.z : v.w));
@@ -45,80 +43,97 @@ __device__ __forceinline__ int first_above(const uint32_t* th, uint32_t u) {
 
 }  // namespace
 
-// Shared memory layout: [q tables][cell tables] then per warp
-//   slots  n_targets x 4 uint32 (128 lanes of one block, bit l&31 of word l>>5)
-//   queue  kQueue x uint2 (channel, head draw)
-__global__ void __launch_bounds__(256) sign_kernel(SignArgs A) {
+constexpr int kSignWarps = 8;       // warps per CTA
+constexpr int kNB = 2;              // 128-shot noise blocks per CTA
+
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+
+struct SignLayout {
+  size_t q_off, c_off, slot_off, queue_off, total;
+};
+
+__host__ __device__ inline SignLayout sign_layout(uint32_t n_qtab, uint32_t n_ctab, uint32_t n_targets) {
+  SignLayout L;
+  L.q_off = 0;
+  L.c_off = align16((size_t)n_qtab * 128 * 4);
+  L.slot_off = L.c_off + align16((size_t)n_ctab * sizeof(CellTableDev));
+  L.queue_off = L.slot_off + (size_t)n_targets * kNB * 16;
+  L.total = L.queue_off + (size_t)kSignWarps * kQueue * 8;
+  return L;
+}
+
+// One CTA samples kNB consecutive 128-shot noise blocks (256 shots, four
+// 64-shot words per column).  Shared memory: the noise tables, then
+//   slots  n_targets x kNB x 4 uint32 (lane l of block b: bit l&31 of word 4b + (l>>5))
+//   queue  kSignWarps x kQueue x uint2 ((block << 28) | channel, head draw)
+__global__ void __launch_bounds__(kSignWarps * 32, 4) sign_kernel(SignArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const int wpb = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5;
   const uint32_t NT = A.p.n_targets;
   const uint32_t k0 = (uint32_t)A.seed, k1 = (uint32_t)(A.seed >> 32);
+  const SignLayout Lay = sign_layout(A.p.n_qtab, A.p.n_ctab, NT);
+  uint32_t* sq = reinterpret_cast<uint32_t*>(smem_raw + Lay.q_off);
+  CellTableDev* sc = reinterpret_cast<CellTableDev*>(smem_raw + Lay.c_off);
+  uint32_t* slots = reinterpret_cast<uint32_t*>(smem_raw + Lay.slot_off);
+  uint2* queue = reinterpret_cast<uint2*>(smem_raw + Lay.queue_off) + warp * kQueue;
 
-  // stage the noise tables (shared by all warps of the block)
-  const bool q_in_smem = A.p.n_qtab <= kMaxSmemQ, c_in_smem = A.p.n_ctab <= kMaxSmemC;
-  uint32_t* sq = reinterpret_cast<uint32_t*>(smem_raw);
-  CellTableDev* sc = reinterpret_cast<CellTableDev*>(smem_raw + kMaxSmemQ * 128 * 4);
-  if (q_in_smem)
-    for (uint32_t i = threadIdx.x; i < A.p.n_qtab * 128; i += blockDim.x) sq[i] = __ldg(A.p.qtheta + i);
-  if (c_in_smem)
-    for (uint32_t i = threadIdx.x; i < A.p.n_ctab; i += blockDim.x) sc[i] = A.p.ctabs[i];
+  for (uint32_t i = threadIdx.x; i < A.p.n_qtab * 128; i += blockDim.x) sq[i] = __ldg(A.p.qtheta + i);
+  for (uint32_t i = threadIdx.x; i < A.p.n_ctab; i += blockDim.x) sc[i] = A.p.ctabs[i];
   __syncthreads();
-  const uint32_t* qtab_base = q_in_smem ? sq : A.p.qtheta;
-  const CellTableDev* ctab_base = c_in_smem ? sc : A.p.ctabs;
-
-  const size_t table_bytes = kMaxSmemQ * 128 * 4 + kMaxSmemC * sizeof(CellTableDev);
-  const size_t per_warp = (size_t)NT * 16 + kQueue * 8;
-  unsigned char* wbase = smem_raw + table_bytes + (size_t)wib * per_warp;
-  uint32_t* slots = reinterpret_cast<uint32_t*>(wbase);
-  uint2* queue = reinterpret_cast<uint2*>(wbase + (size_t)NT * 16);
 
   const uint32_t n_groups = (A.p.n_channels + 3) >> 2;
   const uint32_t lt_mask = (1u << lane) - 1u;
+  const uint64_t n_chunks = (A.n_blocks + kNB - 1) / kNB;
 
-  for (uint64_t lb = (uint64_t)blockIdx.x * wpb + wib; lb < A.n_blocks; lb += (uint64_t)gridDim.x * wpb) {
-    const uint32_t gb = (uint32_t)(A.block0 + lb);
+  for (uint64_t chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x) {
+    const uint64_t b0 = chunk * kNB;                       // first local block
+    const uint32_t nb = (uint32_t)min((uint64_t)kNB, A.n_blocks - b0);
     // 1. constants
-    for (uint32_t i = lane; i < NT; i += 32) {
-      uint32_t v = A.p.tgt_const[i] ? ~0u : 0u;
-      reinterpret_cast<uint4*>(slots)[i] = make_uint4(v, v, v, v);
+    for (uint32_t i = threadIdx.x; i < NT; i += blockDim.x) {
+      const uint32_t v = A.p.tgt_const[i] ? ~0u : 0u;
+      uint4* t = reinterpret_cast<uint4*>(slots) + (size_t)i * kNB;
+#pragma unroll
+      for (int b = 0; b < kNB; ++b) t[b] = make_uint4(v, v, v, v);
     }
-    __syncwarp();
-    // 2. random-measurement bits m1: one Philox block = the 128 bits of this block
-    for (uint32_t j = lane; j < A.p.n_m1; j += 32) {
-      uint4 o = philox(make_uint4(__ldg(A.p.m1_t + j), gb, 0u, kTagMbit), k0, k1);
+    __syncthreads();
+    // 2. random-measurement bits m1: one Philox block = the 128 bits of a block
+    for (uint32_t it = threadIdx.x; it < nb * A.p.n_m1; it += blockDim.x) {
+      const uint32_t b = it / A.p.n_m1, j = it - b * A.p.n_m1;
+      const uint4 o = philox(make_uint4(__ldg(A.p.m1_t + j), (uint32_t)(A.block0 + b0 + b), 0u, kTagMbit), k0, k1);
       const uint32_t e = __ldg(A.p.m1_off + j + 1);
       for (uint32_t q = __ldg(A.p.m1_off + j); q < e; ++q) {
-        uint32_t* t = slots + 4 * __ldg(A.p.m1_tgt + q);
+        uint32_t* t = slots + ((size_t)__ldg(A.p.m1_tgt + q) * kNB + b) * 4;
         atomicXor(t + 0, o.x);
         atomicXor(t + 1, o.y);
         atomicXor(t + 2, o.z);
         atomicXor(t + 3, o.w);
       }
     }
-    // 3. noise.  Phase A: every lane draws the head uniform of four channels
-    //    (one Philox block); channels that fire somewhere in the block are
-    //    queued.  Phase B: each lane runs the rest of one queued channel's
-    //    word-geometric process and scatters its fired lanes into the targets.
+    // 3. noise.  Phase A: each lane draws the head uniforms of four channels of
+    //    one block (one Philox block) and queues the channels that fire in it.
+    //    Phase B: each lane continues one queued channel's word-geometric
+    //    process and scatters its fired lanes into the targets.
     uint32_t qn = 0;
     auto drain = [&](uint32_t count) {
       uint2 ent = make_uint2(0u, 0u);
       if ((uint32_t)lane < count) ent = queue[lane];
       __syncwarp();
       if ((uint32_t)lane < count) {
-        const uint32_t c = ent.x;
+        const uint32_t c = ent.x & 0x0FFFFFFFu, b = ent.x >> 28;
+        const uint32_t gb = (uint32_t)(A.block0 + b0 + b);
         uint32_t u = ent.y;
         const uint4 raw = __ldg(reinterpret_cast<const uint4*>(A.p.ch) + c);
-        const uint32_t qt = raw.y & 0xFFFFu, ctb = raw.y >> 16, comp0 = raw.z;
-        const uint32_t* th = qtab_base + (size_t)qt * 128;
-        const CellTableDev* ct = ctab_base + ctb;
+        const uint32_t* th = sq + (size_t)(raw.y & 0xFFFFu) * 128;
+        const CellTableDev* ct = sc + (raw.y >> 16);
+        const uint32_t comp0 = raw.z;
         const uint32_t ncell = ct->ncell;
+        uint32_t* sb = slots + (size_t)b * 4;
         uint4 cache = make_uint4(0u, 0u, 0u, 0u);
         uint32_t cache_i = 0xFFFFFFFFu, ti = 0;
         int L = 0;
         for (int guard = 0; guard < 129; ++guard) {
-          int j = first_above(th, u);
+          const int j = first_above(th, u);
           if (j > 127 - L) break;
           const int lanebit = L + j;
           uint32_t cell = 0;
@@ -129,18 +144,24 @@ __global__ void __launch_bounds__(256) sign_kernel(SignArgs A) {
             }
             const uint32_t v = pick(cache, ti & 3);
             ++ti;
-            cell = ncell - 1;
-            for (uint32_t kk = 0; kk + 1 < ncell; ++kk)
-              if (v < ct->phi[kk]) { cell = kk; break; }
+            // cell = min{k : v < phi_k}, phi non-decreasing, last cell takes the rest
+            uint32_t lo = 0, hi = ncell - 1;
+            while (lo < hi) {
+              const uint32_t mid = (lo + hi) >> 1;
+              if (v < ct->phi[mid]) hi = mid;
+              else lo = mid + 1;
+            }
+            cell = lo;
           }
           uint32_t mask = ct->mask[cell];
           const uint32_t wsel = (uint32_t)lanebit >> 5, bit = 1u << (lanebit & 31);
           while (mask) {
             const uint32_t comp = comp0 + (__ffs(mask) - 1);
             mask &= mask - 1;
-            const uint32_t e = __ldg(A.p.comp_off + comp + 1);
-            for (uint32_t q = __ldg(A.p.comp_off + comp); q < e; ++q)
-              atomicXor(slots + 4 * __ldg(A.p.comp_tgt + q) + wsel, bit);
+            const uint32_t rng = __ldg(A.p.comp_rng + comp);
+            const uint32_t q0 = rng >> 8, qe = q0 + (rng & 0xFFu);
+            for (uint32_t q = q0; q < qe; ++q)
+              atomicXor(sb + (size_t)__ldg(A.p.comp_tgt + q) * (kNB * 4) + wsel, bit);
           }
           L = lanebit + 1;
           if (L >= 128) break;
@@ -154,21 +175,25 @@ __global__ void __launch_bounds__(256) sign_kernel(SignArgs A) {
       }
       __syncwarp();
     };
-    const uint32_t iters = (n_groups + 31) >> 5;
-    for (uint32_t it = 0; it < iters; ++it) {
-      const uint32_t g = it * 32 + lane;
-      const bool valid = g < n_groups;
+    const uint32_t items = nb * n_groups;
+    for (uint32_t base = warp * 32; base < items; base += kSignWarps * 32) {
+      const uint32_t it = base + lane;
+      const bool valid = it < items;
+      uint32_t b = 0, g = 0;
       uint4 head = make_uint4(0u, 0u, 0u, 0u), th4 = make_uint4(0u, 0u, 0u, 0u);
       if (valid) {
+        b = it / n_groups;
+        g = it - b * n_groups;
         th4 = __ldg(A.p.theta4 + g);
-        if (th4.x | th4.y | th4.z | th4.w) head = philox(make_uint4(g, gb, 0u, kTagHead), k0, k1);
+        if (th4.x | th4.y | th4.z | th4.w)
+          head = philox(make_uint4(g, (uint32_t)(A.block0 + b0 + b), 0u, kTagHead), k0, k1);
       }
 #pragma unroll
-      for (uint32_t s = 0; s < 4; ++s) {
-        const uint32_t u = pick(head, s);
-        const bool fire = valid && u < pick(th4, s);
+      for (uint32_t s2 = 0; s2 < 4; ++s2) {
+        const uint32_t u = pick(head, s2);
+        const bool fire = valid && u < pick(th4, s2);
         const uint32_t bal = __ballot_sync(0xffffffffu, fire);
-        if (fire) queue[qn + __popc(bal & lt_mask)] = make_uint2(4 * g + s, u);
+        if (fire) queue[qn + __popc(bal & lt_mask)] = make_uint2((b << 28) | (4 * g + s2), u);
         qn += __popc(bal);
         __syncwarp();
         if (qn >= 32) {
@@ -180,16 +205,10 @@ __global__ void __launch_bounds__(256) sign_kernel(SignArgs A) {
       }
     }
     if (qn) drain(qn);
-    // 4. write the columns (padding bits cleared)
-    const uint64_t w0 = 2 * lb, w1 = 2 * lb + 1;
-    const bool has1 = w1 < A.W;
-    uint64_t m0 = ~0ull, m1 = ~0ull;
-    {
-      const uint64_t left = A.shots - lb * 128;
-      if (left < 64) { m0 = (1ull << left) - 1; m1 = 0; }
-      else if (left < 128) { m1 = (left == 64) ? 0ull : ((1ull << (left - 64)) - 1); }
-    }
-    for (uint32_t i = lane; i < NT; i += 32) {
+    __syncthreads();
+    // 4. write the columns: 2*kNB words per target, padding bits cleared
+    const uint64_t w0 = 2 * b0;
+    for (uint32_t i = threadIdx.x; i < NT; i += blockDim.x) {
       uint64_t* col;
       uint64_t idx;
       if (i < A.p.tgt_det0) { col = A.meas; idx = i; }
@@ -197,17 +216,31 @@ __global__ void __launch_bounds__(256) sign_kernel(SignArgs A) {
       else if (i < A.p.tgt_sign0) { col = A.obs; idx = i - A.p.tgt_obs0; }
       else { col = A.signs; idx = i - A.p.tgt_sign0; }
       if (col == nullptr) continue;
-      const uint4 v = reinterpret_cast<const uint4*>(slots)[i];
-      const uint64_t v0 = (((uint64_t)v.y << 32) | v.x) & m0, v1 = (((uint64_t)v.w << 32) | v.z) & m1;
+      const uint4* t = reinterpret_cast<const uint4*>(slots) + (size_t)i * kNB;
       uint64_t* dst = col + idx * A.W + w0;
-      if (has1 && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
-        *reinterpret_cast<ulonglong2*>(dst) = make_ulonglong2(v0, v1);
-      } else {
-        dst[0] = v0;
-        if (has1) dst[1] = v1;
+#pragma unroll
+      for (int b = 0; b < kNB; ++b) {
+        const uint4 v = t[b];
+        uint64_t v0 = ((uint64_t)v.y << 32) | v.x, v1 = ((uint64_t)v.w << 32) | v.z;
+        const uint64_t wa = w0 + 2 * b, wb = wa + 1;
+        if (wa >= A.W) break;
+        const uint64_t la = A.shots - 64 * wa;            // shots covered by word wa (>= 1)
+        if (la < 64) v0 &= (1ull << la) - 1;
+        const bool hb = wb < A.W;
+        if (hb) {
+          const uint64_t lbits = A.shots - 64 * wb;
+          if (lbits < 64) v1 &= (1ull << lbits) - 1;
+        }
+        uint64_t* d = dst + 2 * b;
+        if (hb && ((reinterpret_cast<uintptr_t>(d) & 15) == 0)) {
+          *reinterpret_cast<ulonglong2*>(d) = make_ulonglong2(v0, v1);
+        } else {
+          d[0] = v0;
+          if (hb) d[1] = v1;
+        }
       }
     }
-    __syncwarp();
+    __syncthreads();
   }
 }
 
@@ -485,18 +518,20 @@ __global__ void finalize_kernel(FinalArgs A) {
 // ---------------------------------------------------------------------------
 // launch wrappers (host)
 // ---------------------------------------------------------------------------
-size_t sign_smem_bytes(uint32_t n_targets, int warps_per_block) {
-  return kMaxSmemQ * 128 * 4 + kMaxSmemC * sizeof(CellTableDev) +
-         (size_t)warps_per_block * ((size_t)n_targets * 16 + kQueue * 8);
+size_t sign_smem_bytes(const DevPlan& p) { return sign_layout(p.n_qtab, p.n_ctab, p.n_targets).total; }
+
+cudaError_t sign_occupancy(const DevPlan& p, int* ctas_per_sm) {
+  const size_t smem = sign_smem_bytes(p);
+  cudaError_t e = cudaFuncSetAttribute(sign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, sign_kernel, kSignWarps * 32, smem);
 }
 
-cudaError_t launch_sign(const SignArgs& a, int warps_per_block, int grid, cudaStream_t st) {
-  size_t smem = sign_smem_bytes(a.p.n_targets, warps_per_block);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(sign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  sign_kernel<<<grid, warps_per_block * 32, smem, st>>>(a);
+cudaError_t launch_sign(const SignArgs& a, int grid, cudaStream_t st) {
+  const size_t smem = sign_smem_bytes(a.p);
+  cudaError_t e = cudaFuncSetAttribute(sign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  sign_kernel<<<grid, kSignWarps * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -40,8 +40,8 @@ struct DevPlan {
   uint32_t n_qtab, n_ctab;
   const uint32_t* qtheta;       // [n_qtab][128]
   const CellTableDev* ctabs;
-  const uint32_t* comp_off;
-  const uint32_t* comp_tgt;
+  const uint32_t* comp_rng;     // per component: (first incidence << 8) | count
+  const uint16_t* comp_tgt;     // incidence -> target slot
   uint32_t n_m1;
   const uint32_t* m1_t;
   const uint32_t* m1_off;
