@@ -109,7 +109,7 @@ cudaError_t upload(symft_plan* P) {
     o.m3 = d.m3;
     o.c = d.c;
     o.s = d.s;
-    o.sign_target_col = d.sign_target - h.tgt_sign0;
+    o.sign_target_col = d.sign_target - h.n_records;
     o.causal_off = d.causal_off;
     o.causal_n = d.causal_n;
     o.t = d.t;
@@ -118,7 +118,7 @@ cudaError_t upload(symft_plan* P) {
   size_t o_ch = push(blob, ch), o_q = push(blob, qtheta), o_ct = push(blob, ct);
   size_t o_t4 = push(blob, theta4);
   // packed incidence lists (16-bit targets, 24-bit offsets, 8-bit counts)
-  if (h.n_targets >= 65536) throw Error(SYMFT_E_CAPACITY, "more than 65535 bit-packed targets");
+  if (h.n_slots >= 65536) throw Error(SYMFT_E_CAPACITY, "more than 65535 bit-packed slots");
   if (h.comp_tgt.size() >= (1u << 24)) throw Error(SYMFT_E_CAPACITY, "too many sign incidences");
   if (h.n_channels >= (1u << 28)) throw Error(SYMFT_E_CAPACITY, "too many noise channels");
   std::vector<uint32_t> comp_rng(h.n_comp);
@@ -130,7 +130,10 @@ cudaError_t upload(symft_plan* P) {
   std::vector<uint16_t> comp_tgt(h.comp_tgt.begin(), h.comp_tgt.end());
   size_t o_co = push(blob, comp_rng), o_ctg = push(blob, comp_tgt);
   size_t o_m1t = push(blob, h.m1_t), o_m1o = push(blob, h.m1_off), o_m1g = push(blob, h.m1_tgt);
-  size_t o_tc = push(blob, h.tgt_const), o_tco = push(blob, h.tgt_causal_off), o_tca = push(blob, h.tgt_causal);
+  size_t o_tco = push(blob, h.tgt_causal_off), o_tca = push(blob, h.tgt_causal);
+  size_t o_sc = push(blob, h.slot_const), o_po = push(blob, h.par_off), o_pa = push(blob, h.par);
+  size_t o_lo = push(blob, h.lvl_off), o_lr = push(blob, h.lvl_rec);
+  size_t o_go = push(blob, h.gat_off), o_gr = push(blob, h.gat_rec);
   size_t o_pe = push(blob, h.post_events), o_dn = push(blob, dn), o_dc = push(blob, h.dense_causal);
   cudaError_t e = P->plan_buf.ensure(blob.size());
   if (e != cudaSuccess) return e;
@@ -155,7 +158,15 @@ cudaError_t upload(symft_plan* P) {
   d.tgt_det0 = h.tgt_det0;
   d.tgt_obs0 = h.tgt_obs0;
   d.tgt_sign0 = h.tgt_sign0;
-  d.tgt_const = reinterpret_cast<const uint8_t*>(at(o_tc));
+  d.n_slots = h.n_slots;
+  d.slot_const = reinterpret_cast<const uint8_t*>(at(o_sc));
+  d.par_off = reinterpret_cast<const uint32_t*>(at(o_po));
+  d.par = reinterpret_cast<const uint32_t*>(at(o_pa));
+  d.n_levels = h.lvl_off.empty() ? 0 : static_cast<uint32_t>(h.lvl_off.size() - 1);
+  d.lvl_off = reinterpret_cast<const uint32_t*>(at(o_lo));
+  d.lvl_rec = reinterpret_cast<const uint32_t*>(at(o_lr));
+  d.gat_off = reinterpret_cast<const uint32_t*>(at(o_go));
+  d.gat_rec = reinterpret_cast<const uint32_t*>(at(o_gr));
   d.tgt_causal_off = reinterpret_cast<const uint32_t*>(at(o_tco));
   d.tgt_causal = reinterpret_cast<const uint32_t*>(at(o_tca));
   d.n_post_events = static_cast<uint32_t>(h.post_events.size());
@@ -231,7 +242,7 @@ int sample_impl(symft_plan* P, const symft_sample_args* a) {
   if (a->check) CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
 
   // --- sign kernel ---------------------------------------------------------
-  if (h.n_targets > 0) {
+  if (h.n_slots > 0) {
     SignArgs s{};
     s.p = P->dp;
     s.seed = a->seed;
@@ -246,8 +257,8 @@ int sample_impl(symft_plan* P, const symft_sample_args* a) {
     s.status = status;
     const size_t smem = sign_smem_bytes(P->dp);
     if (smem > 220 * 1024)
-      return set_error(SYMFT_E_CAPACITY, "too many bit-packed targets for shared memory (" +
-                                             std::to_string(h.n_targets) + ")");
+      return set_error(SYMFT_E_CAPACITY, "too many bit-packed slots for shared memory (" +
+                                             std::to_string(h.n_slots) + ")");
     const uint64_t chunks = (nblk + kSignBlocksPerCta - 1) / kSignBlocksPerCta;
     int per_sm = 1;
     CUDA_TRY(sign_occupancy(P->dp, &per_sm));
@@ -373,7 +384,7 @@ int symft_plan_info(const symft_plan* p, symft_info* info) {
   for (int i = 0; i < 7; ++i) info->n_instr[i] = h.hist[i];
   info->max_expr_weight = h.max_expr_weight;
   info->n_noise_components = h.n_comp;
-  info->n_targets = h.n_targets;
+  info->n_targets = h.n_slots;
   info->n_causal = h.n_m3;
   info->sign_xor_terms = h.sign_xor_terms;
   return SYMFT_OK;

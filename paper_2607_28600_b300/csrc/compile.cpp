@@ -458,11 +458,6 @@ int chan_ncomp(int chan) {
 }
 
 HostPlan Compiler::run() {
-  if (n_ == 0 && !c_.ops.empty()) {
-    bool any = false;
-    for (auto& op : c_.ops) any |= (op.kind == OP_DET || op.kind == OP_OBS);
-    (void)any;
-  }
   // symbols: noise components first, then measurement ordinals
   chan_comp0_.assign(c_.n_channels, 0);
   chan_ncomp_.assign(c_.n_channels, 0);
@@ -484,7 +479,6 @@ HostPlan Compiler::run() {
     Zb_[q] = pa_.single(q, false, true);
     Xb_[q] = pa_.single(q, true, false);
   }
-  if (n_ == 0) n_ = 0;
   Ex_.assign(nq, ea_.zero());
   Ez_.assign(nq, ea_.zero());
 
@@ -614,63 +608,183 @@ void Compiler::lower(HostPlan& P) {
     }
   }
 
-  // targets: records, detectors, observables, dense signs
+  // ---- outputs: records, detectors, observables (full expressions) ----
   const uint32_t R = c_.n_records, Dn = c_.n_dets, O = c_.n_obs;
   const uint32_t G = static_cast<uint32_t>(dense_lam.size());
   P.tgt_rec0 = 0;
   P.tgt_det0 = R;
   P.tgt_obs0 = R + Dn;
   P.tgt_sign0 = R + Dn + O;
-  P.n_targets = R + Dn + O + G;
-  std::vector<Expr> tgt(P.n_targets);
-  for (uint32_t r = 0; r < R; ++r) tgt[r] = res[c_.record_ordinal[r]];
-  for (uint32_t i = 0; i < Dn + O; ++i) tgt[R + i] = ea_.zero();
+  P.n_targets = R + Dn + O;
+  std::vector<Expr> full(P.n_targets);
+  for (uint32_t r = 0; r < R; ++r) full[r] = res[c_.record_ordinal[r]];
+  std::vector<std::vector<uint32_t>> gat(Dn + O);
+  for (uint32_t i = 0; i < Dn + O; ++i) full[R + i] = ea_.zero();
+  std::vector<int32_t> rec_of_t(NM, -1);
+  for (uint32_t r = 0; r < R; ++r) rec_of_t[c_.record_ordinal[r]] = static_cast<int32_t>(r);
   for (const Op& op : c_.ops) {
-    if (op.kind == OP_DET)
-      for (uint32_t t : op.conds) ea_.xor_into(tgt[R + op.index], res[t]);
-    if (op.kind == OP_OBS)
-      for (uint32_t t : op.conds) ea_.xor_into(tgt[R + Dn + op.index], res[t]);
+    if (op.kind != OP_DET && op.kind != OP_OBS) continue;
+    uint32_t slot = (op.kind == OP_DET ? 0 : Dn) + op.index;
+    for (uint32_t t : op.conds) {
+      ea_.xor_into(full[R + slot], res[t]);
+      gat[slot].push_back(static_cast<uint32_t>(rec_of_t[t]));
+    }
   }
-  for (uint32_t g = 0; g < G; ++g) tgt[P.tgt_sign0 + g] = dense_lam[g];
-
-  // incidence lists
-  std::vector<std::vector<uint32_t>> comp_t(n_comp_), m1_t(P.m1_t.size());
-  P.tgt_const.assign(P.n_targets, 0);
+  // gather lists with duplicates cancelled (parity)
+  P.gat_off.assign(Dn + O + 1, 0);
+  for (uint32_t i = 0; i < Dn + O; ++i) {
+    std::sort(gat[i].begin(), gat[i].end());
+    std::vector<uint32_t> keep;
+    for (size_t j = 0; j < gat[i].size();) {
+      size_t e = j;
+      while (e < gat[i].size() && gat[i][e] == gat[i][j]) ++e;
+      if ((e - j) & 1) keep.push_back(gat[i][j]);
+      j = e;
+    }
+    P.gat_rec.insert(P.gat_rec.end(), keep.begin(), keep.end());
+    P.gat_off[i + 1] = static_cast<uint32_t>(P.gat_rec.size());
+  }
+  // causal (active-outcome) parts of every output, for the finalize pass
   P.tgt_causal_off.assign(P.n_targets + 1, 0);
-  std::vector<std::vector<uint32_t>> causal(P.n_targets);
   for (uint32_t i = 0; i < P.n_targets; ++i) {
-    const Expr& e = tgt[i];
-    P.tgt_const[i] = ea_.constant(e);
-    ea_.for_each(e, 0, NS, [&](uint32_t s) {
-      if (s < n_comp_) {
-        comp_t[s].push_back(i);
+    ea_.for_each(full[i], n_comp_, NS, [&](uint32_t s) {
+      uint32_t t = s - n_comp_;
+      if (cls[t] == 3) P.tgt_causal.push_back(static_cast<uint32_t>(m3_index[t]));
+      else if (cls[t] == 2) throw Error(SYMFT_E_DEVICE, "internal: unresolved deterministic symbol");
+    });
+    P.tgt_causal_off[i + 1] = static_cast<uint32_t>(P.tgt_causal.size());
+  }
+
+  // ---- exogenous record parts, delta-chained to earlier records ----
+  // The sign kernel evaluates exo_r = const ^ delta_r ^ XOR(parents).  A parent
+  // is taken when it removes enough weighted incidences: a noise component
+  // costs work only in the rare blocks where it fires, a random-measurement
+  // bit every block, a parent one word-XOR per block.
+  Expr m3mask = ea_.zero(), m1mask = ea_.zero();
+  for (uint32_t t = 0; t < NM; ++t) {
+    if (cls[t] == 3) ea_.flip(m3mask, msym(t));
+    if (cls[t] == 1) ea_.flip(m1mask, msym(t));
+  }
+  auto strip_causal = [&](const Expr& e) {
+    Expr o = e;
+    for (uint32_t w = 0; w < ea_.nw; ++w) o.w[w] &= ~m3mask.w[w];
+    return o;
+  };
+  const uint32_t sym_words = ea_.nw;
+  const uint64_t const_bit_mask_word = NS >> 6;
+  const uint64_t const_bit = 1ull << (NS & 63);
+  auto cost = [&](const Expr& e) {
+    uint64_t c = 0;
+    for (uint32_t w = 0; w < sym_words; ++w) {
+      uint64_t v = e.w[w];
+      if (w == const_bit_mask_word) v &= ~const_bit;
+      c += __builtin_popcountll(v) + 15ull * __builtin_popcountll(v & m1mask.w[w]);
+    }
+    return c;
+  };
+  std::vector<Expr> exo(R);
+  for (uint32_t r = 0; r < R; ++r) exo[r] = strip_causal(full[r]);
+  std::vector<std::vector<uint32_t>> parents(R);
+  std::vector<Expr> delta(R);
+  std::vector<std::vector<uint32_t>> inv(NS);       // symbol -> records containing it
+  constexpr uint64_t kParentGain = 20;
+  constexpr int kMaxParents = 4;
+  constexpr size_t kMaxCand = 96;
+  std::vector<uint32_t> seen_mark(R, 0xFFFFFFFFu);
+  for (uint32_t r = 0; r < R; ++r) {
+    Expr resid = exo[r];
+    uint64_t cres = cost(resid);
+    for (int it = 0; it < kMaxParents && cres > kParentGain; ++it) {
+      // candidates: earlier records sharing a symbol with the residual
+      std::vector<uint32_t> cand;
+      ea_.for_each(resid, 0, NS, [&](uint32_t sidx) {
+        if (cand.size() >= kMaxCand) return;
+        const auto& lst = inv[sidx];
+        for (size_t j = lst.size(); j-- > 0 && cand.size() < kMaxCand;) {
+          uint32_t p = lst[j];
+          if (seen_mark[p] != r * 8 + it) {
+            seen_mark[p] = r * 8 + it;
+            cand.push_back(p);
+          }
+        }
+      });
+      uint64_t best_c = cres;
+      int64_t best = -1;
+      for (uint32_t p : cand) {
+        Expr x = resid;
+        ea_.xor_into(x, exo[p]);
+        uint64_t c = cost(x);
+        if (c < best_c) {
+          best_c = c;
+          best = p;
+        }
+      }
+      if (best < 0 || cres - best_c < kParentGain) break;
+      ea_.xor_into(resid, exo[best]);
+      cres = best_c;
+      parents[r].push_back(static_cast<uint32_t>(best));
+    }
+    delta[r] = std::move(resid);
+    ea_.for_each(exo[r], 0, NS, [&](uint32_t sidx) { inv[sidx].push_back(r); });
+  }
+  std::vector<uint32_t> level(R, 0);
+  uint32_t max_level = 0;
+  for (uint32_t r = 0; r < R; ++r) {
+    for (uint32_t p : parents[r]) level[r] = std::max(level[r], level[p] + 1);
+    max_level = std::max(max_level, level[r]);
+  }
+  P.par_off.assign(R + 1, 0);
+  for (uint32_t r = 0; r < R; ++r) {
+    P.par.insert(P.par.end(), parents[r].begin(), parents[r].end());
+    P.par_off[r + 1] = static_cast<uint32_t>(P.par.size());
+  }
+  P.lvl_off.assign(max_level + 1, 0);    // levels 1..max_level
+  for (uint32_t L = 1; L <= max_level; ++L) {
+    for (uint32_t r = 0; r < R; ++r)
+      if (level[r] == L) P.lvl_rec.push_back(r);
+    P.lvl_off[L] = static_cast<uint32_t>(P.lvl_rec.size());
+  }
+
+  // ---- sign-kernel slots: [records (deltas)][dense signs (exogenous part)] ----
+  P.n_slots = R + G;
+  std::vector<Expr> slot_expr(P.n_slots);
+  for (uint32_t r = 0; r < R; ++r) slot_expr[r] = std::move(delta[r]);
+  std::vector<std::vector<uint32_t>> sign_causal(G);
+  for (uint32_t g = 0; g < G; ++g) {
+    slot_expr[R + g] = strip_causal(dense_lam[g]);
+    ea_.for_each(dense_lam[g], n_comp_, NS, [&](uint32_t sidx) {
+      uint32_t t = sidx - n_comp_;
+      if (cls[t] == 3) sign_causal[g].push_back(static_cast<uint32_t>(m3_index[t]));
+    });
+  }
+  std::vector<std::vector<uint32_t>> comp_t(n_comp_), m1_t(P.m1_t.size());
+  P.slot_const.assign(P.n_slots, 0);
+  for (uint32_t i = 0; i < P.n_slots; ++i) {
+    const Expr& e = slot_expr[i];
+    P.slot_const[i] = ea_.constant(e);
+    ea_.for_each(e, 0, NS, [&](uint32_t sidx) {
+      if (sidx < n_comp_) {
+        comp_t[sidx].push_back(i);
         P.sign_xor_terms++;
       } else {
-        uint32_t t = s - n_comp_;
+        uint32_t t = sidx - n_comp_;
         if (cls[t] == 1) {
           m1_t[m1_index[t]].push_back(i);
           P.sign_xor_terms++;
-        } else if (cls[t] == 3) {
-          causal[i].push_back(static_cast<uint32_t>(m3_index[t]));
         } else {
-          throw Error(SYMFT_E_DEVICE, "internal: unresolved deterministic symbol");
+          throw Error(SYMFT_E_DEVICE, "internal: non-exogenous symbol in a slot");
         }
       }
     });
   }
   P.comp_off.assign(n_comp_ + 1, 0);
-  for (uint32_t s = 0; s < n_comp_; ++s) P.comp_off[s + 1] = P.comp_off[s] + static_cast<uint32_t>(comp_t[s].size());
+  for (uint32_t sidx = 0; sidx < n_comp_; ++sidx)
+    P.comp_off[sidx + 1] = P.comp_off[sidx] + static_cast<uint32_t>(comp_t[sidx].size());
   P.comp_tgt.reserve(P.comp_off[n_comp_]);
   for (auto& v : comp_t) P.comp_tgt.insert(P.comp_tgt.end(), v.begin(), v.end());
   P.m1_off.assign(P.m1_t.size() + 1, 0);
   for (size_t j = 0; j < m1_t.size(); ++j) P.m1_off[j + 1] = P.m1_off[j] + static_cast<uint32_t>(m1_t[j].size());
   for (auto& v : m1_t) P.m1_tgt.insert(P.m1_tgt.end(), v.begin(), v.end());
-  // causal parts: records/dets/obs go to the finalize pass, signs to the dense stream
-  for (uint32_t i = 0; i < P.tgt_sign0; ++i) {
-    P.tgt_causal_off[i + 1] = P.tgt_causal_off[i] + static_cast<uint32_t>(causal[i].size());
-    P.tgt_causal.insert(P.tgt_causal.end(), causal[i].begin(), causal[i].end());
-  }
-  for (uint32_t i = P.tgt_sign0; i < P.n_targets; ++i) P.tgt_causal_off[i + 1] = P.tgt_causal_off[i];
 
   // dense instruction stream
   for (uint32_t g = 0; g < G; ++g) {
@@ -685,9 +799,9 @@ void Compiler::lower(HostPlan& P) {
     D.eta = I.eta;
     D.c = std::cos(I.theta / 2.0);
     D.s = std::sin(I.theta / 2.0);
-    D.sign_target = P.tgt_sign0 + g;
+    D.sign_target = R + g;
     D.causal_off = static_cast<uint32_t>(P.dense_causal.size());
-    const auto& cl = causal[P.tgt_sign0 + g];
+    const auto& cl = sign_causal[g];
     D.causal_n = static_cast<uint32_t>(cl.size());
     P.dense_causal.insert(P.dense_causal.end(), cl.begin(), cl.end());
     D.m3 = -1;

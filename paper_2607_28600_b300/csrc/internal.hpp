@@ -119,10 +119,17 @@ struct HostPlan {
   // random measurements (m1): ordinal and targets (CSR)
   std::vector<uint32_t> m1_t, m1_off, m1_tgt;
 
-  // targets: [records][dets][obs][dense signs]
+  // outputs in finalize numbering: [records][dets][obs]; tgt_sign0 = their count
   uint32_t n_targets = 0, tgt_rec0 = 0, tgt_det0 = 0, tgt_obs0 = 0, tgt_sign0 = 0;
-  std::vector<uint8_t> tgt_const;
-  std::vector<uint32_t> tgt_causal_off, tgt_causal;   // m3 indices per target
+  std::vector<uint32_t> tgt_causal_off, tgt_causal;   // m3 indices per output
+
+  // sign-kernel slots: [records][dense signs]; a record slot accumulates
+  // const + delta (noise and random bits) and then XORs in its parent records
+  uint32_t n_slots = 0;
+  std::vector<uint8_t> slot_const;
+  std::vector<uint32_t> par_off, par;        // record -> parent records (CSR)
+  std::vector<uint32_t> lvl_off, lvl_rec;    // records with parents, grouped by level
+  std::vector<uint32_t> gat_off, gat_rec;    // det / obs -> records (CSR)
 
   // postselection order: events in circuit order, rec (>=0) or det (-1-i)
   std::vector<int32_t> post_events;

@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kSignWarps * 32, 4) sign_kernel(SignArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const uint32_t NT = A.p.n_targets;
+  const uint32_t NT = A.p.n_slots;
   const uint32_t k0 = (uint32_t)A.seed, k1 = (uint32_t)(A.seed >> 32);
   const SignLayout Lay = sign_layout(A.p.n_qtab, A.p.n_ctab, NT);
   uint32_t* sq = reinterpret_cast<uint32_t*>(smem_raw + Lay.q_off);
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kSignWarps * 32, 4) sign_kernel(SignArgs A) {
     const uint32_t nb = (uint32_t)min((uint64_t)kNB, A.n_blocks - b0);
     // 1. constants
     for (uint32_t i = threadIdx.x; i < NT; i += blockDim.x) {
-      const uint32_t v = A.p.tgt_const[i] ? ~0u : 0u;
+      const uint32_t v = A.p.slot_const[i] ? ~0u : 0u;
       uint4* t = reinterpret_cast<uint4*>(slots) + (size_t)i * kNB;
 #pragma unroll
       for (int b = 0; b < kNB; ++b) t[b] = make_uint4(v, v, v, v);
@@ -206,21 +206,72 @@ __global__ void __launch_bounds__(kSignWarps * 32, 4) sign_kernel(SignArgs A) {
     }
     if (qn) drain(qn);
     __syncthreads();
-    // 4. write the columns: 2*kNB words per target, padding bits cleared
+    // 4. records: XOR in the parent records level by level (exo_r = delta_r ^ parents)
+    for (uint32_t L = 1; L <= A.p.n_levels; ++L) {
+      const uint32_t lo = __ldg(A.p.lvl_off + L - 1), hi = __ldg(A.p.lvl_off + L);
+      for (uint32_t x = lo + threadIdx.x; x < hi; x += blockDim.x) {
+        const uint32_t r = __ldg(A.p.lvl_rec + x);
+        uint4* t = reinterpret_cast<uint4*>(slots) + (size_t)r * kNB;
+        uint4 acc[kNB];
+#pragma unroll
+        for (int b = 0; b < kNB; ++b) acc[b] = t[b];
+        const uint32_t pe = __ldg(A.p.par_off + r + 1);
+        for (uint32_t q = __ldg(A.p.par_off + r); q < pe; ++q) {
+          const uint4* pt = reinterpret_cast<const uint4*>(slots) + (size_t)__ldg(A.p.par + q) * kNB;
+#pragma unroll
+          for (int b = 0; b < kNB; ++b) {
+            const uint4 v = pt[b];
+            acc[b].x ^= v.x; acc[b].y ^= v.y; acc[b].z ^= v.z; acc[b].w ^= v.w;
+          }
+        }
+#pragma unroll
+        for (int b = 0; b < kNB; ++b) t[b] = acc[b];
+      }
+      __syncthreads();
+    }
+    // 5. write the columns (records, gathered detectors / observables, dense
+    //    signs): 2*kNB words per column, padding bits cleared
     const uint64_t w0 = 2 * b0;
-    for (uint32_t i = threadIdx.x; i < NT; i += blockDim.x) {
+    const uint32_t R = A.p.n_records, DO = A.p.n_dets + A.p.n_obs;
+    const uint32_t n_out = R + DO + (NT - R);
+    for (uint32_t i = threadIdx.x; i < n_out; i += blockDim.x) {
       uint64_t* col;
       uint64_t idx;
-      if (i < A.p.tgt_det0) { col = A.meas; idx = i; }
-      else if (i < A.p.tgt_obs0) { col = A.det; idx = i - A.p.tgt_det0; }
-      else if (i < A.p.tgt_sign0) { col = A.obs; idx = i - A.p.tgt_obs0; }
-      else { col = A.signs; idx = i - A.p.tgt_sign0; }
-      if (col == nullptr) continue;
-      const uint4* t = reinterpret_cast<const uint4*>(slots) + (size_t)i * kNB;
+      uint4 val[kNB];
+      if (i < R) {
+        col = A.meas;
+        idx = i;
+        if (col == nullptr) continue;
+#pragma unroll
+        for (int b = 0; b < kNB; ++b) val[b] = reinterpret_cast<const uint4*>(slots)[(size_t)i * kNB + b];
+      } else if (i < R + DO) {
+        const uint32_t j = i - R;
+        if (j < A.p.n_dets) { col = A.det; idx = j; }
+        else { col = A.obs; idx = j - A.p.n_dets; }
+        if (col == nullptr) continue;
+#pragma unroll
+        for (int b = 0; b < kNB; ++b) val[b] = make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t ge = __ldg(A.p.gat_off + j + 1);
+        for (uint32_t q = __ldg(A.p.gat_off + j); q < ge; ++q) {
+          const uint4* pt = reinterpret_cast<const uint4*>(slots) + (size_t)__ldg(A.p.gat_rec + q) * kNB;
+#pragma unroll
+          for (int b = 0; b < kNB; ++b) {
+            const uint4 v = pt[b];
+            val[b].x ^= v.x; val[b].y ^= v.y; val[b].z ^= v.z; val[b].w ^= v.w;
+          }
+        }
+      } else {
+        const uint32_t g = i - R - DO;
+        col = A.signs;
+        idx = g;
+        if (col == nullptr) continue;
+#pragma unroll
+        for (int b = 0; b < kNB; ++b) val[b] = reinterpret_cast<const uint4*>(slots)[(size_t)(R + g) * kNB + b];
+      }
       uint64_t* dst = col + idx * A.W + w0;
 #pragma unroll
       for (int b = 0; b < kNB; ++b) {
-        const uint4 v = t[b];
+        const uint4 v = val[b];
         uint64_t v0 = ((uint64_t)v.y << 32) | v.x, v1 = ((uint64_t)v.w << 32) | v.z;
         const uint64_t wa = w0 + 2 * b, wb = wa + 1;
         if (wa >= A.W) break;
@@ -518,7 +569,7 @@ __global__ void finalize_kernel(FinalArgs A) {
 // ---------------------------------------------------------------------------
 // launch wrappers (host)
 // ---------------------------------------------------------------------------
-size_t sign_smem_bytes(const DevPlan& p) { return sign_layout(p.n_qtab, p.n_ctab, p.n_targets).total; }
+size_t sign_smem_bytes(const DevPlan& p) { return sign_layout(p.n_qtab, p.n_ctab, p.n_slots).total; }
 
 cudaError_t sign_occupancy(const DevPlan& p, int* ctas_per_sm) {
   const size_t smem = sign_smem_bytes(p);

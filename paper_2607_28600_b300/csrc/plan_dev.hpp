@@ -46,10 +46,20 @@ struct DevPlan {
   const uint32_t* m1_t;
   const uint32_t* m1_off;
   const uint32_t* m1_tgt;
+  // outputs in finalize numbering [records][dets][obs] (tgt_sign0 = count)
   uint32_t n_targets, tgt_det0, tgt_obs0, tgt_sign0;
-  const uint8_t* tgt_const;
   const uint32_t* tgt_causal_off;
   const uint32_t* tgt_causal;
+  // sign-kernel slots [records][dense signs]
+  uint32_t n_slots;
+  const uint8_t* slot_const;
+  const uint32_t* par_off;      // record -> parents (CSR)
+  const uint32_t* par;
+  uint32_t n_levels;
+  const uint32_t* lvl_off;      // n_levels + 1 offsets into lvl_rec
+  const uint32_t* lvl_rec;
+  const uint32_t* gat_off;      // det / obs -> records (CSR)
+  const uint32_t* gat_rec;
   uint32_t n_post_events;
   const int32_t* post_events;
   uint32_t n_dense;
