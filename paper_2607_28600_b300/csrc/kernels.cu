@@ -58,15 +58,15 @@ __host__ __device__ inline SignLayout sign_layout(uint32_t n_qtab, uint32_t n_ct
   L.c_off = align16((size_t)n_qtab * 128 * 4);
   L.slot_off = L.c_off + align16((size_t)n_ctab * sizeof(CellTableDev));
   L.queue_off = L.slot_off + (size_t)n_targets * kNB * 16;
-  L.total = L.queue_off + (size_t)kSignWarps * kQueue * 8;
+  L.total = L.queue_off + (size_t)kSignWarps * kQueue * 16;
   return L;
 }
 
 // One CTA samples kNB consecutive 128-shot noise blocks (256 shots, four
 // 64-shot words per column).  Shared memory: the noise tables, then
 //   slots  n_targets x kNB x 4 uint32 (lane l of block b: bit l&31 of word 4b + (l>>5))
-//   queue  kSignWarps x kQueue x uint2 ((block << 28) | channel, head draw)
-__global__ void __launch_bounds__(kSignWarps * 32, 4) sign_kernel(SignArgs A) {
+//   queue  kSignWarps x kQueue x uint4 ((block << 28) | channel, u, L | draw << 8, -)
+__global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kSignWarps * 32, 4) sign_kernel(SignArgs A) {
   uint32_t* sq = reinterpret_cast<uint32_t*>(smem_raw + Lay.q_off);
   CellTableDev* sc = reinterpret_cast<CellTableDev*>(smem_raw + Lay.c_off);
   uint32_t* slots = reinterpret_cast<uint32_t*>(smem_raw + Lay.slot_off);
-  uint2* queue = reinterpret_cast<uint2*>(smem_raw + Lay.queue_off) + warp * kQueue;
+  uint4* queue = reinterpret_cast<uint4*>(smem_raw + Lay.queue_off) + warp * kQueue;
 
   for (uint32_t i = threadIdx.x; i < A.p.n_qtab * 128; i += blockDim.x) sq[i] = __ldg(A.p.qtheta + i);
   for (uint32_t i = threadIdx.x; i < A.p.n_ctab; i += blockDim.x) sc[i] = A.p.ctabs[i];
@@ -112,40 +112,37 @@ __global__ void __launch_bounds__(kSignWarps * 32, 4) sign_kernel(SignArgs A) {
     }
     // 3. noise.  Phase A: each lane draws the head uniforms of four channels of
     //    one block (one Philox block) and queues the channels that fire in it.
-    //    Phase B: each lane continues one queued channel's word-geometric
-    //    process and scatters its fired lanes into the targets.
+    //    Phase B: each lane takes one queued (channel, block, u, L, draw index)
+    //    state, resolves exactly one fire -- lane L + j*, its Pauli cell and the
+    //    scatter of its components -- and re-queues the channel if its
+    //    word-geometric process continues, so every step costs the same.
     uint32_t qn = 0;
     auto drain = [&](uint32_t count) {
-      uint2 ent = make_uint2(0u, 0u);
+      uint4 ent = make_uint4(0u, 0u, 0u, 0u);
       if ((uint32_t)lane < count) ent = queue[lane];
       __syncwarp();
+      bool more = false;
+      uint4 next = make_uint4(0u, 0u, 0u, 0u);
       if ((uint32_t)lane < count) {
         const uint32_t c = ent.x & 0x0FFFFFFFu, b = ent.x >> 28;
         const uint32_t gb = (uint32_t)(A.block0 + b0 + b);
-        uint32_t u = ent.y;
+        const uint32_t u = ent.y;
+        const int L = (int)(ent.z & 0xFFu);
+        uint32_t ti = ent.z >> 8;
         const uint4 raw = __ldg(reinterpret_cast<const uint4*>(A.p.ch) + c);
         const uint32_t* th = sq + (size_t)(raw.y & 0xFFFFu) * 128;
         const CellTableDev* ct = sc + (raw.y >> 16);
-        const uint32_t comp0 = raw.z;
-        const uint32_t ncell = ct->ncell;
-        uint32_t* sb = slots + (size_t)b * 4;
-        uint4 cache = make_uint4(0u, 0u, 0u, 0u);
-        uint32_t cache_i = 0xFFFFFFFFu, ti = 0;
-        int L = 0;
-        for (int guard = 0; guard < 129; ++guard) {
-          const int j = first_above(th, u);
-          if (j > 127 - L) break;
+        const int j = first_above(th, u);
+        if (j <= 127 - L) {
           const int lanebit = L + j;
+          const uint32_t ncell = ct->ncell;
+          // the draws of one fire (cell, next u) lie in one Philox block
+          const uint4 tail = philox(make_uint4(c, gb, ti >> 2, kTagTail), k0, k1);
           uint32_t cell = 0;
           if (ncell > 1) {
-            if ((ti >> 2) != cache_i) {
-              cache_i = ti >> 2;
-              cache = philox(make_uint4(c, gb, cache_i, kTagTail), k0, k1);
-            }
-            const uint32_t v = pick(cache, ti & 3);
+            const uint32_t v = pick(tail, ti & 3);
             ++ti;
-            // cell = min{k : v < phi_k}, phi non-decreasing, last cell takes the rest
-            uint32_t lo = 0, hi = ncell - 1;
+            uint32_t lo = 0, hi = ncell - 1;     // min{k : v < phi_k}
             while (lo < hi) {
               const uint32_t mid = (lo + hi) >> 1;
               if (v < ct->phi[mid]) hi = mid;
@@ -155,56 +152,58 @@ __global__ void __launch_bounds__(kSignWarps * 32, 4) sign_kernel(SignArgs A) {
           }
           uint32_t mask = ct->mask[cell];
           const uint32_t wsel = (uint32_t)lanebit >> 5, bit = 1u << (lanebit & 31);
+          uint32_t* sb = slots + (size_t)b * 4 + wsel;
           while (mask) {
-            const uint32_t comp = comp0 + (__ffs(mask) - 1);
+            const uint32_t comp = raw.z + (__ffs(mask) - 1);
             mask &= mask - 1;
             const uint32_t rng = __ldg(A.p.comp_rng + comp);
             const uint32_t q0 = rng >> 8, qe = q0 + (rng & 0xFFu);
             for (uint32_t q = q0; q < qe; ++q)
-              atomicXor(sb + (size_t)__ldg(A.p.comp_tgt + q) * (kNB * 4) + wsel, bit);
+              atomicXor(sb + (size_t)__ldg(A.p.comp_tgt + q) * (kNB * 4), bit);
           }
-          L = lanebit + 1;
-          if (L >= 128) break;
-          if ((ti >> 2) != cache_i) {
-            cache_i = ti >> 2;
-            cache = philox(make_uint4(c, gb, cache_i, kTagTail), k0, k1);
+          if (lanebit < 127) {
+            // next uniform: draw index ti, in the same Philox block as the cell draw
+            next = make_uint4(ent.x, pick(tail, ti & 3), (uint32_t)(lanebit + 1) | ((ti + 1) << 8), 0u);
+            more = true;
           }
-          u = pick(cache, ti & 3);
-          ++ti;
         }
       }
       __syncwarp();
+      // compact the unprocessed tail to the front, then append continuing channels
+      const uint32_t rest = qn - count;       // < 32
+      uint4 mv = make_uint4(0u, 0u, 0u, 0u);
+      if ((uint32_t)lane < rest) mv = queue[count + lane];
+      __syncwarp();
+      if ((uint32_t)lane < rest) queue[lane] = mv;
+      __syncwarp();
+      const uint32_t bal = __ballot_sync(0xffffffffu, more);
+      if (more) queue[rest + __popc(bal & lt_mask)] = next;
+      qn = rest + __popc(bal);
+      __syncwarp();
     };
-    const uint32_t items = nb * n_groups;
-    for (uint32_t base = warp * 32; base < items; base += kSignWarps * 32) {
-      const uint32_t it = base + lane;
-      const bool valid = it < items;
-      uint32_t b = 0, g = 0;
-      uint4 head = make_uint4(0u, 0u, 0u, 0u), th4 = make_uint4(0u, 0u, 0u, 0u);
-      if (valid) {
-        b = it / n_groups;
-        g = it - b * n_groups;
-        th4 = __ldg(A.p.theta4 + g);
-        if (th4.x | th4.y | th4.z | th4.w)
-          head = philox(make_uint4(g, (uint32_t)(A.block0 + b0 + b), 0u, kTagHead), k0, k1);
-      }
+    for (uint32_t b = 0; b < nb; ++b) {
+      const uint32_t gb = (uint32_t)(A.block0 + b0 + b);
+      for (uint32_t base = warp * 32; base < n_groups; base += kSignWarps * 32) {
+        const uint32_t g = base + lane;
+        const bool valid = g < n_groups;
+        uint4 head = make_uint4(0u, 0u, 0u, 0u), th4 = make_uint4(0u, 0u, 0u, 0u);
+        if (valid) {
+          th4 = __ldg(A.p.theta4 + g);
+          if (th4.x | th4.y | th4.z | th4.w) head = philox(make_uint4(g, gb, 0u, kTagHead), k0, k1);
+        }
 #pragma unroll
-      for (uint32_t s2 = 0; s2 < 4; ++s2) {
-        const uint32_t u = pick(head, s2);
-        const bool fire = valid && u < pick(th4, s2);
-        const uint32_t bal = __ballot_sync(0xffffffffu, fire);
-        if (fire) queue[qn + __popc(bal & lt_mask)] = make_uint2((b << 28) | (4 * g + s2), u);
-        qn += __popc(bal);
-        __syncwarp();
-        if (qn >= 32) {
-          drain(32);
-          qn -= 32;
-          if ((uint32_t)lane < qn) queue[lane] = queue[32 + lane];
+        for (uint32_t s2 = 0; s2 < 4; ++s2) {
+          const uint32_t u = pick(head, s2);
+          const bool fire = valid && u < pick(th4, s2);
+          const uint32_t bal = __ballot_sync(0xffffffffu, fire);
+          if (fire) queue[qn + __popc(bal & lt_mask)] = make_uint4((b << 28) | (4 * g + s2), u, 0u, 0u);
+          qn += __popc(bal);
           __syncwarp();
+          while (qn >= 32) drain(32);
         }
       }
     }
-    if (qn) drain(qn);
+    while (qn) drain(qn < 32 ? qn : 32);
     __syncthreads();
     // 4. records: XOR in the parent records level by level (exo_r = delta_r ^ parents)
     for (uint32_t L = 1; L <= A.p.n_levels; ++L) {
