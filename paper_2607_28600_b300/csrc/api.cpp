@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -16,7 +17,7 @@
 #include "symft.h"
 
 namespace symft {
-constexpr int kSignBlocksPerCta = 2;   // 128-shot noise blocks per CTA (256 shots)
+int sign_blocks_per_cta(const DevPlan& p);
 cudaError_t launch_sign(const SignArgs& a, int grid, cudaStream_t st);
 size_t sign_smem_bytes(const DevPlan& p);
 cudaError_t sign_occupancy(const DevPlan& p, int* ctas_per_sm);
@@ -88,7 +89,12 @@ cudaError_t upload(symft_plan* P) {
   std::vector<uint32_t> theta4(((h.n_channels + 3) / 4) * 4, 0u);
   for (uint32_t c = 0; c < h.n_channels; ++c) theta4[c] = h.ch_theta_last[c];
   std::vector<uint32_t> qtheta;
-  for (auto& q : h.qtabs) qtheta.insert(qtheta.end(), q.theta, q.theta + kNoiseBlock);
+  std::vector<float> qinv;
+  for (auto& q : h.qtabs) {
+    qtheta.insert(qtheta.end(), q.theta, q.theta + kNoiseBlock);
+    double l = std::log1p(-q.q);
+    qinv.push_back((q.q > 0.0 && q.q < 1.0) ? static_cast<float>(1.0 / l) : 0.0f);
+  }
   std::vector<CellTableDev> ct(h.ctabs.size());
   for (size_t i = 0; i < h.ctabs.size(); ++i) {
     ct[i].ncell = h.ctabs[i].ncell;
@@ -116,16 +122,24 @@ cudaError_t upload(symft_plan* P) {
   }
   std::vector<unsigned char> blob;
   size_t o_ch = push(blob, ch), o_q = push(blob, qtheta), o_ct = push(blob, ct);
-  size_t o_t4 = push(blob, theta4);
+  size_t o_t4 = push(blob, theta4), o_qi = push(blob, qinv);
   // packed incidence lists (16-bit targets, 24-bit offsets, 8-bit counts)
   if (h.n_slots >= 65536) throw Error(SYMFT_E_CAPACITY, "more than 65535 bit-packed slots");
   if (h.comp_tgt.size() >= (1u << 24)) throw Error(SYMFT_E_CAPACITY, "too many sign incidences");
   if (h.n_channels >= (1u << 28)) throw Error(SYMFT_E_CAPACITY, "too many noise channels");
   std::vector<uint32_t> comp_rng(h.n_comp);
   for (uint32_t k = 0; k < h.n_comp; ++k) {
-    uint32_t n = h.comp_off[k + 1] - h.comp_off[k];
-    if (n >= 256) throw Error(SYMFT_E_CAPACITY, "a noise component reaches more than 255 targets");
-    comp_rng[k] = (h.comp_off[k] << 8) | n;
+    const uint32_t off = h.comp_off[k], n = h.comp_off[k + 1] - off;
+    bool inl = n <= 2;
+    for (uint32_t j = 0; j < n && inl; ++j) inl = h.comp_tgt[off + j] < 16384;
+    if (inl) {
+      uint32_t t0 = n > 0 ? h.comp_tgt[off] : 0, t1 = n > 1 ? h.comp_tgt[off + 1] : 0;
+      comp_rng[k] = 0x80000000u | (n << 28) | (t1 << 14) | t0;
+    } else {
+      if (n >= 256) throw Error(SYMFT_E_CAPACITY, "a noise component reaches more than 255 targets");
+      if (off >= (1u << 23)) throw Error(SYMFT_E_CAPACITY, "too many sign incidences");
+      comp_rng[k] = (off << 8) | n;
+    }
   }
   std::vector<uint16_t> comp_tgt(h.comp_tgt.begin(), h.comp_tgt.end());
   size_t o_co = push(blob, comp_rng), o_ctg = push(blob, comp_tgt);
@@ -147,6 +161,7 @@ cudaError_t upload(symft_plan* P) {
   d.n_qtab = static_cast<uint32_t>(h.qtabs.size());
   d.n_ctab = static_cast<uint32_t>(h.ctabs.size());
   d.qtheta = reinterpret_cast<const uint32_t*>(at(o_q));
+  d.qinv = reinterpret_cast<const float*>(at(o_qi));
   d.ctabs = reinterpret_cast<const CellTableDev*>(at(o_ct));
   d.comp_rng = reinterpret_cast<const uint32_t*>(at(o_co));
   d.comp_tgt = reinterpret_cast<const uint16_t*>(at(o_ctg));
@@ -259,7 +274,8 @@ int sample_impl(symft_plan* P, const symft_sample_args* a) {
     if (smem > 220 * 1024)
       return set_error(SYMFT_E_CAPACITY, "too many bit-packed slots for shared memory (" +
                                              std::to_string(h.n_slots) + ")");
-    const uint64_t chunks = (nblk + kSignBlocksPerCta - 1) / kSignBlocksPerCta;
+    const int nb_cta = sign_blocks_per_cta(P->dp);
+    const uint64_t chunks = (nblk + nb_cta - 1) / nb_cta;
     int per_sm = 1;
     CUDA_TRY(sign_occupancy(P->dp, &per_sm));
     uint64_t cap = static_cast<uint64_t>(P->sm_count) * std::max(1, per_sm);

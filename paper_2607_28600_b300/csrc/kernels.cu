@@ -25,76 +25,89 @@ namespace symft {
 
 namespace {
 
-constexpr int kQueue = 64;          // per-warp queue of channels that fire in the block
+constexpr int kQueue = 64;          // per-warp queue of (channel, block) fire states
+constexpr int kSignWarps = 8;       // warps per CTA
 
 __device__ __forceinline__ uint32_t pick(uint4 v, uint32_t s) {
   return s == 0 ? v.x : (s == 1 ? v.y : (s == 2 ? v.z : v.w));
 }
 
-// smallest j in [0,128) with u < theta[j]  (128 if none); theta in shared memory
-__device__ __forceinline__ int first_above(const uint32_t* th, uint32_t u) {
-  int lo = 0;
-#pragma unroll
-  for (int step = 64; step; step >>= 1)
-    if (u >= th[lo + step - 1]) lo += step;
-  if (lo == 127 && u >= th[127]) lo = 128;
-  return lo;
+__device__ __forceinline__ uint4 xor4(uint4 a, uint4 b) {
+  return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
 }
 
-}  // namespace
-
-constexpr int kSignWarps = 8;       // warps per CTA
-constexpr int kNB = 2;              // 128-shot noise blocks per CTA
+// smallest j in [0,128) with u < theta[j] (128 if none).  A guess from the
+// logarithm of the geometric law is corrected by exact integer comparisons
+// against the threshold table, so the result is the table's own answer.
+__device__ __forceinline__ int first_above(const uint32_t* th, float inv_log1m_q, uint32_t u) {
+  int j = 0;
+  if (inv_log1m_q != 0.0f) {
+    const float x = (float)u * 2.3283064365386963e-10f;          // u / 2^32
+    const float est = log1pf(-x) * inv_log1m_q;                  // ~ j*
+    j = est < 0.0f ? 0 : (est > 127.0f ? 127 : (int)est);
+  }
+  while (j > 0 && u < th[j - 1]) --j;
+  while (j < 128 && u >= th[j]) ++j;
+  return j;
+}
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
 struct SignLayout {
-  size_t q_off, c_off, slot_off, queue_off, total;
+  size_t q_off, qi_off, c_off, slot_off, qa_off, qb_off, total;
 };
 
-__host__ __device__ inline SignLayout sign_layout(uint32_t n_qtab, uint32_t n_ctab, uint32_t n_targets) {
+__host__ __device__ inline SignLayout sign_layout(uint32_t n_qtab, uint32_t n_ctab, uint32_t n_slots, int nb) {
   SignLayout L;
   L.q_off = 0;
-  L.c_off = align16((size_t)n_qtab * 128 * 4);
+  L.qi_off = align16((size_t)n_qtab * 128 * 4);
+  L.c_off = L.qi_off + align16((size_t)n_qtab * 4);
   L.slot_off = L.c_off + align16((size_t)n_ctab * sizeof(CellTableDev));
-  L.queue_off = L.slot_off + (size_t)n_targets * kNB * 16;
-  L.total = L.queue_off + (size_t)kSignWarps * kQueue * 16;
+  L.qa_off = L.slot_off + (size_t)n_slots * nb * 16;
+  L.qb_off = L.qa_off + (size_t)kSignWarps * kQueue * 16;
+  L.total = L.qb_off + (size_t)kSignWarps * kQueue * 4;
   return L;
 }
 
-// One CTA samples kNB consecutive 128-shot noise blocks (256 shots, four
+}  // namespace
+
+// One CTA samples NB consecutive 128-shot noise blocks (128*NB shots, 2*NB
 // 64-shot words per column).  Shared memory: the noise tables, then
-//   slots  n_targets x kNB x 4 uint32 (lane l of block b: bit l&31 of word 4b + (l>>5))
-//   queue  kSignWarps x kQueue x uint4 ((block << 28) | channel, u, L | draw << 8, -)
+//   slots  n_slots x NB x uint4  (lane l of block b: bit l&31 of word l>>5)
+//   queue  kSignWarps x kQueue x {uint4 ((b << 28) | c, u, L | draw << 8, qtab | ctab << 16),
+//                                 uint32 first component}
+template <int NB>
 __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const uint32_t NT = A.p.n_slots;
   const uint32_t k0 = (uint32_t)A.seed, k1 = (uint32_t)(A.seed >> 32);
-  const SignLayout Lay = sign_layout(A.p.n_qtab, A.p.n_ctab, NT);
+  const SignLayout Lay = sign_layout(A.p.n_qtab, A.p.n_ctab, NT, NB);
   uint32_t* sq = reinterpret_cast<uint32_t*>(smem_raw + Lay.q_off);
+  float* sqi = reinterpret_cast<float*>(smem_raw + Lay.qi_off);
   CellTableDev* sc = reinterpret_cast<CellTableDev*>(smem_raw + Lay.c_off);
-  uint32_t* slots = reinterpret_cast<uint32_t*>(smem_raw + Lay.slot_off);
-  uint4* queue = reinterpret_cast<uint4*>(smem_raw + Lay.queue_off) + warp * kQueue;
+  uint4* slots = reinterpret_cast<uint4*>(smem_raw + Lay.slot_off);
+  uint4* qa = reinterpret_cast<uint4*>(smem_raw + Lay.qa_off) + warp * kQueue;
+  uint32_t* qb = reinterpret_cast<uint32_t*>(smem_raw + Lay.qb_off) + warp * kQueue;
 
   for (uint32_t i = threadIdx.x; i < A.p.n_qtab * 128; i += blockDim.x) sq[i] = __ldg(A.p.qtheta + i);
+  for (uint32_t i = threadIdx.x; i < A.p.n_qtab; i += blockDim.x) sqi[i] = __ldg(A.p.qinv + i);
   for (uint32_t i = threadIdx.x; i < A.p.n_ctab; i += blockDim.x) sc[i] = A.p.ctabs[i];
   __syncthreads();
 
   const uint32_t n_groups = (A.p.n_channels + 3) >> 2;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  const uint64_t n_chunks = (A.n_blocks + kNB - 1) / kNB;
+  const uint64_t n_chunks = (A.n_blocks + NB - 1) / NB;
+  const uint32_t R = A.p.n_records, DO = A.p.n_dets + A.p.n_obs;
 
   for (uint64_t chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x) {
-    const uint64_t b0 = chunk * kNB;                       // first local block
-    const uint32_t nb = (uint32_t)min((uint64_t)kNB, A.n_blocks - b0);
+    const uint64_t b0 = chunk * NB;                       // first local block
+    const uint32_t nb = (uint32_t)min((uint64_t)NB, A.n_blocks - b0);
     // 1. constants
-    for (uint32_t i = threadIdx.x; i < NT; i += blockDim.x) {
-      const uint32_t v = A.p.slot_const[i] ? ~0u : 0u;
-      uint4* t = reinterpret_cast<uint4*>(slots) + (size_t)i * kNB;
-#pragma unroll
-      for (int b = 0; b < kNB; ++b) t[b] = make_uint4(v, v, v, v);
+    for (uint32_t i = threadIdx.x; i < NT * NB; i += blockDim.x) {
+      const uint32_t v = A.p.slot_const[i / NB] ? ~0u : 0u;
+      slots[i] = make_uint4(v, v, v, v);
     }
     __syncthreads();
     // 2. random-measurement bits m1: one Philox block = the 128 bits of a block
@@ -103,7 +116,7 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
       const uint4 o = philox(make_uint4(__ldg(A.p.m1_t + j), (uint32_t)(A.block0 + b0 + b), 0u, kTagMbit), k0, k1);
       const uint32_t e = __ldg(A.p.m1_off + j + 1);
       for (uint32_t q = __ldg(A.p.m1_off + j); q < e; ++q) {
-        uint32_t* t = slots + ((size_t)__ldg(A.p.m1_tgt + q) * kNB + b) * 4;
+        uint32_t* t = reinterpret_cast<uint32_t*>(slots + (size_t)__ldg(A.p.m1_tgt + q) * NB + b);
         atomicXor(t + 0, o.x);
         atomicXor(t + 1, o.y);
         atomicXor(t + 2, o.z);
@@ -119,20 +132,22 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
     uint32_t qn = 0;
     auto drain = [&](uint32_t count) {
       uint4 ent = make_uint4(0u, 0u, 0u, 0u);
-      if ((uint32_t)lane < count) ent = queue[lane];
+      uint32_t comp0 = 0;
+      if ((uint32_t)lane < count) {
+        ent = qa[lane];
+        comp0 = qb[lane];
+      }
       __syncwarp();
       bool more = false;
       uint4 next = make_uint4(0u, 0u, 0u, 0u);
       if ((uint32_t)lane < count) {
         const uint32_t c = ent.x & 0x0FFFFFFFu, b = ent.x >> 28;
         const uint32_t gb = (uint32_t)(A.block0 + b0 + b);
-        const uint32_t u = ent.y;
         const int L = (int)(ent.z & 0xFFu);
         uint32_t ti = ent.z >> 8;
-        const uint4 raw = __ldg(reinterpret_cast<const uint4*>(A.p.ch) + c);
-        const uint32_t* th = sq + (size_t)(raw.y & 0xFFFFu) * 128;
-        const CellTableDev* ct = sc + (raw.y >> 16);
-        const int j = first_above(th, u);
+        const uint32_t qt = ent.w & 0xFFFFu;
+        const CellTableDev* ct = sc + (ent.w >> 16);
+        const int j = first_above(sq + (size_t)qt * 128, sqi[qt], ent.y);
         if (j <= 127 - L) {
           const int lanebit = L + j;
           const uint32_t ncell = ct->ncell;
@@ -142,28 +157,32 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
           if (ncell > 1) {
             const uint32_t v = pick(tail, ti & 3);
             ++ti;
-            uint32_t lo = 0, hi = ncell - 1;     // min{k : v < phi_k}
-            while (lo < hi) {
-              const uint32_t mid = (lo + hi) >> 1;
-              if (v < ct->phi[mid]) hi = mid;
-              else lo = mid + 1;
-            }
-            cell = lo;
+            // min{k : v < phi_k}: equal-weight guess, then exact correction
+            int cc = (int)(((uint64_t)v * ncell) >> 32);
+            while (cc > 0 && v < ct->phi[cc - 1]) --cc;
+            while (cc < (int)ncell - 1 && v >= ct->phi[cc]) ++cc;
+            cell = (uint32_t)cc;
           }
           uint32_t mask = ct->mask[cell];
           const uint32_t wsel = (uint32_t)lanebit >> 5, bit = 1u << (lanebit & 31);
-          uint32_t* sb = slots + (size_t)b * 4 + wsel;
+          uint32_t* sb = reinterpret_cast<uint32_t*>(slots + b) + wsel;
           while (mask) {
-            const uint32_t comp = raw.z + (__ffs(mask) - 1);
+            const uint32_t comp = comp0 + (__ffs(mask) - 1);
             mask &= mask - 1;
             const uint32_t rng = __ldg(A.p.comp_rng + comp);
-            const uint32_t q0 = rng >> 8, qe = q0 + (rng & 0xFFu);
-            for (uint32_t q = q0; q < qe; ++q)
-              atomicXor(sb + (size_t)__ldg(A.p.comp_tgt + q) * (kNB * 4), bit);
+            if (rng & 0x80000000u) {
+              const uint32_t n = (rng >> 28) & 3u;
+              if (n > 0) atomicXor(sb + (size_t)(rng & 0x3FFFu) * (NB * 4), bit);
+              if (n > 1) atomicXor(sb + (size_t)((rng >> 14) & 0x3FFFu) * (NB * 4), bit);
+            } else {
+              const uint32_t q0 = rng >> 8, qe = q0 + (rng & 0xFFu);
+              for (uint32_t q = q0; q < qe; ++q)
+                atomicXor(sb + (size_t)__ldg(A.p.comp_tgt + q) * (NB * 4), bit);
+            }
           }
           if (lanebit < 127) {
             // next uniform: draw index ti, in the same Philox block as the cell draw
-            next = make_uint4(ent.x, pick(tail, ti & 3), (uint32_t)(lanebit + 1) | ((ti + 1) << 8), 0u);
+            next = make_uint4(ent.x, pick(tail, ti & 3), (uint32_t)(lanebit + 1) | ((ti + 1) << 8), ent.w);
             more = true;
           }
         }
@@ -172,35 +191,56 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
       // compact the unprocessed tail to the front, then append continuing channels
       const uint32_t rest = qn - count;       // < 32
       uint4 mv = make_uint4(0u, 0u, 0u, 0u);
-      if ((uint32_t)lane < rest) mv = queue[count + lane];
+      uint32_t mvb = 0;
+      if ((uint32_t)lane < rest) {
+        mv = qa[count + lane];
+        mvb = qb[count + lane];
+      }
       __syncwarp();
-      if ((uint32_t)lane < rest) queue[lane] = mv;
+      if ((uint32_t)lane < rest) {
+        qa[lane] = mv;
+        qb[lane] = mvb;
+      }
       __syncwarp();
       const uint32_t bal = __ballot_sync(0xffffffffu, more);
-      if (more) queue[rest + __popc(bal & lt_mask)] = next;
+      if (more) {
+        const uint32_t pos = rest + __popc(bal & lt_mask);
+        qa[pos] = next;
+        qb[pos] = comp0;
+      }
       qn = rest + __popc(bal);
       __syncwarp();
     };
-    for (uint32_t b = 0; b < nb; ++b) {
-      const uint32_t gb = (uint32_t)(A.block0 + b0 + b);
-      for (uint32_t base = warp * 32; base < n_groups; base += kSignWarps * 32) {
-        const uint32_t g = base + lane;
-        const bool valid = g < n_groups;
-        uint4 head = make_uint4(0u, 0u, 0u, 0u), th4 = make_uint4(0u, 0u, 0u, 0u);
-        if (valid) {
-          th4 = __ldg(A.p.theta4 + g);
-          if (th4.x | th4.y | th4.z | th4.w) head = philox(make_uint4(g, gb, 0u, kTagHead), k0, k1);
-        }
+    const uint32_t items = nb * n_groups;
+    for (uint32_t base = warp * 32; base < items; base += kSignWarps * 32) {
+      const uint32_t it = base + lane;
+      const bool valid = it < items;
+      uint32_t b = 0, g = it;
+      while (g >= n_groups && b + 1 < (uint32_t)NB) {
+        g -= n_groups;
+        ++b;
+      }
+      uint4 head = make_uint4(0u, 0u, 0u, 0u), th4 = make_uint4(0u, 0u, 0u, 0u);
+      if (valid) {
+        th4 = __ldg(A.p.theta4 + g);
+        if (th4.x | th4.y | th4.z | th4.w)
+          head = philox(make_uint4(g, (uint32_t)(A.block0 + b0 + b), 0u, kTagHead), k0, k1);
+      }
 #pragma unroll
-        for (uint32_t s2 = 0; s2 < 4; ++s2) {
-          const uint32_t u = pick(head, s2);
-          const bool fire = valid && u < pick(th4, s2);
-          const uint32_t bal = __ballot_sync(0xffffffffu, fire);
-          if (fire) queue[qn + __popc(bal & lt_mask)] = make_uint4((b << 28) | (4 * g + s2), u, 0u, 0u);
-          qn += __popc(bal);
-          __syncwarp();
-          while (qn >= 32) drain(32);
+      for (uint32_t s2 = 0; s2 < 4; ++s2) {
+        const uint32_t u = pick(head, s2);
+        const bool fire = valid && u < pick(th4, s2);
+        const uint32_t bal = __ballot_sync(0xffffffffu, fire);
+        if (fire) {
+          const uint32_t c = 4 * g + s2;
+          const uint4 raw = __ldg(reinterpret_cast<const uint4*>(A.p.ch) + c);
+          const uint32_t pos = qn + __popc(bal & lt_mask);
+          qa[pos] = make_uint4((b << 28) | c, u, 0u, raw.y);
+          qb[pos] = raw.z;
         }
+        qn += __popc(bal);
+        __syncwarp();
+        while (qn >= 32) drain(32);
       }
     }
     while (qn) drain(qn < 32 ? qn : 32);
@@ -208,86 +248,63 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
     // 4. records: XOR in the parent records level by level (exo_r = delta_r ^ parents)
     for (uint32_t L = 1; L <= A.p.n_levels; ++L) {
       const uint32_t lo = __ldg(A.p.lvl_off + L - 1), hi = __ldg(A.p.lvl_off + L);
-      for (uint32_t x = lo + threadIdx.x; x < hi; x += blockDim.x) {
-        const uint32_t r = __ldg(A.p.lvl_rec + x);
-        uint4* t = reinterpret_cast<uint4*>(slots) + (size_t)r * kNB;
-        uint4 acc[kNB];
-#pragma unroll
-        for (int b = 0; b < kNB; ++b) acc[b] = t[b];
+      for (uint32_t x = threadIdx.x; x < (hi - lo) * NB; x += blockDim.x) {
+        const uint32_t r = __ldg(A.p.lvl_rec + lo + x / NB), b = x % NB;
+        uint4 acc = slots[(size_t)r * NB + b];
         const uint32_t pe = __ldg(A.p.par_off + r + 1);
-        for (uint32_t q = __ldg(A.p.par_off + r); q < pe; ++q) {
-          const uint4* pt = reinterpret_cast<const uint4*>(slots) + (size_t)__ldg(A.p.par + q) * kNB;
-#pragma unroll
-          for (int b = 0; b < kNB; ++b) {
-            const uint4 v = pt[b];
-            acc[b].x ^= v.x; acc[b].y ^= v.y; acc[b].z ^= v.z; acc[b].w ^= v.w;
-          }
-        }
-#pragma unroll
-        for (int b = 0; b < kNB; ++b) t[b] = acc[b];
+        for (uint32_t q = __ldg(A.p.par_off + r); q < pe; ++q)
+          acc = xor4(acc, slots[(size_t)__ldg(A.p.par + q) * NB + b]);
+        slots[(size_t)r * NB + b] = acc;
       }
       __syncthreads();
     }
     // 5. write the columns (records, gathered detectors / observables, dense
-    //    signs): 2*kNB words per column, padding bits cleared
-    const uint64_t w0 = 2 * b0;
-    const uint32_t R = A.p.n_records, DO = A.p.n_dets + A.p.n_obs;
+    //    signs): NB pieces of 16 bytes per column, consecutive threads writing
+    //    consecutive pieces of one column; padding bits cleared
     const uint32_t n_out = R + DO + (NT - R);
-    for (uint32_t i = threadIdx.x; i < n_out; i += blockDim.x) {
+    for (uint32_t x = threadIdx.x; x < n_out * NB; x += blockDim.x) {
+      const uint32_t i = x / NB, b = x % NB;
+      if (b >= nb) continue;
       uint64_t* col;
       uint64_t idx;
-      uint4 val[kNB];
+      uint4 v;
       if (i < R) {
         col = A.meas;
         idx = i;
         if (col == nullptr) continue;
-#pragma unroll
-        for (int b = 0; b < kNB; ++b) val[b] = reinterpret_cast<const uint4*>(slots)[(size_t)i * kNB + b];
+        v = slots[(size_t)i * NB + b];
       } else if (i < R + DO) {
         const uint32_t j = i - R;
         if (j < A.p.n_dets) { col = A.det; idx = j; }
         else { col = A.obs; idx = j - A.p.n_dets; }
         if (col == nullptr) continue;
-#pragma unroll
-        for (int b = 0; b < kNB; ++b) val[b] = make_uint4(0u, 0u, 0u, 0u);
+        v = make_uint4(0u, 0u, 0u, 0u);
         const uint32_t ge = __ldg(A.p.gat_off + j + 1);
-        for (uint32_t q = __ldg(A.p.gat_off + j); q < ge; ++q) {
-          const uint4* pt = reinterpret_cast<const uint4*>(slots) + (size_t)__ldg(A.p.gat_rec + q) * kNB;
-#pragma unroll
-          for (int b = 0; b < kNB; ++b) {
-            const uint4 v = pt[b];
-            val[b].x ^= v.x; val[b].y ^= v.y; val[b].z ^= v.z; val[b].w ^= v.w;
-          }
-        }
+        for (uint32_t q = __ldg(A.p.gat_off + j); q < ge; ++q)
+          v = xor4(v, slots[(size_t)__ldg(A.p.gat_rec + q) * NB + b]);
       } else {
         const uint32_t g = i - R - DO;
         col = A.signs;
         idx = g;
         if (col == nullptr) continue;
-#pragma unroll
-        for (int b = 0; b < kNB; ++b) val[b] = reinterpret_cast<const uint4*>(slots)[(size_t)(R + g) * kNB + b];
+        v = slots[(size_t)(R + g) * NB + b];
       }
-      uint64_t* dst = col + idx * A.W + w0;
-#pragma unroll
-      for (int b = 0; b < kNB; ++b) {
-        const uint4 v = val[b];
-        uint64_t v0 = ((uint64_t)v.y << 32) | v.x, v1 = ((uint64_t)v.w << 32) | v.z;
-        const uint64_t wa = w0 + 2 * b, wb = wa + 1;
-        if (wa >= A.W) break;
-        const uint64_t la = A.shots - 64 * wa;            // shots covered by word wa (>= 1)
-        if (la < 64) v0 &= (1ull << la) - 1;
-        const bool hb = wb < A.W;
-        if (hb) {
-          const uint64_t lbits = A.shots - 64 * wb;
-          if (lbits < 64) v1 &= (1ull << lbits) - 1;
-        }
-        uint64_t* d = dst + 2 * b;
-        if (hb && ((reinterpret_cast<uintptr_t>(d) & 15) == 0)) {
-          *reinterpret_cast<ulonglong2*>(d) = make_ulonglong2(v0, v1);
-        } else {
-          d[0] = v0;
-          if (hb) d[1] = v1;
-        }
+      uint64_t v0 = ((uint64_t)v.y << 32) | v.x, v1 = ((uint64_t)v.w << 32) | v.z;
+      const uint64_t wa = 2 * (b0 + b), wb = wa + 1;
+      if (wa >= A.W) continue;
+      const uint64_t la = A.shots - 64 * wa;            // shots covered by word wa (>= 1)
+      if (la < 64) v0 &= (1ull << la) - 1;
+      const bool hb = wb < A.W;
+      if (hb) {
+        const uint64_t lbits = A.shots - 64 * wb;
+        if (lbits < 64) v1 &= (1ull << lbits) - 1;
+      }
+      uint64_t* d = col + idx * A.W + wa;
+      if (hb && ((reinterpret_cast<uintptr_t>(d) & 15) == 0)) {
+        *reinterpret_cast<ulonglong2*>(d) = make_ulonglong2(v0, v1);
+      } else {
+        d[0] = v0;
+        if (hb) d[1] = v1;
       }
     }
     __syncthreads();
@@ -568,20 +585,32 @@ __global__ void finalize_kernel(FinalArgs A) {
 // ---------------------------------------------------------------------------
 // launch wrappers (host)
 // ---------------------------------------------------------------------------
-size_t sign_smem_bytes(const DevPlan& p) { return sign_layout(p.n_qtab, p.n_ctab, p.n_slots).total; }
+// 512-shot CTAs when their slots fit comfortably, else 256-shot CTAs
+int sign_blocks_per_cta(const DevPlan& p) { return (size_t)p.n_slots * 4 * 16 <= 40 * 1024 ? 4 : 2; }
+
+size_t sign_smem_bytes(const DevPlan& p) {
+  return sign_layout(p.n_qtab, p.n_ctab, p.n_slots, sign_blocks_per_cta(p)).total;
+}
+
+static const void* sign_fn(const DevPlan& p) {
+  return sign_blocks_per_cta(p) == 4 ? (const void*)sign_kernel<4> : (const void*)sign_kernel<2>;
+}
 
 cudaError_t sign_occupancy(const DevPlan& p, int* ctas_per_sm) {
   const size_t smem = sign_smem_bytes(p);
-  cudaError_t e = cudaFuncSetAttribute(sign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(sign_fn(p), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, sign_kernel, kSignWarps * 32, smem);
+  e = cudaFuncSetAttribute(sign_fn(p), cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, sign_fn(p), kSignWarps * 32, smem);
 }
 
 cudaError_t launch_sign(const SignArgs& a, int grid, cudaStream_t st) {
   const size_t smem = sign_smem_bytes(a.p);
-  cudaError_t e = cudaFuncSetAttribute(sign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(sign_fn(a.p), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  sign_kernel<<<grid, kSignWarps * 32, smem, st>>>(a);
+  if (sign_blocks_per_cta(a.p) == 4) sign_kernel<4><<<grid, kSignWarps * 32, smem, st>>>(a);
+  else sign_kernel<2><<<grid, kSignWarps * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -23,6 +23,12 @@ struct CellTableDev {
   uint8_t mask[16];
 };
 
+// q-table acceleration: 1 / log(1 - q), used only to guess the fired lane
+// before the exact integer threshold comparisons
+struct QInvDev {
+  float inv_log1m_q;
+};
+
 struct DenseInstrDev {
   int32_t kind, k, h, mu;
   uint32_t a, b;
@@ -39,8 +45,11 @@ struct DevPlan {
   const uint4* theta4;          // THETA_127 of channels 4g..4g+3 (0 = never fires)
   uint32_t n_qtab, n_ctab;
   const uint32_t* qtheta;       // [n_qtab][128]
+  const float* qinv;            // [n_qtab] 1 / log(1 - q)
   const CellTableDev* ctabs;
-  const uint32_t* comp_rng;     // per component: (first incidence << 8) | count
+  // per component: bit 31 set -> inline list: count in bits 28-29, slots in
+  // bits 0-13 and 14-27; else (first incidence << 8) | count into comp_tgt
+  const uint32_t* comp_rng;
   const uint16_t* comp_tgt;     // incidence -> target slot
   uint32_t n_m1;
   const uint32_t* m1_t;
