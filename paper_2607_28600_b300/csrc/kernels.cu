@@ -25,7 +25,7 @@ namespace symft {
 
 namespace {
 
-constexpr int kQueue = 64;          // per-warp queue of (channel, block) fire states
+constexpr int kQueue = 96;          // per-warp queue of (channel, block) fire states
 constexpr int kSignWarps = 8;       // warps per CTA
 
 __device__ __forceinline__ uint32_t pick(uint4 v, uint32_t s) {
@@ -54,7 +54,7 @@ __device__ __forceinline__ int first_above(const uint32_t* th, float inv_log1m_q
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
 struct SignLayout {
-  size_t q_off, qi_off, c_off, slot_off, qa_off, qb_off, total;
+  size_t q_off, qi_off, c_off, slot_off, qa_off, qb_off, cnt_off, total;
 };
 
 __host__ __device__ inline SignLayout sign_layout(uint32_t n_qtab, uint32_t n_ctab, uint32_t n_slots, int nb) {
@@ -65,7 +65,8 @@ __host__ __device__ inline SignLayout sign_layout(uint32_t n_qtab, uint32_t n_ct
   L.slot_off = L.c_off + align16((size_t)n_ctab * sizeof(CellTableDev));
   L.qa_off = L.slot_off + (size_t)n_slots * nb * 16;
   L.qb_off = L.qa_off + (size_t)kSignWarps * kQueue * 16;
-  L.total = L.qb_off + (size_t)kSignWarps * kQueue * 4;
+  L.cnt_off = L.qb_off + (size_t)kSignWarps * kQueue * 4;
+  L.total = L.cnt_off + 64;
   return L;
 }
 
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
   uint4* slots = reinterpret_cast<uint4*>(smem_raw + Lay.slot_off);
   uint4* qa = reinterpret_cast<uint4*>(smem_raw + Lay.qa_off) + warp * kQueue;
   uint32_t* qb = reinterpret_cast<uint32_t*>(smem_raw + Lay.qb_off) + warp * kQueue;
+  uint32_t* sqn = reinterpret_cast<uint32_t*>(smem_raw + Lay.cnt_off);
 
   for (uint32_t i = threadIdx.x; i < A.p.n_qtab * 128; i += blockDim.x) sq[i] = __ldg(A.p.qtheta + i);
   for (uint32_t i = threadIdx.x; i < A.p.n_qtab; i += blockDim.x) sqi[i] = __ldg(A.p.qinv + i);
@@ -130,78 +132,77 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
     //    scatter of its components -- and re-queues the channel if its
     //    word-geometric process continues, so every step costs the same.
     uint32_t qn = 0;
-    auto drain = [&](uint32_t count) {
-      uint4 ent = make_uint4(0u, 0u, 0u, 0u);
-      uint32_t comp0 = 0;
-      if ((uint32_t)lane < count) {
-        ent = qa[lane];
-        comp0 = qb[lane];
+    // resolve the fire of one queued state; returns true (and the next state)
+    // if the channel's word-geometric process continues
+    auto fire_step = [&](uint4 ent, uint32_t comp0, uint4& next) -> bool {
+      const uint32_t c = ent.x & 0x0FFFFFFFu, b = ent.x >> 28;
+      const uint32_t gb = (uint32_t)(A.block0 + b0 + b);
+      const int L = (int)(ent.z & 0xFFu);
+      uint32_t ti = ent.z >> 8;
+      const uint32_t qt = ent.w & 0xFFFFu;
+      const CellTableDev* ct = sc + (ent.w >> 16);
+      const int j = first_above(sq + (size_t)qt * 128, sqi[qt], ent.y);
+      if (j > 127 - L) return false;
+      const int lanebit = L + j;
+      const uint32_t ncell = ct->ncell;
+      // the draws of one fire (cell, next u) lie in one Philox block
+      const uint4 tail = philox(make_uint4(c, gb, ti >> 2, kTagTail), k0, k1);
+      uint32_t cell = 0;
+      if (ncell > 1) {
+        const uint32_t v = pick(tail, ti & 3);
+        ++ti;
+        // min{k : v < phi_k}: equal-weight guess, then exact correction
+        int cc = (int)(((uint64_t)v * ncell) >> 32);
+        while (cc > 0 && v < ct->phi[cc - 1]) --cc;
+        while (cc < (int)ncell - 1 && v >= ct->phi[cc]) ++cc;
+        cell = (uint32_t)cc;
       }
-      __syncwarp();
-      bool more = false;
-      uint4 next = make_uint4(0u, 0u, 0u, 0u);
-      if ((uint32_t)lane < count) {
-        const uint32_t c = ent.x & 0x0FFFFFFFu, b = ent.x >> 28;
-        const uint32_t gb = (uint32_t)(A.block0 + b0 + b);
-        const int L = (int)(ent.z & 0xFFu);
-        uint32_t ti = ent.z >> 8;
-        const uint32_t qt = ent.w & 0xFFFFu;
-        const CellTableDev* ct = sc + (ent.w >> 16);
-        const int j = first_above(sq + (size_t)qt * 128, sqi[qt], ent.y);
-        if (j <= 127 - L) {
-          const int lanebit = L + j;
-          const uint32_t ncell = ct->ncell;
-          // the draws of one fire (cell, next u) lie in one Philox block
-          const uint4 tail = philox(make_uint4(c, gb, ti >> 2, kTagTail), k0, k1);
-          uint32_t cell = 0;
-          if (ncell > 1) {
-            const uint32_t v = pick(tail, ti & 3);
-            ++ti;
-            // min{k : v < phi_k}: equal-weight guess, then exact correction
-            int cc = (int)(((uint64_t)v * ncell) >> 32);
-            while (cc > 0 && v < ct->phi[cc - 1]) --cc;
-            while (cc < (int)ncell - 1 && v >= ct->phi[cc]) ++cc;
-            cell = (uint32_t)cc;
-          }
-          uint32_t mask = ct->mask[cell];
-          const uint32_t wsel = (uint32_t)lanebit >> 5, bit = 1u << (lanebit & 31);
-          uint32_t* sb = reinterpret_cast<uint32_t*>(slots + b) + wsel;
-          while (mask) {
-            const uint32_t comp = comp0 + (__ffs(mask) - 1);
-            mask &= mask - 1;
-            const uint32_t rng = __ldg(A.p.comp_rng + comp);
-            if (rng & 0x80000000u) {
-              const uint32_t n = (rng >> 28) & 3u;
-              if (n > 0) atomicXor(sb + (size_t)(rng & 0x3FFFu) * (NB * 4), bit);
-              if (n > 1) atomicXor(sb + (size_t)((rng >> 14) & 0x3FFFu) * (NB * 4), bit);
-            } else {
-              const uint32_t q0 = rng >> 8, qe = q0 + (rng & 0xFFu);
-              for (uint32_t q = q0; q < qe; ++q)
-                atomicXor(sb + (size_t)__ldg(A.p.comp_tgt + q) * (NB * 4), bit);
-            }
-          }
-          if (lanebit < 127) {
-            // next uniform: draw index ti, in the same Philox block as the cell draw
-            next = make_uint4(ent.x, pick(tail, ti & 3), (uint32_t)(lanebit + 1) | ((ti + 1) << 8), ent.w);
-            more = true;
-          }
+      uint32_t mask = ct->mask[cell];
+      const uint32_t wsel = (uint32_t)lanebit >> 5, bit = 1u << (lanebit & 31);
+      uint32_t* sb = reinterpret_cast<uint32_t*>(slots + b) + wsel;
+      while (mask) {
+        const uint32_t comp = comp0 + (__ffs(mask) - 1);
+        mask &= mask - 1;
+        const uint32_t rng = __ldg(A.p.comp_rng + comp);
+        if (rng & 0x80000000u) {
+          const uint32_t n = (rng >> 28) & 3u;
+          if (n > 0) atomicXor(sb + (size_t)(rng & 0x3FFFu) * (NB * 4), bit);
+          if (n > 1) atomicXor(sb + (size_t)((rng >> 14) & 0x3FFFu) * (NB * 4), bit);
+        } else {
+          const uint32_t q0 = rng >> 8, qe = q0 + (rng & 0xFFu);
+          for (uint32_t q = q0; q < qe; ++q)
+            atomicXor(sb + (size_t)__ldg(A.p.comp_tgt + q) * (NB * 4), bit);
         }
       }
+      if (lanebit >= 127) return false;
+      // next uniform: draw index ti, in the same Philox block as the cell draw
+      next = make_uint4(ent.x, pick(tail, ti & 3), (uint32_t)(lanebit + 1) | ((ti + 1) << 8), ent.w);
+      return true;
+    };
+    // full-warp drain of the first 32 queued states; continuing channels are re-queued
+    auto drain32 = [&]() {
+      const uint4 ent = qa[lane];
+      const uint32_t comp0 = qb[lane];
       __syncwarp();
-      // compact the unprocessed tail to the front, then append continuing channels
-      const uint32_t rest = qn - count;       // < 32
-      uint4 mv = make_uint4(0u, 0u, 0u, 0u);
-      uint32_t mvb = 0;
-      if ((uint32_t)lane < rest) {
-        mv = qa[count + lane];
-        mvb = qb[count + lane];
+      uint4 next = make_uint4(0u, 0u, 0u, 0u);
+      const bool more = fire_step(ent, comp0, next);
+      __syncwarp();
+      const uint32_t rest = qn - 32;          // < 64: move [32, qn) to [0, rest)
+      for (uint32_t i0 = 0; i0 < rest; i0 += 32) {
+        uint4 mv = make_uint4(0u, 0u, 0u, 0u);
+        uint32_t mvb = 0;
+        const uint32_t i = i0 + lane;
+        if (i < rest) {
+          mv = qa[32 + i];
+          mvb = qb[32 + i];
+        }
+        __syncwarp();
+        if (i < rest) {
+          qa[i] = mv;
+          qb[i] = mvb;
+        }
+        __syncwarp();
       }
-      __syncwarp();
-      if ((uint32_t)lane < rest) {
-        qa[lane] = mv;
-        qb[lane] = mvb;
-      }
-      __syncwarp();
       const uint32_t bal = __ballot_sync(0xffffffffu, more);
       if (more) {
         const uint32_t pos = rest + __popc(bal & lt_mask);
@@ -226,24 +227,70 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
         if (th4.x | th4.y | th4.z | th4.w)
           head = philox(make_uint4(g, (uint32_t)(A.block0 + b0 + b), 0u, kTagHead), k0, k1);
       }
+      // queue the firing channels, two channel slots at a time (<= 64 new states)
 #pragma unroll
-      for (uint32_t s2 = 0; s2 < 4; ++s2) {
-        const uint32_t u = pick(head, s2);
-        const bool fire = valid && u < pick(th4, s2);
-        const uint32_t bal = __ballot_sync(0xffffffffu, fire);
-        if (fire) {
-          const uint32_t c = 4 * g + s2;
-          const uint4 raw = __ldg(reinterpret_cast<const uint4*>(A.p.ch) + c);
-          const uint32_t pos = qn + __popc(bal & lt_mask);
-          qa[pos] = make_uint4((b << 28) | c, u, 0u, raw.y);
-          qb[pos] = raw.z;
+      for (uint32_t h2 = 0; h2 < 4; h2 += 2) {
+        const bool f0 = valid && pick(head, h2) < pick(th4, h2);
+        const bool f1 = valid && pick(head, h2 + 1) < pick(th4, h2 + 1);
+        const uint32_t b0m = __ballot_sync(0xffffffffu, f0), b1m = __ballot_sync(0xffffffffu, f1);
+        if (b0m | b1m) {
+          // slot order: lane-major pairs; position = entries of lower lanes + own
+          const uint32_t lower = __popc(b0m & lt_mask) + __popc(b1m & lt_mask);
+          uint32_t pos = qn + lower;
+          if (f0) {
+            const uint32_t c = 4 * g + h2;
+            const uint4 raw = __ldg(reinterpret_cast<const uint4*>(A.p.ch) + c);
+            qa[pos] = make_uint4((b << 28) | c, pick(head, h2), 0u, raw.y);
+            qb[pos] = raw.z;
+            ++pos;
+          }
+          if (f1) {
+            const uint32_t c = 4 * g + h2 + 1;
+            const uint4 raw = __ldg(reinterpret_cast<const uint4*>(A.p.ch) + c);
+            qa[pos] = make_uint4((b << 28) | c, pick(head, h2 + 1), 0u, raw.y);
+            qb[pos] = raw.z;
+          }
+          qn += __popc(b0m) + __popc(b1m);
+          __syncwarp();
+          while (qn >= 32) drain32();
         }
-        qn += __popc(bal);
-        __syncwarp();
-        while (qn >= 32) drain(32);
       }
     }
-    while (qn) drain(qn < 32 ? qn : 32);
+    // pool the leftover states of all warps and finish each channel in one
+    // thread (few continue past one more fire)
+    __syncthreads();
+    if (lane == 0) sqn[warp] = qn;
+    __syncthreads();
+    uint32_t off = 0, total = 0;
+    for (int w2 = 0; w2 < kSignWarps; ++w2) {
+      const uint32_t n2 = sqn[w2];
+      if (w2 < warp) off += n2;
+      total += n2;
+    }
+    // gather into the pool area (the queues of all warps, read before written)
+    uint4 mine = make_uint4(0u, 0u, 0u, 0u);
+    uint32_t mineb = 0;
+    if ((uint32_t)lane < qn) {
+      mine = qa[lane];
+      mineb = qb[lane];
+    }
+    __syncthreads();
+    uint4* pool_a = reinterpret_cast<uint4*>(smem_raw + Lay.qa_off);
+    uint32_t* pool_b = reinterpret_cast<uint32_t*>(smem_raw + Lay.qb_off);
+    if ((uint32_t)lane < qn) {
+      pool_a[off + lane] = mine;
+      pool_b[off + lane] = mineb;
+    }
+    __syncthreads();
+    for (uint32_t x = threadIdx.x; x < total; x += blockDim.x) {
+      uint4 ent = pool_a[x];
+      const uint32_t comp0 = pool_b[x];
+      for (int guard = 0; guard < 128; ++guard) {
+        uint4 next;
+        if (!fire_step(ent, comp0, next)) break;
+        ent = next;
+      }
+    }
     __syncthreads();
     // 4. records: XOR in the parent records level by level (exo_r = delta_r ^ parents)
     for (uint32_t L = 1; L <= A.p.n_levels; ++L) {
