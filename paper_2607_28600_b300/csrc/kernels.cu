@@ -27,6 +27,7 @@ namespace {
 
 constexpr int kQueue = 96;          // per-warp queue of (channel, block) fire states
 constexpr int kSignWarps = 8;       // warps per CTA
+constexpr int kMaxPairs = 8;        // inline incidences of one fire (4 components x 2 slots)
 
 __device__ __forceinline__ uint32_t pick(uint4 v, uint32_t s) {
   return s == 0 ? v.x : (s == 1 ? v.y : (s == 2 ? v.z : v.w));
@@ -54,7 +55,7 @@ __device__ __forceinline__ int first_above(const uint32_t* th, float inv_log1m_q
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
 struct SignLayout {
-  size_t q_off, qi_off, c_off, slot_off, qa_off, qb_off, cnt_off, total;
+  size_t q_off, qi_off, c_off, slot_off, qa_off, qb_off, wl_off, cnt_off, total;
 };
 
 __host__ __device__ inline SignLayout sign_layout(uint32_t n_qtab, uint32_t n_ctab, uint32_t n_slots, int nb) {
@@ -65,7 +66,8 @@ __host__ __device__ inline SignLayout sign_layout(uint32_t n_qtab, uint32_t n_ct
   L.slot_off = L.c_off + align16((size_t)n_ctab * sizeof(CellTableDev));
   L.qa_off = L.slot_off + (size_t)n_slots * nb * 16;
   L.qb_off = L.qa_off + (size_t)kSignWarps * kQueue * 16;
-  L.cnt_off = L.qb_off + (size_t)kSignWarps * kQueue * 4;
+  L.wl_off = L.qb_off + (size_t)kSignWarps * kQueue * 4;
+  L.cnt_off = L.wl_off + (size_t)kSignWarps * 32 * kMaxPairs * 8;
   L.total = L.cnt_off + 64;
   return L;
 }
@@ -92,6 +94,7 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
   uint4* qa = reinterpret_cast<uint4*>(smem_raw + Lay.qa_off) + warp * kQueue;
   uint32_t* qb = reinterpret_cast<uint32_t*>(smem_raw + Lay.qb_off) + warp * kQueue;
   uint32_t* sqn = reinterpret_cast<uint32_t*>(smem_raw + Lay.cnt_off);
+  uint2* wl = reinterpret_cast<uint2*>(smem_raw + Lay.wl_off) + (size_t)warp * 32 * kMaxPairs;
 
   for (uint32_t i = threadIdx.x; i < A.p.n_qtab * 128; i += blockDim.x) sq[i] = __ldg(A.p.qtheta + i);
   for (uint32_t i = threadIdx.x; i < A.p.n_qtab; i += blockDim.x) sqi[i] = __ldg(A.p.qinv + i);
@@ -134,16 +137,20 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
     uint32_t qn = 0;
     // resolve the fire of one queued state; returns true (and the next state)
     // if the channel's word-geometric process continues
-    auto fire_step = [&](uint4 ent, uint32_t comp0, uint4& next) -> bool {
+    // Resolve the fire of one queued state (whose uniform is known to fire):
+    // lane, Pauli cell, and the (slot word, bit) pairs of its components,
+    // appended to `pairs` (one pair per incidence).  The next uniform is tested
+    // here; returns true (and the next state) only if the channel fires again.
+    auto fire_step = [&](uint4 ent, uint32_t comp0, uint4& next, uint32_t (&pw)[8], uint32_t& bit) -> bool {
       const uint32_t c = ent.x & 0x0FFFFFFFu, b = ent.x >> 28;
       const uint32_t gb = (uint32_t)(A.block0 + b0 + b);
       const int L = (int)(ent.z & 0xFFu);
       uint32_t ti = ent.z >> 8;
       const uint32_t qt = ent.w & 0xFFFFu;
+      const uint32_t* th = sq + (size_t)qt * 128;
+      const float qi = sqi[qt];
       const CellTableDev* ct = sc + (ent.w >> 16);
-      const int j = first_above(sq + (size_t)qt * 128, sqi[qt], ent.y);
-      if (j > 127 - L) return false;
-      const int lanebit = L + j;
+      const int lanebit = L + first_above(th, qi, ent.y);     // <= 127 by construction
       const uint32_t ncell = ct->ncell;
       // the draws of one fire (cell, next u) lie in one Philox block
       const uint4 tail = philox(make_uint4(c, gb, ti >> 2, kTagTail), k0, k1);
@@ -157,26 +164,34 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
         while (cc < (int)ncell - 1 && v >= ct->phi[cc]) ++cc;
         cell = (uint32_t)cc;
       }
-      uint32_t mask = ct->mask[cell];
-      const uint32_t wsel = (uint32_t)lanebit >> 5, bit = 1u << (lanebit & 31);
-      uint32_t* sb = reinterpret_cast<uint32_t*>(slots + b) + wsel;
-      while (mask) {
-        const uint32_t comp = comp0 + (__ffs(mask) - 1);
-        mask &= mask - 1;
-        const uint32_t rng = __ldg(A.p.comp_rng + comp);
-        if (rng & 0x80000000u) {
-          const uint32_t n = (rng >> 28) & 3u;
-          if (n > 0) atomicXor(sb + (size_t)(rng & 0x3FFFu) * (NB * 4), bit);
-          if (n > 1) atomicXor(sb + (size_t)((rng >> 14) & 0x3FFFu) * (NB * 4), bit);
-        } else {
-          const uint32_t q0 = rng >> 8, qe = q0 + (rng & 0xFFu);
-          for (uint32_t q = q0; q < qe; ++q)
-            atomicXor(sb + (size_t)__ldg(A.p.comp_tgt + q) * (NB * 4), bit);
+      const uint32_t mask = ct->mask[cell];
+      const uint32_t wbase = b * 4 + ((uint32_t)lanebit >> 5);   // word offset inside a slot
+      bit = 1u << (lanebit & 31);
+      // up to four components with up to two inline slots each; longer lists
+      // are applied here directly
+#pragma unroll
+      for (int bp = 0; bp < 4; ++bp) {
+        pw[2 * bp] = 0xFFFFFFFFu;
+        pw[2 * bp + 1] = 0xFFFFFFFFu;
+        if ((mask >> bp) & 1u) {
+          const uint32_t rng = __ldg(A.p.comp_rng + comp0 + bp);
+          if (rng & 0x80000000u) {
+            const uint32_t n = (rng >> 28) & 3u;
+            if (n > 0) pw[2 * bp] = (rng & 0x3FFFu) * (NB * 4) + wbase;
+            if (n > 1) pw[2 * bp + 1] = ((rng >> 14) & 0x3FFFu) * (NB * 4) + wbase;
+          } else {
+            uint32_t* sw = reinterpret_cast<uint32_t*>(slots);
+            const uint32_t q0 = rng >> 8, qe = q0 + (rng & 0xFFu);
+            for (uint32_t q = q0; q < qe; ++q)
+              atomicXor(sw + (uint32_t)__ldg(A.p.comp_tgt + q) * (NB * 4) + wbase, bit);
+          }
         }
       }
       if (lanebit >= 127) return false;
-      // next uniform: draw index ti, in the same Philox block as the cell draw
-      next = make_uint4(ent.x, pick(tail, ti & 3), (uint32_t)(lanebit + 1) | ((ti + 1) << 8), ent.w);
+      const uint32_t u2 = pick(tail, ti & 3);        // next uniform, draw index ti
+      const int L2 = lanebit + 1;
+      if (u2 >= th[127 - L2]) return false;          // no further fire in lanes L2..127
+      next = make_uint4(ent.x, u2, (uint32_t)L2 | ((ti + 1) << 8), ent.w);
       return true;
     };
     // full-warp drain of the first 32 queued states; continuing channels are re-queued
@@ -185,7 +200,30 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
       const uint32_t comp0 = qb[lane];
       __syncwarp();
       uint4 next = make_uint4(0u, 0u, 0u, 0u);
-      const bool more = fire_step(ent, comp0, next);
+      uint32_t pw[8];
+      uint32_t bit = 0;
+      const bool more = fire_step(ent, comp0, next, pw, bit);
+      // flush the (word, bit) pairs of the whole warp with full-warp atomics
+      uint32_t np = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) np += pw[k] != 0xFFFFFFFFu;
+      uint32_t incl = np;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      uint32_t at = incl - np;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (pw[k] != 0xFFFFFFFFu) wl[at++] = make_uint2(pw[k], bit);
+      __syncwarp();
+      uint32_t* sw = reinterpret_cast<uint32_t*>(slots);
+      for (uint32_t k = lane; k < total; k += 32) {
+        const uint2 pr = wl[k];
+        atomicXor(sw + pr.x, pr.y);
+      }
       __syncwarp();
       const uint32_t rest = qn - 32;          // < 64: move [32, qn) to [0, rest)
       for (uint32_t i0 = 0; i0 < rest; i0 += 32) {
@@ -285,9 +323,16 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
     for (uint32_t x = threadIdx.x; x < total; x += blockDim.x) {
       uint4 ent = pool_a[x];
       const uint32_t comp0 = pool_b[x];
+      uint32_t* sw = reinterpret_cast<uint32_t*>(slots);
       for (int guard = 0; guard < 128; ++guard) {
         uint4 next;
-        if (!fire_step(ent, comp0, next)) break;
+        uint32_t pw[8];
+        uint32_t bit = 0;
+        const bool more = fire_step(ent, comp0, next, pw, bit);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (pw[k] != 0xFFFFFFFFu) atomicXor(sw + pw[k], bit);
+        if (!more) break;
         ent = next;
       }
     }
