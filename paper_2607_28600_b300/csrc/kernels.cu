@@ -27,7 +27,6 @@ namespace {
 
 constexpr int kQueue = 96;          // per-warp queue of (channel, block) fire states
 constexpr int kSignWarps = 8;       // warps per CTA
-constexpr int kMaxPairs = 8;        // inline incidences of one fire (4 components x 2 slots)
 
 __device__ __forceinline__ uint32_t pick(uint4 v, uint32_t s) {
   return s == 0 ? v.x : (s == 1 ? v.y : (s == 2 ? v.z : v.w));
@@ -55,7 +54,7 @@ __device__ __forceinline__ int first_above(const uint32_t* th, float inv_log1m_q
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
 struct SignLayout {
-  size_t q_off, qi_off, c_off, slot_off, qa_off, qb_off, wl_off, cnt_off, total;
+  size_t q_off, qi_off, c_off, slot_off, qa_off, qb_off, cnt_off, total;
 };
 
 __host__ __device__ inline SignLayout sign_layout(uint32_t n_qtab, uint32_t n_ctab, uint32_t n_slots, int nb) {
@@ -66,8 +65,7 @@ __host__ __device__ inline SignLayout sign_layout(uint32_t n_qtab, uint32_t n_ct
   L.slot_off = L.c_off + align16((size_t)n_ctab * sizeof(CellTableDev));
   L.qa_off = L.slot_off + (size_t)n_slots * nb * 16;
   L.qb_off = L.qa_off + (size_t)kSignWarps * kQueue * 16;
-  L.wl_off = L.qb_off + (size_t)kSignWarps * kQueue * 4;
-  L.cnt_off = L.wl_off + (size_t)kSignWarps * 32 * kMaxPairs * 8;
+  L.cnt_off = L.qb_off + (size_t)kSignWarps * kQueue * 4;
   L.total = L.cnt_off + 64;
   return L;
 }
@@ -94,7 +92,6 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
   uint4* qa = reinterpret_cast<uint4*>(smem_raw + Lay.qa_off) + warp * kQueue;
   uint32_t* qb = reinterpret_cast<uint32_t*>(smem_raw + Lay.qb_off) + warp * kQueue;
   uint32_t* sqn = reinterpret_cast<uint32_t*>(smem_raw + Lay.cnt_off);
-  uint2* wl = reinterpret_cast<uint2*>(smem_raw + Lay.wl_off) + (size_t)warp * 32 * kMaxPairs;
 
   for (uint32_t i = threadIdx.x; i < A.p.n_qtab * 128; i += blockDim.x) sq[i] = __ldg(A.p.qtheta + i);
   for (uint32_t i = threadIdx.x; i < A.p.n_qtab; i += blockDim.x) sqi[i] = __ldg(A.p.qinv + i);
@@ -203,28 +200,10 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
       uint32_t pw[8];
       uint32_t bit = 0;
       const bool more = fire_step(ent, comp0, next, pw, bit);
-      // flush the (word, bit) pairs of the whole warp with full-warp atomics
-      uint32_t np = 0;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) np += pw[k] != 0xFFFFFFFFu;
-      uint32_t incl = np;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-      uint32_t at = incl - np;
+      uint32_t* sw = reinterpret_cast<uint32_t*>(slots);
 #pragma unroll
       for (int k = 0; k < 8; ++k)
-        if (pw[k] != 0xFFFFFFFFu) wl[at++] = make_uint2(pw[k], bit);
-      __syncwarp();
-      uint32_t* sw = reinterpret_cast<uint32_t*>(slots);
-      for (uint32_t k = lane; k < total; k += 32) {
-        const uint2 pr = wl[k];
-        atomicXor(sw + pr.x, pr.y);
-      }
-      __syncwarp();
+        if (pw[k] != 0xFFFFFFFFu) atomicXor(sw + pw[k], bit);
       const uint32_t rest = qn - 32;          // < 64: move [32, qn) to [0, rest)
       for (uint32_t i0 = 0; i0 < rest; i0 += 32) {
         uint4 mv = make_uint4(0u, 0u, 0u, 0u);
