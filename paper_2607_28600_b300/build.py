@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsymft.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["circuit.cpp", "compile.cpp", "api.cpp", "kernels.cu"]
-HEADERS = ["internal.hpp", "plan_dev.hpp", "device.cuh"]
+HEADERS = ["internal.hpp", "plan_dev.hpp", "plan_host.hpp", "device.cuh"]
 
 
 def _nvcc():

@@ -12,19 +12,11 @@
 #include <string>
 #include <vector>
 
-#include "plan_dev.hpp"
 #include "internal.hpp"
+#include "plan_dev.hpp"
+#include "plan_host.hpp"
 #include "symft.h"
 
-namespace symft {
-int sign_blocks_per_cta(const DevPlan& p);
-cudaError_t launch_sign(const SignArgs& a, int grid, cudaStream_t st);
-size_t sign_smem_bytes(const DevPlan& p);
-cudaError_t sign_occupancy(const DevPlan& p, int* ctas_per_sm);
-cudaError_t launch_dense(const DenseArgs& a, bool fp64, int warps_per_block, int grid, size_t smem,
-                         cudaStream_t st);
-cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t st);
-}  // namespace symft
 
 
 
@@ -39,37 +31,7 @@ int set_error(int code, const std::string& msg) {
   return code;
 }
 
-struct DevBuf {
-  void* ptr = nullptr;
-  size_t bytes = 0;
-  cudaError_t ensure(size_t need) {
-    if (need <= bytes) return cudaSuccess;
-    if (ptr) cudaFree(ptr);
-    ptr = nullptr;
-    bytes = 0;
-    cudaError_t e = cudaMalloc(&ptr, need);
-    if (e == cudaSuccess) bytes = need;
-    return e;
-  }
-  void release() {
-    if (ptr) cudaFree(ptr);
-    ptr = nullptr;
-    bytes = 0;
-  }
-};
 }  // namespace
-
-struct symft_plan {
-  HostPlan hp;
-  std::mutex mu;
-  bool uploaded = false;
-  int device = -1;
-  DevBuf plan_buf;
-  DevPlan dp{};
-  DevBuf signs, m3, det_scratch, gvec, status;
-  DevBuf h_meas, h_det, h_obs, h_disc;   // staging for host outputs
-  int sm_count = 0;
-};
 
 namespace {
 
@@ -81,7 +43,11 @@ size_t push(std::vector<unsigned char>& blob, const std::vector<T>& v) {
   return off;
 }
 
-cudaError_t upload(symft_plan* P) {
+}  // namespace
+
+namespace symft {
+
+void build_blob(symft_plan* P) {
   const HostPlan& h = P->hp;
   std::vector<ChannelDev> ch(h.n_channels);
   for (uint32_t c = 0; c < h.n_channels; ++c)
@@ -120,9 +86,13 @@ cudaError_t upload(symft_plan* P) {
     o.causal_n = d.causal_n;
     o.t = d.t;
   }
-  std::vector<unsigned char> blob;
-  size_t o_ch = push(blob, ch), o_q = push(blob, qtheta), o_ct = push(blob, ct);
-  size_t o_t4 = push(blob, theta4), o_qi = push(blob, qinv);
+  std::vector<unsigned char>& blob = P->blob;
+  blob.clear();
+  P->off.ch = push(blob, ch);
+  P->off.q = push(blob, qtheta);
+  P->off.ct = push(blob, ct);
+  P->off.t4 = push(blob, theta4);
+  P->off.qi = push(blob, qinv);
   // packed incidence lists (16-bit targets, 24-bit offsets, 8-bit counts)
   if (h.n_slots >= 65536) throw Error(SYMFT_E_CAPACITY, "more than 65535 bit-packed slots");
   if (h.comp_tgt.size() >= (1u << 24)) throw Error(SYMFT_E_CAPACITY, "too many sign incidences");
@@ -142,62 +112,86 @@ cudaError_t upload(symft_plan* P) {
     }
   }
   std::vector<uint16_t> comp_tgt(h.comp_tgt.begin(), h.comp_tgt.end());
-  size_t o_co = push(blob, comp_rng), o_ctg = push(blob, comp_tgt);
-  size_t o_m1t = push(blob, h.m1_t), o_m1o = push(blob, h.m1_off), o_m1g = push(blob, h.m1_tgt);
-  size_t o_tco = push(blob, h.tgt_causal_off), o_tca = push(blob, h.tgt_causal);
-  size_t o_sc = push(blob, h.slot_const), o_po = push(blob, h.par_off), o_pa = push(blob, h.par);
-  size_t o_lo = push(blob, h.lvl_off), o_lr = push(blob, h.lvl_rec);
-  size_t o_go = push(blob, h.gat_off), o_gr = push(blob, h.gat_rec);
-  size_t o_pe = push(blob, h.post_events), o_dn = push(blob, dn), o_dc = push(blob, h.dense_causal);
-  cudaError_t e = P->plan_buf.ensure(blob.size());
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpy(P->plan_buf.ptr, blob.data(), blob.size(), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return e;
-  auto at = [&](size_t off) { return static_cast<unsigned char*>(P->plan_buf.ptr) + off; };
-  DevPlan& d = P->dp;
+  P->off.co = push(blob, comp_rng);
+  P->off.ctg = push(blob, comp_tgt);
+  P->off.m1t = push(blob, h.m1_t);
+  P->off.m1o = push(blob, h.m1_off);
+  P->off.m1g = push(blob, h.m1_tgt);
+  P->off.tco = push(blob, h.tgt_causal_off);
+  P->off.tca = push(blob, h.tgt_causal);
+  P->off.sc = push(blob, h.slot_const);
+  P->off.po = push(blob, h.par_off);
+  P->off.pa = push(blob, h.par);
+  P->off.lo = push(blob, h.lvl_off);
+  P->off.lr = push(blob, h.lvl_rec);
+  P->off.go = push(blob, h.gat_off);
+  P->off.gr = push(blob, h.gat_rec);
+  P->off.pe = push(blob, h.post_events);
+  P->off.dn = push(blob, dn);
+  P->off.dc = push(blob, h.dense_causal);
+}
+
+void bind_plan(const symft_plan* P, unsigned char* base, DevPlan* dptr) {
+  const HostPlan& h = P->hp;
+  auto at = [&](size_t off) { return base + off; };
+  DevPlan& d = *dptr;
   d.n_channels = h.n_channels;
-  d.ch = reinterpret_cast<const ChannelDev*>(at(o_ch));
-  d.theta4 = reinterpret_cast<const uint4*>(at(o_t4));
+  d.ch = reinterpret_cast<const ChannelDev*>(at(P->off.ch));
+  d.theta4 = reinterpret_cast<const uint4*>(at(P->off.t4));
   d.n_qtab = static_cast<uint32_t>(h.qtabs.size());
   d.n_ctab = static_cast<uint32_t>(h.ctabs.size());
-  d.qtheta = reinterpret_cast<const uint32_t*>(at(o_q));
-  d.qinv = reinterpret_cast<const float*>(at(o_qi));
-  d.ctabs = reinterpret_cast<const CellTableDev*>(at(o_ct));
-  d.comp_rng = reinterpret_cast<const uint32_t*>(at(o_co));
-  d.comp_tgt = reinterpret_cast<const uint16_t*>(at(o_ctg));
+  d.qtheta = reinterpret_cast<const uint32_t*>(at(P->off.q));
+  d.qinv = reinterpret_cast<const float*>(at(P->off.qi));
+  d.ctabs = reinterpret_cast<const CellTableDev*>(at(P->off.ct));
+  d.comp_rng = reinterpret_cast<const uint32_t*>(at(P->off.co));
+  d.comp_tgt = reinterpret_cast<const uint16_t*>(at(P->off.ctg));
   d.n_m1 = static_cast<uint32_t>(h.m1_t.size());
-  d.m1_t = reinterpret_cast<const uint32_t*>(at(o_m1t));
-  d.m1_off = reinterpret_cast<const uint32_t*>(at(o_m1o));
-  d.m1_tgt = reinterpret_cast<const uint32_t*>(at(o_m1g));
+  d.m1_t = reinterpret_cast<const uint32_t*>(at(P->off.m1t));
+  d.m1_off = reinterpret_cast<const uint32_t*>(at(P->off.m1o));
+  d.m1_tgt = reinterpret_cast<const uint32_t*>(at(P->off.m1g));
   d.n_targets = h.n_targets;
   d.tgt_det0 = h.tgt_det0;
   d.tgt_obs0 = h.tgt_obs0;
   d.tgt_sign0 = h.tgt_sign0;
   d.n_slots = h.n_slots;
-  d.slot_const = reinterpret_cast<const uint8_t*>(at(o_sc));
-  d.par_off = reinterpret_cast<const uint32_t*>(at(o_po));
-  d.par = reinterpret_cast<const uint32_t*>(at(o_pa));
+  d.slot_const = reinterpret_cast<const uint8_t*>(at(P->off.sc));
+  d.par_off = reinterpret_cast<const uint32_t*>(at(P->off.po));
+  d.par = reinterpret_cast<const uint32_t*>(at(P->off.pa));
   d.n_levels = h.lvl_off.empty() ? 0 : static_cast<uint32_t>(h.lvl_off.size() - 1);
-  d.lvl_off = reinterpret_cast<const uint32_t*>(at(o_lo));
-  d.lvl_rec = reinterpret_cast<const uint32_t*>(at(o_lr));
-  d.gat_off = reinterpret_cast<const uint32_t*>(at(o_go));
-  d.gat_rec = reinterpret_cast<const uint32_t*>(at(o_gr));
-  d.tgt_causal_off = reinterpret_cast<const uint32_t*>(at(o_tco));
-  d.tgt_causal = reinterpret_cast<const uint32_t*>(at(o_tca));
+  d.lvl_off = reinterpret_cast<const uint32_t*>(at(P->off.lo));
+  d.lvl_rec = reinterpret_cast<const uint32_t*>(at(P->off.lr));
+  d.gat_off = reinterpret_cast<const uint32_t*>(at(P->off.go));
+  d.gat_rec = reinterpret_cast<const uint32_t*>(at(P->off.gr));
+  d.tgt_causal_off = reinterpret_cast<const uint32_t*>(at(P->off.tco));
+  d.tgt_causal = reinterpret_cast<const uint32_t*>(at(P->off.tca));
   d.n_post_events = static_cast<uint32_t>(h.post_events.size());
-  d.post_events = reinterpret_cast<const int32_t*>(at(o_pe));
+  d.post_events = reinterpret_cast<const int32_t*>(at(P->off.pe));
   d.n_dense = static_cast<uint32_t>(h.dense.size());
-  d.dense = reinterpret_cast<const DenseInstrDev*>(at(o_dn));
-  d.dense_causal = reinterpret_cast<const uint32_t*>(at(o_dc));
+  d.dense = reinterpret_cast<const DenseInstrDev*>(at(P->off.dn));
+  d.dense_causal = reinterpret_cast<const uint32_t*>(at(P->off.dc));
   d.n_m3 = h.n_m3;
   d.n_records = h.n_records;
   d.n_dets = h.n_dets;
   d.n_obs = h.n_obs;
   d.postselect = h.postselect;
+}
+
+}  // namespace symft
+
+namespace {
+
+cudaError_t upload(symft_plan* P) {
+  cudaError_t e = P->plan_buf.ensure(P->blob.size());
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(P->plan_buf.ptr, P->blob.data(), P->blob.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  bind_plan(P, static_cast<unsigned char*>(P->plan_buf.ptr), &P->dp);
   int dev = 0;
-  cudaGetDevice(&dev);
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
   P->device = dev;
-  cudaDeviceGetAttribute(&P->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaDeviceGetAttribute(&P->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
   P->uploaded = true;
   return cudaSuccess;
 }
@@ -372,7 +366,13 @@ int symft_compile_ex(const char* text, const symft_options* opt, symft_plan** ou
   try {
     Circuit c = parse_circuit(text);
     symft_plan* p = new symft_plan();
-    p->hp = compile_plan(c, o);
+    try {
+      p->hp = compile_plan(c, o);
+      build_blob(p);
+    } catch (...) {
+      delete p;
+      throw;
+    }
     *out = p;
     return SYMFT_OK;
   } catch (const Error& e) {

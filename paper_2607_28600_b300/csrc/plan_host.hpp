@@ -1,0 +1,67 @@
+// Host-side plan object shared by the C ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <vector>
+
+#include "internal.hpp"
+#include "plan_dev.hpp"
+
+namespace symft {
+
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t need) {
+    if (need <= bytes) return cudaSuccess;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&ptr, need);
+    if (e == cudaSuccess) bytes = need;
+    return e;
+  }
+  void release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+  }
+};
+
+// Byte offsets of the plan arrays inside the device blob.
+struct BlobOffsets {
+  size_t ch, q, ct, t4, qi, co, ctg, m1t, m1o, m1g, tco, tca, sc, po, pa, lo, lr, go, gr, pe, dn, dc;
+};
+
+cudaError_t launch_sign(const SignArgs& a, int grid, cudaStream_t st);
+int sign_blocks_per_cta(const DevPlan& p);
+size_t sign_smem_bytes(const DevPlan& p);
+cudaError_t sign_occupancy(const DevPlan& p, int* ctas_per_sm);
+cudaError_t launch_dense(const DenseArgs& a, bool fp64, int warps_per_block, int grid, size_t smem,
+                         cudaStream_t st);
+cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t st);
+
+}  // namespace symft
+
+struct symft_plan {
+  symft::HostPlan hp;
+  std::vector<unsigned char> blob;   // device image of the plan, built at compile time
+  symft::BlobOffsets off{};
+  std::mutex mu;
+  bool uploaded = false;
+  int device = -1;
+  symft::DevBuf plan_buf;
+  symft::DevPlan dp{};
+  symft::DevBuf signs, m3, det_scratch, gvec, status;
+  symft::DevBuf h_meas, h_det, h_obs, h_disc;   // staging for host outputs
+  int sm_count = 0;
+};
+
+namespace symft {
+// Build the device image of a compiled plan (throws Error on capacity limits).
+void build_blob(symft_plan* P);
+// Point the DevPlan arrays into a copy of the blob at `base` (device address).
+void bind_plan(const symft_plan* P, unsigned char* base, DevPlan* d);
+}  // namespace symft
