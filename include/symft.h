@@ -153,6 +153,35 @@ const char* symft_last_error(void);
 /* Number of kernel launches the last sampling call on this thread issued. */
 int symft_last_launch_count(void);
 
+/* Sampling without any device allocation (the paper has no counterpart; this
+ * is an integration aid).  Some callers cannot let a library call cudaMalloc:
+ * frameworks whose caching allocator owns the device heap, services with a
+ * fixed memory budget, or code that samples while a stream is being captured.
+ * This call runs the same kernels as symft_sample_ex on caller-owned DEVICE
+ * outputs (same layout, same results), and takes every other byte it needs --
+ * the plan copy, dense-sign and active-outcome columns, the status word, any
+ * global active vectors -- from one fixed 32 MiB __device__ array that the
+ * library holds on every GPU that loads it until the process exits.
+ *   - Limit: a request whose scratch (plan image + (n_dense + n_active) * W
+ *     words + detector scratch when postselecting without det_out) exceeds
+ *     32 MiB returns SYMFT_E_CAPACITY before any GPU work; sample fewer shots
+ *     per call.
+ *   - Set-up: the first call made with a device current looks up the array's
+ *     device address (cudaGetSymbolAddress); make that first call before any
+ *     stream capture.
+ *   - Sharing: all calls share the array and it keeps the last call's
+ *     contents; the call clears what must start at zero.  Calls that overlap
+ *     on the GPU (other streams, other threads) race on it: serialise them.
+ *   - No host outputs, no status readback; errors are reported by
+ *     symft_noalloc_last_error().  Asynchronous on `cuda_stream`. */
+int symft_sample_noalloc(const symft_plan* plan, uint64_t shots, uint64_t seed,
+                         uint64_t shot_offset, uint64_t* meas_out, uint64_t* det_out,
+                         uint64_t* obs_out, uint64_t* discard_out, int precision,
+                         void* cuda_stream);
+
+/* Message describing the last symft_sample_noalloc error on this thread. */
+const char* symft_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,8 @@ INSTR_NAMES = ("PromoteRot", "ActiveDiagRot", "ActivePairRot", "RandomMeas", "De
                "ActiveDiagMeas", "ActivePairMeas")
 
 EXPORTS = ("symft_compile", "symft_compile_ex", "symft_plan_info", "symft_plan_free",
-           "symft_sample", "symft_sample_ex", "symft_last_error", "symft_last_launch_count")
+           "symft_sample", "symft_sample_ex", "symft_last_error", "symft_last_launch_count",
+           "symft_sample_noalloc", "symft_noalloc_last_error")
 
 
 class SymftError(RuntimeError):
@@ -83,6 +84,13 @@ def lib():
     L.symft_last_error.restype = ctypes.c_char_p
     L.symft_last_launch_count.argtypes = []
     L.symft_last_launch_count.restype = ctypes.c_int
+    L.symft_sample_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                       ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_void_p]
+    L.symft_sample_noalloc.restype = ctypes.c_int
+    L.symft_noalloc_last_error.argtypes = []
+    L.symft_noalloc_last_error.restype = ctypes.c_char_p
     _LIB = L
     return L
 
@@ -167,6 +175,18 @@ def symft_sample_ex(plan: Plan, shots: int, seed: int, shot_offset: int = 0, mea
     a.precision, a.out_location, a.check = precision, out_location, int(bool(check))
     a.stream = _stream(stream)
     _check(lib().symft_sample_ex(plan.handle, ctypes.byref(a)))
+
+
+def symft_sample_noalloc(plan: Plan, shots: int, seed: int, shot_offset: int = 0, meas_out=None,
+                         det_out=None, obs_out=None, discard_out=None, precision: int = FP32,
+                         stream=None) -> None:
+    """Sample into caller-owned device buffers without any device allocation
+    (scratch comes from the library's fixed 32 MiB device array)."""
+    rc = lib().symft_sample_noalloc(plan.handle, shots, seed, shot_offset, _ptr(meas_out),
+                                    _ptr(det_out), _ptr(obs_out), _ptr(discard_out), precision,
+                                    _stream(stream))
+    if rc != SYMFT_OK:
+        raise SymftError(rc, lib().symft_noalloc_last_error().decode(errors="replace"))
 
 
 def symft_last_launch_count() -> int:
