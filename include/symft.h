@@ -8,7 +8,7 @@
  *     and factorized-circuit), adaptive stabilizer-coordinate planning over the
  *     stabilizer-destabilizer tableau (Sec. 4, seven instruction kinds), and
  *     lowering of the affine sign expressions into a flat device plan (Sec. 6,
- *     "Precompiled sampling instructions").
+ *     precompiled instruction descriptors).
  *   - symft_sample runs the per-shot sampler (Sec. 5, single-shot algorithm)
  *     on the GPU for many shots at once: counter-based noise and random bits,
  *     bit-packed sign evaluation (64 shots per word), and the dense
@@ -64,11 +64,11 @@ typedef struct symft_plan symft_plan;   /* opaque; immutable after compile */
 
 typedef struct {
   int postselect;   /* SYMFT_POSTSELECT_*: reject a shot at the first fired
-                       detector (Sec. 6, "Detector postselection") */
+                       detector (Sec. 6, detector postselection) */
   int reserved[7];
 } symft_options;
 
-/* Counts of a compiled plan (Sec. 5, "Sampling complexity"). */
+/* Counts of a compiled plan (Sec. 5, sampling complexity). */
 typedef struct {
   uint32_t n_qubits;
   uint32_t n_meas_events;     /* all measurements, recorded and hidden (resets) */

@@ -2,7 +2,7 @@
 
 Test infrastructure only.  Detectors and observables are parities of recorded
 measurement outcomes (DETECTOR / OBSERVABLE_INCLUDE annotations of the
-Stim-style input, Sec. 7).  Postselection (Sec. 6 "Detector postselection")
+Stim-style input, Sec. 7).  Postselection (Sec. 6, detector postselection)
 rejects a shot at the first postselected detector, in annotation order, whose
 parity is 1; rejected shots keep every bit produced up to and including that
 detector and report zeros afterwards:

@@ -1,8 +1,8 @@
 """Shared random-stream specification, oracle side (test infrastructure only).
 
 The paper samples its independent symbols (noise choices s and random
-measurement bits m1, Sec. 5 "Symbol variable assignments"; Sec. 6 "Sampling
-independent symbols") but fixes no generator, seed layout or stream order.
+measurement bits m1, Sec. 5, symbol classes; Sec. 6, sampling of
+independent symbols) but fixes no generator, seed layout or stream order.
 To compare samplers shot by shot, every sampler here (state vector, tableau,
 plain SymFT, CUDA) draws from one counter-based specification, written out
 independently on each side:

@@ -2,7 +2,7 @@
 //
 // The plan owns its host description, its device copy (uploaded by the first
 // sampling call) and a workspace that grows to the largest request seen and
-// is reused by later calls (Sec. 6, "Reusing the prepared state").
+// is reused by later calls (Sec. 6, reuse of prepared buffers).
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -1,6 +1,6 @@
 // Compile step: symbolic Clifford-Pauli frame factorization (Sec. 3),
 // stabilizer-coordinate planning (Sec. 4) and lowering to the device plan
-// (Sec. 6, "Precompiled sampling instructions", "Sampling independent symbols").
+// (Sec. 6: precompiled instruction descriptors, packed independent symbols).
 //
 // Representation choices (all host side, run once per circuit):
 //  * Paulis are i^e X^x Z^z over n qubits with x, z as 64-bit word vectors.
