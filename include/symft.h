@@ -99,7 +99,8 @@ typedef struct {
   int precision;           /* SYMFT_FP32 (default) or SYMFT_FP64 dense vectors */
   int out_location;        /* SYMFT_OUT_DEVICE (default) or SYMFT_OUT_HOST */
   int check;               /* non-zero: synchronise and read the device status */
-  int reserved;
+  int plain;               /* non-zero: per-shot unpacked evaluation, one CTA per shot
+                              (the paper's GPU design, kept for comparison; same bits) */
   void* stream;            /* cudaStream_t (NULL: legacy default stream) */
 } symft_sample_args;
 

@@ -52,7 +52,7 @@ class _SampleArgs(ctypes.Structure):
                 ("det_out", ctypes.c_void_p), ("obs_out", ctypes.c_void_p),
                 ("discard_out", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("out_location", ctypes.c_int), ("check", ctypes.c_int),
-                ("reserved", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("plain", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 _LIB = None
@@ -167,12 +167,14 @@ def symft_sample(plan: Plan, shots: int, seed: int, meas_out=None, det_out=None,
 
 def symft_sample_ex(plan: Plan, shots: int, seed: int, shot_offset: int = 0, meas_out=None,
                     det_out=None, obs_out=None, discard_out=None, precision: int = FP32,
-                    out_location: int = OUT_DEVICE, check: bool = False, stream=None) -> None:
+                    out_location: int = OUT_DEVICE, check: bool = False, stream=None,
+                    plain: bool = False) -> None:
     a = _SampleArgs()
     a.shots, a.seed, a.shot_offset = shots, seed, shot_offset
     a.meas_out, a.det_out = _ptr(meas_out), _ptr(det_out)
     a.obs_out, a.discard_out = _ptr(obs_out), _ptr(discard_out)
     a.precision, a.out_location, a.check = precision, out_location, int(bool(check))
+    a.plain = int(bool(plain))
     a.stream = _stream(stream)
     _check(lib().symft_sample_ex(plan.handle, ctypes.byref(a)))
 
@@ -194,7 +196,7 @@ def symft_last_launch_count() -> int:
 
 
 def sample_to_tensors(plan: Plan, shots: int, seed: int, shot_offset: int = 0,
-                      precision: int = FP32, stream=None, device="cuda"):
+                      precision: int = FP32, stream=None, device="cuda", plain: bool = False):
     """Allocate device output columns (torch int64 holding the uint64 words) and sample."""
     import torch
     W = plan.words(shots)
@@ -207,5 +209,5 @@ def sample_to_tensors(plan: Plan, shots: int, seed: int, shot_offset: int = 0,
                     meas_out=meas if meas.numel() else None,
                     det_out=det if det.numel() else None,
                     obs_out=obs if obs.numel() else None,
-                    discard_out=disc, precision=precision, stream=stream)
+                    discard_out=disc, precision=precision, stream=stream, plain=plain)
     return meas, det, obs, disc

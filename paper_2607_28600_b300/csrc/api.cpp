@@ -129,6 +129,9 @@ void build_blob(symft_plan* P) {
   P->off.pe = push(blob, h.post_events);
   P->off.dn = push(blob, dn);
   P->off.dc = push(blob, h.dense_causal);
+  P->off.plc = push(blob, h.plain_const);
+  P->off.plo = push(blob, h.plain_off);
+  P->off.pls = push(blob, h.plain_sym);
 }
 
 void bind_plan(const symft_plan* P, unsigned char* base, DevPlan* dptr) {
@@ -174,6 +177,10 @@ void bind_plan(const symft_plan* P, unsigned char* base, DevPlan* dptr) {
   d.n_dets = h.n_dets;
   d.n_obs = h.n_obs;
   d.postselect = h.postselect;
+  d.n_comp = h.n_comp;
+  d.plain_const = reinterpret_cast<const uint8_t*>(at(P->off.plc));
+  d.plain_off = reinterpret_cast<const uint32_t*>(at(P->off.plo));
+  d.plain_sym = reinterpret_cast<const uint32_t*>(at(P->off.pls));
 }
 
 }  // namespace symft
@@ -250,8 +257,33 @@ int sample_impl(symft_plan* P, const symft_sample_args* a) {
   int* status = static_cast<int*>(P->status.ptr);
   if (a->check) CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
 
+  // --- plain form: one CTA per shot -----------------------------------------
+  if (a->plain) {
+    const bool fp64 = a->precision == SYMFT_FP64;
+    if (plain_smem_bytes(P->dp, h.k_max, fp64) > 200 * 1024)
+      return set_error(SYMFT_E_CAPACITY, "plain form: per-shot state exceeds shared memory");
+    if (meas) CUDA_TRY(cudaMemsetAsync(meas, 0, h.n_records * W * 8, st));
+    if (det) CUDA_TRY(cudaMemsetAsync(det, 0, h.n_dets * W * 8, st));
+    if (obs) CUDA_TRY(cudaMemsetAsync(obs, 0, h.n_obs * W * 8, st));
+    if (disc) CUDA_TRY(cudaMemsetAsync(disc, 0, W * 8, st));
+    PlainArgs pa{};
+    pa.p = P->dp;
+    pa.seed = a->seed;
+    pa.shot0 = a->shot_offset;
+    pa.shots = a->shots;
+    pa.W = W;
+    pa.meas = meas;
+    pa.det = det;
+    pa.obs = obs;
+    pa.discard = disc;
+    pa.kmax = h.k_max;
+    pa.status = status;
+    const uint64_t cap = static_cast<uint64_t>(P->sm_count) * 16;
+    CUDA_TRY(launch_plain(pa, fp64, static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(a->shots, cap))), st));
+    ++launches;
+  }
   // --- sign kernel ---------------------------------------------------------
-  if (h.n_slots > 0) {
+  if (!a->plain && h.n_slots > 0) {
     SignArgs s{};
     s.p = P->dp;
     s.seed = a->seed;
@@ -278,7 +310,7 @@ int sample_impl(symft_plan* P, const symft_sample_args* a) {
     ++launches;
   }
   // --- dense kernel --------------------------------------------------------
-  if (G) {
+  if (!a->plain && G) {
     const bool fp64 = a->precision == SYMFT_FP64;
     CUDA_TRY(P->m3.ensure(std::max<uint64_t>(1, h.n_m3 * W) * 8));
     if (h.n_m3) CUDA_TRY(cudaMemsetAsync(P->m3.ptr, 0, h.n_m3 * W * 8, st));
@@ -322,7 +354,7 @@ int sample_impl(symft_plan* P, const symft_sample_args* a) {
     ++launches;
   }
   // --- finalize ------------------------------------------------------------
-  if (need_final) {
+  if (!a->plain && need_final) {
     FinalArgs f{};
     f.p = P->dp;
     f.W = W;

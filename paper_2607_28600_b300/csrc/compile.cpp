@@ -655,6 +655,26 @@ void Compiler::lower(HostPlan& P) {
     P.tgt_causal_off[i + 1] = static_cast<uint32_t>(P.tgt_causal.size());
   }
 
+  // ---- plain form: full exogenous symbol lists of every output and dense sign ----
+  {
+    const uint32_t NTP = R + Dn + O + G;
+    P.plain_const.assign(NTP, 0);
+    P.plain_off.assign(NTP + 1, 0);
+    for (uint32_t i = 0; i < NTP; ++i) {
+      const Expr& e = i < R + Dn + O ? full[i] : dense_lam[i - (R + Dn + O)];
+      P.plain_const[i] = ea_.constant(e);
+      ea_.for_each(e, 0, NS, [&](uint32_t sidx) {
+        if (sidx < n_comp_) {
+          P.plain_sym.push_back(sidx);
+        } else {
+          uint32_t t = sidx - n_comp_;
+          if (cls[t] == 1) P.plain_sym.push_back(n_comp_ + static_cast<uint32_t>(m1_index[t]));
+        }
+      });
+      P.plain_off[i + 1] = static_cast<uint32_t>(P.plain_sym.size());
+    }
+  }
+
   // ---- exogenous record parts, delta-chained to earlier records ----
   // The sign kernel evaluates exo_r = const ^ delta_r ^ XOR(parents).  A parent
   // is taken when it removes enough weighted incidences: a noise component

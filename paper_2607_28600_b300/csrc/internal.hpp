@@ -131,6 +131,12 @@ struct HostPlan {
   std::vector<uint32_t> lvl_off, lvl_rec;    // records with parents, grouped by level
   std::vector<uint32_t> gat_off, gat_rec;    // det / obs -> records (CSR)
 
+  // plain (per-shot, unpacked) form: full exogenous expression of every output
+  // [records][dets][obs][dense signs] as symbol lists; symbol < n_comp is a
+  // noise component, else n_comp + m1 index
+  std::vector<uint8_t> plain_const;
+  std::vector<uint32_t> plain_off, plain_sym;
+
   // postselection order: events in circuit order, rec (>=0) or det (-1-i)
   std::vector<int32_t> post_events;
   std::vector<int32_t> rec_det_before;   // last detector index before record r (-1 none)

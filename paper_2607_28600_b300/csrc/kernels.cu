@@ -609,6 +609,342 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
 }
 
 // ---------------------------------------------------------------------------
+// Plain form (the paper's GPU design rebuilt, for comparison): one CTA per
+// shot; the shot draws its own noise components and random bits from the
+// same streams, evaluates every sign unpacked from its full symbol list, runs
+// the dense instructions on a vector in shared memory and OR-s its output bits
+// into the (zeroed) columns.
+// ---------------------------------------------------------------------------
+constexpr int kPlainThreads = 128;
+
+struct PlainLayout {
+  size_t fired, m1, val, m3, vec, red, total;
+};
+
+__host__ __device__ inline PlainLayout plain_layout(const DevPlan& p, uint32_t kmax, size_t amp) {
+  PlainLayout L;
+  const uint32_t NTP = p.tgt_sign0 + p.n_dense;
+  L.fired = 0;
+  L.m1 = L.fired + align16(((p.n_comp + 31) / 32) * 4);
+  L.val = L.m1 + align16(((p.n_m1 + 31) / 32) * 4);
+  L.m3 = L.val + align16(NTP);
+  L.vec = L.m3 + align16(((p.n_m3 + 31) / 32) * 4 + 16);
+  L.red = L.vec + align16(((size_t)1 << kmax) * amp);
+  L.total = L.red + 2 * kPlainThreads * sizeof(double) + 32;
+  return L;
+}
+
+__device__ __forceinline__ int first_above_global(const uint32_t* __restrict__ th, uint32_t u) {
+  int lo = 0, hi = 128;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (u < __ldg(th + mid)) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+// block-wide sum of two doubles (all threads get the result)
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    red[warp] = a;
+    red[kPlainThreads / 32 + warp] = b;
+  }
+  __syncthreads();
+  a = 0.0;
+  b = 0.0;
+  for (int w = 0; w < kPlainThreads / 32; ++w) {
+    a += red[w];
+    b += red[kPlainThreads / 32 + w];
+  }
+  __syncthreads();
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs A) {
+  extern __shared__ __align__(16) unsigned char psm[];
+  const DevPlan& P = A.p;
+  const PlainLayout Lay = plain_layout(P, A.kmax, sizeof(Cplx<Real>));
+  uint32_t* fired = reinterpret_cast<uint32_t*>(psm + Lay.fired);
+  uint32_t* m1b = reinterpret_cast<uint32_t*>(psm + Lay.m1);
+  uint8_t* val = psm + Lay.val;
+  uint32_t* m3b = reinterpret_cast<uint32_t*>(psm + Lay.m3);
+  Cplx<Real>* vec = reinterpret_cast<Cplx<Real>*>(psm + Lay.vec);
+  double* red = reinterpret_cast<double*>(psm + Lay.red);
+  int* bcast = reinterpret_cast<int*>(red + 2 * kPlainThreads);
+  const uint32_t tid = threadIdx.x;
+  const uint32_t k0 = (uint32_t)A.seed, k1 = (uint32_t)(A.seed >> 32);
+  const uint32_t R = P.n_records, DO = P.n_dets + P.n_obs, NO = P.tgt_sign0;
+  const uint32_t NTP = NO + P.n_dense;
+  const uint32_t n_groups = (P.n_channels + 3) >> 2;
+
+  for (uint64_t r = blockIdx.x; r < A.shots; r += gridDim.x) {
+    const uint64_t rg = A.shot0 + r;
+    const uint32_t gb = (uint32_t)(rg >> 7), my_lane = (uint32_t)(rg & 127);
+    const uint64_t w = r >> 6;
+    const uint64_t bitmask = 1ull << (r & 63);
+    for (uint32_t i = tid; i < (P.n_comp + 31) / 32; i += blockDim.x) fired[i] = 0u;
+    for (uint32_t i = tid; i < (P.n_m1 + 31) / 32; i += blockDim.x) m1b[i] = 0u;
+    for (uint32_t i = tid; i < (P.n_m3 + 31) / 32; i += blockDim.x) m3b[i] = 0u;
+    __syncthreads();
+    // 1. this shot's noise: run each channel's process up to the shot's lane
+    for (uint32_t g = tid; g < n_groups; g += blockDim.x) {
+      const uint4 th4 = __ldg(P.theta4 + g);
+      if (!(th4.x | th4.y | th4.z | th4.w)) continue;
+      const uint4 head = philox(make_uint4(g, gb, 0u, kTagHead), k0, k1);
+      for (uint32_t s2 = 0; s2 < 4; ++s2) {
+        const uint32_t c = 4 * g + s2;
+        if (c >= P.n_channels) break;
+        uint32_t u = pick(head, s2);
+        if (u >= pick(th4, s2)) continue;
+        const uint4 raw = __ldg(reinterpret_cast<const uint4*>(P.ch) + c);
+        const uint32_t* th = P.qtheta + (size_t)(raw.y & 0xFFFFu) * 128;
+        const CellTableDev* ct = P.ctabs + (raw.y >> 16);
+        const uint32_t ncell = ct->ncell;
+        uint32_t ti = 0;
+        int L = 0;
+        for (int guard = 0; guard < 129; ++guard) {
+          const int j = first_above_global(th, u);
+          if (j > 127 - L) break;
+          const int lanebit = L + j;
+          if ((uint32_t)lanebit > my_lane) break;
+          uint32_t cell = 0;
+          if (ncell > 1) {
+            const uint4 t4 = philox(make_uint4(c, gb, ti >> 2, kTagTail), k0, k1);
+            const uint32_t v = pick(t4, ti & 3);
+            ++ti;
+            cell = ncell - 1;
+            for (uint32_t kk = 0; kk + 1 < ncell; ++kk)
+              if (v < ct->phi[kk]) { cell = kk; break; }
+          }
+          if ((uint32_t)lanebit == my_lane) {
+            uint32_t mask = ct->mask[cell];
+            while (mask) {
+              const uint32_t comp = raw.z + (__ffs(mask) - 1);
+              mask &= mask - 1;
+              atomicOr(fired + (comp >> 5), 1u << (comp & 31));
+            }
+            break;
+          }
+          L = lanebit + 1;
+          if (L >= 128) break;
+          const uint4 t4 = philox(make_uint4(c, gb, ti >> 2, kTagTail), k0, k1);
+          u = pick(t4, ti & 3);
+          ++ti;
+        }
+      }
+    }
+    // 2. random measurement bits
+    for (uint32_t j = tid; j < P.n_m1; j += blockDim.x) {
+      const uint64_t wg = rg >> 6;
+      const uint4 o = philox(make_uint4(__ldg(P.m1_t + j), (uint32_t)(wg >> 1), (uint32_t)(wg >> 33), kTagMbit), k0, k1);
+      const uint64_t word = (wg & 1) ? ((uint64_t)o.z | ((uint64_t)o.w << 32)) : ((uint64_t)o.x | ((uint64_t)o.y << 32));
+      if ((word >> (rg & 63)) & 1ull) atomicOr(m1b + (j >> 5), 1u << (j & 31));
+    }
+    __syncthreads();
+    // 3. every exogenous sign, unpacked, from its full symbol list
+    for (uint32_t i = tid; i < NTP; i += blockDim.x) {
+      uint32_t v = __ldg(P.plain_const + i);
+      const uint32_t e = __ldg(P.plain_off + i + 1);
+      for (uint32_t q = __ldg(P.plain_off + i); q < e; ++q) {
+        const uint32_t sy = __ldg(P.plain_sym + q);
+        v ^= sy < P.n_comp ? (fired[sy >> 5] >> (sy & 31)) & 1u
+                           : (m1b[(sy - P.n_comp) >> 5] >> ((sy - P.n_comp) & 31)) & 1u;
+      }
+      val[i] = (uint8_t)v;
+    }
+    if (tid == 0) {
+      vec[0].re = (Real)1;
+      vec[0].im = (Real)0;
+    }
+    __syncthreads();
+    // 4. dense instructions on the shot's vector
+    uint32_t k = 0;
+    for (uint32_t g = 0; g < P.n_dense; ++g) {
+      const DenseInstrDev I = P.dense[g];
+      if (tid == 0) {
+        uint32_t lam = val[NO + g];
+        for (uint32_t q = 0; q < I.causal_n; ++q) {
+          const uint32_t j = __ldg(P.dense_causal + I.causal_off + q);
+          lam ^= (m3b[j >> 5] >> (j & 31)) & 1u;
+        }
+        bcast[0] = (int)lam;
+      }
+      __syncthreads();
+      const uint32_t lam = (uint32_t)bcast[0];
+      const Real sg = lam ? (Real)-1 : (Real)1;
+      const Real c = (Real)I.c, s = (Real)I.s;
+      const uint32_t n = 1u << k;
+      if (I.kind == 0) {
+        for (uint32_t x = tid; x < n; x += blockDim.x) {
+          Cplx<Real> v = vec[x], hi;
+          hi.re = sg * s * v.im;
+          hi.im = -sg * s * v.re;
+          vec[x + n] = hi;
+          v.re *= c;
+          v.im *= c;
+          vec[x] = v;
+        }
+        ++k;
+      } else if (I.kind == 1) {
+        const Real mu = I.mu == 0 ? (Real)1 : (Real)-1;
+        for (uint32_t x = tid; x < n; x += blockDim.x) {
+          const Real f = sg * mu * s * ((__popc(x & I.b) & 1) ? (Real)-1 : (Real)1);
+          const Cplx<Real> v = vec[x];
+          Cplx<Real> o;
+          o.re = c * v.re + f * v.im;
+          o.im = c * v.im - f * v.re;
+          vec[x] = o;
+        }
+      } else if (I.kind == 2) {
+        const int pb = 31 - __clz(I.a);
+        Real cr, ci;
+        switch (I.mu & 3) {
+          case 0: cr = 0; ci = -1; break;
+          case 1: cr = 1; ci = 0; break;
+          case 2: cr = 0; ci = 1; break;
+          default: cr = -1; ci = 0; break;
+        }
+        cr *= sg * s;
+        ci *= sg * s;
+        for (uint32_t z = tid; z < (n >> 1); z += blockDim.x) {
+          const uint32_t x0 = insert_bit(z, pb, 0u), x1 = x0 ^ I.a;
+          const Cplx<Real> v0 = vec[x0], v1 = vec[x1];
+          const Real s1 = (__popc(x1 & I.b) & 1) ? (Real)-1 : (Real)1;
+          const Real s0 = (__popc(x0 & I.b) & 1) ? (Real)-1 : (Real)1;
+          Cplx<Real> o0, o1;
+          o0.re = c * v0.re + s1 * (cr * v1.re - ci * v1.im);
+          o0.im = c * v0.im + s1 * (cr * v1.im + ci * v1.re);
+          o1.re = c * v1.re + s0 * (cr * v0.re - ci * v0.im);
+          o1.im = c * v1.im + s0 * (cr * v0.im + ci * v0.re);
+          vec[x0] = o0;
+          vec[x1] = o1;
+        }
+      } else {
+        const int h = I.h;
+        const Real inv_sqrt2 = (Real)0.70710678118654752440;
+        Real mcr = 0, mci = 0;
+        if (I.kind == 6) {
+          switch (I.mu & 3) {
+            case 0: mcr = 1; mci = 0; break;
+            case 1: mcr = 0; mci = -1; break;
+            case 2: mcr = -1; mci = 0; break;
+            default: mcr = 0; mci = 1; break;
+          }
+        }
+        double S0 = 0.0, S1 = 0.0;
+        if (I.kind == 5) {
+          for (uint32_t x = tid; x < n; x += blockDim.x) {
+            const double v = norm2(vec[x]);
+            if (__popc(x & I.b) & 1) S1 += v; else S0 += v;
+          }
+        } else {
+          for (uint32_t z = tid; z < (n >> 1); z += blockDim.x) {
+            const uint32_t u0 = insert_bit(z, h, 0u);
+            const Cplx<Real> a0 = vec[u0], a1 = vec[u0 ^ I.a];
+            const Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
+            const Real tr = sb * (mcr * a1.re - mci * a1.im), tim = sb * (mcr * a1.im + mci * a1.re);
+            Cplx<Real> b0, b1;
+            b0.re = (a0.re + tr) * inv_sqrt2; b0.im = (a0.im + tim) * inv_sqrt2;
+            b1.re = (a0.re - tr) * inv_sqrt2; b1.im = (a0.im - tim) * inv_sqrt2;
+            S0 += norm2(b0);
+            S1 += norm2(b1);
+          }
+        }
+        block_sum2(S0, S1, red);
+        const uint32_t l0 = I.kind == 5 ? (lam ^ (uint32_t)I.eta) : lam;
+        const double p0 = (l0 ? S1 : S0) / (S0 + S1);
+        if (tid == 0) {
+          const uint32_t m = meas_uniform(A.seed, I.t, rg) < p0 ? 0u : 1u;
+          bcast[1] = (int)m;
+          if (m) m3b[I.m3 >> 5] |= 1u << (I.m3 & 31);
+        }
+        __syncthreads();
+        const uint32_t m = (uint32_t)bcast[1];
+        const uint32_t lab = l0 ^ m;
+        const Real scale = (Real)(1.0 / sqrt(lab ? S1 : S0));
+        const uint32_t half = n >> 1;
+        for (uint32_t z0 = 0; z0 < half; z0 += blockDim.x) {
+          const uint32_t z = z0 + tid;
+          Cplx<Real> v;
+          v.re = 0;
+          v.im = 0;
+          if (z < half) {
+            if (I.kind == 5) {
+              const uint32_t u = insert_bit(z, h, lab);
+              v = vec[u ^ ((uint32_t)(__popc(u & I.b & ~(1u << h)) & 1) << h)];
+            } else {
+              const uint32_t u0 = insert_bit(z, h, 0u);
+              const Cplx<Real> a0 = vec[u0], a1 = vec[u0 ^ I.a];
+              Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
+              if (lab) sb = -sb;
+              const Real tr = sb * (mcr * a1.re - mci * a1.im), tim = sb * (mcr * a1.im + mci * a1.re);
+              v.re = (a0.re + tr) * inv_sqrt2;
+              v.im = (a0.im + tim) * inv_sqrt2;
+            }
+            v.re *= scale;
+            v.im *= scale;
+          }
+          __syncthreads();
+          if (z < half) vec[z] = v;
+          __syncthreads();
+        }
+        --k;
+      }
+      __syncthreads();
+    }
+    // 5. outputs: causal residuals, postselection, OR into the columns
+    for (uint32_t i = tid; i < NO; i += blockDim.x) {
+      uint32_t v = val[i];
+      const uint32_t e = __ldg(P.tgt_causal_off + i + 1);
+      for (uint32_t q = __ldg(P.tgt_causal_off + i); q < e; ++q) {
+        const uint32_t j = __ldg(P.tgt_causal + q);
+        v ^= (m3b[j >> 5] >> (j & 31)) & 1u;
+      }
+      val[i] = (uint8_t)v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int cut = 0;
+      if (P.postselect) {
+        for (uint32_t e = 0; e < P.n_post_events; ++e) {
+          const int32_t ev = __ldg(P.post_events + e);
+          if (ev >= 0) {
+            if (cut) val[ev] = 0;
+          } else {
+            const uint32_t di = R + (uint32_t)(-1 - ev);
+            if (cut) val[di] = 0;
+            else if (val[di]) cut = 1;
+          }
+        }
+        if (cut)
+          for (uint32_t j = 0; j < P.n_obs; ++j) val[R + P.n_dets + j] = 0;
+      }
+      bcast[2] = cut;
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < NO; i += blockDim.x) {
+      if (!val[i]) continue;
+      uint64_t* col;
+      uint64_t idx;
+      if (i < R) { col = A.meas; idx = i; }
+      else if (i < R + P.n_dets) { col = A.det; idx = i - R; }
+      else { col = A.obs; idx = i - R - P.n_dets; }
+      if (col) atomicOr(reinterpret_cast<unsigned long long*>(col + idx * A.W + w), (unsigned long long)bitmask);
+    }
+    if (tid == 0 && bcast[2] && A.discard)
+      atomicOr(reinterpret_cast<unsigned long long*>(A.discard + w), (unsigned long long)bitmask);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Finalize: causal residuals of records/detectors/observables and postselection.
 // ---------------------------------------------------------------------------
 
@@ -698,6 +1034,20 @@ cudaError_t launch_dense_t(const DenseArgs& a, int warps_per_block, int grid, si
 cudaError_t launch_dense(const DenseArgs& a, bool fp64, int warps_per_block, int grid, size_t smem, cudaStream_t st) {
   return fp64 ? launch_dense_t<double>(a, warps_per_block, grid, smem, st)
               : launch_dense_t<float>(a, warps_per_block, grid, smem, st);
+}
+
+size_t plain_smem_bytes(const DevPlan& p, uint32_t kmax, bool fp64) {
+  return plain_layout(p, kmax, fp64 ? 16 : 8).total;
+}
+
+cudaError_t launch_plain(const PlainArgs& a, bool fp64, int grid, cudaStream_t st) {
+  const size_t smem = plain_smem_bytes(a.p, a.kmax, fp64);
+  const void* fn = fp64 ? (const void*)plain_kernel<double> : (const void*)plain_kernel<float>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (fp64) plain_kernel<double><<<grid, kPlainThreads, smem, st>>>(a);
+  else plain_kernel<float><<<grid, kPlainThreads, smem, st>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t st) {

@@ -77,6 +77,11 @@ struct DevPlan {
   uint32_t n_m3;
   uint32_t n_records, n_dets, n_obs;
   int postselect;
+  // plain (per-shot) form
+  uint32_t n_comp;
+  const uint8_t* plain_const;   // [records][dets][obs][dense signs]
+  const uint32_t* plain_off;
+  const uint32_t* plain_sym;
 };
 
 
@@ -106,6 +111,20 @@ struct DenseArgs {
   uint64_t gvec_stride;   // amplitudes per warp slot in gvec
   uint32_t kmax;
   int use_smem;
+  int* status;
+};
+
+struct PlainArgs {
+  DevPlan p;
+  uint64_t seed;
+  uint64_t shot0;         // absolute index of local shot 0
+  uint64_t shots;
+  uint64_t W;
+  uint64_t* meas;         // zeroed before launch (bits are OR-ed in)
+  uint64_t* det;
+  uint64_t* obs;
+  uint64_t* discard;
+  uint32_t kmax;
   int* status;
 };
 

@@ -33,6 +33,7 @@ struct DevBuf {
 // Byte offsets of the plan arrays inside the device blob.
 struct BlobOffsets {
   size_t ch, q, ct, t4, qi, co, ctg, m1t, m1o, m1g, tco, tca, sc, po, pa, lo, lr, go, gr, pe, dn, dc;
+  size_t plc, plo, pls;
 };
 
 cudaError_t launch_sign(const SignArgs& a, int grid, cudaStream_t st);
@@ -42,6 +43,8 @@ cudaError_t sign_occupancy(const DevPlan& p, int* ctas_per_sm);
 cudaError_t launch_dense(const DenseArgs& a, bool fp64, int warps_per_block, int grid, size_t smem,
                          cudaStream_t st);
 cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t st);
+size_t plain_smem_bytes(const DevPlan& p, uint32_t kmax, bool fp64);
+cudaError_t launch_plain(const PlainArgs& a, bool fp64, int grid, cudaStream_t st);
 
 }  // namespace symft
 

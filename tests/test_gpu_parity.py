@@ -162,3 +162,34 @@ def test_d7_full_size_sampled_shots():
     # detector firing rate is a property at any size
     rate = float(unpack(det[:, :1024].cpu().numpy().view(np.uint64), 65536).mean())
     assert 0.005 < rate < 0.05
+
+
+# ---- plain form (one CTA per shot, unpacked signs): same bits as the batched form ----
+
+@pytest.mark.parametrize("d,p,post", [(3, 2e-2, 0), (5, 1e-2, 0), (3, 2e-2, 1)])
+def test_plain_form_equals_batched_clifford(d, p, post):
+    text = rotated_surface_code_memory(d, d, p)
+    shots = 1000
+    _, m1, d1, o1, x1 = gpu_sample(text, shots, 3, postselect=post)
+    import paper_2607_28600_b300 as S
+    plan = S.symft_compile(text, postselect=post)
+    meas, det, obs, disc = S.sample_to_tensors(plan, shots, 3, plain=True)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(meas.cpu().numpy().view(np.uint64), m1)
+    np.testing.assert_array_equal(det.cpu().numpy().view(np.uint64), d1)
+    np.testing.assert_array_equal(obs.cpu().numpy().view(np.uint64), o1)
+    np.testing.assert_array_equal(disc.cpu().numpy().view(np.uint64), x1)
+
+
+@pytest.mark.parametrize("trial", range(4))
+def test_plain_form_fp64_matches_statevector(trial):
+    import paper_2607_28600_b300 as S
+    rng = random.Random(4000 + trial)
+    text = random_clifford_text(rng, rng.randint(2, 7), 60, rot=0.25)
+    plan = S.symft_compile(text)
+    shots = 300
+    meas, det, obs, disc = S.sample_to_tensors(plan, shots, trial + 11, precision=S.FP64, plain=True)
+    torch.cuda.synchronize()
+    o = oracle_sample(text, trial + 11, range(shots), kind="sv")
+    np.testing.assert_array_equal(unpack(meas.cpu().numpy().view(np.uint64), shots), o["records"])
+    np.testing.assert_array_equal(unpack(det.cpu().numpy().view(np.uint64), shots), o["dets"])
