@@ -187,3 +187,198 @@ def random_near_clifford(n: int, layers: int, n_rot: int, p: float = 1e-3,
             e.raw(f"R_PAULI({th!r}) {prod}")
     e.measure(list(range(n)), "Z")
     return e.text()
+
+
+# ---------------------------------------------------------------------------
+# [[15,1,3]] quantum Reed-Muller code and 15-to-1 distillation
+# ---------------------------------------------------------------------------
+
+def _rref_pivots(rows):
+    """Reduced row echelon form over GF(2); returns (rows, pivot columns)."""
+    rows = [list(r) for r in rows]
+    n = len(rows[0])
+    piv = []
+    r = 0
+    for col in range(n):
+        sel = None
+        for i in range(r, len(rows)):
+            if rows[i][col]:
+                sel = i
+                break
+        if sel is None:
+            continue
+        rows[r], rows[sel] = rows[sel], rows[r]
+        for i in range(len(rows)):
+            if i != r and rows[i][col]:
+                rows[i] = [a ^ b for a, b in zip(rows[i], rows[r])]
+        piv.append(col)
+        r += 1
+        if r == len(rows):
+            break
+    return rows, piv
+
+
+def reed_muller_15_encoder():
+    """CSS encoder of the [[15,1,3]] code (qubit v-1 <-> nonzero v in F_2^4).
+
+    X stabilizers: X on {v : v_i = 1}, i = 0..3; logical X = X on all 15.
+    Returns (stab_pivots, logical_pivot, cnots) such that: logical state on
+    logical_pivot, |+> on stab_pivots, |0> elsewhere, then the CNOTs (control,
+    target) in order, gives the encoded state.  The logical row (all-ones word
+    reduced against the stabilizer rows, so it is zero on their pivots) is
+    spread first; the stabilizer rows, which may cover the logical pivot,
+    follow.
+    """
+    gx = [[(v >> i) & 1 for v in range(1, 16)] for i in range(4)]
+    rows, piv = _rref_pivots(gx)
+    logical = [1] * 15
+    for r, p in zip(rows, piv):
+        if logical[p]:
+            logical = [a ^ b for a, b in zip(logical, r)]
+    lp = logical.index(1)
+    cnots = [(lp, j) for j in range(15) if j != lp and logical[j]]
+    for r, p in zip(rows, piv):
+        cnots += [(p, j) for j in range(15) if j != p and r[j]]
+    return piv, lp, cnots
+
+
+def distillation_15_to_1(p: float = 1e-3, variant: str = "literal") -> str:
+    """15-to-1 T-state distillation on 16 qubits (15 code qubits + output 15).
+
+    literal: 15 qubits in |+>, DEPOLARIZE1(p) then R_Z(pi/4) = exp(-i pi/8 Z)
+             on each, the Reed-Muller decoder (inverse encoder), 14 mid-circuit
+             Z measurements (detectors on the four X-type syndromes, the only
+             deterministic ones for ideal inputs), the logical moved to qubit
+             15 with record-controlled Z feedback, output measured in X.
+    encoded: |+_L> encoded first, then the noisy rotations (transversal T on
+             the encoded state), then the same decoder / measurement stage.
+    """
+    stab_piv, log_piv, cnots = reed_muller_15_encoder()
+    e = _Emitter(p)
+    qs = list(range(15))
+    e.reset(qs + [15])
+    if variant == "encoded":
+        e.g1("H", sorted(stab_piv + [log_piv]))
+        for c in cnots:              # sequential: the two row groups do not commute
+            e.cx([c])
+    elif variant == "literal":
+        e.g1("H", qs)
+    else:
+        raise ValueError(variant)
+    e.raw(f"DEPOLARIZE1({p!r}) " + " ".join(map(str, qs)) if p > 0 else "TICK")
+    e.raw(f"R_Z({PI / 4!r}) " + " ".join(map(str, qs)))
+    # decoder: inverse encoder
+    for c in reversed(cnots):
+        e.cx([c])
+    e.g1("H", sorted(stab_piv))
+    syn = [q for q in qs if q != log_piv]
+    base = e.nrec
+    e.measure(syn, "Z")
+    rec = {q: base + i for i, q in enumerate(syn)}
+    # literal: only the X-type syndromes (stabilizer pivots) are deterministic
+    # for ideal T|+> inputs; the encoded variant checks all fourteen
+    for q in (syn if variant == "encoded" else sorted(stab_piv)):
+        e.raw(f"DETECTOR rec[-{e.nrec - rec[q]}]")
+    # move the logical to the output qubit, with record-controlled Z feedback
+    e.cx([(log_piv, 15)])
+    e.cx([(15, log_piv)])
+    for q in stab_piv:
+        e.raw(f"CZ rec[-{e.nrec - rec[q]}] 15")
+    e.g1("H", [15])
+    e.measure([15], "Z")
+    e.raw("OBSERVABLE_INCLUDE(0) rec[-1]")
+    return e.text()
+
+
+# ---------------------------------------------------------------------------
+# cultivation-shaped circuit: d=3 color code, T-check layer, growth to d=9
+# ---------------------------------------------------------------------------
+
+COLOR_CODE_D3 = [(0, 1, 2, 3), (1, 2, 4, 5), (2, 3, 5, 6)]   # Steane plaquettes
+
+
+def cultivation_shaped(p: float = 1e-3, grow_d: int = 9, grow_rounds: int = 3,
+                       check_layers: int = 2, stage: str = "full") -> str:
+    """Cultivation-shaped near-Clifford circuit.
+
+    1. d=3 color code (7 data qubits 0..6), logical |+> prepared by measuring
+       the Z plaquettes of |+>^7, two rounds of X / Z plaquette checks (MPP),
+       detectors comparing rounds;
+    2. `check_layers` transversal check layers: exp(+i pi/8 Z) on each data
+       qubit, a logical X check (MPP X^7) and the plaquette checks, then
+       exp(-i pi/8 Z) on each data qubit; detectors on deterministic checks;
+    3. (stage "full") growth to a d=`grow_d` rotated surface code whose first
+       data qubits are the color-code qubits, `grow_rounds` rounds of its
+       stabilizer checks, detectors between consecutive grown rounds.
+    Noise: DEPOLARIZE1(p) on the data before every check, X_ERROR/Z_ERROR on
+    MPP results via DEPOLARIZE1 on the measured qubits.  Every detector is a
+    candidate for postselection.
+    """
+    e = _Emitter(p)
+    data = list(range(7))
+    e.reset(data)
+    e.g1("H", data)
+
+    def checks(prev):
+        cur = {}
+        for kind in ("X", "Z"):
+            for i, pl in enumerate(COLOR_CODE_D3):
+                if p > 0:
+                    e.raw(f"DEPOLARIZE1({p!r}) " + " ".join(map(str, pl)))
+                e.raw("MPP " + "*".join(f"{kind}{q}" for q in pl))
+                e.nrec += 1
+                cur[(kind, i)] = e.nrec - 1
+                if prev is not None and (kind, i) in prev:
+                    e.raw(f"DETECTOR rec[-1] rec[-{e.nrec - prev[(kind, i)]}]")
+        return cur
+
+    # round 0 fixes the random Z plaquettes; rounds 1..2 compare to it
+    prev = checks(None)
+    for _ in range(2):
+        prev = checks(prev)
+    for _ in range(check_layers):
+        e.raw(f"R_Z({PI / 4!r}) " + " ".join(map(str, data)))
+        if p > 0:
+            e.raw(f"DEPOLARIZE1({p!r}) " + " ".join(map(str, data)))
+        e.raw("MPP " + "*".join(f"X{q}" for q in data))
+        e.nrec += 1
+        prev = checks(prev)
+        e.raw(f"R_Z({-PI / 4!r}) " + " ".join(map(str, data)))
+    if stage != "full":
+        base = e.nrec
+        e.measure(data, "X")
+        e.raw("OBSERVABLE_INCLUDE(0) " + " ".join(f"rec[-{e.nrec - (base + i)}]" for i in range(7)))
+        return e.text()
+    # growth: a d=grow_d rotated surface code whose data qubits 0..6 are the
+    # color-code qubits; the other data qubits start in |0>
+    d = grow_d
+    plaqs = rotated_surface_code_layout(d)
+    new_data = list(range(7, d * d))
+    e.reset(new_data)
+    ancs = [a for _, _, a in plaqs]
+    xanc = [a for t, _, a in plaqs if t == "X"]
+    e.reset(ancs)
+    anc_rec = None
+    for rnd in range(grow_rounds):
+        e.g1("H", xanc)
+        for layer in range(4):
+            pairs = []
+            for typ, ds, a in plaqs:
+                dq = ds[layer]
+                if dq is None:
+                    continue
+                pairs.append((a, dq) if typ == "X" else (dq, a))
+            e.cx(pairs)
+        e.g1("H", xanc)
+        base = e.nrec
+        e.measure(ancs, "Z", reset=True)
+        cur = {a: base + i for i, a in enumerate(ancs)}
+        if anc_rec is not None:
+            for _, _, a in plaqs:
+                e.raw(f"DETECTOR rec[-{e.nrec - cur[a]}] rec[-{e.nrec - anc_rec[a]}]")
+        anc_rec = cur
+    base = e.nrec
+    dq = list(range(d * d))
+    e.measure(dq, "Z")
+    e.raw("OBSERVABLE_INCLUDE(0) " + " ".join(f"rec[-{e.nrec - (base + c)}]" for c in range(d)))
+    return e.text()

@@ -193,3 +193,44 @@ def test_plain_form_fp64_matches_statevector(trial):
     o = oracle_sample(text, trial + 11, range(shots), kind="sv")
     np.testing.assert_array_equal(unpack(meas.cpu().numpy().view(np.uint64), shots), o["records"])
     np.testing.assert_array_equal(unpack(det.cpu().numpy().view(np.uint64), shots), o["dets"])
+
+
+# ---- distillation and cultivation-shaped workloads ----
+
+@pytest.mark.parametrize("variant", ["encoded", "literal"])
+def test_distillation_fp64_matches_statevector(variant):
+    from paper_2607_28600_b300.workloads import distillation_15_to_1
+    text = distillation_15_to_1(1e-3, variant)
+    plan, g, o = _compare(text, 200, seed=4, precision=1, postselect=1, kind="sv")
+    assert plan.info["k_max"] == (15 if variant == "literal" else 5)
+    np.testing.assert_array_equal(g["discard"], o["discard"])
+    np.testing.assert_array_equal(g["records"], o["records"])
+    np.testing.assert_array_equal(g["obs"], o["obs"])
+
+
+@pytest.mark.parametrize("variant", ["encoded", "literal"])
+def test_distillation_fp32_flip_rate_vs_symft_oracle(variant):
+    from paper_2607_28600_b300.workloads import distillation_15_to_1
+    text = distillation_15_to_1(1e-3, variant)
+    _, g, o = _compare(text, 2000, seed=5, precision=0, postselect=1, kind="symft")
+    diff = (g["records"] != o["records"]).any(axis=1)
+    assert diff.mean() <= 0.005
+
+
+def test_cultivation_injection_stage_vs_statevector():
+    from paper_2607_28600_b300.workloads import cultivation_shaped
+    text = cultivation_shaped(1e-3, stage="injection")
+    _, g, o = _compare(text, 300, seed=6, precision=1, postselect=1, kind="sv")
+    np.testing.assert_array_equal(g["discard"], o["discard"])
+    np.testing.assert_array_equal(g["records"], o["records"])
+
+
+def test_cultivation_full_vs_symft_oracle_sampled():
+    from paper_2607_28600_b300.workloads import cultivation_shaped
+    text = cultivation_shaped(1e-3)
+    for prec in (1, 0):
+        plan, g, o = _compare(text, 400, seed=7, precision=prec, postselect=1, kind="symft")
+        assert plan.info["n_qubits"] == 161 and plan.info["k_max"] >= 4
+        diff = (g["records"] != o["records"]).any(axis=1)
+        assert diff.sum() <= (0 if prec == 1 else 2)
+        np.testing.assert_array_equal(g["discard"][~diff], o["discard"][~diff])
