@@ -160,6 +160,77 @@ def cpu_baseline(budget_s=12.0):
                       f"Aaronson-Gottesman tableau oracle in {dt:.1f} s on one host core"}
 
 
+NEAR_CLIFFORD = {
+    # name: (generator, postselect, shots per step)
+    "c1_surface_d3_r3_T": ("surface_t", 0, 100_000),
+    "c3_cultivation_d3_to_d9": ("cultivation", 1, 10_000_000),
+    "c4_distill_15to1_encoded": ("distill_encoded", 1, 10_000_000),
+    "c4_distill_15to1_literal": ("distill_literal", 1, 1_000_000),
+}
+
+
+def _near_clifford_text(kind):
+    from paper_2607_28600_b300.workloads import (cultivation_shaped, distillation_15_to_1,
+                                                 rotated_surface_code_memory)
+    if kind == "surface_t":
+        return rotated_surface_code_memory(3, 3, 1e-3, t_on_data0_after_round=0)
+    if kind == "cultivation":
+        return cultivation_shaped(1e-3)
+    if kind == "distill_encoded":
+        return distillation_15_to_1(1e-3, "encoded")
+    return distillation_15_to_1(1e-3, "literal")
+
+
+def measure_near_clifford(S, torch, dev, stream, steps, warmup, scale=1.0):
+    """FP32-batched vs FP64-plain (and FP64-batched) shots/s per near-Clifford config."""
+    out = {}
+    for name, (kind, post, shots0) in NEAR_CLIFFORD.items():
+        plan = S.symft_compile(_near_clifford_text(kind), postselect=post)
+        info = plan.info
+        entry = {"k_max": info["k_max"], "n_qubits": info["n_qubits"],
+                 "dense_instructions": sum(info["n_instr"][k] for k in
+                                           ("PromoteRot", "ActiveDiagRot", "ActivePairRot",
+                                            "ActiveDiagMeas", "ActivePairMeas")),
+                 "postselect": bool(post)}
+        for mode, prec, plain in (("fp32_batched", S.FP32, False), ("fp64_batched", S.FP64, False),
+                                  ("fp64_plain", S.FP64, True)):
+            shots = max(128, int(shots0 * scale * (0.1 if plain else 1.0)))
+            W = (shots + 63) // 64
+            meas = torch.empty((max(1, info["n_records"]), W), dtype=torch.int64, device=dev)
+            det = torch.empty((max(1, info["n_dets"]), W), dtype=torch.int64, device=dev)
+            obs = torch.empty((max(1, info["n_obs"]), W), dtype=torch.int64, device=dev)
+            disc = torch.empty((W,), dtype=torch.int64, device=dev)
+
+            def step(i):
+                S.symft_sample_ex(plan, shots, 100 + i, meas_out=meas, det_out=det, obs_out=obs,
+                                  discard_out=disc, precision=prec, plain=plain, stream=stream)
+            try:
+                for i in range(warmup):
+                    step(i)
+            except S.SymftError as e:
+                entry[mode] = {"unavailable": str(e)}
+                continue
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(steps):
+                step(warmup + i)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / steps
+            import numpy as np
+            words = disc.cpu().numpy().view(np.uint64)
+            entry[mode] = {"shots_per_step": shots, "ms_per_step": ms,
+                           "shots_per_s": shots / (ms / 1e3),
+                           "discard_rate": int(np.bitwise_count(words).sum()) / shots,
+                           "launches_per_step": S.symft_last_launch_count()}
+        if "shots_per_s" in entry.get("fp64_plain", {}) and "shots_per_s" in entry.get("fp32_batched", {}):
+            entry["fp32_batched_over_fp64_plain"] = (entry["fp32_batched"]["shots_per_s"] /
+                                                     entry["fp64_plain"]["shots_per_s"])
+        out[name] = entry
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -170,6 +241,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--only", default=None, help="run one workload (profiling)")
+    ap.add_argument("--no-near-clifford", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -238,6 +310,28 @@ def main():
             "n_channels": info["n_channels"], "n_records": info["n_records"],
             "n_dets": info["n_dets"],
         }
+        # the same circuit through the plain form (one CTA per shot), on fewer shots
+        pshots = max(128, shots // 20)
+        pW = (pshots + 63) // 64
+        pm = torch.empty((info["n_records"], pW), dtype=torch.int64, device=dev)
+        pd = torch.empty((info["n_dets"], pW), dtype=torch.int64, device=dev)
+        po = torch.empty((info["n_obs"], pW), dtype=torch.int64, device=dev)
+        for i in range(2):
+            S.symft_sample_ex(plan, pshots, 5 + i, meas_out=pm, det_out=pd, obs_out=po,
+                              precision=S.FP64, plain=True, stream=stream)
+        pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        psteps = 3
+        pe0.record(stream)
+        for i in range(psteps):
+            S.symft_sample_ex(plan, pshots, 50 + i, meas_out=pm, det_out=pd, obs_out=po,
+                              precision=S.FP64, plain=True, stream=stream)
+        pe1.record(stream)
+        torch.cuda.synchronize(dev)
+        pms = pe0.elapsed_time(pe1) / psteps
+        per_circuit[name]["fp64_plain"] = {"shots_per_step": pshots, "ms_per_step": pms,
+                                           "shots_per_s": pshots / (pms / 1e3)}
+        per_circuit[name]["batched_over_plain"] = per_circuit[name]["shots_per_s"] / (pshots / (pms / 1e3))
+        del pm, pd, po
         if name == HEADLINE:
             headline = dict(plan=plan, info=info, clk=clk.summary(), t_host=t_host,
                             kernel_ms=kernel_ms, out_bytes=out_bytes, ms_step=ms_step,
@@ -301,6 +395,8 @@ def main():
         "gpu_launches": h["launches"] * args.steps,
         "clocks": h["clk"],
     }
+    if not args.no_near_clifford and world == 1:
+        line["near_clifford"] = measure_near_clifford(S, torch, dev, stream, steps=5, warmup=3)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
