@@ -337,6 +337,32 @@ int sample_impl(symft_plan* P, const symft_sample_args* a) {
       d.use_smem = 0;
       smem = wpb * m3bytes + 16;
     }
+    if (h.k_max <= 5 && dense_reg_smem_bytes(P->dp) <= 96 * 1024) {
+      // register-resident form: lane x holds amplitude x
+      const uint64_t want_r = (a->shots + 7) / 8;
+      const uint64_t cap_r = static_cast<uint64_t>(P->sm_count) * 8;
+      CUDA_TRY(launch_dense_reg(d, fp64, static_cast<int>(std::max<uint64_t>(1, std::min(want_r, cap_r))), st));
+      ++launches;
+      goto dense_done;
+    }
+    if (!d.use_smem) {
+      // large k: one CTA per shot, vector in shared memory up to ~200 KB, else a
+      // global slot per resident CTA (sized to stay L2-resident)
+      const bool in_smem = dense_cta_smem_bytes(P->dp, vec_bytes, true) <= 200 * 1024;
+      const size_t csmem = dense_cta_smem_bytes(P->dp, vec_bytes, in_smem);
+      int grid_c = P->sm_count * (in_smem ? 1 : 2);
+      grid_c = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(a->shots, grid_c)));
+      d.use_smem = in_smem ? 1 : 0;
+      if (!in_smem) {
+        d.gvec_stride = static_cast<uint64_t>(1) << h.k_max;
+        CUDA_TRY(P->gvec.ensure(static_cast<size_t>(grid_c) * vec_bytes));
+        d.gvec = P->gvec.ptr;
+      }
+      CUDA_TRY(launch_dense_cta(d, fp64, grid_c, csmem, st));
+      ++launches;
+      goto dense_done;
+    }
+    {
     uint64_t want = (a->shots + wpb - 1) / wpb;
     uint64_t cap = static_cast<uint64_t>(P->sm_count) * (d.use_smem ? 16 : 8);
     if (!d.use_smem) {
@@ -352,6 +378,8 @@ int sample_impl(symft_plan* P, const symft_sample_args* a) {
     }
     CUDA_TRY(launch_dense(d, fp64, wpb, grid, smem, st));
     ++launches;
+    }
+  dense_done:;
   }
   // --- finalize ------------------------------------------------------------
   if (!a->plain && need_final) {

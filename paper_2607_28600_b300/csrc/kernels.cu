@@ -609,6 +609,346 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
 }
 
 // ---------------------------------------------------------------------------
+// Register-resident dense executor for k_max <= 5: one warp per shot, lane x
+// holds amplitude alpha_x (zero beyond 2^k); PromoteRot, pair partners and
+// compaction sources are warp shuffles.  The instruction stream sits in shared
+// memory and each shot's exogenous sign bits are fetched in one coalesced pass.
+// ---------------------------------------------------------------------------
+constexpr int kRegWarps = 8;
+
+template <typename Real>
+__device__ __forceinline__ Real shfl_r(Real v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) {
+  extern __shared__ __align__(16) unsigned char rsm[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const uint32_t G = A.p.n_dense;
+  const uint32_t sgw = (G + 31) / 32;
+  const uint32_t m3w = (A.p.n_m3 + 31) / 32;
+  DenseInstrDev* ins = reinterpret_cast<DenseInstrDev*>(rsm);
+  uint32_t* sgn = reinterpret_cast<uint32_t*>(rsm + (size_t)G * sizeof(DenseInstrDev)) + (size_t)warp * (sgw + m3w);
+  uint32_t* m3b = sgn + sgw;
+  for (uint32_t i = threadIdx.x; i < G * (sizeof(DenseInstrDev) / 4); i += blockDim.x)
+    reinterpret_cast<uint32_t*>(ins)[i] = reinterpret_cast<const uint32_t*>(A.p.dense)[i];
+  __syncthreads();
+
+  for (uint64_t r = (uint64_t)blockIdx.x * kRegWarps + warp; r < A.shots; r += (uint64_t)gridDim.x * kRegWarps) {
+    const uint64_t rg = A.shot0 + r;
+    const uint64_t w = r >> 6;
+    const uint32_t bitpos = (uint32_t)(r & 63);
+    // exogenous sign bits of this shot, 32 instructions per ballot
+    for (uint32_t base = 0; base < G; base += 32) {
+      const uint32_t g = base + lane;
+      bool bit = false;
+      if (g < G) bit = (__ldg(A.signs + (uint64_t)ins[g].sign_target_col * A.W + w) >> bitpos) & 1ull;
+      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+      if (lane == 0) sgn[base >> 5] = bal;
+    }
+    for (uint32_t i = lane; i < m3w; i += 32) m3b[i] = 0u;
+    __syncwarp();
+    Real re = lane == 0 ? (Real)1 : (Real)0, im = (Real)0;
+    uint32_t k = 0;
+    for (uint32_t g = 0; g < G; ++g) {
+      const DenseInstrDev& I = ins[g];
+      uint32_t lam = (sgn[g >> 5] >> (g & 31)) & 1u;
+      for (uint32_t q = 0; q < I.causal_n; ++q) {
+        const uint32_t j = __ldg(A.p.dense_causal + I.causal_off + q);
+        lam ^= (m3b[j >> 5] >> (j & 31)) & 1u;
+      }
+      const Real sg = lam ? (Real)-1 : (Real)1;
+      const Real c = (Real)I.c, s = (Real)I.s;
+      const uint32_t n = 1u << k;
+      if (I.kind == 0) {                       // PromoteRot
+        const int src = lane >= (int)n ? lane - (int)n : lane;
+        const Real ore = shfl_r(re, src), oim = shfl_r(im, src);
+        if ((uint32_t)lane < n) {
+          re *= c;
+          im *= c;
+        } else if ((uint32_t)lane < 2 * n) {
+          re = sg * s * oim;                   // -i sg s alpha
+          im = -sg * s * ore;
+        }
+        ++k;
+      } else if (I.kind == 1) {                // ActiveDiagRot
+        const Real mu = I.mu == 0 ? (Real)1 : (Real)-1;
+        const Real f = sg * mu * s * ((__popc((uint32_t)lane & I.b) & 1) ? (Real)-1 : (Real)1);
+        const Real nre = c * re + f * im, nim = c * im - f * re;
+        re = nre;
+        im = nim;
+      } else if (I.kind == 2) {                // ActivePairRot
+        Real cr, ci;                           // -i * i^mu
+        switch (I.mu & 3) {
+          case 0: cr = 0; ci = -1; break;
+          case 1: cr = 1; ci = 0; break;
+          case 2: cr = 0; ci = 1; break;
+          default: cr = -1; ci = 0; break;
+        }
+        const int partner = lane ^ (int)I.a;
+        const Real pre = shfl_r(re, partner & 31), pim = shfl_r(im, partner & 31);
+        const Real sp = ((__popc((uint32_t)partner & I.b) & 1) ? (Real)-1 : (Real)1) * sg * s;
+        const Real nre = c * re + sp * (cr * pre - ci * pim), nim = c * im + sp * (cr * pim + ci * pre);
+        if ((uint32_t)lane < n) {
+          re = nre;
+          im = nim;
+        }
+      } else {                                 // active measurements
+        const int h = I.h;
+        const uint32_t half = n >> 1;
+        const Real inv_sqrt2 = (Real)0.70710678118654752440;
+        double S0 = 0.0, S1 = 0.0;
+        // diag: partition by parity(b.x); pair: beta_z(y) from (u0, u0^a)
+        Real b0re = 0, b0im = 0, b1re = 0, b1im = 0;
+        const uint32_t z = (uint32_t)lane;
+        const uint32_t u0 = insert_bit(z & (half - 1 + (half == 0)), h, 0u);
+        Real mcr = 0, mci = 0;
+        if (I.kind == 5) {
+          if ((uint32_t)lane < n) {
+            const double v = (double)re * re + (double)im * im;
+            if (__popc((uint32_t)lane & I.b) & 1) S1 = v; else S0 = v;
+          }
+        } else {
+          switch (I.mu & 3) {
+            case 0: mcr = 1; mci = 0; break;
+            case 1: mcr = 0; mci = -1; break;
+            case 2: mcr = -1; mci = 0; break;
+            default: mcr = 0; mci = 1; break;
+          }
+          const Real a0re = shfl_r(re, (int)(u0 & 31)), a0im = shfl_r(im, (int)(u0 & 31));
+          const Real a1re = shfl_r(re, (int)((u0 ^ I.a) & 31)), a1im = shfl_r(im, (int)((u0 ^ I.a) & 31));
+          const Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
+          const Real tr = sb * (mcr * a1re - mci * a1im), ti = sb * (mcr * a1im + mci * a1re);
+          b0re = (a0re + tr) * inv_sqrt2; b0im = (a0im + ti) * inv_sqrt2;
+          b1re = (a0re - tr) * inv_sqrt2; b1im = (a0im - ti) * inv_sqrt2;
+          if (z < half) {
+            S0 = (double)b0re * b0re + (double)b0im * b0im;
+            S1 = (double)b1re * b1re + (double)b1im * b1im;
+          }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+          S0 += __shfl_xor_sync(0xffffffffu, S0, o);
+          S1 += __shfl_xor_sync(0xffffffffu, S1, o);
+        }
+        const uint32_t l0 = I.kind == 5 ? (lam ^ (uint32_t)I.eta) : lam;
+        const double p0 = (l0 ? S1 : S0) / (S0 + S1);
+        uint32_t m = 0;
+        if (lane == 0) m = meas_uniform(A.seed, I.t, rg) < p0 ? 0u : 1u;
+        m = __shfl_sync(0xffffffffu, m, 0);
+        const uint32_t lab = l0 ^ m;
+        const Real scale = (Real)(1.0 / sqrt(lab ? S1 : S0));
+        if (I.kind == 5) {
+          const uint32_t u = insert_bit(z & (half - 1 + (half == 0)), h, lab);
+          const uint32_t x = u ^ ((uint32_t)(__popc(u & I.b & ~(1u << h)) & 1) << h);
+          const Real nre = shfl_r(re, (int)(x & 31)), nim = shfl_r(im, (int)(x & 31));
+          re = z < half ? nre * scale : (Real)0;
+          im = z < half ? nim * scale : (Real)0;
+        } else {
+          re = z < half ? (lab ? b1re : b0re) * scale : (Real)0;
+          im = z < half ? (lab ? b1im : b0im) * scale : (Real)0;
+        }
+        --k;
+        if (m && lane == 0) {
+          m3b[I.m3 >> 5] |= 1u << (I.m3 & 31);
+          atomicOr(reinterpret_cast<unsigned long long*>(A.m3_out) + (uint64_t)I.m3 * A.W + w,
+                   1ull << bitpos);
+        }
+        __syncwarp();
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CTA-per-shot dense executor for large k: the whole CTA works on one shot's
+// vector, held in shared memory when it fits and otherwise in a per-CTA slot
+// of a global workspace small enough to stay in L2 (one slot per resident CTA).
+// ---------------------------------------------------------------------------
+constexpr int kCtaThreads = 256;
+
+template <typename Real>
+__global__ void __launch_bounds__(kCtaThreads) dense_cta_kernel(DenseArgs A) {
+  extern __shared__ __align__(16) unsigned char csm[];
+  const uint32_t tid = threadIdx.x;
+  const uint32_t G = A.p.n_dense;
+  const uint32_t m3w = (A.p.n_m3 + 31) / 32;
+  uint32_t* m3b = reinterpret_cast<uint32_t*>(csm);
+  double* red = reinterpret_cast<double*>(csm + align16(m3w * 4 + 16));
+  int* bcast = reinterpret_cast<int*>(red + 2 * (kCtaThreads / 32));
+  Cplx<Real>* vec = A.use_smem
+                        ? reinterpret_cast<Cplx<Real>*>(csm + align16(m3w * 4 + 16) + align16(2 * (kCtaThreads / 32) * 8 + 16))
+                        : reinterpret_cast<Cplx<Real>*>(A.gvec) + (uint64_t)blockIdx.x * A.gvec_stride;
+  for (uint64_t r = blockIdx.x; r < A.shots; r += gridDim.x) {
+    const uint64_t rg = A.shot0 + r;
+    const uint64_t w = r >> 6;
+    const uint64_t bitmask = 1ull << (r & 63);
+    for (uint32_t i = tid; i < m3w; i += blockDim.x) m3b[i] = 0u;
+    if (tid == 0) {
+      vec[0].re = (Real)1;
+      vec[0].im = (Real)0;
+    }
+    __syncthreads();
+    uint32_t k = 0;
+    for (uint32_t g = 0; g < G; ++g) {
+      const DenseInstrDev I = A.p.dense[g];
+      if (tid == 0) {
+        uint32_t lam = (uint32_t)((__ldg(A.signs + (uint64_t)I.sign_target_col * A.W + w) & bitmask) != 0);
+        for (uint32_t q = 0; q < I.causal_n; ++q) {
+          const uint32_t j = __ldg(A.p.dense_causal + I.causal_off + q);
+          lam ^= (m3b[j >> 5] >> (j & 31)) & 1u;
+        }
+        bcast[0] = (int)lam;
+      }
+      __syncthreads();
+      const uint32_t lam = (uint32_t)bcast[0];
+      const Real sg = lam ? (Real)-1 : (Real)1;
+      const Real c = (Real)I.c, s = (Real)I.s;
+      const uint32_t n = 1u << k;
+      if (I.kind == 0) {
+        for (uint32_t x = tid; x < n; x += blockDim.x) {
+          Cplx<Real> v = vec[x], hi;
+          hi.re = sg * s * v.im;
+          hi.im = -sg * s * v.re;
+          vec[x + n] = hi;
+          v.re *= c;
+          v.im *= c;
+          vec[x] = v;
+        }
+        ++k;
+      } else if (I.kind == 1) {
+        const Real mu = I.mu == 0 ? (Real)1 : (Real)-1;
+        for (uint32_t x = tid; x < n; x += blockDim.x) {
+          const Real f = sg * mu * s * ((__popc(x & I.b) & 1) ? (Real)-1 : (Real)1);
+          const Cplx<Real> v = vec[x];
+          Cplx<Real> o;
+          o.re = c * v.re + f * v.im;
+          o.im = c * v.im - f * v.re;
+          vec[x] = o;
+        }
+      } else if (I.kind == 2) {
+        const int pb = 31 - __clz(I.a);
+        Real cr, ci;
+        switch (I.mu & 3) {
+          case 0: cr = 0; ci = -1; break;
+          case 1: cr = 1; ci = 0; break;
+          case 2: cr = 0; ci = 1; break;
+          default: cr = -1; ci = 0; break;
+        }
+        cr *= sg * s;
+        ci *= sg * s;
+        for (uint32_t z = tid; z < (n >> 1); z += blockDim.x) {
+          const uint32_t x0 = insert_bit(z, pb, 0u), x1 = x0 ^ I.a;
+          const Cplx<Real> v0 = vec[x0], v1 = vec[x1];
+          const Real s1 = (__popc(x1 & I.b) & 1) ? (Real)-1 : (Real)1;
+          const Real s0 = (__popc(x0 & I.b) & 1) ? (Real)-1 : (Real)1;
+          Cplx<Real> o0, o1;
+          o0.re = c * v0.re + s1 * (cr * v1.re - ci * v1.im);
+          o0.im = c * v0.im + s1 * (cr * v1.im + ci * v1.re);
+          o1.re = c * v1.re + s0 * (cr * v0.re - ci * v0.im);
+          o1.im = c * v1.im + s0 * (cr * v0.im + ci * v0.re);
+          vec[x0] = o0;
+          vec[x1] = o1;
+        }
+      } else {
+        const int h = I.h;
+        const Real inv_sqrt2 = (Real)0.70710678118654752440;
+        Real mcr = 0, mci = 0;
+        if (I.kind == 6) {
+          switch (I.mu & 3) {
+            case 0: mcr = 1; mci = 0; break;
+            case 1: mcr = 0; mci = -1; break;
+            case 2: mcr = -1; mci = 0; break;
+            default: mcr = 0; mci = 1; break;
+          }
+        }
+        double S0 = 0.0, S1 = 0.0;
+        if (I.kind == 5) {
+          for (uint32_t x = tid; x < n; x += blockDim.x) {
+            const double v = norm2(vec[x]);
+            if (__popc(x & I.b) & 1) S1 += v; else S0 += v;
+          }
+        } else {
+          for (uint32_t z = tid; z < (n >> 1); z += blockDim.x) {
+            const uint32_t u0 = insert_bit(z, h, 0u);
+            const Cplx<Real> a0 = vec[u0], a1 = vec[u0 ^ I.a];
+            const Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
+            const Real tr = sb * (mcr * a1.re - mci * a1.im), tim = sb * (mcr * a1.im + mci * a1.re);
+            Cplx<Real> b0, b1;
+            b0.re = (a0.re + tr) * inv_sqrt2; b0.im = (a0.im + tim) * inv_sqrt2;
+            b1.re = (a0.re - tr) * inv_sqrt2; b1.im = (a0.im - tim) * inv_sqrt2;
+            S0 += norm2(b0);
+            S1 += norm2(b1);
+          }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+          S0 += __shfl_xor_sync(0xffffffffu, S0, o);
+          S1 += __shfl_xor_sync(0xffffffffu, S1, o);
+        }
+        if ((tid & 31) == 0) {
+          red[tid >> 5] = S0;
+          red[kCtaThreads / 32 + (tid >> 5)] = S1;
+        }
+        __syncthreads();
+        S0 = 0.0;
+        S1 = 0.0;
+        for (int w2 = 0; w2 < kCtaThreads / 32; ++w2) {
+          S0 += red[w2];
+          S1 += red[kCtaThreads / 32 + w2];
+        }
+        const uint32_t l0 = I.kind == 5 ? (lam ^ (uint32_t)I.eta) : lam;
+        const double p0 = (l0 ? S1 : S0) / (S0 + S1);
+        if (tid == 0) {
+          const uint32_t m = meas_uniform(A.seed, I.t, rg) < p0 ? 0u : 1u;
+          bcast[1] = (int)m;
+          if (m) {
+            m3b[I.m3 >> 5] |= 1u << (I.m3 & 31);
+            atomicOr(reinterpret_cast<unsigned long long*>(A.m3_out) + (uint64_t)I.m3 * A.W + w,
+                     (unsigned long long)bitmask);
+          }
+        }
+        __syncthreads();
+        const uint32_t m = (uint32_t)bcast[1];
+        const uint32_t lab = l0 ^ m;
+        const Real scale = (Real)(1.0 / sqrt(lab ? S1 : S0));
+        const uint32_t half = n >> 1;
+        for (uint32_t z0 = 0; z0 < half; z0 += blockDim.x) {
+          const uint32_t z = z0 + tid;
+          Cplx<Real> v;
+          v.re = 0;
+          v.im = 0;
+          if (z < half) {
+            if (I.kind == 5) {
+              const uint32_t u = insert_bit(z, h, lab);
+              v = vec[u ^ ((uint32_t)(__popc(u & I.b & ~(1u << h)) & 1) << h)];
+            } else {
+              const uint32_t u0 = insert_bit(z, h, 0u);
+              const Cplx<Real> a0 = vec[u0], a1 = vec[u0 ^ I.a];
+              Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
+              if (lab) sb = -sb;
+              const Real tr = sb * (mcr * a1.re - mci * a1.im), tim = sb * (mcr * a1.im + mci * a1.re);
+              v.re = (a0.re + tr) * inv_sqrt2;
+              v.im = (a0.im + tim) * inv_sqrt2;
+            }
+            v.re *= scale;
+            v.im *= scale;
+          }
+          __syncthreads();
+          if (z < half) vec[z] = v;
+          __syncthreads();
+        }
+        --k;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Plain form (the paper's GPU design rebuilt, for comparison): one CTA per
 // shot; the shot draws its own noise components and random bits from the
 // same streams, evaluates every sign unpacked from its full symbol list, runs
@@ -1028,6 +1368,35 @@ cudaError_t launch_dense_t(const DenseArgs& a, int warps_per_block, int grid, si
     if (e != cudaSuccess) return e;
   }
   dense_kernel<Real><<<grid, warps_per_block * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+size_t dense_cta_smem_bytes(const DevPlan& p, size_t vec_bytes, bool vec_in_smem) {
+  return align16(((p.n_m3 + 31) / 32) * 4 + 16) + align16(2 * (kCtaThreads / 32) * 8 + 16) +
+         (vec_in_smem ? vec_bytes : 0);
+}
+
+cudaError_t launch_dense_cta(const DenseArgs& a, bool fp64, int grid, size_t smem, cudaStream_t st) {
+  const void* fn = fp64 ? (const void*)dense_cta_kernel<double> : (const void*)dense_cta_kernel<float>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (fp64) dense_cta_kernel<double><<<grid, kCtaThreads, smem, st>>>(a);
+  else dense_cta_kernel<float><<<grid, kCtaThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+size_t dense_reg_smem_bytes(const DevPlan& p) {
+  const size_t G = p.n_dense;
+  return G * sizeof(DenseInstrDev) + (size_t)kRegWarps * (((G + 31) / 32) + ((p.n_m3 + 31) / 32)) * 4 + 16;
+}
+
+cudaError_t launch_dense_reg(const DenseArgs& a, bool fp64, int grid, cudaStream_t st) {
+  const size_t smem = dense_reg_smem_bytes(a.p);
+  const void* fn = fp64 ? (const void*)dense_reg_kernel<double> : (const void*)dense_reg_kernel<float>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (fp64) dense_reg_kernel<double><<<grid, kRegWarps * 32, smem, st>>>(a);
+  else dense_reg_kernel<float><<<grid, kRegWarps * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 

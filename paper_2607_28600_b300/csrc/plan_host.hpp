@@ -44,6 +44,10 @@ cudaError_t launch_dense(const DenseArgs& a, bool fp64, int warps_per_block, int
                          cudaStream_t st);
 cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t st);
 size_t plain_smem_bytes(const DevPlan& p, uint32_t kmax, bool fp64);
+size_t dense_reg_smem_bytes(const DevPlan& p);
+size_t dense_cta_smem_bytes(const DevPlan& p, size_t vec_bytes, bool vec_in_smem);
+cudaError_t launch_dense_cta(const DenseArgs& a, bool fp64, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_dense_reg(const DenseArgs& a, bool fp64, int grid, cudaStream_t st);
 cudaError_t launch_plain(const PlainArgs& a, bool fp64, int grid, cudaStream_t st);
 
 }  // namespace symft
