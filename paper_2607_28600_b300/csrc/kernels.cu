@@ -414,6 +414,81 @@ __device__ __forceinline__ double norm2(Cplx<Real> v) {
   return (double)v.re * (double)v.re + (double)v.im * (double)v.im;
 }
 
+// U = u * 2^53 of the shared measurement rule: an integer below 2^53
+__device__ __forceinline__ uint64_t meas_U(uint64_t seed, uint32_t t, uint64_t r) {
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  const uint64_t w = r >> 6;
+  const uint4 ob = philox(make_uint4(t, (uint32_t)(w >> 1), (uint32_t)(w >> 33), kTagMbit), k0, k1);
+  const uint64_t word = (w & 1) ? ((uint64_t)ob.z | ((uint64_t)ob.w << 32)) : ((uint64_t)ob.x | ((uint64_t)ob.y << 32));
+  const uint64_t bit = (word >> (r & 63)) & 1ull;
+  const uint4 of = philox(make_uint4(t, (uint32_t)(r >> 1), (uint32_t)(r >> 33), kTagMfrac), k0, k1);
+  const uint64_t fw = (r & 1) ? ((uint64_t)of.z | ((uint64_t)of.w << 32)) : ((uint64_t)of.x | ((uint64_t)of.y << 32));
+  return (bit << 52) + (fw >> 12);
+}
+
+// recorded bit: 0 iff u < p0, i.e. U < p0 * 2^53 (both sides exact in FP64)
+__device__ __forceinline__ uint32_t decide64(uint64_t U, double p0) {
+  return (double)U < p0 * 9007199254740992.0 ? 0u : 1u;
+}
+
+// the same rule for an FP32 p0, in integers: U < p0 * 2^53 <=> U < ceil(p0 * 2^53)
+__device__ __forceinline__ uint32_t decide32(uint64_t U, float p0) {
+  if (!(p0 > 0.0f)) return 1u;
+  if (p0 >= 1.0f) return 0u;
+  const uint32_t bits = __float_as_uint(p0);
+  const int e = (int)((bits >> 23) & 0xFFu);
+  uint64_t mant;
+  int shift;                                   // p0 * 2^53 = mant * 2^shift
+  if (e == 0) {
+    mant = bits & 0x7FFFFFu;
+    shift = -149 + 53;
+  } else {
+    mant = (bits & 0x7FFFFFu) | 0x800000u;
+    shift = e - 127 - 23 + 53;                 // <= 29 since p0 < 1
+  }
+  uint64_t T;
+  if (shift >= 0) T = mant << shift;
+  else if (-shift >= 40) T = 1;                // 0 < p0 * 2^53 < 1
+  else T = (mant + ((1ull << -shift) - 1)) >> -shift;
+  return U < T ? 0u : 1u;
+}
+
+template <typename Acc>
+__device__ __forceinline__ void warp_sum2(Acc& a, Acc& b) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+}
+
+// Branch sums of an active measurement over this thread's share of the vector:
+// diagonal -> S_y over parity(b.x) = y; pair -> S_y = sum_z |beta_z(y)|^2.
+template <typename Real, typename Acc>
+__device__ __forceinline__ void branch_sums(const Cplx<Real>* vec, const DenseInstrDev& I, uint32_t n,
+                                            uint32_t start, uint32_t stride, Real mcr, Real mci,
+                                            Acc& S0, Acc& S1) {
+  const Real inv_sqrt2 = (Real)0.70710678118654752440;
+  if (I.kind == 5) {
+    for (uint32_t x = start; x < n; x += stride) {
+      const Cplx<Real> a = vec[x];
+      const Acc v = (Acc)a.re * (Acc)a.re + (Acc)a.im * (Acc)a.im;
+      if (__popc(x & I.b) & 1) S1 += v; else S0 += v;
+    }
+  } else {
+    for (uint32_t z = start; z < (n >> 1); z += stride) {
+      const uint32_t u0 = insert_bit(z, I.h, 0u);
+      const Cplx<Real> a0 = vec[u0], a1 = vec[u0 ^ I.a];
+      const Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
+      const Real tr = sb * (mcr * a1.re - mci * a1.im), ti = sb * (mcr * a1.im + mci * a1.re);
+      const Real b0r = (a0.re + tr) * inv_sqrt2, b0i = (a0.im + ti) * inv_sqrt2;
+      const Real b1r = (a0.re - tr) * inv_sqrt2, b1i = (a0.im - ti) * inv_sqrt2;
+      S0 += (Acc)b0r * (Acc)b0r + (Acc)b0i * (Acc)b0i;
+      S1 += (Acc)b1r * (Acc)b1r + (Acc)b1i * (Acc)b1i;
+    }
+  }
+}
+
 template <typename Real>
 __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
   extern __shared__ unsigned char dsm[];
@@ -516,7 +591,6 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
         case 5:
         case 6: {  // active measurements
           const int h = I.h;
-          double S0 = 0.0, S1 = 0.0;   // by effective label y (pair) / parity (diag)
           const Real inv_sqrt2 = (Real)0.70710678118654752440;
           Real mcr = 0, mci = 0;       // conj(mu)
           if (I.kind == 6) {
@@ -527,40 +601,26 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
               default: mcr = 0; mci = 1; break;
             }
           }
-          if (I.kind == 5) {
-            for (uint32_t x = lane; x < n; x += 32) {
-              double v = norm2(vec[x]);
-              if (__popc(x & I.b) & 1) S1 += v; else S0 += v;
-            }
-          } else {
-            for (uint32_t z = lane; z < (n >> 1); z += 32) {
-              uint32_t u0 = insert_bit(z, h, 0u);
-              Cplx<Real> a0 = vec[u0], a1 = vec[u0 ^ I.a];
-              Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
-              // t = conj(mu) (-1)^{b.u0} a1 ; beta(y) = (a0 + (-1)^y t)/sqrt2
-              Real tr = sb * (mcr * a1.re - mci * a1.im), ti = sb * (mcr * a1.im + mci * a1.re);
-              Cplx<Real> b0, b1;
-              b0.re = (a0.re + tr) * inv_sqrt2; b0.im = (a0.im + ti) * inv_sqrt2;
-              b1.re = (a0.re - tr) * inv_sqrt2; b1.im = (a0.im - ti) * inv_sqrt2;
-              S0 += norm2(b0);
-              S1 += norm2(b1);
-            }
-          }
-#pragma unroll
-          for (int off = 16; off; off >>= 1) {
-            S0 += __shfl_xor_sync(0xffffffffu, S0, off);
-            S1 += __shfl_xor_sync(0xffffffffu, S1, off);
-          }
           // label for m = 0: diag -> parity lam^eta ; pair -> y = lam
           const uint32_t l0 = I.kind == 5 ? (lam ^ (uint32_t)I.eta) : lam;
-          const double Sl0 = l0 ? S1 : S0;
-          const double p0 = Sl0 / (S0 + S1);
           uint32_t m = 0;
-          if (lane == 0) m = meas_uniform(A.seed, I.t, rg) < p0 ? 0u : 1u;
-          m = __shfl_sync(0xffffffffu, m, 0);
+          Real scale;
+          if (sizeof(Real) == 8 || n >= (1u << 14)) {      // FP64 sums
+            double S0 = 0.0, S1 = 0.0;
+            branch_sums<Real, double>(vec, I, n, lane, 32, mcr, mci, S0, S1);
+            warp_sum2(S0, S1);
+            if (lane == 0) m = decide64(meas_U(A.seed, I.t, rg), (l0 ? S1 : S0) / (S0 + S1));
+            m = __shfl_sync(0xffffffffu, m, 0);
+            scale = (Real)(1.0 / sqrt((l0 ^ m) ? S1 : S0));
+          } else {                                         // FP32 sums below 2^14 terms
+            float S0 = 0.0f, S1 = 0.0f;
+            branch_sums<Real, float>(vec, I, n, lane, 32, mcr, mci, S0, S1);
+            warp_sum2(S0, S1);
+            if (lane == 0) m = decide32(meas_U(A.seed, I.t, rg), (l0 ? S1 : S0) / (S0 + S1));
+            m = __shfl_sync(0xffffffffu, m, 0);
+            scale = (Real)rsqrtf((l0 ^ m) ? S1 : S0);
+          }
           const uint32_t lab = l0 ^ m;
-          const double Sm = lab ? S1 : S0;
-          const Real scale = (Real)(1.0 / sqrt(Sm));
           // in-place compaction in increasing z order (sources are never below z)
           const uint32_t half = n >> 1;
           for (uint32_t z0 = 0; z0 < half; z0 += 32) {
@@ -699,16 +759,16 @@ __global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) 
         const int h = I.h;
         const uint32_t half = n >> 1;
         const Real inv_sqrt2 = (Real)0.70710678118654752440;
-        double S0 = 0.0, S1 = 0.0;
         // diag: partition by parity(b.x); pair: beta_z(y) from (u0, u0^a)
         Real b0re = 0, b0im = 0, b1re = 0, b1im = 0;
         const uint32_t z = (uint32_t)lane;
         const uint32_t u0 = insert_bit(z & (half - 1 + (half == 0)), h, 0u);
         Real mcr = 0, mci = 0;
+        Real s0 = 0, s1 = 0;                   // this lane's share (one amplitude)
         if (I.kind == 5) {
           if ((uint32_t)lane < n) {
-            const double v = (double)re * re + (double)im * im;
-            if (__popc((uint32_t)lane & I.b) & 1) S1 = v; else S0 = v;
+            const Real v = re * re + im * im;
+            if (__popc((uint32_t)lane & I.b) & 1) s1 = v; else s0 = v;
           }
         } else {
           switch (I.mu & 3) {
@@ -724,22 +784,23 @@ __global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) 
           b0re = (a0re + tr) * inv_sqrt2; b0im = (a0im + ti) * inv_sqrt2;
           b1re = (a0re - tr) * inv_sqrt2; b1im = (a0im - ti) * inv_sqrt2;
           if (z < half) {
-            S0 = (double)b0re * b0re + (double)b0im * b0im;
-            S1 = (double)b1re * b1re + (double)b1im * b1im;
+            s0 = b0re * b0re + b0im * b0im;
+            s1 = b1re * b1re + b1im * b1im;
           }
         }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-          S0 += __shfl_xor_sync(0xffffffffu, S0, o);
-          S1 += __shfl_xor_sync(0xffffffffu, S1, o);
-        }
+        // at most 32 terms: sums in the vector's own precision
+        warp_sum2(s0, s1);
         const uint32_t l0 = I.kind == 5 ? (lam ^ (uint32_t)I.eta) : lam;
-        const double p0 = (l0 ? S1 : S0) / (S0 + S1);
         uint32_t m = 0;
-        if (lane == 0) m = meas_uniform(A.seed, I.t, rg) < p0 ? 0u : 1u;
+        if (lane == 0) {
+          const uint64_t U = meas_U(A.seed, I.t, rg);
+          m = sizeof(Real) == 8 ? decide64(U, (double)(l0 ? s1 : s0) / (double)(s0 + s1))
+                                : decide32(U, (float)((l0 ? s1 : s0) / (s0 + s1)));
+        }
         m = __shfl_sync(0xffffffffu, m, 0);
         const uint32_t lab = l0 ^ m;
-        const Real scale = (Real)(1.0 / sqrt(lab ? S1 : S0));
+        const Real scale = sizeof(Real) == 8 ? (Real)(1.0 / sqrt((double)(lab ? s1 : s0)))
+                                             : (Real)rsqrtf((float)(lab ? s1 : s0));
         if (I.kind == 5) {
           const uint32_t u = insert_bit(z & (half - 1 + (half == 0)), h, lab);
           const uint32_t x = u ^ ((uint32_t)(__popc(u & I.b & ~(1u << h)) & 1) << h);
@@ -865,29 +926,17 @@ __global__ void __launch_bounds__(kCtaThreads) dense_cta_kernel(DenseArgs A) {
             default: mcr = 0; mci = 1; break;
           }
         }
+        const uint32_t l0 = I.kind == 5 ? (lam ^ (uint32_t)I.eta) : lam;
         double S0 = 0.0, S1 = 0.0;
-        if (I.kind == 5) {
-          for (uint32_t x = tid; x < n; x += blockDim.x) {
-            const double v = norm2(vec[x]);
-            if (__popc(x & I.b) & 1) S1 += v; else S0 += v;
-          }
-        } else {
-          for (uint32_t z = tid; z < (n >> 1); z += blockDim.x) {
-            const uint32_t u0 = insert_bit(z, h, 0u);
-            const Cplx<Real> a0 = vec[u0], a1 = vec[u0 ^ I.a];
-            const Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
-            const Real tr = sb * (mcr * a1.re - mci * a1.im), tim = sb * (mcr * a1.im + mci * a1.re);
-            Cplx<Real> b0, b1;
-            b0.re = (a0.re + tr) * inv_sqrt2; b0.im = (a0.im + tim) * inv_sqrt2;
-            b1.re = (a0.re - tr) * inv_sqrt2; b1.im = (a0.im - tim) * inv_sqrt2;
-            S0 += norm2(b0);
-            S1 += norm2(b1);
-          }
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-          S0 += __shfl_xor_sync(0xffffffffu, S0, o);
-          S1 += __shfl_xor_sync(0xffffffffu, S1, o);
+        if (sizeof(Real) == 8 || n >= (1u << 14)) {    // FP64 sums
+          branch_sums<Real, double>(vec, I, n, tid, blockDim.x, mcr, mci, S0, S1);
+          warp_sum2(S0, S1);
+        } else {                                       // FP32 sums below 2^14 terms
+          float F0 = 0.0f, F1 = 0.0f;
+          branch_sums<Real, float>(vec, I, n, tid, blockDim.x, mcr, mci, F0, F1);
+          warp_sum2(F0, F1);
+          S0 = F0;
+          S1 = F1;
         }
         if ((tid & 31) == 0) {
           red[tid >> 5] = S0;
@@ -900,10 +949,8 @@ __global__ void __launch_bounds__(kCtaThreads) dense_cta_kernel(DenseArgs A) {
           S0 += red[w2];
           S1 += red[kCtaThreads / 32 + w2];
         }
-        const uint32_t l0 = I.kind == 5 ? (lam ^ (uint32_t)I.eta) : lam;
-        const double p0 = (l0 ? S1 : S0) / (S0 + S1);
         if (tid == 0) {
-          const uint32_t m = meas_uniform(A.seed, I.t, rg) < p0 ? 0u : 1u;
+          const uint32_t m = decide64(meas_U(A.seed, I.t, rg), (l0 ? S1 : S0) / (S0 + S1));
           bcast[1] = (int)m;
           if (m) {
             m3b[I.m3 >> 5] |= 1u << (I.m3 & 31);
