@@ -104,6 +104,19 @@ typedef struct {
   void* stream;            /* cudaStream_t (NULL: legacy default stream) */
 } symft_sample_args;
 
+/* One job of a batched request (symft_sample_batch). */
+typedef struct {
+  uint32_t plan;           /* index into the plans[] array of the call */
+  uint32_t reserved0;
+  uint64_t shots, seed, shot_offset;              /* as in symft_sample_args */
+  uint64_t* meas_out;      /* DEVICE outputs (NULL skips), layout as above */
+  uint64_t* det_out;
+  uint64_t* obs_out;
+  uint64_t* discard_out;
+  int precision;           /* SYMFT_FP32 / SYMFT_FP64 */
+  int plain;               /* per-shot plain form */
+} symft_job;
+
 /* Compile circuit text (grammar below) with default options.
  * circuit_text: NUL-terminated, caller-owned, only read during the call.
  * *out receives a plan owned by the library; free with symft_plan_free.
@@ -147,6 +160,21 @@ int symft_sample(const symft_plan* plan, uint64_t shots, uint64_t seed,
  * (out_location = SYMFT_OUT_HOST: the pointers are host memory, preferably
  * pinned; the call copies results back and returns after the copy). */
 int symft_sample_ex(const symft_plan* plan, const symft_sample_args* args);
+
+/* Pick the plan's launch shapes for one precision by timing candidates
+ * (noise blocks per sign-kernel CTA, executor grid sizes, warps per CTA) on
+ * `shots` shots with throw-away outputs; later calls on the plan use the
+ * winner.  Runs synchronously on `cuda_stream`; allocates probe buffers. */
+int symft_autotune(symft_plan* plan, uint64_t shots, int precision, void* cuda_stream);
+
+/* Run many jobs (possibly of different plans) as ONE CUDA graph launch on
+ * `cuda_stream`: every job's kernels are captured into a graph whose branches
+ * (one per plan) run concurrently; jobs of the same plan run in order on its
+ * branch (they share its workspace).  The graph is cached per thread and
+ * updated in place when only parameters change.  Asynchronous; outputs are
+ * device buffers.  Plans must not be used by another call meanwhile. */
+int symft_sample_batch(const symft_plan* const* plans, int n_plans, const symft_job* jobs,
+                       int n_jobs, void* cuda_stream);
 
 /* Message describing the last error on the calling thread ("" if none). */
 const char* symft_last_error(void);

@@ -23,7 +23,8 @@ INSTR_NAMES = ("PromoteRot", "ActiveDiagRot", "ActivePairRot", "RandomMeas", "De
 
 EXPORTS = ("symft_compile", "symft_compile_ex", "symft_plan_info", "symft_plan_free",
            "symft_sample", "symft_sample_ex", "symft_last_error", "symft_last_launch_count",
-           "symft_sample_noalloc", "symft_noalloc_last_error")
+           "symft_sample_noalloc", "symft_noalloc_last_error", "symft_autotune",
+           "symft_sample_batch")
 
 
 class SymftError(RuntimeError):
@@ -53,6 +54,15 @@ class _SampleArgs(ctypes.Structure):
                 ("discard_out", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("out_location", ctypes.c_int), ("check", ctypes.c_int),
                 ("plain", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class _Job(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
+                ("shots", ctypes.c_uint64), ("seed", ctypes.c_uint64),
+                ("shot_offset", ctypes.c_uint64), ("meas_out", ctypes.c_void_p),
+                ("det_out", ctypes.c_void_p), ("obs_out", ctypes.c_void_p),
+                ("discard_out", ctypes.c_void_p), ("precision", ctypes.c_int),
+                ("plain", ctypes.c_int)]
 
 
 _LIB = None
@@ -91,6 +101,11 @@ def lib():
     L.symft_sample_noalloc.restype = ctypes.c_int
     L.symft_noalloc_last_error.argtypes = []
     L.symft_noalloc_last_error.restype = ctypes.c_char_p
+    L.symft_autotune.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p]
+    L.symft_autotune.restype = ctypes.c_int
+    L.symft_sample_batch.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                     ctypes.POINTER(_Job), ctypes.c_int, ctypes.c_void_p]
+    L.symft_sample_batch.restype = ctypes.c_int
     _LIB = L
     return L
 
@@ -189,6 +204,34 @@ def symft_sample_noalloc(plan: Plan, shots: int, seed: int, shot_offset: int = 0
                                     _stream(stream))
     if rc != SYMFT_OK:
         raise SymftError(rc, lib().symft_noalloc_last_error().decode(errors="replace"))
+
+
+def symft_autotune(plan: Plan, shots: int, precision: int = FP32, stream=None) -> None:
+    """Time candidate launch shapes on `shots` shots and keep the fastest (synchronous)."""
+    _check(lib().symft_autotune(plan.handle, shots, precision, _stream(stream)))
+
+
+def symft_sample_batch(plans, jobs, stream=None) -> None:
+    """Run jobs (dicts with plan index, shots, seed, outputs ...) as one CUDA graph launch.
+
+    Each job: {"plan": i, "shots": n, "seed": s, "shot_offset": 0, "meas_out": t,
+    "det_out": t, "obs_out": t, "discard_out": t, "precision": FP32, "plain": False}.
+    """
+    arr_p = (ctypes.c_void_p * len(plans))(*[p.handle for p in plans])
+    arr_j = (_Job * len(jobs))()
+    for k, j in enumerate(jobs):
+        J = arr_j[k]
+        J.plan = j["plan"]
+        J.shots = j["shots"]
+        J.seed = j.get("seed", 0)
+        J.shot_offset = j.get("shot_offset", 0)
+        J.meas_out = _ptr(j.get("meas_out"))
+        J.det_out = _ptr(j.get("det_out"))
+        J.obs_out = _ptr(j.get("obs_out"))
+        J.discard_out = _ptr(j.get("discard_out"))
+        J.precision = j.get("precision", FP32)
+        J.plain = int(bool(j.get("plain", False)))
+    _check(lib().symft_sample_batch(arr_p, len(plans), arr_j, len(jobs), _stream(stream)))
 
 
 def symft_last_launch_count() -> int:

@@ -211,15 +211,38 @@ cudaError_t upload(symft_plan* P) {
                        std::string(#expr) + ": " + cudaGetErrorString(_e));              \
   } while (0)
 
-int sample_impl(symft_plan* P, const symft_sample_args* a) {
-  const HostPlan& h = P->hp;
+// Launch shapes and workspace pointers of one sampling request.  prepare()
+// allocates and decides everything on the host; enqueue() only issues
+// memsets and kernel launches, so it can also run inside a stream capture.
+struct Prep {
+  uint64_t W = 0, nblk = 0;
+  bool plain = false, fp64 = false, need_final = false;
+  uint64_t *meas = nullptr, *det = nullptr, *obs = nullptr, *disc = nullptr;
+  uint64_t *signs = nullptr, *m3 = nullptr;
+  int* status = nullptr;
+  int sign_nb = 0, sign_grid = 0;
+  int dense_kind = 0;   // 0 none, 1 register, 2 warp, 3 CTA per shot
+  int dense_grid = 0, dense_wpb = 0, dense_use_smem = 0;
+  size_t dense_smem = 0;
+  void* gvec = nullptr;
+  uint64_t gvec_stride = 0;
+  int plain_grid = 0;
+};
+
+int validate(const symft_sample_args* a) {
   if (a->shots == 0) return set_error(SYMFT_E_ARG, "shots must be >= 1");
   if (a->shot_offset % kNoiseBlock) return set_error(SYMFT_E_ARG, "shot_offset must be a multiple of 128");
   if (a->shots + a->shot_offset > (1ull << 39)) return set_error(SYMFT_E_ARG, "shot index beyond 2^39");
   if (a->precision != SYMFT_FP32 && a->precision != SYMFT_FP64) return set_error(SYMFT_E_ARG, "bad precision");
   if (a->out_location != SYMFT_OUT_DEVICE && a->out_location != SYMFT_OUT_HOST)
     return set_error(SYMFT_E_ARG, "bad out_location");
-  cudaStream_t st = static_cast<cudaStream_t>(a->stream);
+  return SYMFT_OK;
+}
+
+// outputs: the device pointers the kernels write (caller's or host staging)
+int prepare(symft_plan* P, const symft_sample_args* a, uint64_t* meas, uint64_t* det, uint64_t* obs,
+            uint64_t* disc, Prep* o) {
+  const HostPlan& h = P->hp;
   if (!P->uploaded) {
     try {
       CUDA_TRY(upload(P));
@@ -227,11 +250,178 @@ int sample_impl(symft_plan* P, const symft_sample_args* a) {
       return set_error(e.code, e.what());
     }
   }
-  int launches = 0;
-  const uint64_t W = (a->shots + 63) / 64;
-  const uint64_t nblk = (a->shots + kNoiseBlock - 1) / kNoiseBlock;
-  const bool host = a->out_location == SYMFT_OUT_HOST;
+  CUDA_TRY(set_smem_limits());
+  const Tune& t = P->tune[a->precision == SYMFT_FP64 ? 1 : 0];
+  o->W = (a->shots + 63) / 64;
+  o->nblk = (a->shots + kNoiseBlock - 1) / kNoiseBlock;
+  o->plain = a->plain != 0;
+  o->fp64 = a->precision == SYMFT_FP64;
+  const uint64_t W = o->W;
+  if (h.n_records == 0) meas = nullptr;
+  if (h.n_dets == 0) det = nullptr;
+  if (h.n_obs == 0) obs = nullptr;
+  o->need_final = h.n_m3 > 0 || h.postselect || disc != nullptr;
+  if (h.postselect && det == nullptr && h.n_dets > 0) {
+    CUDA_TRY(P->det_scratch.ensure(h.n_dets * W * 8));
+    det = static_cast<uint64_t*>(P->det_scratch.ptr);
+  }
+  o->meas = meas;
+  o->det = det;
+  o->obs = obs;
+  o->disc = disc;
+  const uint32_t G = static_cast<uint32_t>(h.dense.size());
+  CUDA_TRY(P->status.ensure(16));
+  o->status = static_cast<int*>(P->status.ptr);
+  if (o->plain) {
+    if (plain_smem_bytes(P->dp, h.k_max, o->fp64) > 200 * 1024)
+      return set_error(SYMFT_E_CAPACITY, "plain form: per-shot state exceeds shared memory");
+    const uint64_t cap = static_cast<uint64_t>(P->sm_count) * 16;
+    o->plain_grid = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(a->shots, cap)));
+    return SYMFT_OK;
+  }
+  if (G) {
+    CUDA_TRY(P->signs.ensure(G * W * 8));
+    o->signs = static_cast<uint64_t*>(P->signs.ptr);
+    CUDA_TRY(P->m3.ensure(std::max<uint64_t>(1, h.n_m3 * W) * 8));
+    o->m3 = static_cast<uint64_t*>(P->m3.ptr);
+  }
+  if (h.n_slots > 0) {
+    const int nb = t.sign_nb ? t.sign_nb : sign_blocks_per_cta(P->dp);
+    if (sign_smem_bytes(P->dp, nb) > 220 * 1024)
+      return set_error(SYMFT_E_CAPACITY, "too many bit-packed slots for shared memory (" +
+                                             std::to_string(h.n_slots) + ")");
+    int per_sm = 1;
+    CUDA_TRY(sign_occupancy(P->dp, nb, &per_sm));
+    const uint64_t chunks = (o->nblk + nb - 1) / nb;
+    const uint64_t cap = static_cast<uint64_t>(P->sm_count) * std::max(1, per_sm);
+    o->sign_nb = nb;
+    o->sign_grid = static_cast<int>(std::max<uint64_t>(1, std::min(chunks, cap)));
+  }
+  if (G) {
+    const size_t amp = o->fp64 ? 16 : 8;
+    const size_t m3bytes = ((h.n_m3 + 31) / 32) * 4;
+    const size_t vec_bytes = (static_cast<size_t>(1) << h.k_max) * amp;
+    if (h.k_max <= 5 && dense_reg_smem_bytes(P->dp) <= 96 * 1024) {
+      o->dense_kind = 1;   // register-resident: lane x holds amplitude x
+      const uint64_t want = (a->shots + 7) / 8;
+      const uint64_t cap = static_cast<uint64_t>(P->sm_count) * t.dense_grid_mult;
+      o->dense_grid = static_cast<int>(std::max<uint64_t>(1, std::min(want, cap)));
+    } else if (vec_bytes + m3bytes <= 48 * 1024) {
+      o->dense_kind = 2;   // warp per shot, vector in shared memory
+      int wpb = t.dense_wpb ? t.dense_wpb
+                            : static_cast<int>(std::min<size_t>(8, std::max<size_t>(1, (160 * 1024) / (vec_bytes + m3bytes + 16))));
+      while (wpb > 1 && ((wpb * m3bytes + 15) & ~size_t(15)) + wpb * vec_bytes > 200 * 1024) --wpb;
+      o->dense_wpb = wpb;
+      o->dense_use_smem = 1;
+      o->dense_smem = ((wpb * m3bytes + 15) & ~size_t(15)) + wpb * vec_bytes;
+      const uint64_t want = (a->shots + wpb - 1) / wpb;
+      const uint64_t cap = static_cast<uint64_t>(P->sm_count) * t.dense_grid_mult * 2;
+      o->dense_grid = static_cast<int>(std::max<uint64_t>(1, std::min(want, cap)));
+    } else {
+      o->dense_kind = 3;   // CTA per shot, vector in shared memory or a global slot
+      const bool in_smem = dense_cta_smem_bytes(P->dp, vec_bytes, true) <= 200 * 1024;
+      o->dense_smem = dense_cta_smem_bytes(P->dp, vec_bytes, in_smem);
+      o->dense_use_smem = in_smem ? 1 : 0;
+      int grid = P->sm_count * (in_smem ? 1 : t.cta_grid_mult);
+      if (!in_smem) {
+        // bound the global slots to ~8 GB
+        const uint64_t max_slots = std::max<uint64_t>(1, (8ull << 30) / vec_bytes);
+        grid = static_cast<int>(std::min<uint64_t>(grid, max_slots));
+      }
+      o->dense_grid = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(a->shots, grid)));
+      if (!in_smem) {
+        o->gvec_stride = static_cast<uint64_t>(1) << h.k_max;
+        CUDA_TRY(P->gvec.ensure(static_cast<size_t>(o->dense_grid) * vec_bytes));
+        o->gvec = P->gvec.ptr;
+      }
+    }
+  }
+  return SYMFT_OK;
+}
 
+int enqueue(symft_plan* P, const symft_sample_args* a, const Prep& o, cudaStream_t st, int* launches) {
+  const HostPlan& h = P->hp;
+  const uint64_t W = o.W;
+  if (o.plain) {
+    if (o.meas) CUDA_TRY(cudaMemsetAsync(o.meas, 0, h.n_records * W * 8, st));
+    if (o.det) CUDA_TRY(cudaMemsetAsync(o.det, 0, h.n_dets * W * 8, st));
+    if (o.obs) CUDA_TRY(cudaMemsetAsync(o.obs, 0, h.n_obs * W * 8, st));
+    if (o.disc) CUDA_TRY(cudaMemsetAsync(o.disc, 0, W * 8, st));
+    PlainArgs pa{};
+    pa.p = P->dp;
+    pa.seed = a->seed;
+    pa.shot0 = a->shot_offset;
+    pa.shots = a->shots;
+    pa.W = W;
+    pa.meas = o.meas;
+    pa.det = o.det;
+    pa.obs = o.obs;
+    pa.discard = o.disc;
+    pa.kmax = h.k_max;
+    pa.status = o.status;
+    CUDA_TRY(launch_plain(pa, o.fp64, o.plain_grid, st));
+    ++*launches;
+    return SYMFT_OK;
+  }
+  if (o.sign_grid > 0) {
+    SignArgs s{};
+    s.p = P->dp;
+    s.seed = a->seed;
+    s.block0 = a->shot_offset / kNoiseBlock;
+    s.n_blocks = o.nblk;
+    s.W = W;
+    s.shots = a->shots;
+    s.meas = o.meas;
+    s.det = o.det;
+    s.obs = o.obs;
+    s.signs = o.signs;
+    s.status = o.status;
+    CUDA_TRY(launch_sign(s, o.sign_nb, o.sign_grid, st));
+    ++*launches;
+  }
+  if (o.dense_kind) {
+    if (h.n_m3) CUDA_TRY(cudaMemsetAsync(o.m3, 0, h.n_m3 * W * 8, st));
+    DenseArgs d{};
+    d.p = P->dp;
+    d.seed = a->seed;
+    d.shot0 = a->shot_offset;
+    d.shots = a->shots;
+    d.W = W;
+    d.signs = o.signs;
+    d.m3_out = o.m3;
+    d.kmax = h.k_max;
+    d.status = o.status;
+    d.use_smem = o.dense_use_smem;
+    d.gvec = o.gvec;
+    d.gvec_stride = o.gvec_stride;
+    if (o.dense_kind == 1) CUDA_TRY(launch_dense_reg(d, o.fp64, o.dense_grid, st));
+    else if (o.dense_kind == 2) CUDA_TRY(launch_dense(d, o.fp64, o.dense_wpb, o.dense_grid, o.dense_smem, st));
+    else CUDA_TRY(launch_dense_cta(d, o.fp64, o.dense_grid, o.dense_smem, st));
+    ++*launches;
+  }
+  if (o.need_final) {
+    FinalArgs f{};
+    f.p = P->dp;
+    f.W = W;
+    f.shots = a->shots;
+    f.m3 = h.n_m3 ? o.m3 : nullptr;
+    f.meas = o.meas;
+    f.det = o.det;
+    f.obs = o.obs;
+    f.discard = o.disc;
+    CUDA_TRY(launch_finalize(f, st));
+    ++*launches;
+  }
+  return SYMFT_OK;
+}
+
+int sample_impl(symft_plan* P, const symft_sample_args* a) {
+  const HostPlan& h = P->hp;
+  int rc = validate(a);
+  if (rc != SYMFT_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(a->stream);
+  const uint64_t W = (a->shots + 63) / 64;
+  const bool host = a->out_location == SYMFT_OUT_HOST;
   uint64_t *meas = a->meas_out, *det = a->det_out, *obs = a->obs_out, *disc = a->discard_out;
   if (host) {
     if (meas) { CUDA_TRY(P->h_meas.ensure(std::max<uint64_t>(1, h.n_records * W) * 8)); meas = (uint64_t*)P->h_meas.ptr; }
@@ -239,175 +429,231 @@ int sample_impl(symft_plan* P, const symft_sample_args* a) {
     if (obs) { CUDA_TRY(P->h_obs.ensure(std::max<uint64_t>(1, h.n_obs * W) * 8)); obs = (uint64_t*)P->h_obs.ptr; }
     if (disc) { CUDA_TRY(P->h_disc.ensure(W * 8)); disc = (uint64_t*)P->h_disc.ptr; }
   }
-  if (h.n_records == 0) meas = nullptr;
-  if (h.n_dets == 0) det = nullptr;
-  if (h.n_obs == 0) obs = nullptr;
-  const bool need_final = h.n_m3 > 0 || h.postselect || disc != nullptr;
-  if (h.postselect && det == nullptr && h.n_dets > 0) {
-    CUDA_TRY(P->det_scratch.ensure(h.n_dets * W * 8));
-    det = static_cast<uint64_t*>(P->det_scratch.ptr);
-  }
-  const uint32_t G = static_cast<uint32_t>(h.dense.size());
-  uint64_t* signs = nullptr;
-  if (G) {
-    CUDA_TRY(P->signs.ensure(G * W * 8));
-    signs = static_cast<uint64_t*>(P->signs.ptr);
-  }
-  CUDA_TRY(P->status.ensure(16));
-  int* status = static_cast<int*>(P->status.ptr);
-  if (a->check) CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
-
-  // --- plain form: one CTA per shot -----------------------------------------
-  if (a->plain) {
-    const bool fp64 = a->precision == SYMFT_FP64;
-    if (plain_smem_bytes(P->dp, h.k_max, fp64) > 200 * 1024)
-      return set_error(SYMFT_E_CAPACITY, "plain form: per-shot state exceeds shared memory");
-    if (meas) CUDA_TRY(cudaMemsetAsync(meas, 0, h.n_records * W * 8, st));
-    if (det) CUDA_TRY(cudaMemsetAsync(det, 0, h.n_dets * W * 8, st));
-    if (obs) CUDA_TRY(cudaMemsetAsync(obs, 0, h.n_obs * W * 8, st));
-    if (disc) CUDA_TRY(cudaMemsetAsync(disc, 0, W * 8, st));
-    PlainArgs pa{};
-    pa.p = P->dp;
-    pa.seed = a->seed;
-    pa.shot0 = a->shot_offset;
-    pa.shots = a->shots;
-    pa.W = W;
-    pa.meas = meas;
-    pa.det = det;
-    pa.obs = obs;
-    pa.discard = disc;
-    pa.kmax = h.k_max;
-    pa.status = status;
-    const uint64_t cap = static_cast<uint64_t>(P->sm_count) * 16;
-    CUDA_TRY(launch_plain(pa, fp64, static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(a->shots, cap))), st));
-    ++launches;
-  }
-  // --- sign kernel ---------------------------------------------------------
-  if (!a->plain && h.n_slots > 0) {
-    SignArgs s{};
-    s.p = P->dp;
-    s.seed = a->seed;
-    s.block0 = a->shot_offset / kNoiseBlock;
-    s.n_blocks = nblk;
-    s.W = W;
-    s.shots = a->shots;
-    s.meas = meas;
-    s.det = det;
-    s.obs = obs;
-    s.signs = signs;
-    s.status = status;
-    const size_t smem = sign_smem_bytes(P->dp);
-    if (smem > 220 * 1024)
-      return set_error(SYMFT_E_CAPACITY, "too many bit-packed slots for shared memory (" +
-                                             std::to_string(h.n_slots) + ")");
-    const int nb_cta = sign_blocks_per_cta(P->dp);
-    const uint64_t chunks = (nblk + nb_cta - 1) / nb_cta;
-    int per_sm = 1;
-    CUDA_TRY(sign_occupancy(P->dp, &per_sm));
-    uint64_t cap = static_cast<uint64_t>(P->sm_count) * std::max(1, per_sm);
-    int grid = static_cast<int>(std::max<uint64_t>(1, std::min(chunks, cap)));
-    CUDA_TRY(launch_sign(s, grid, st));
-    ++launches;
-  }
-  // --- dense kernel --------------------------------------------------------
-  if (!a->plain && G) {
-    const bool fp64 = a->precision == SYMFT_FP64;
-    CUDA_TRY(P->m3.ensure(std::max<uint64_t>(1, h.n_m3 * W) * 8));
-    if (h.n_m3) CUDA_TRY(cudaMemsetAsync(P->m3.ptr, 0, h.n_m3 * W * 8, st));
-    DenseArgs d{};
-    d.p = P->dp;
-    d.seed = a->seed;
-    d.shot0 = a->shot_offset;
-    d.shots = a->shots;
-    d.W = W;
-    d.signs = signs;
-    d.m3_out = static_cast<uint64_t*>(P->m3.ptr);
-    d.kmax = h.k_max;
-    d.status = status;
-    const size_t amp = fp64 ? 16 : 8;
-    const size_t m3bytes = ((h.n_m3 + 31) / 32) * 4;
-    const size_t vec_bytes = (static_cast<size_t>(1) << h.k_max) * amp;
-    int wpb = 4;
-    size_t smem;
-    if (vec_bytes + m3bytes <= 48 * 1024) {
-      wpb = static_cast<int>(std::min<size_t>(8, std::max<size_t>(1, (160 * 1024) / (vec_bytes + m3bytes + 16))));
-      d.use_smem = 1;
-      smem = ((wpb * m3bytes + 15) & ~size_t(15)) + wpb * vec_bytes;
-    } else {
-      d.use_smem = 0;
-      smem = wpb * m3bytes + 16;
-    }
-    if (h.k_max <= 5 && dense_reg_smem_bytes(P->dp) <= 96 * 1024) {
-      // register-resident form: lane x holds amplitude x
-      const uint64_t want_r = (a->shots + 7) / 8;
-      const uint64_t cap_r = static_cast<uint64_t>(P->sm_count) * 8;
-      CUDA_TRY(launch_dense_reg(d, fp64, static_cast<int>(std::max<uint64_t>(1, std::min(want_r, cap_r))), st));
-      ++launches;
-      goto dense_done;
-    }
-    if (!d.use_smem) {
-      // large k: one CTA per shot, vector in shared memory up to ~200 KB, else a
-      // global slot per resident CTA (sized to stay L2-resident)
-      const bool in_smem = dense_cta_smem_bytes(P->dp, vec_bytes, true) <= 200 * 1024;
-      const size_t csmem = dense_cta_smem_bytes(P->dp, vec_bytes, in_smem);
-      int grid_c = P->sm_count * (in_smem ? 1 : 2);
-      grid_c = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(a->shots, grid_c)));
-      d.use_smem = in_smem ? 1 : 0;
-      if (!in_smem) {
-        d.gvec_stride = static_cast<uint64_t>(1) << h.k_max;
-        CUDA_TRY(P->gvec.ensure(static_cast<size_t>(grid_c) * vec_bytes));
-        d.gvec = P->gvec.ptr;
-      }
-      CUDA_TRY(launch_dense_cta(d, fp64, grid_c, csmem, st));
-      ++launches;
-      goto dense_done;
-    }
-    {
-    uint64_t want = (a->shots + wpb - 1) / wpb;
-    uint64_t cap = static_cast<uint64_t>(P->sm_count) * (d.use_smem ? 16 : 8);
-    if (!d.use_smem) {
-      // bound the global-memory vectors to ~8 GB of resident warp slots
-      uint64_t max_warps = std::max<uint64_t>(1, (8ull << 30) / vec_bytes);
-      cap = std::min<uint64_t>(cap, std::max<uint64_t>(1, max_warps / wpb));
-    }
-    int grid = static_cast<int>(std::max<uint64_t>(1, std::min(want, cap)));
-    if (!d.use_smem) {
-      d.gvec_stride = static_cast<uint64_t>(1) << h.k_max;
-      CUDA_TRY(P->gvec.ensure(static_cast<size_t>(grid) * wpb * vec_bytes));
-      d.gvec = P->gvec.ptr;
-    }
-    CUDA_TRY(launch_dense(d, fp64, wpb, grid, smem, st));
-    ++launches;
-    }
-  dense_done:;
-  }
-  // --- finalize ------------------------------------------------------------
-  if (!a->plain && need_final) {
-    FinalArgs f{};
-    f.p = P->dp;
-    f.W = W;
-    f.shots = a->shots;
-    f.m3 = h.n_m3 ? static_cast<const uint64_t*>(P->m3.ptr) : nullptr;
-    f.meas = meas;
-    f.det = det;
-    f.obs = obs;
-    f.discard = disc;
-    CUDA_TRY(launch_finalize(f, st));
-    ++launches;
-  }
-  if (host) {
-    if (a->meas_out && meas) CUDA_TRY(cudaMemcpyAsync(a->meas_out, meas, h.n_records * W * 8, cudaMemcpyDeviceToHost, st));
-    if (a->det_out && det) CUDA_TRY(cudaMemcpyAsync(a->det_out, det, h.n_dets * W * 8, cudaMemcpyDeviceToHost, st));
-    if (a->obs_out && obs) CUDA_TRY(cudaMemcpyAsync(a->obs_out, obs, h.n_obs * W * 8, cudaMemcpyDeviceToHost, st));
-    if (a->discard_out && disc) CUDA_TRY(cudaMemcpyAsync(a->discard_out, disc, W * 8, cudaMemcpyDeviceToHost, st));
-  }
+  Prep o;
+  rc = prepare(P, a, meas, det, obs, disc, &o);
+  if (rc != SYMFT_OK) return rc;
+  if (a->check) CUDA_TRY(cudaMemsetAsync(o.status, 0, sizeof(int), st));
+  int launches = 0;
+  rc = enqueue(P, a, o, st, &launches);
   g_last_launches = launches;
+  if (rc != SYMFT_OK) return rc;
+  if (host) {
+    if (a->meas_out && o.meas) CUDA_TRY(cudaMemcpyAsync(a->meas_out, o.meas, h.n_records * W * 8, cudaMemcpyDeviceToHost, st));
+    if (a->det_out && o.det) CUDA_TRY(cudaMemcpyAsync(a->det_out, o.det, h.n_dets * W * 8, cudaMemcpyDeviceToHost, st));
+    if (a->obs_out && o.obs) CUDA_TRY(cudaMemcpyAsync(a->obs_out, o.obs, h.n_obs * W * 8, cudaMemcpyDeviceToHost, st));
+    if (a->discard_out && o.disc) CUDA_TRY(cudaMemcpyAsync(a->discard_out, o.disc, W * 8, cudaMemcpyDeviceToHost, st));
+  }
   if (host || a->check) CUDA_TRY(cudaStreamSynchronize(st));
   if (a->check) {
     int hs = 0;
-    CUDA_TRY(cudaMemcpy(&hs, status, sizeof(int), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(&hs, o.status, sizeof(int), cudaMemcpyDeviceToHost));
     if (hs != 0) return set_error(SYMFT_E_DEVICE, "device status " + std::to_string(hs));
   }
+  return SYMFT_OK;
+}
+
+// ---- autotuning: pick launch shapes by timing candidates on the plan --------
+int autotune_impl(symft_plan* P, uint64_t shots, int precision, cudaStream_t st) {
+  const HostPlan& h = P->hp;
+  const uint64_t W = (shots + 63) / 64;
+  CUDA_TRY(P->t_meas.ensure(std::max<uint64_t>(1, h.n_records * W) * 8));
+  CUDA_TRY(P->t_det.ensure(std::max<uint64_t>(1, h.n_dets * W) * 8));
+  CUDA_TRY(P->t_obs.ensure(std::max<uint64_t>(1, h.n_obs * W) * 8));
+  CUDA_TRY(P->t_disc.ensure(W * 8));
+  symft_sample_args a{};
+  a.shots = shots;
+  a.seed = 12345;
+  a.precision = precision;
+  a.stream = st;
+  Tune& t = P->tune[precision == SYMFT_FP64 ? 1 : 0];
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  auto time_cfg = [&](float* ms) -> int {
+    Prep o;
+    int rc = prepare(P, &a, static_cast<uint64_t*>(P->t_meas.ptr), static_cast<uint64_t*>(P->t_det.ptr),
+                     static_cast<uint64_t*>(P->t_obs.ptr), static_cast<uint64_t*>(P->t_disc.ptr), &o);
+    if (rc != SYMFT_OK) return rc;
+    int l = 0;
+    rc = enqueue(P, &a, o, st, &l);   // warm-up
+    if (rc != SYMFT_OK) return rc;
+    CUDA_TRY(cudaEventRecord(e0, st));
+    for (int i = 0; i < 3; ++i) {
+      a.seed = 12346 + i;
+      rc = enqueue(P, &a, o, st, &l);
+      if (rc != SYMFT_OK) return rc;
+    }
+    CUDA_TRY(cudaEventRecord(e1, st));
+    CUDA_TRY(cudaEventSynchronize(e1));
+    CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
+    return SYMFT_OK;
+  };
+  int rc = SYMFT_OK;
+  float best = 0.0f;
+  Tune base = t;
+  rc = time_cfg(&best);
+  // sign kernel: noise blocks per CTA
+  if (rc == SYMFT_OK && h.n_slots > 0) {
+    for (int nb : {2, 4}) {
+      if (sign_smem_bytes(P->dp, nb) > 200 * 1024) continue;
+      Tune cand = base;
+      cand.sign_nb = nb;
+      t = cand;
+      float ms = 0.0f;
+      rc = time_cfg(&ms);
+      if (rc != SYMFT_OK) break;
+      if (ms < best) { best = ms; base = cand; }
+    }
+    t = base;
+  }
+  // dense executor: grid size (register / warp kernels), warps per CTA, CTA slots
+  if (rc == SYMFT_OK && !h.dense.empty()) {
+    std::vector<Tune> cands;
+    for (int gm : {2, 4, 8, 16, 32}) { Tune c = base; c.dense_grid_mult = gm; cands.push_back(c); }
+    for (int wpb : {2, 4, 8}) { Tune c = base; c.dense_wpb = wpb; cands.push_back(c); }
+    for (int cm : {1, 2, 4}) { Tune c = base; c.cta_grid_mult = cm; cands.push_back(c); }
+    for (const Tune& cand : cands) {
+      t = cand;
+      float ms = 0.0f;
+      rc = time_cfg(&ms);
+      if (rc != SYMFT_OK) break;
+      if (ms < best) { best = ms; base = cand; }
+    }
+    t = base;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != SYMFT_OK) return rc;
+  t.tuned = true;
+  t.best_ms_per_shot = best / 3.0f / static_cast<float>(shots);
+  return SYMFT_OK;
+}
+
+// ---- batched jobs captured into one CUDA graph --------------------------------
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> ev;
+  ~GraphCache() {
+    if (exec) cudaGraphExecDestroy(exec);
+    for (auto s : branch) cudaStreamDestroy(s);
+    for (auto e : ev) cudaEventDestroy(e);
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+thread_local GraphCache g_graph;
+
+int batch_impl(const symft_plan* const* plans, int n_plans, const symft_job* jobs, int n_jobs,
+               cudaStream_t user) {
+  if (!plans || !jobs || n_plans <= 0 || n_jobs <= 0) return set_error(SYMFT_E_ARG, "empty batch");
+  std::vector<symft_sample_args> args(n_jobs);
+  std::vector<uint64_t> max_shots(n_plans, 0);
+  for (int j = 0; j < n_jobs; ++j) {
+    const symft_job& J = jobs[j];
+    if (J.plan >= static_cast<uint32_t>(n_plans) || !plans[J.plan])
+      return set_error(SYMFT_E_ARG, "job " + std::to_string(j) + ": bad plan index");
+    symft_sample_args& a = args[j];
+    a = symft_sample_args{};
+    a.shots = J.shots;
+    a.seed = J.seed;
+    a.shot_offset = J.shot_offset;
+    a.meas_out = J.meas_out;
+    a.det_out = J.det_out;
+    a.obs_out = J.obs_out;
+    a.discard_out = J.discard_out;
+    a.precision = J.precision;
+    a.plain = J.plain;
+    int rc = validate(&a);
+    if (rc != SYMFT_OK) return set_error(rc, "job " + std::to_string(j) + ": " + g_last_error);
+    max_shots[J.plan] = std::max(max_shots[J.plan], J.shots);
+  }
+  // size every plan's workspace for its largest job first, so no later
+  // prepare() moves a buffer another job of the same plan already uses
+  for (int p = 0; p < n_plans; ++p) {
+    if (!max_shots[p]) continue;
+    symft_plan* P = const_cast<symft_plan*>(plans[p]);
+    for (int prec : {SYMFT_FP32, SYMFT_FP64}) {
+      symft_sample_args a{};
+      a.shots = max_shots[p];
+      a.precision = prec;
+      Prep o;
+      int rc = prepare(P, &a, nullptr, nullptr, nullptr, nullptr, &o);
+      if (rc != SYMFT_OK) return rc;
+      if (P->hp.postselect && P->hp.n_dets) CUDA_TRY(P->det_scratch.ensure(P->hp.n_dets * o.W * 8));
+    }
+  }
+  std::vector<Prep> preps(n_jobs);
+  for (int j = 0; j < n_jobs; ++j) {
+    symft_plan* P = const_cast<symft_plan*>(plans[jobs[j].plan]);
+    int rc = prepare(P, &args[j], args[j].meas_out, args[j].det_out, args[j].obs_out, args[j].discard_out, &preps[j]);
+    if (rc != SYMFT_OK) return set_error(rc, "job " + std::to_string(j) + ": " + g_last_error);
+  }
+  // capture: one branch per plan (jobs of a plan share its workspace, in order)
+  GraphCache& G = g_graph;
+  if (!G.cap) CUDA_TRY(cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking));
+  const int nbr = std::min(n_plans, 32);
+  while (static_cast<int>(G.branch.size()) < nbr) {
+    cudaStream_t s;
+    CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    G.branch.push_back(s);
+  }
+  while (static_cast<int>(G.ev.size()) < nbr + 1) {
+    cudaEvent_t e;
+    CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    G.ev.push_back(e);
+  }
+  CUDA_TRY(cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal));
+  int launches = 0;
+  int rc = SYMFT_OK;
+  cudaError_t ce = cudaEventRecord(G.ev[nbr], G.cap);
+  std::vector<char> used(nbr, 0);
+  for (int j = 0; j < n_jobs && rc == SYMFT_OK && ce == cudaSuccess; ++j) {
+    const int b = static_cast<int>(jobs[j].plan) % nbr;
+    if (!used[b]) {
+      ce = cudaStreamWaitEvent(G.branch[b], G.ev[nbr], 0);
+      used[b] = 1;
+    }
+    if (ce == cudaSuccess)
+      rc = enqueue(const_cast<symft_plan*>(plans[jobs[j].plan]), &args[j], preps[j], G.branch[b], &launches);
+  }
+  for (int b = 0; b < nbr && ce == cudaSuccess; ++b) {
+    if (!used[b]) continue;
+    ce = cudaEventRecord(G.ev[b], G.branch[b]);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(G.cap, G.ev[b], 0);
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(G.cap, &graph);
+  if (rc != SYMFT_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return set_error(SYMFT_E_CUDA, std::string("batch capture: ") + cudaGetErrorString(ce));
+  }
+  if (ee != cudaSuccess) return set_error(SYMFT_E_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ee));
+  bool ok = false;
+  if (G.exec) {
+    cudaGraphExecUpdateResultInfo info;
+    ok = cudaGraphExecUpdate(G.exec, graph, &info) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(G.exec);
+      G.exec = nullptr;
+    }
+  }
+  if (!ok) {
+    cudaError_t ie = cudaGraphInstantiate(&G.exec, graph, 0);
+    if (ie != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      G.exec = nullptr;
+      return set_error(SYMFT_E_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+    }
+  }
+  cudaGraphDestroy(graph);
+  CUDA_TRY(cudaGraphLaunch(G.exec, user));
+  g_last_launches = launches;
   return SYMFT_OK;
 }
 
@@ -478,6 +724,10 @@ void symft_plan_free(symft_plan* p) {
   p->h_det.release();
   p->h_obs.release();
   p->h_disc.release();
+  p->t_meas.release();
+  p->t_det.release();
+  p->t_obs.release();
+  p->t_disc.release();
   delete p;
 }
 
@@ -504,6 +754,30 @@ int symft_sample(const symft_plan* plan, uint64_t shots, uint64_t seed, uint64_t
   a.obs_out = obs_out;
   a.stream = stream;
   return symft_sample_ex(plan, &a);
+}
+
+int symft_autotune(symft_plan* plan, uint64_t shots, int precision, void* stream) {
+  g_last_error.clear();
+  if (!plan) return set_error(SYMFT_E_ARG, "null plan");
+  if (shots == 0) return set_error(SYMFT_E_ARG, "shots must be >= 1");
+  if (precision != SYMFT_FP32 && precision != SYMFT_FP64) return set_error(SYMFT_E_ARG, "bad precision");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  try {
+    return autotune_impl(plan, shots, precision, static_cast<cudaStream_t>(stream));
+  } catch (const std::bad_alloc&) {
+    return set_error(SYMFT_E_NOMEM, "host allocation failed");
+  }
+}
+
+int symft_sample_batch(const symft_plan* const* plans, int n_plans, const symft_job* jobs, int n_jobs,
+                       void* stream) {
+  g_last_error.clear();
+  g_last_launches = 0;
+  try {
+    return batch_impl(plans, n_plans, jobs, n_jobs, static_cast<cudaStream_t>(stream));
+  } catch (const std::bad_alloc&) {
+    return set_error(SYMFT_E_NOMEM, "host allocation failed");
+  }
 }
 
 const char* symft_last_error(void) { return g_last_error.c_str(); }

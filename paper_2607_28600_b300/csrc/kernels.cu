@@ -1379,41 +1379,37 @@ __global__ void finalize_kernel(FinalArgs A) {
 // ---------------------------------------------------------------------------
 // launch wrappers (host)
 // ---------------------------------------------------------------------------
+cudaError_t set_smem_limits();
+
 // 512-shot CTAs when their slots fit comfortably, else 256-shot CTAs
 int sign_blocks_per_cta(const DevPlan& p) { return (size_t)p.n_slots * 4 * 16 <= 40 * 1024 ? 4 : 2; }
 
-size_t sign_smem_bytes(const DevPlan& p) {
-  return sign_layout(p.n_qtab, p.n_ctab, p.n_slots, sign_blocks_per_cta(p)).total;
+size_t sign_smem_bytes(const DevPlan& p, int nb) {
+  return sign_layout(p.n_qtab, p.n_ctab, p.n_slots, nb).total;
 }
 
-static const void* sign_fn(const DevPlan& p) {
-  return sign_blocks_per_cta(p) == 4 ? (const void*)sign_kernel<4> : (const void*)sign_kernel<2>;
+static const void* sign_fn(int nb) {
+  return nb == 4 ? (const void*)sign_kernel<4> : (const void*)sign_kernel<2>;
 }
 
-cudaError_t sign_occupancy(const DevPlan& p, int* ctas_per_sm) {
-  const size_t smem = sign_smem_bytes(p);
-  cudaError_t e = cudaFuncSetAttribute(sign_fn(p), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t sign_occupancy(const DevPlan& p, int nb, int* ctas_per_sm) {
+  const size_t smem = sign_smem_bytes(p, nb);
+  cudaError_t e = set_smem_limits();
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(sign_fn(p), cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  e = cudaFuncSetAttribute(sign_fn(nb), cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, sign_fn(p), kSignWarps * 32, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, sign_fn(nb), kSignWarps * 32, smem);
 }
 
-cudaError_t launch_sign(const SignArgs& a, int grid, cudaStream_t st) {
-  const size_t smem = sign_smem_bytes(a.p);
-  cudaError_t e = cudaFuncSetAttribute(sign_fn(a.p), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  if (sign_blocks_per_cta(a.p) == 4) sign_kernel<4><<<grid, kSignWarps * 32, smem, st>>>(a);
+cudaError_t launch_sign(const SignArgs& a, int nb, int grid, cudaStream_t st) {
+  const size_t smem = sign_smem_bytes(a.p, nb);
+  if (nb == 4) sign_kernel<4><<<grid, kSignWarps * 32, smem, st>>>(a);
   else sign_kernel<2><<<grid, kSignWarps * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 template <typename Real>
 cudaError_t launch_dense_t(const DenseArgs& a, int warps_per_block, int grid, size_t smem, cudaStream_t st) {
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(dense_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
   dense_kernel<Real><<<grid, warps_per_block * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
@@ -1424,9 +1420,6 @@ size_t dense_cta_smem_bytes(const DevPlan& p, size_t vec_bytes, bool vec_in_smem
 }
 
 cudaError_t launch_dense_cta(const DenseArgs& a, bool fp64, int grid, size_t smem, cudaStream_t st) {
-  const void* fn = fp64 ? (const void*)dense_cta_kernel<double> : (const void*)dense_cta_kernel<float>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   if (fp64) dense_cta_kernel<double><<<grid, kCtaThreads, smem, st>>>(a);
   else dense_cta_kernel<float><<<grid, kCtaThreads, smem, st>>>(a);
   return cudaGetLastError();
@@ -1439,9 +1432,6 @@ size_t dense_reg_smem_bytes(const DevPlan& p) {
 
 cudaError_t launch_dense_reg(const DenseArgs& a, bool fp64, int grid, cudaStream_t st) {
   const size_t smem = dense_reg_smem_bytes(a.p);
-  const void* fn = fp64 ? (const void*)dense_reg_kernel<double> : (const void*)dense_reg_kernel<float>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   if (fp64) dense_reg_kernel<double><<<grid, kRegWarps * 32, smem, st>>>(a);
   else dense_reg_kernel<float><<<grid, kRegWarps * 32, smem, st>>>(a);
   return cudaGetLastError();
@@ -1456,11 +1446,27 @@ size_t plain_smem_bytes(const DevPlan& p, uint32_t kmax, bool fp64) {
   return plain_layout(p, kmax, fp64 ? 16 : 8).total;
 }
 
+// Raise every kernel's dynamic shared-memory limit once (host call, outside
+// any stream capture); launches then only enqueue.
+cudaError_t set_smem_limits() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  const int lim = 227 * 1024;
+  const void* fns[] = {(const void*)sign_kernel<2>, (const void*)sign_kernel<4>,
+                       (const void*)dense_kernel<float>, (const void*)dense_kernel<double>,
+                       (const void*)dense_reg_kernel<float>, (const void*)dense_reg_kernel<double>,
+                       (const void*)dense_cta_kernel<float>, (const void*)dense_cta_kernel<double>,
+                       (const void*)plain_kernel<float>, (const void*)plain_kernel<double>};
+  for (const void* f : fns) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e != cudaSuccess) return e;
+  }
+  done = true;
+  return cudaSuccess;
+}
+
 cudaError_t launch_plain(const PlainArgs& a, bool fp64, int grid, cudaStream_t st) {
   const size_t smem = plain_smem_bytes(a.p, a.kmax, fp64);
-  const void* fn = fp64 ? (const void*)plain_kernel<double> : (const void*)plain_kernel<float>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   if (fp64) plain_kernel<double><<<grid, kPlainThreads, smem, st>>>(a);
   else plain_kernel<float><<<grid, kPlainThreads, smem, st>>>(a);
   return cudaGetLastError();

@@ -130,6 +130,8 @@ extern "C" int symft_sample_noalloc(const symft_plan* plan, uint64_t shots, uint
   e = setup(dev, &base, &sms);
   if (e != cudaSuccess) return fail(SYMFT_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  e = set_smem_limits();
+  if (e != cudaSuccess) return fail(SYMFT_E_CUDA, cudaGetErrorString(e));
 
   // the plan image goes into the array on every call (calls may alternate plans)
   e = cudaMemcpyAsync(base + o_plan, plan->blob.data(), plan->blob.size(), cudaMemcpyHostToDevice, st);
@@ -154,14 +156,14 @@ extern "C" int symft_sample_noalloc(const symft_plan* plan, uint64_t shots, uint
     s.obs = obs_out;
     s.signs = signs;
     s.status = status;
-    if (sign_smem_bytes(dp) > 220 * 1024) return fail(SYMFT_E_CAPACITY, "too many bit-packed slots");
-    int per_sm = 1;
-    e = sign_occupancy(dp, &per_sm);
-    if (e != cudaSuccess) return fail(SYMFT_E_CUDA, cudaGetErrorString(e));
     const int nb_cta = sign_blocks_per_cta(dp);
+    if (sign_smem_bytes(dp, nb_cta) > 220 * 1024) return fail(SYMFT_E_CAPACITY, "too many bit-packed slots");
+    int per_sm = 1;
+    e = sign_occupancy(dp, nb_cta, &per_sm);
+    if (e != cudaSuccess) return fail(SYMFT_E_CUDA, cudaGetErrorString(e));
     const uint64_t chunks = (nblk + nb_cta - 1) / nb_cta;
     const uint64_t cap = static_cast<uint64_t>(sms) * std::max(1, per_sm);
-    e = launch_sign(s, static_cast<int>(std::max<uint64_t>(1, std::min(chunks, cap))), st);
+    e = launch_sign(s, nb_cta, static_cast<int>(std::max<uint64_t>(1, std::min(chunks, cap))), st);
     if (e != cudaSuccess) return fail(SYMFT_E_CUDA, cudaGetErrorString(e));
   }
   if (G) {

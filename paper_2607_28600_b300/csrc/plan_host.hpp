@@ -36,19 +36,30 @@ struct BlobOffsets {
   size_t plc, plo, pls;
 };
 
-cudaError_t launch_sign(const SignArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_sign(const SignArgs& a, int nb, int grid, cudaStream_t st);
 int sign_blocks_per_cta(const DevPlan& p);
-size_t sign_smem_bytes(const DevPlan& p);
-cudaError_t sign_occupancy(const DevPlan& p, int* ctas_per_sm);
+size_t sign_smem_bytes(const DevPlan& p, int nb);
+cudaError_t sign_occupancy(const DevPlan& p, int nb, int* ctas_per_sm);
 cudaError_t launch_dense(const DenseArgs& a, bool fp64, int warps_per_block, int grid, size_t smem,
                          cudaStream_t st);
 cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t st);
+cudaError_t set_smem_limits();
 size_t plain_smem_bytes(const DevPlan& p, uint32_t kmax, bool fp64);
 size_t dense_reg_smem_bytes(const DevPlan& p);
 size_t dense_cta_smem_bytes(const DevPlan& p, size_t vec_bytes, bool vec_in_smem);
 cudaError_t launch_dense_cta(const DenseArgs& a, bool fp64, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_dense_reg(const DenseArgs& a, bool fp64, int grid, cudaStream_t st);
 cudaError_t launch_plain(const PlainArgs& a, bool fp64, int grid, cudaStream_t st);
+
+// Launch shapes chosen by symft_autotune (0 = built-in heuristic).
+struct Tune {
+  bool tuned = false;
+  int sign_nb = 0;           // 128-shot noise blocks per sign-kernel CTA
+  int dense_grid_mult = 8;   // register / warp executors: CTAs per SM
+  int dense_wpb = 0;         // warp executor: warps (shots) per CTA
+  int cta_grid_mult = 2;     // CTA executor with global vectors: CTAs per SM
+  float best_ms_per_shot = 0.0f;
+};
 
 }  // namespace symft
 
@@ -63,6 +74,8 @@ struct symft_plan {
   symft::DevPlan dp{};
   symft::DevBuf signs, m3, det_scratch, gvec, status;
   symft::DevBuf h_meas, h_det, h_obs, h_disc;   // staging for host outputs
+  symft::DevBuf t_meas, t_det, t_obs, t_disc;   // outputs of autotuning probes
+  symft::Tune tune[2];                          // FP32, FP64
   int sm_count = 0;
 };
 

@@ -382,3 +382,32 @@ def cultivation_shaped(p: float = 1e-3, grow_d: int = 9, grow_rounds: int = 3,
     e.measure(dq, "Z")
     e.raw("OBSERVABLE_INCLUDE(0) " + " ".join(f"rec[-{e.nrec - (base + c)}]" for c in range(d)))
     return e.text()
+
+
+def mixed_batch(seed: int = 1, n: int = 64, p: float = 1e-3):
+    """Mixed workload: `n` circuits drawn from a seed.
+
+    Surface-code memory (d = 3..11, d rounds), cultivation-shaped circuits
+    (growth to d = 5 or 9), 15-to-1 distillation (encoded / literal) and random
+    near-Clifford circuits on 20..100 qubits with 0..24 rotations of uniform
+    random angle on weight-1..4 Paulis.  Returns [(name, text, postselect)].
+    """
+    rng = random.Random(seed)
+    out = []
+    for i in range(n):
+        kind = rng.choices(["surface", "cultivation", "distill", "random"], [0.3, 0.15, 0.15, 0.4])[0]
+        if kind == "surface":
+            d = rng.choice([3, 5, 7, 9, 11])
+            out.append((f"surface_d{d}_{i}", rotated_surface_code_memory(d, d, p), 0))
+        elif kind == "cultivation":
+            g = rng.choice([5, 9])
+            out.append((f"cultivation_g{g}_{i}", cultivation_shaped(p, grow_d=g), 1))
+        elif kind == "distill":
+            v = rng.choice(["encoded", "literal"])
+            out.append((f"distill_{v}_{i}", distillation_15_to_1(p, v), 1))
+        else:
+            nq = rng.randint(20, 100)
+            nr = rng.randint(0, 24)
+            out.append((f"random_n{nq}_r{nr}_{i}",
+                        random_near_clifford(nq, rng.randint(8, 30), nr, p=p, seed=rng.randrange(1 << 30)), 0))
+    return out

@@ -234,3 +234,57 @@ def test_cultivation_full_vs_symft_oracle_sampled():
         diff = (g["records"] != o["records"]).any(axis=1)
         assert diff.sum() <= (0 if prec == 1 else 2)
         np.testing.assert_array_equal(g["discard"][~diff], o["discard"][~diff])
+
+
+# ---- autotuning and graph-batched jobs leave every bit unchanged ----
+
+def _dev_outputs(plan, shots):
+    W = (shots + 63) // 64
+    info = plan.info
+    mk = lambda n: torch.zeros((max(1, n), W), dtype=torch.int64, device="cuda")
+    return {"meas_out": mk(info["n_records"]), "det_out": mk(info["n_dets"]),
+            "obs_out": mk(info["n_obs"]), "discard_out": torch.zeros((W,), dtype=torch.int64, device="cuda")}
+
+
+def test_autotune_keeps_results():
+    import paper_2607_28600_b300 as S
+    from paper_2607_28600_b300.workloads import distillation_15_to_1
+    for text, post in ((rotated_surface_code_memory(5, 5, 1e-2), 0),
+                       (distillation_15_to_1(1e-3, "encoded"), 1)):
+        plan = S.symft_compile(text, postselect=post)
+        before = _dev_outputs(plan, 5000)
+        S.symft_sample_ex(plan, 5000, 9, **before)
+        S.symft_autotune(plan, 20000, S.FP32)
+        after = _dev_outputs(plan, 5000)
+        S.symft_sample_ex(plan, 5000, 9, **after)
+        torch.cuda.synchronize()
+        for k in before:
+            assert torch.equal(before[k], after[k]), k
+
+
+def test_graph_batch_equals_individual_calls():
+    import paper_2607_28600_b300 as S
+    from paper_2607_28600_b300.workloads import mixed_batch
+    circuits = [c for c in mixed_batch(seed=3, n=12)]
+    plans = [S.symft_compile(t, postselect=post) for _, t, post in circuits]
+    keep = [i for i, pl in enumerate(plans) if pl.info["k_max"] <= 12]
+    plans = [plans[i] for i in keep]
+    jobs, refs = [], []
+    for i, pl in enumerate(plans):
+        shots = 700 + 128 * i
+        outs = _dev_outputs(pl, shots)
+        jobs.append({"plan": i, "shots": shots, "seed": 40 + i, "precision": S.FP32, **outs})
+        ref = _dev_outputs(pl, shots)
+        S.symft_sample_ex(pl, shots, 40 + i, **ref)
+        refs.append(ref)
+    # a second job on plan 0 (same branch, in order)
+    extra = _dev_outputs(plans[0], 512)
+    jobs.append({"plan": 0, "shots": 512, "seed": 99, "shot_offset": 1024, "precision": S.FP32, **extra})
+    extra_ref = _dev_outputs(plans[0], 512)
+    S.symft_sample_ex(plans[0], 512, 99, shot_offset=1024, **extra_ref)
+    for rep in range(2):                      # second launch reuses / updates the cached graph
+        S.symft_sample_batch(plans, jobs)
+        torch.cuda.synchronize()
+        for j, ref in zip(jobs, refs + [extra_ref]):
+            for k in ref:
+                assert torch.equal(j[k], ref[k]), (rep, j["plan"], k)
