@@ -231,6 +231,83 @@ def measure_near_clifford(S, torch, dev, stream, steps, warmup, scale=1.0):
     return out
 
 
+def measure_mixed_batch(S, torch, dev, stream, steps, warmup, n_circuits=64, target_ms=2.0):
+    """64 mixed circuits (k_max <= 20): autotuned FP32 jobs in one graph launch per step,
+    against untuned sequential FP64 runs (plain form where it fits, batched form)."""
+    import numpy as np
+    from paper_2607_28600_b300.workloads import mixed_batch
+    plans, names = [], []
+    for name, text, post in mixed_batch(seed=1, n=4 * n_circuits):
+        pl = S.symft_compile(text, postselect=post)
+        if pl.info["k_max"] > 20:
+            continue
+        plans.append(pl)
+        names.append(name)
+        if len(plans) == n_circuits:
+            break
+    t0 = time.perf_counter()
+    for pl in plans:
+        k = pl.info["k_max"]
+        S.symft_autotune(pl, int(min(65536, max(256, (1 << 22) >> k))), S.FP32, stream=stream)
+    tune_s = time.perf_counter() - t0
+    shots = []
+    for pl in plans:
+        ns = max(pl.refresh_info()["tuned_ns_per_shot"][0], 1e-3)
+        shots.append(int(min(10_000_000, max(128, (target_ms * 1e6 / ns) // 128 * 128))))
+    outs = []
+    for pl, n in zip(plans, shots):
+        W = (n + 63) // 64
+        info = pl.info
+        mk = lambda m: torch.empty((max(1, m), W), dtype=torch.int64, device=dev)
+        outs.append({"meas_out": mk(info["n_records"]), "det_out": mk(info["n_dets"]),
+                     "obs_out": mk(info["n_obs"]),
+                     "discard_out": torch.empty((W,), dtype=torch.int64, device=dev)})
+
+    def jobs_for(step, precision=S.FP32, plain=False):
+        return [{"plan": i, "shots": n, "seed": 1000 * step + i, "precision": precision,
+                 "plain": plain, **o} for i, (n, o) in enumerate(zip(shots, outs))]
+    for w in range(warmup):
+        S.symft_sample_batch(plans, jobs_for(w), stream=stream)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for st in range(steps):
+        S.symft_sample_batch(plans, jobs_for(warmup + st), stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_batch = e0.elapsed_time(e1) / steps
+    total = sum(shots)
+    res = {"n_circuits": len(plans), "total_shots_per_step": total,
+           "k_max_hist": {str(k): sum(1 for p in plans if p.info["k_max"] == k)
+                          for k in sorted(set(p.info["k_max"] for p in plans))},
+           "autotune_s": tune_s,
+           "fp32_autotuned_graph": {"ms_per_step": ms_batch, "shots_per_s": total / (ms_batch / 1e3),
+                                    "kernel_launches_per_step": S.symft_last_launch_count(),
+                                    "graph_launches_per_step": 1}}
+    # untuned FP64, sequential calls on fresh plans (no autotuning)
+    fresh = [S.symft_compile(t, postselect=post) for name, t, post in mixed_batch(seed=1, n=4 * n_circuits)
+             if name in set(names)]
+    for label, plain in (("fp64_plain_untuned", True), ("fp64_batched_untuned", False)):
+        ok_shots, skipped = 0, 0
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for pl, n, o in zip(fresh, shots, outs):
+            try:
+                S.symft_sample_ex(pl, n, 7, precision=S.FP64, plain=plain, stream=stream, **o)
+                ok_shots += n
+            except S.SymftError:
+                skipped += 1
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        res[label] = {"ms": ms, "shots": ok_shots, "circuits_skipped": skipped,
+                      "shots_per_s": ok_shots / (ms / 1e3) if ms > 0 else None}
+    if res["fp64_plain_untuned"]["shots_per_s"]:
+        res["fp32_autotuned_over_fp64_plain"] = (res["fp32_autotuned_graph"]["shots_per_s"] /
+                                                 res["fp64_plain_untuned"]["shots_per_s"])
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -397,6 +474,7 @@ def main():
     }
     if not args.no_near_clifford and world == 1:
         line["near_clifford"] = measure_near_clifford(S, torch, dev, stream, steps=5, warmup=3)
+        line["mixed_batch"] = measure_mixed_batch(S, torch, dev, stream, steps=5, warmup=3)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

@@ -85,6 +85,8 @@ typedef struct {
   uint32_t n_targets;         /* bit-packed outputs the sign kernel computes */
   uint32_t n_causal;          /* active-measurement outcomes (m3 symbols) */
   uint64_t sign_xor_terms;    /* total (symbol, target) incidences */
+  float tuned_ns_per_shot[2]; /* GPU time per shot of the autotuned shape
+                                 (FP32, FP64); 0 until symft_autotune ran */
 } symft_info;
 
 /* One sampling request.  All pointers may be NULL to skip that output. */

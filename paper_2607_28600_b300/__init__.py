@@ -44,7 +44,7 @@ class _Info(ctypes.Structure):
                 ("k_max", ctypes.c_uint32), ("n_instr", ctypes.c_uint32 * 7),
                 ("max_expr_weight", ctypes.c_uint32), ("n_noise_components", ctypes.c_uint32),
                 ("n_targets", ctypes.c_uint32), ("n_causal", ctypes.c_uint32),
-                ("sign_xor_terms", ctypes.c_uint64)]
+                ("sign_xor_terms", ctypes.c_uint64), ("tuned_ns_per_shot", ctypes.c_float * 2)]
 
 
 class _SampleArgs(ctypes.Structure):
@@ -154,6 +154,10 @@ class Plan:
             self._info = symft_plan_info(self)
         return self._info
 
+    def refresh_info(self) -> dict:
+        self._info = symft_plan_info(self)
+        return self._info
+
     def words(self, shots: int) -> int:
         return (shots + 63) // 64
 
@@ -169,7 +173,9 @@ def symft_compile(circuit_text: str, postselect: int = POSTSELECT_NONE) -> Plan:
 def symft_plan_info(plan: Plan) -> dict:
     info = _Info()
     _check(lib().symft_plan_info(plan.handle, ctypes.byref(info)))
-    d = {name: getattr(info, name) for name, _ in _Info._fields_ if name != "n_instr"}
+    d = {name: getattr(info, name) for name, _ in _Info._fields_
+         if name not in ("n_instr", "tuned_ns_per_shot")}
+    d["tuned_ns_per_shot"] = [float(info.tuned_ns_per_shot[0]), float(info.tuned_ns_per_shot[1])]
     d["n_instr"] = {INSTR_NAMES[i]: int(info.n_instr[i]) for i in range(7)}
     return d
 

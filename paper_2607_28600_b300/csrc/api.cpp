@@ -709,6 +709,8 @@ int symft_plan_info(const symft_plan* p, symft_info* info) {
   info->n_targets = h.n_slots;
   info->n_causal = h.n_m3;
   info->sign_xor_terms = h.sign_xor_terms;
+  for (int i = 0; i < 2; ++i)
+    info->tuned_ns_per_shot[i] = p->tune[i].tuned ? p->tune[i].best_ms_per_shot * 1e6f : 0.0f;
   return SYMFT_OK;
 }
 
