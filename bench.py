@@ -181,6 +181,36 @@ def _near_clifford_text(kind):
     return distillation_15_to_1(1e-3, "literal")
 
 
+def fp32_accuracy(S, torch, plan, dev, stream, shots=1 << 16, seed=77):
+    """FP32 executor against the FP64 one on the same shots: the fraction of shots
+    whose outputs differ (an active outcome flipped) and the largest branch-
+    probability difference over the shots whose outputs agree."""
+    import numpy as np
+    info = plan.info
+    W = (shots + 63) // 64
+    res = {}
+    for prec in (S.FP32, S.FP64):
+        cols = [torch.zeros((max(1, info[k]), W), dtype=torch.int64, device=dev)
+                for k in ("n_records", "n_dets", "n_obs")]
+        disc = torch.zeros((W,), dtype=torch.int64, device=dev)
+        prob = torch.zeros((max(1, info["n_causal"]), shots), dtype=torch.float64, device=dev)
+        S.symft_sample_ex(plan, shots, seed, meas_out=cols[0], det_out=cols[1], obs_out=cols[2],
+                          discard_out=disc, precision=prec, prob_out=prob, stream=stream, check=True)
+        res[prec] = (torch.cat(cols + [disc.view(1, -1)]), prob)
+    torch.cuda.synchronize(dev)
+    a, pa = res[S.FP32]
+    b, pb = res[S.FP64]
+    anyw = torch.bitwise_xor(a, b).cpu().numpy().view(np.uint64)
+    anyw = np.bitwise_or.reduce(anyw, axis=0)
+    flipped = np.unpackbits(anyw.view(np.uint8), bitorder="little").astype(bool)[:shots]
+    err = 0.0
+    if info["n_causal"] and (~flipped).any():
+        keep = torch.from_numpy(~flipped).to(dev)
+        err = float((pa - pb).abs()[:, keep].max().item())
+    return {"shots": shots, "flip_rate": float(flipped.mean()),
+            "max_prob_err_unflipped": err, "n_active_meas": info["n_causal"]}
+
+
 def measure_near_clifford(S, torch, dev, stream, steps, warmup, scale=1.0):
     """FP32-batched vs FP64-plain (and FP64-batched) shots/s per near-Clifford config."""
     out = {}
@@ -224,6 +254,7 @@ def measure_near_clifford(S, torch, dev, stream, steps, warmup, scale=1.0):
                            "shots_per_s": shots / (ms / 1e3),
                            "discard_rate": int(np.bitwise_count(words).sum()) / shots,
                            "launches_per_step": S.symft_last_launch_count()}
+        entry["fp32_vs_fp64"] = fp32_accuracy(S, torch, plan, dev, stream)
         if "shots_per_s" in entry.get("fp64_plain", {}) and "shots_per_s" in entry.get("fp32_batched", {}):
             entry["fp32_batched_over_fp64_plain"] = (entry["fp32_batched"]["shots_per_s"] /
                                                      entry["fp64_plain"]["shots_per_s"])
@@ -317,7 +348,9 @@ def main():
     ap.add_argument("--shots", type=int, default=SHOTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--only", default=None, help="run one workload (profiling)")
+    ap.add_argument("--only", default=None,
+                    help="run one part (profiling): a surface-code workload name, "
+                         "near_clifford or mixed_batch")
     ap.add_argument("--no-near-clifford", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -338,6 +371,12 @@ def main():
     shots = args.shots
     W = (shots + 63) // 64
     offset = rank * ((shots + 127) // 128) * 128
+    if args.only in ("near_clifford", "mixed_batch"):
+        fn = measure_near_clifford if args.only == "near_clifford" else measure_mixed_batch
+        res = fn(S, torch, dev, stream, steps=args.steps, warmup=args.warmup)
+        if rank == 0:
+            print(json.dumps({args.only: res}), flush=True)
+        return
 
     per_circuit = {}
     headline = None

@@ -56,16 +56,23 @@ typedef enum {
   SYMFT_E_DEVICE = -8        /* device-side check failed (status word) */
 } symft_status;
 
-enum { SYMFT_POSTSELECT_NONE = 0, SYMFT_POSTSELECT_ALL = 1 };
+enum { SYMFT_POSTSELECT_NONE = 0, SYMFT_POSTSELECT_ALL = 1, SYMFT_POSTSELECT_LISTED = 2 };
 enum { SYMFT_FP32 = 0, SYMFT_FP64 = 1 };
 enum { SYMFT_OUT_DEVICE = 0, SYMFT_OUT_HOST = 1 };
 
 typedef struct symft_plan symft_plan;   /* opaque; immutable after compile */
 
 typedef struct {
-  int postselect;   /* SYMFT_POSTSELECT_*: reject a shot at the first fired
-                       detector (Sec. 6, detector postselection) */
-  int reserved[7];
+  int postselect;          /* SYMFT_POSTSELECT_*: reject a shot at the first
+                              fired postselected detector (Sec. 6, detector
+                              postselection): NONE, ALL detectors, or the
+                              LISTED ones */
+  uint32_t n_post_dets;    /* LISTED: number of entries of post_dets */
+  const uint32_t* post_dets;   /* LISTED: detector indices (annotation order,
+                              0-based, duplicates allowed); caller-owned, read
+                              only during symft_compile_ex; an index >= the
+                              number of detectors is SYMFT_E_ARG */
+  int reserved[4];
 } symft_options;
 
 /* Counts of a compiled plan (Sec. 5, sampling complexity). */
@@ -104,6 +111,14 @@ typedef struct {
   int plain;               /* non-zero: per-shot unpacked evaluation, one CTA per shot
                               (the paper's GPU design, kept for comparison; same bits) */
   void* stream;            /* cudaStream_t (NULL: legacy default stream) */
+  double* prob_out;        /* n_causal * shots doubles, [j * shots + r]: Pr(m = 0)
+                              of active measurement j (plan order) in shot r as
+                              the executor computed it (Sec. 4, Eqs. of
+                              ActiveDiagMeas / ActivePairMeas), rounded from
+                              FP32 when precision = FP32; for checking branch
+                              probabilities against an FP64 reference */
+  uint64_t* counts_out;    /* 2 + n_obs words: [0] kept shots, [1] discarded
+                              shots, [2 + j] kept shots whose observable j is 1 */
 } symft_sample_args;
 
 /* One job of a batched request (symft_sample_batch). */
@@ -117,6 +132,7 @@ typedef struct {
   uint64_t* discard_out;
   int precision;           /* SYMFT_FP32 / SYMFT_FP64 */
   int plain;               /* per-shot plain form */
+  uint64_t* counts_out;    /* DEVICE, 2 + n_obs words as in symft_sample_args */
 } symft_job;
 
 /* Compile circuit text (grammar below) with default options.
@@ -144,6 +160,15 @@ int symft_compile_ex(const char* circuit_text, const symft_options* opt, symft_p
 
 /* Fill *info with the plan's counts.  Host only, no GPU needed. */
 int symft_plan_info(const symft_plan* plan, symft_info* info);
+
+/* Measurement ordinals (0-based, every measurement event in circuit order,
+ * resets included) of the plan's active measurements -- the ActiveDiagMeas /
+ * ActivePairMeas instructions of Sec. 4, whose outcomes are the causal m3
+ * symbols -- in plan order: entry j is the measurement whose branch
+ * probability prob_out row j holds.  Writes min(capacity, n_causal) entries
+ * to t_out (caller-owned host memory; NULL with capacity 0 only queries) and
+ * returns n_causal, or a negative status.  Host only. */
+int symft_plan_active_meas(const symft_plan* plan, uint32_t* t_out, uint32_t capacity);
 
 /* Release a plan and its device workspace.  NULL is a no-op.  The caller must
  * make sure no sampling call on the plan is still running. */

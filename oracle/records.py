@@ -14,7 +14,9 @@ detector and report zeros afterwards:
   * all observable bits are 0, and the discard flag is 1.
 
 Modes: POSTSELECT_NONE (0) never rejects, POSTSELECT_ALL (1) postselects every
-detector.
+detector, POSTSELECT_LISTED (2) postselects the detectors whose indices are
+given; the others are still reported (and zeroed after a rejection) but never
+reject.
 """
 from __future__ import annotations
 
@@ -22,13 +24,16 @@ import numpy as np
 
 POSTSELECT_NONE = 0
 POSTSELECT_ALL = 1
+POSTSELECT_LISTED = 2
 
 
-def finalize(circuit, outcomes, postselect: int = POSTSELECT_NONE):
+def finalize(circuit, outcomes, postselect: int = POSTSELECT_NONE, post_dets=None):
     """outcomes: sequence over measurement ordinals of one shot's bits.
 
+    post_dets: detector indices that reject (POSTSELECT_LISTED only).
     Returns (records, dets, obs, discard) as numpy uint8 arrays / int.
     """
+    listed = set(int(i) for i in post_dets) if post_dets is not None else set()
     rec = np.zeros(circuit.num_records, dtype=np.uint8)
     det = np.zeros(circuit.num_dets, dtype=np.uint8)
     obs = np.zeros(circuit.num_obs, dtype=np.uint8)
@@ -44,7 +49,9 @@ def finalize(circuit, outcomes, postselect: int = POSTSELECT_NONE):
             for t in op.conds:
                 v ^= int(outcomes[t])
             det[op.index] = v
-            if postselect == POSTSELECT_ALL and v == 1:
+            rejects = (postselect == POSTSELECT_ALL
+                       or (postselect == POSTSELECT_LISTED and op.index in listed))
+            if rejects and v == 1:
                 discarded = True
         elif op.kind == "obs":
             if discarded:

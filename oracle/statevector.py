@@ -162,7 +162,7 @@ def sample_shot(circuit, seed: int, r: int, noise: NoiseSampler | None = None,
     return out
 
 
-def sample(circuit, seed: int, shots, postselect: int = POSTSELECT_NONE):
+def sample(circuit, seed: int, shots, postselect: int = POSTSELECT_NONE, post_dets=None):
     """Sample the listed shot indices (iterable of ints).
 
     Returns dict of uint8 arrays: records (S, R), dets (S, D), obs (S, O),
@@ -173,7 +173,7 @@ def sample(circuit, seed: int, shots, postselect: int = POSTSELECT_NONE):
     recs, dets, obss, disc, outs = [], [], [], [], []
     for r in shots:
         o = sample_shot(circuit, seed, r, noise)
-        rec, det, obs, d = finalize(circuit, o, postselect)
+        rec, det, obs, d = finalize(circuit, o, postselect, post_dets)
         recs.append(rec)
         dets.append(det)
         obss.append(obs)

@@ -560,7 +560,7 @@ def sample_shot(plan: Plan, seed: int, r: int, noise: NoiseSampler, prob_log=Non
 
 
 def sample(circuit, seed: int, shots, postselect: int = POSTSELECT_NONE, plan: Plan | None = None,
-           prob_log=None):
+           prob_log=None, post_dets=None):
     if plan is None:
         plan = Plan(circuit)
     shots = list(shots)
@@ -568,7 +568,7 @@ def sample(circuit, seed: int, shots, postselect: int = POSTSELECT_NONE, plan: P
     recs, dets, obss, disc, outs = [], [], [], [], []
     for r in shots:
         o = sample_shot(plan, seed, r, noise, prob_log=prob_log)
-        rec, det, obs, d = finalize(circuit, o, postselect)
+        rec, det, obs, d = finalize(circuit, o, postselect, post_dets)
         recs.append(rec)
         dets.append(det)
         obss.append(obs)

@@ -226,12 +226,12 @@ def outcomes(circuit, seed: int, shots):
     return out
 
 
-def sample(circuit, seed: int, shots, postselect: int = POSTSELECT_NONE):
+def sample(circuit, seed: int, shots, postselect: int = POSTSELECT_NONE, post_dets=None):
     shots = list(shots)
     o = outcomes(circuit, seed, shots)
     recs, dets, obss, disc = [], [], [], []
     for j in range(len(shots)):
-        rec, det, obs, d = finalize(circuit, o[j], postselect)
+        rec, det, obs, d = finalize(circuit, o[j], postselect, post_dets)
         recs.append(rec)
         dets.append(det)
         obss.append(obs)

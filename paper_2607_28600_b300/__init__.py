@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsymft.so")
 
 SYMFT_OK = 0
-POSTSELECT_NONE, POSTSELECT_ALL = 0, 1
+POSTSELECT_NONE, POSTSELECT_ALL, POSTSELECT_LISTED = 0, 1, 2
 FP32, FP64 = 0, 1
 OUT_DEVICE, OUT_HOST = 0, 1
 INSTR_NAMES = ("PromoteRot", "ActiveDiagRot", "ActivePairRot", "RandomMeas", "DetMeas",
@@ -24,7 +24,7 @@ INSTR_NAMES = ("PromoteRot", "ActiveDiagRot", "ActivePairRot", "RandomMeas", "De
 EXPORTS = ("symft_compile", "symft_compile_ex", "symft_plan_info", "symft_plan_free",
            "symft_sample", "symft_sample_ex", "symft_last_error", "symft_last_launch_count",
            "symft_sample_noalloc", "symft_noalloc_last_error", "symft_autotune",
-           "symft_sample_batch")
+           "symft_sample_batch", "symft_plan_active_meas")
 
 
 class SymftError(RuntimeError):
@@ -34,7 +34,8 @@ class SymftError(RuntimeError):
 
 
 class _Options(ctypes.Structure):
-    _fields_ = [("postselect", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+    _fields_ = [("postselect", ctypes.c_int), ("n_post_dets", ctypes.c_uint32),
+                ("post_dets", ctypes.POINTER(ctypes.c_uint32)), ("reserved", ctypes.c_int * 4)]
 
 
 class _Info(ctypes.Structure):
@@ -53,7 +54,8 @@ class _SampleArgs(ctypes.Structure):
                 ("det_out", ctypes.c_void_p), ("obs_out", ctypes.c_void_p),
                 ("discard_out", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("out_location", ctypes.c_int), ("check", ctypes.c_int),
-                ("plain", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("plain", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("prob_out", ctypes.c_void_p), ("counts_out", ctypes.c_void_p)]
 
 
 class _Job(ctypes.Structure):
@@ -62,7 +64,7 @@ class _Job(ctypes.Structure):
                 ("shot_offset", ctypes.c_uint64), ("meas_out", ctypes.c_void_p),
                 ("det_out", ctypes.c_void_p), ("obs_out", ctypes.c_void_p),
                 ("discard_out", ctypes.c_void_p), ("precision", ctypes.c_int),
-                ("plain", ctypes.c_int)]
+                ("plain", ctypes.c_int), ("counts_out", ctypes.c_void_p)]
 
 
 _LIB = None
@@ -83,6 +85,8 @@ def lib():
     L.symft_compile_ex.restype = ctypes.c_int
     L.symft_plan_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Info)]
     L.symft_plan_info.restype = ctypes.c_int
+    L.symft_plan_active_meas.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32]
+    L.symft_plan_active_meas.restype = ctypes.c_int
     L.symft_plan_free.argtypes = [ctypes.c_void_p]
     L.symft_plan_free.restype = None
     L.symft_sample.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
@@ -161,11 +165,22 @@ class Plan:
     def words(self, shots: int) -> int:
         return (shots + 63) // 64
 
+    def active_meas(self) -> list:
+        """Measurement ordinals of the active measurements (rows of prob_out)."""
+        return symft_plan_active_meas(self)
 
-def symft_compile(circuit_text: str, postselect: int = POSTSELECT_NONE) -> Plan:
+
+def symft_compile(circuit_text: str, postselect: int = POSTSELECT_NONE, post_dets=None) -> Plan:
+    """Compile circuit text.  postselect=POSTSELECT_LISTED rejects a shot only at
+    the detectors whose indices are listed in `post_dets`."""
     h = ctypes.c_void_p()
     opt = _Options()
     opt.postselect = postselect
+    if post_dets is not None:
+        dets = [int(d) for d in post_dets]
+        arr = (ctypes.c_uint32 * max(1, len(dets)))(*dets)
+        opt.n_post_dets = len(dets)
+        opt.post_dets = ctypes.cast(arr, ctypes.POINTER(ctypes.c_uint32))
     _check(lib().symft_compile_ex(circuit_text.encode(), ctypes.byref(opt), ctypes.byref(h)))
     return Plan(h.value)
 
@@ -180,6 +195,15 @@ def symft_plan_info(plan: Plan) -> dict:
     return d
 
 
+def symft_plan_active_meas(plan: Plan) -> list:
+    n = lib().symft_plan_active_meas(plan.handle, None, 0)
+    if n < 0:
+        _check(n)
+    buf = (ctypes.c_uint32 * max(1, n))()
+    _check(min(0, lib().symft_plan_active_meas(plan.handle, buf, n)))
+    return [int(buf[j]) for j in range(n)]
+
+
 def symft_sample(plan: Plan, shots: int, seed: int, meas_out=None, det_out=None, obs_out=None,
                  stream=None) -> None:
     _check(lib().symft_sample(plan.handle, shots, seed, _ptr(meas_out), _ptr(det_out),
@@ -189,7 +213,7 @@ def symft_sample(plan: Plan, shots: int, seed: int, meas_out=None, det_out=None,
 def symft_sample_ex(plan: Plan, shots: int, seed: int, shot_offset: int = 0, meas_out=None,
                     det_out=None, obs_out=None, discard_out=None, precision: int = FP32,
                     out_location: int = OUT_DEVICE, check: bool = False, stream=None,
-                    plain: bool = False) -> None:
+                    plain: bool = False, prob_out=None, counts_out=None) -> None:
     a = _SampleArgs()
     a.shots, a.seed, a.shot_offset = shots, seed, shot_offset
     a.meas_out, a.det_out = _ptr(meas_out), _ptr(det_out)
@@ -197,6 +221,7 @@ def symft_sample_ex(plan: Plan, shots: int, seed: int, shot_offset: int = 0, mea
     a.precision, a.out_location, a.check = precision, out_location, int(bool(check))
     a.plain = int(bool(plain))
     a.stream = _stream(stream)
+    a.prob_out, a.counts_out = _ptr(prob_out), _ptr(counts_out)
     _check(lib().symft_sample_ex(plan.handle, ctypes.byref(a)))
 
 
@@ -221,7 +246,8 @@ def symft_sample_batch(plans, jobs, stream=None) -> None:
     """Run jobs (dicts with plan index, shots, seed, outputs ...) as one CUDA graph launch.
 
     Each job: {"plan": i, "shots": n, "seed": s, "shot_offset": 0, "meas_out": t,
-    "det_out": t, "obs_out": t, "discard_out": t, "precision": FP32, "plain": False}.
+    "det_out": t, "obs_out": t, "discard_out": t, "precision": FP32, "plain": False,
+    "counts_out": t}.
     """
     arr_p = (ctypes.c_void_p * len(plans))(*[p.handle for p in plans])
     arr_j = (_Job * len(jobs))()
@@ -237,6 +263,7 @@ def symft_sample_batch(plans, jobs, stream=None) -> None:
         J.discard_out = _ptr(j.get("discard_out"))
         J.precision = j.get("precision", FP32)
         J.plain = int(bool(j.get("plain", False)))
+        J.counts_out = _ptr(j.get("counts_out"))
     _check(lib().symft_sample_batch(arr_p, len(plans), arr_j, len(jobs), _stream(stream)))
 
 

@@ -215,10 +215,12 @@ cudaError_t upload(symft_plan* P) {
 // allocates and decides everything on the host; enqueue() only issues
 // memsets and kernel launches, so it can also run inside a stream capture.
 struct Prep {
-  uint64_t W = 0, nblk = 0;
+  uint64_t W = 0, nblk = 0, shots = 0;
   bool plain = false, fp64 = false, need_final = false;
   uint64_t *meas = nullptr, *det = nullptr, *obs = nullptr, *disc = nullptr;
   uint64_t *signs = nullptr, *m3 = nullptr;
+  double* prob = nullptr;
+  uint64_t* counts = nullptr;
   int* status = nullptr;
   int sign_nb = 0, sign_grid = 0;
   int dense_kind = 0;   // 0 none, 1 register, 2 warp, 3 CTA per shot
@@ -241,7 +243,7 @@ int validate(const symft_sample_args* a) {
 
 // outputs: the device pointers the kernels write (caller's or host staging)
 int prepare(symft_plan* P, const symft_sample_args* a, uint64_t* meas, uint64_t* det, uint64_t* obs,
-            uint64_t* disc, Prep* o) {
+            uint64_t* disc, double* prob, uint64_t* counts, Prep* o) {
   const HostPlan& h = P->hp;
   if (!P->uploaded) {
     try {
@@ -253,6 +255,7 @@ int prepare(symft_plan* P, const symft_sample_args* a, uint64_t* meas, uint64_t*
   CUDA_TRY(set_smem_limits());
   const Tune& t = P->tune[a->precision == SYMFT_FP64 ? 1 : 0];
   o->W = (a->shots + 63) / 64;
+  o->shots = a->shots;
   o->nblk = (a->shots + kNoiseBlock - 1) / kNoiseBlock;
   o->plain = a->plain != 0;
   o->fp64 = a->precision == SYMFT_FP64;
@@ -260,11 +263,23 @@ int prepare(symft_plan* P, const symft_sample_args* a, uint64_t* meas, uint64_t*
   if (h.n_records == 0) meas = nullptr;
   if (h.n_dets == 0) det = nullptr;
   if (h.n_obs == 0) obs = nullptr;
-  o->need_final = h.n_m3 > 0 || h.postselect || disc != nullptr;
   if (h.postselect && det == nullptr && h.n_dets > 0) {
     CUDA_TRY(P->det_scratch.ensure(h.n_dets * W * 8));
     det = static_cast<uint64_t*>(P->det_scratch.ptr);
   }
+  if (counts) {   // the tallies read the observable and discard columns
+    if (h.n_obs && obs == nullptr) {
+      CUDA_TRY(P->obs_scratch.ensure(h.n_obs * W * 8));
+      obs = static_cast<uint64_t*>(P->obs_scratch.ptr);
+    }
+    if (h.postselect && disc == nullptr) {
+      CUDA_TRY(P->disc_scratch.ensure(W * 8));
+      disc = static_cast<uint64_t*>(P->disc_scratch.ptr);
+    }
+  }
+  o->need_final = h.n_m3 > 0 || h.postselect || disc != nullptr;
+  o->prob = h.n_m3 ? prob : nullptr;
+  o->counts = counts;
   o->meas = meas;
   o->det = det;
   o->obs = obs;
@@ -339,6 +354,23 @@ int prepare(symft_plan* P, const symft_sample_args* a, uint64_t* meas, uint64_t*
   return SYMFT_OK;
 }
 
+// tallies after the outputs are final (same stream, so in order)
+int enqueue_counts(symft_plan* P, const Prep& o, cudaStream_t st, int* launches) {
+  if (!o.counts) return SYMFT_OK;
+  const HostPlan& h = P->hp;
+  CUDA_TRY(cudaMemsetAsync(o.counts, 0, (2 + static_cast<size_t>(h.n_obs)) * 8, st));
+  CountArgs c{};
+  c.W = o.W;
+  c.shots = o.shots;
+  c.n_obs = o.obs ? h.n_obs : 0;
+  c.obs = o.obs;
+  c.discard = o.disc;
+  c.counts = reinterpret_cast<unsigned long long*>(o.counts);
+  CUDA_TRY(launch_count(c, P->sm_count, st));
+  ++*launches;
+  return SYMFT_OK;
+}
+
 int enqueue(symft_plan* P, const symft_sample_args* a, const Prep& o, cudaStream_t st, int* launches) {
   const HostPlan& h = P->hp;
   const uint64_t W = o.W;
@@ -359,9 +391,10 @@ int enqueue(symft_plan* P, const symft_sample_args* a, const Prep& o, cudaStream
     pa.discard = o.disc;
     pa.kmax = h.k_max;
     pa.status = o.status;
+    pa.prob = o.prob;
     CUDA_TRY(launch_plain(pa, o.fp64, o.plain_grid, st));
     ++*launches;
-    return SYMFT_OK;
+    return enqueue_counts(P, o, st, launches);
   }
   if (o.sign_grid > 0) {
     SignArgs s{};
@@ -394,6 +427,7 @@ int enqueue(symft_plan* P, const symft_sample_args* a, const Prep& o, cudaStream
     d.use_smem = o.dense_use_smem;
     d.gvec = o.gvec;
     d.gvec_stride = o.gvec_stride;
+    d.prob = o.prob;
     if (o.dense_kind == 1) CUDA_TRY(launch_dense_reg(d, o.fp64, o.dense_grid, st));
     else if (o.dense_kind == 2) CUDA_TRY(launch_dense(d, o.fp64, o.dense_wpb, o.dense_grid, o.dense_smem, st));
     else CUDA_TRY(launch_dense_cta(d, o.fp64, o.dense_grid, o.dense_smem, st));
@@ -412,7 +446,7 @@ int enqueue(symft_plan* P, const symft_sample_args* a, const Prep& o, cudaStream
     CUDA_TRY(launch_finalize(f, st));
     ++*launches;
   }
-  return SYMFT_OK;
+  return enqueue_counts(P, o, st, launches);
 }
 
 int sample_impl(symft_plan* P, const symft_sample_args* a) {
@@ -423,14 +457,18 @@ int sample_impl(symft_plan* P, const symft_sample_args* a) {
   const uint64_t W = (a->shots + 63) / 64;
   const bool host = a->out_location == SYMFT_OUT_HOST;
   uint64_t *meas = a->meas_out, *det = a->det_out, *obs = a->obs_out, *disc = a->discard_out;
+  double* prob = a->prob_out;
+  uint64_t* counts = a->counts_out;
   if (host) {
     if (meas) { CUDA_TRY(P->h_meas.ensure(std::max<uint64_t>(1, h.n_records * W) * 8)); meas = (uint64_t*)P->h_meas.ptr; }
     if (det) { CUDA_TRY(P->h_det.ensure(std::max<uint64_t>(1, h.n_dets * W) * 8)); det = (uint64_t*)P->h_det.ptr; }
     if (obs) { CUDA_TRY(P->h_obs.ensure(std::max<uint64_t>(1, h.n_obs * W) * 8)); obs = (uint64_t*)P->h_obs.ptr; }
     if (disc) { CUDA_TRY(P->h_disc.ensure(W * 8)); disc = (uint64_t*)P->h_disc.ptr; }
+    if (prob && h.n_m3) { CUDA_TRY(P->h_prob.ensure(h.n_m3 * a->shots * 8)); prob = (double*)P->h_prob.ptr; }
+    if (counts) { CUDA_TRY(P->h_counts.ensure((2 + h.n_obs) * 8)); counts = (uint64_t*)P->h_counts.ptr; }
   }
   Prep o;
-  rc = prepare(P, a, meas, det, obs, disc, &o);
+  rc = prepare(P, a, meas, det, obs, disc, prob, counts, &o);
   if (rc != SYMFT_OK) return rc;
   if (a->check) CUDA_TRY(cudaMemsetAsync(o.status, 0, sizeof(int), st));
   int launches = 0;
@@ -442,6 +480,10 @@ int sample_impl(symft_plan* P, const symft_sample_args* a) {
     if (a->det_out && o.det) CUDA_TRY(cudaMemcpyAsync(a->det_out, o.det, h.n_dets * W * 8, cudaMemcpyDeviceToHost, st));
     if (a->obs_out && o.obs) CUDA_TRY(cudaMemcpyAsync(a->obs_out, o.obs, h.n_obs * W * 8, cudaMemcpyDeviceToHost, st));
     if (a->discard_out && o.disc) CUDA_TRY(cudaMemcpyAsync(a->discard_out, o.disc, W * 8, cudaMemcpyDeviceToHost, st));
+    if (a->prob_out && o.prob)
+      CUDA_TRY(cudaMemcpyAsync(a->prob_out, o.prob, h.n_m3 * a->shots * 8, cudaMemcpyDeviceToHost, st));
+    if (a->counts_out && o.counts)
+      CUDA_TRY(cudaMemcpyAsync(a->counts_out, o.counts, (2 + h.n_obs) * 8, cudaMemcpyDeviceToHost, st));
   }
   if (host || a->check) CUDA_TRY(cudaStreamSynchronize(st));
   if (a->check) {
@@ -472,7 +514,7 @@ int autotune_impl(symft_plan* P, uint64_t shots, int precision, cudaStream_t st)
   auto time_cfg = [&](float* ms) -> int {
     Prep o;
     int rc = prepare(P, &a, static_cast<uint64_t*>(P->t_meas.ptr), static_cast<uint64_t*>(P->t_det.ptr),
-                     static_cast<uint64_t*>(P->t_obs.ptr), static_cast<uint64_t*>(P->t_disc.ptr), &o);
+                     static_cast<uint64_t*>(P->t_obs.ptr), static_cast<uint64_t*>(P->t_disc.ptr), nullptr, nullptr, &o);
     if (rc != SYMFT_OK) return rc;
     int l = 0;
     rc = enqueue(P, &a, o, st, &l);   // warm-up
@@ -549,6 +591,7 @@ int batch_impl(const symft_plan* const* plans, int n_plans, const symft_job* job
   if (!plans || !jobs || n_plans <= 0 || n_jobs <= 0) return set_error(SYMFT_E_ARG, "empty batch");
   std::vector<symft_sample_args> args(n_jobs);
   std::vector<uint64_t> max_shots(n_plans, 0);
+  std::vector<char> any_counts(n_plans, 0);
   for (int j = 0; j < n_jobs; ++j) {
     const symft_job& J = jobs[j];
     if (J.plan >= static_cast<uint32_t>(n_plans) || !plans[J.plan])
@@ -564,9 +607,11 @@ int batch_impl(const symft_plan* const* plans, int n_plans, const symft_job* job
     a.discard_out = J.discard_out;
     a.precision = J.precision;
     a.plain = J.plain;
+    a.counts_out = J.counts_out;
     int rc = validate(&a);
     if (rc != SYMFT_OK) return set_error(rc, "job " + std::to_string(j) + ": " + g_last_error);
     max_shots[J.plan] = std::max(max_shots[J.plan], J.shots);
+    if (J.counts_out) any_counts[J.plan] = 1;
   }
   // size every plan's workspace for its largest job first, so no later
   // prepare() moves a buffer another job of the same plan already uses
@@ -578,15 +623,20 @@ int batch_impl(const symft_plan* const* plans, int n_plans, const symft_job* job
       a.shots = max_shots[p];
       a.precision = prec;
       Prep o;
-      int rc = prepare(P, &a, nullptr, nullptr, nullptr, nullptr, &o);
+      int rc = prepare(P, &a, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, &o);
       if (rc != SYMFT_OK) return rc;
       if (P->hp.postselect && P->hp.n_dets) CUDA_TRY(P->det_scratch.ensure(P->hp.n_dets * o.W * 8));
+      if (any_counts[p]) {
+        if (P->hp.n_obs) CUDA_TRY(P->obs_scratch.ensure(P->hp.n_obs * o.W * 8));
+        if (P->hp.postselect) CUDA_TRY(P->disc_scratch.ensure(o.W * 8));
+      }
     }
   }
   std::vector<Prep> preps(n_jobs);
   for (int j = 0; j < n_jobs; ++j) {
     symft_plan* P = const_cast<symft_plan*>(plans[jobs[j].plan]);
-    int rc = prepare(P, &args[j], args[j].meas_out, args[j].det_out, args[j].obs_out, args[j].discard_out, &preps[j]);
+    int rc = prepare(P, &args[j], args[j].meas_out, args[j].det_out, args[j].obs_out, args[j].discard_out,
+                     nullptr, args[j].counts_out, &preps[j]);
     if (rc != SYMFT_OK) return set_error(rc, "job " + std::to_string(j) + ": " + g_last_error);
   }
   // capture: one branch per plan (jobs of a plan share its workspace, in order)
@@ -667,10 +717,18 @@ int symft_compile_ex(const char* text, const symft_options* opt, symft_plan** ou
   *out = nullptr;
   symft_options o{};
   if (opt) o = *opt;
-  if (o.postselect != SYMFT_POSTSELECT_NONE && o.postselect != SYMFT_POSTSELECT_ALL)
+  if (o.postselect != SYMFT_POSTSELECT_NONE && o.postselect != SYMFT_POSTSELECT_ALL &&
+      o.postselect != SYMFT_POSTSELECT_LISTED)
     return set_error(SYMFT_E_ARG, "bad postselect mode");
+  if (o.postselect == SYMFT_POSTSELECT_LISTED && o.n_post_dets > 0 && o.post_dets == nullptr)
+    return set_error(SYMFT_E_ARG, "postselect LISTED: null post_dets");
   try {
     Circuit c = parse_circuit(text);
+    if (o.postselect == SYMFT_POSTSELECT_LISTED)
+      for (uint32_t i = 0; i < o.n_post_dets; ++i)
+        if (o.post_dets[i] >= c.n_dets)
+          return set_error(SYMFT_E_ARG, "postselect LISTED: detector " + std::to_string(o.post_dets[i]) +
+                                            " out of range (" + std::to_string(c.n_dets) + " detectors)");
     symft_plan* p = new symft_plan();
     try {
       p->hp = compile_plan(c, o);
@@ -714,12 +772,24 @@ int symft_plan_info(const symft_plan* p, symft_info* info) {
   return SYMFT_OK;
 }
 
+int symft_plan_active_meas(const symft_plan* p, uint32_t* t_out, uint32_t capacity) {
+  if (!p) return set_error(SYMFT_E_ARG, "null plan");
+  if (capacity > 0 && t_out == nullptr) return set_error(SYMFT_E_ARG, "null t_out");
+  const auto& t = p->hp.m3_t;
+  for (uint32_t j = 0; j < capacity && j < t.size(); ++j) t_out[j] = t[j];
+  return static_cast<int>(t.size());
+}
+
 void symft_plan_free(symft_plan* p) {
   if (!p) return;
   p->plan_buf.release();
   p->signs.release();
   p->m3.release();
   p->det_scratch.release();
+  p->obs_scratch.release();
+  p->disc_scratch.release();
+  p->h_prob.release();
+  p->h_counts.release();
   p->gvec.release();
   p->status.release();
   p->h_meas.release();

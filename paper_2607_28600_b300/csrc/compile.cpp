@@ -536,7 +536,6 @@ void Compiler::lower(HostPlan& P) {
   P.n_obs = c_.n_obs;
   P.n_channels = c_.n_channels;
   P.k_max = kmax_;
-  P.postselect = opt_.postselect;
   P.n_comp = n_comp_;
   for (auto& I : instrs_) P.hist[I.kind]++;
 
@@ -898,16 +897,21 @@ void Compiler::lower(HostPlan& P) {
     P.ch_theta_last[op.channel] = live ? P.qtabs[qi].theta[kNoiseBlock - 1] : 0;
   }
 
-  // postselection event order
-  int32_t last_det = -1;
-  P.rec_det_before.assign(R, -1);
+  // postselection event order (Sec. 6, detector postselection): which
+  // detectors reject a shot, and where each sits among the records
+  std::vector<uint8_t> post(c_.n_dets, 0);
+  if (opt_.postselect == SYMFT_POSTSELECT_ALL) {
+    std::fill(post.begin(), post.end(), 1);
+  } else if (opt_.postselect == SYMFT_POSTSELECT_LISTED) {
+    for (uint32_t i = 0; i < opt_.n_post_dets; ++i) post[opt_.post_dets[i]] = 1;
+  }
+  P.postselect = 0;
+  for (uint8_t v : post) P.postselect |= v;
   for (const Op& op : c_.ops) {
     if (op.kind == OP_MEAS && op.rec >= 0) {
       P.post_events.push_back(op.rec);
-      P.rec_det_before[op.rec] = last_det;
     } else if (op.kind == OP_DET) {
-      P.post_events.push_back(-1 - static_cast<int32_t>(op.index));
-      last_det = static_cast<int32_t>(op.index);
+      P.post_events.push_back(-1 - static_cast<int32_t>(2 * op.index + post[op.index]));
     }
   }
 }

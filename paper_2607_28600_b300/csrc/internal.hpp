@@ -137,9 +137,9 @@ struct HostPlan {
   std::vector<uint8_t> plain_const;
   std::vector<uint32_t> plain_off, plain_sym;
 
-  // postselection order: events in circuit order, rec (>=0) or det (-1-i)
+  // postselection order: events in circuit order, record r (>= 0) or
+  // detector i (-1 - (2 i + p), p = 1 when detector i is postselected)
   std::vector<int32_t> post_events;
-  std::vector<int32_t> rec_det_before;   // last detector index before record r (-1 none)
 
   // dense executor
   std::vector<DenseInstr> dense;

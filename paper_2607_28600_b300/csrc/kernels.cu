@@ -609,14 +609,22 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
             double S0 = 0.0, S1 = 0.0;
             branch_sums<Real, double>(vec, I, n, lane, 32, mcr, mci, S0, S1);
             warp_sum2(S0, S1);
-            if (lane == 0) m = decide64(meas_U(A.seed, I.t, rg), (l0 ? S1 : S0) / (S0 + S1));
+            if (lane == 0) {
+              const double p0 = (l0 ? S1 : S0) / (S0 + S1);
+              m = decide64(meas_U(A.seed, I.t, rg), p0);
+              if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = p0;
+            }
             m = __shfl_sync(0xffffffffu, m, 0);
             scale = (Real)(1.0 / sqrt((l0 ^ m) ? S1 : S0));
           } else {                                         // FP32 sums below 2^14 terms
             float S0 = 0.0f, S1 = 0.0f;
             branch_sums<Real, float>(vec, I, n, lane, 32, mcr, mci, S0, S1);
             warp_sum2(S0, S1);
-            if (lane == 0) m = decide32(meas_U(A.seed, I.t, rg), (l0 ? S1 : S0) / (S0 + S1));
+            if (lane == 0) {
+              const float p0 = (l0 ? S1 : S0) / (S0 + S1);
+              m = decide32(meas_U(A.seed, I.t, rg), p0);
+              if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = (double)p0;
+            }
             m = __shfl_sync(0xffffffffu, m, 0);
             scale = (Real)rsqrtf((l0 ^ m) ? S1 : S0);
           }
@@ -794,8 +802,16 @@ __global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) 
         uint32_t m = 0;
         if (lane == 0) {
           const uint64_t U = meas_U(A.seed, I.t, rg);
-          m = sizeof(Real) == 8 ? decide64(U, (double)(l0 ? s1 : s0) / (double)(s0 + s1))
-                                : decide32(U, (float)((l0 ? s1 : s0) / (s0 + s1)));
+          double pd;
+          if (sizeof(Real) == 8) {
+            pd = (double)(l0 ? s1 : s0) / (double)(s0 + s1);
+            m = decide64(U, pd);
+          } else {
+            const float pf = (float)((l0 ? s1 : s0) / (s0 + s1));
+            m = decide32(U, pf);
+            pd = (double)pf;
+          }
+          if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = pd;
         }
         m = __shfl_sync(0xffffffffu, m, 0);
         const uint32_t lab = l0 ^ m;
@@ -950,7 +966,9 @@ __global__ void __launch_bounds__(kCtaThreads) dense_cta_kernel(DenseArgs A) {
           S1 += red[kCtaThreads / 32 + w2];
         }
         if (tid == 0) {
-          const uint32_t m = decide64(meas_U(A.seed, I.t, rg), (l0 ? S1 : S0) / (S0 + S1));
+          const double p0 = (l0 ? S1 : S0) / (S0 + S1);
+          const uint32_t m = decide64(meas_U(A.seed, I.t, rg), p0);
+          if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = p0;
           bcast[1] = (int)m;
           if (m) {
             m3b[I.m3 >> 5] |= 1u << (I.m3 & 31);
@@ -1249,6 +1267,7 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs A) {
         const double p0 = (l0 ? S1 : S0) / (S0 + S1);
         if (tid == 0) {
           const uint32_t m = meas_uniform(A.seed, I.t, rg) < p0 ? 0u : 1u;
+          if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = p0;
           bcast[1] = (int)m;
           if (m) m3b[I.m3 >> 5] |= 1u << (I.m3 & 31);
         }
@@ -1305,9 +1324,10 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs A) {
           if (ev >= 0) {
             if (cut) val[ev] = 0;
           } else {
-            const uint32_t di = R + (uint32_t)(-1 - ev);
+            const uint32_t code = (uint32_t)(-1 - ev);
+            const uint32_t di = R + (code >> 1);
             if (cut) val[di] = 0;
-            else if (val[di]) cut = 1;
+            else if ((code & 1u) && val[di]) cut = 1;
           }
         }
         if (cut)
@@ -1361,10 +1381,11 @@ __global__ void finalize_kernel(FinalArgs A) {
         if (ev >= 0) {
           if (A.meas) A.meas[(uint64_t)ev * A.W + w] &= ~cut;
         } else {
-          uint64_t* d = A.det + (uint64_t)(-1 - ev) * A.W + w;
+          const uint32_t code = (uint32_t)(-1 - ev);
+          uint64_t* d = A.det + (uint64_t)(code >> 1) * A.W + w;
           uint64_t v = *d & ~cut;
           *d = v;
-          cut |= v;
+          if (code & 1u) cut |= v;
         }
       }
       if (A.obs)
@@ -1372,6 +1393,43 @@ __global__ void finalize_kernel(FinalArgs A) {
       if (A.discard) A.discard[w] = cut & pad;
     } else if (A.discard) {
       A.discard[w] = 0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tallies of a request: kept and discarded shots, and for each observable the
+// kept shots that read 1 (the undetected logical errors of a memory or
+// distillation experiment).  Pass j = 0 counts kept/discarded, pass j >= 1
+// observable j - 1; each warp adds its partial counts with one atomic.
+// ---------------------------------------------------------------------------
+__global__ void count_kernel(CountArgs A) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t w0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (uint32_t j = 0; j <= A.n_obs; ++j) {
+    unsigned long long c0 = 0, c1 = 0;
+    for (uint64_t w = w0; w < A.W; w += stride) {
+      uint64_t pad = ~0ull;
+      if (w == A.W - 1 && (A.shots & 63)) pad = (1ull << (A.shots & 63)) - 1;
+      const uint64_t d = A.discard ? (A.discard[w] & pad) : 0ull;
+      if (j == 0) {
+        c0 += (unsigned long long)__popcll(pad & ~d);
+        c1 += (unsigned long long)__popcll(d);
+      } else {
+        c0 += (unsigned long long)__popcll(A.obs[(uint64_t)(j - 1) * A.W + w] & pad & ~d);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      c0 += __shfl_down_sync(0xffffffffu, c0, o);
+      c1 += __shfl_down_sync(0xffffffffu, c1, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      if (j == 0) {
+        if (c0) atomicAdd(A.counts + 0, c0);
+        if (c1) atomicAdd(A.counts + 1, c1);
+      } else if (c0) {
+        atomicAdd(A.counts + 1 + j, c0);
+      }
     }
   }
 }
@@ -1478,6 +1536,16 @@ cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t st) {
   if (blocks > 65535) blocks = 65535;
   if (blocks == 0) blocks = 1;
   finalize_kernel<<<(unsigned)blocks, threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count(const CountArgs& a, int sm_count, cudaStream_t st) {
+  const int threads = 256;
+  uint64_t blocks = (a.W + threads - 1) / threads;
+  const uint64_t cap = static_cast<uint64_t>(sm_count > 0 ? sm_count : 1) * 4;
+  if (blocks > cap) blocks = cap;
+  if (blocks == 0) blocks = 1;
+  count_kernel<<<(unsigned)blocks, threads, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -69,6 +69,8 @@ struct DevPlan {
   const uint32_t* lvl_rec;
   const uint32_t* gat_off;      // det / obs -> records (CSR)
   const uint32_t* gat_rec;
+  // postselection walk in circuit order: record r as r (>= 0), detector i as
+  // -1 - (2 i + p) with p = 1 when detector i is postselected
   uint32_t n_post_events;
   const int32_t* post_events;
   uint32_t n_dense;
@@ -76,7 +78,7 @@ struct DevPlan {
   const uint32_t* dense_causal;
   uint32_t n_m3;
   uint32_t n_records, n_dets, n_obs;
-  int postselect;
+  int postselect;               // non-zero when any detector is postselected
   // plain (per-shot) form
   uint32_t n_comp;
   const uint8_t* plain_const;   // [records][dets][obs][dense signs]
@@ -112,6 +114,7 @@ struct DenseArgs {
   uint32_t kmax;
   int use_smem;
   int* status;
+  double* prob;           // Pr(m = 0) per active measurement and shot (n_m3 x shots) or null
 };
 
 struct PlainArgs {
@@ -126,6 +129,7 @@ struct PlainArgs {
   uint64_t* discard;
   uint32_t kmax;
   int* status;
+  double* prob;           // as in DenseArgs
 };
 
 struct FinalArgs {
@@ -137,6 +141,17 @@ struct FinalArgs {
   uint64_t* det;          // required when postselecting
   uint64_t* obs;
   uint64_t* discard;
+};
+
+// Tallies of one request: kept shots, discarded shots, and per observable the
+// kept shots whose observable bit is 1.
+struct CountArgs {
+  uint64_t W;
+  uint64_t shots;
+  uint32_t n_obs;
+  const uint64_t* obs;      // may be null when n_obs == 0
+  const uint64_t* discard;  // may be null (no postselection)
+  unsigned long long* counts;   // 2 + n_obs, zeroed before launch
 };
 
 }  // namespace symft

@@ -43,6 +43,7 @@ cudaError_t sign_occupancy(const DevPlan& p, int nb, int* ctas_per_sm);
 cudaError_t launch_dense(const DenseArgs& a, bool fp64, int warps_per_block, int grid, size_t smem,
                          cudaStream_t st);
 cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t st);
+cudaError_t launch_count(const CountArgs& a, int sm_count, cudaStream_t st);
 cudaError_t set_smem_limits();
 size_t plain_smem_bytes(const DevPlan& p, uint32_t kmax, bool fp64);
 size_t dense_reg_smem_bytes(const DevPlan& p);
@@ -73,7 +74,9 @@ struct symft_plan {
   symft::DevBuf plan_buf;
   symft::DevPlan dp{};
   symft::DevBuf signs, m3, det_scratch, gvec, status;
+  symft::DevBuf obs_scratch, disc_scratch;      // tallies without obs / discard outputs
   symft::DevBuf h_meas, h_det, h_obs, h_disc;   // staging for host outputs
+  symft::DevBuf h_prob, h_counts;
   symft::DevBuf t_meas, t_det, t_obs, t_disc;   // outputs of autotuning probes
   symft::Tune tune[2];                          // FP32, FP64
   int sm_count = 0;

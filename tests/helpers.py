@@ -25,22 +25,23 @@ def padding_is_zero(cols, shots):
     return bool((tail == 0).all())
 
 
-def oracle_sample(text, seed, shots, postselect=0, kind="auto"):
+def oracle_sample(text, seed, shots, postselect=0, kind="auto", post_dets=None):
     c = oparse(text)
     has_rot = any(op.kind == "rot" for op in c.ops)
     if kind == "auto":
         kind = "symft" if has_rot else "tableau"
     if kind == "tableau":
-        return otab.sample(c, seed, shots, postselect)
+        return otab.sample(c, seed, shots, postselect, post_dets=post_dets)
     if kind == "sv":
-        return osv.sample(c, seed, shots, postselect)
-    return osymft.sample(c, seed, shots, postselect)
+        return osv.sample(c, seed, shots, postselect, post_dets=post_dets)
+    return osymft.sample(c, seed, shots, postselect, post_dets=post_dets)
 
 
-def gpu_sample(text, shots, seed, shot_offset=0, precision=0, postselect=0, host=False):
+def gpu_sample(text, shots, seed, shot_offset=0, precision=0, postselect=0, host=False,
+               post_dets=None):
     import torch
     import paper_2607_28600_b300 as S
-    plan = S.symft_compile(text, postselect=postselect)
+    plan = S.symft_compile(text, postselect=postselect, post_dets=post_dets)
     info = plan.info
     W = (shots + 63) // 64
     if host:

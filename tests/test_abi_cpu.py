@@ -101,3 +101,58 @@ def test_repeat_and_generators_compile():
     assert p.info["n_records"] == 4 and p.info["n_dets"] == 3
     p2 = S.symft_compile(random_near_clifford(20, 30, 6, seed=3))
     assert p2.info["n_qubits"] == 20
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the ABI structs have the C sizes and field offsets."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    structs = {"symft_options": S._Options, "symft_info": S._Info,
+               "symft_sample_args": S._SampleArgs, "symft_job": S._Job}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "symft.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                   text=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert int(got[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
+
+
+def test_listed_postselection_validation():
+    txt = "M 0\nDETECTOR rec[-1]\nM 1\nDETECTOR rec[-1]\n"
+    S.symft_compile(txt, postselect=S.POSTSELECT_LISTED, post_dets=[1, 1, 0])
+    S.symft_compile(txt, postselect=S.POSTSELECT_LISTED, post_dets=[])
+    with pytest.raises(S.SymftError) as ei:
+        S.symft_compile(txt, postselect=S.POSTSELECT_LISTED, post_dets=[2])
+    assert ei.value.code == -3 and "out of range" in str(ei.value)
+    with pytest.raises(S.SymftError) as ei:
+        S.symft_compile(txt, postselect=3)
+    assert ei.value.code == -3
+    opt = S._Options()
+    opt.postselect = S.POSTSELECT_LISTED
+    opt.n_post_dets = 2            # no list given
+    h = ctypes.c_void_p()
+    assert S.lib().symft_compile_ex(txt.encode(), ctypes.byref(opt), ctypes.byref(h)) == -3
+
+
+def test_active_measurement_ordinals_match_the_oracle_plan():
+    for trial in range(10):
+        rng = random.Random(700 + trial)
+        txt = random_clifford_text(rng, rng.randint(2, 7), 60, rot=0.3)
+        p = S.symft_compile(txt)
+        o = osymft.Plan(oparse(txt))
+        want = [ins["t"] for ins in o.instrs if ins["op"] in ("ActiveDiagMeas", "ActivePairMeas")]
+        assert p.active_meas() == want
+        assert len(want) == p.info["n_causal"]
+    assert S.symft_compile("H 0\nM 0\n").active_meas() == []

@@ -1,0 +1,187 @@
+"""GPU checks of the optional outputs: branch probabilities of the active
+measurements (prob_out), listed-detector postselection, and the kept /
+discarded / observable tallies (counts_out), all through the C-ABI.
+
+Branch probabilities are compared with the state-vector oracle, which computes
+Pr(m = 0) of every measurement from the full state (Sec. 4: the active
+measurement formulas must give the same number).  FP64 runs agree to 1e-9 on
+every active measurement.  FP32 runs must agree to 1e-5 on every active
+measurement up to and including the first outcome flip of a shot (a flip is a
+measurement whose FP32 and FP64 probabilities fall on different sides of the
+shot's uniform; later measurements of that shot follow a different branch).
+"""
+import random
+
+import numpy as np
+import pytest
+
+from oracle import statevector as osv
+from oracle.circuit import parse as oparse
+from oracle.noise import NoiseSampler
+from oracle.streams import meas_uniform, outcome_from
+from paper_2607_28600_b300.workloads import random_near_clifford, rotated_surface_code_memory
+from tests.circuits_for_tests import random_clifford_text
+from tests.helpers import gpu_sample, oracle_sample, unpack
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    rng = random.Random(4002)
+    return {
+        # k <= 5: register-resident warp executor
+        "reg": random_clifford_text(rng, 6, 60, rot=0.25),
+        # k = 10: warp per shot, vector in shared memory
+        "warp": random_near_clifford(12, 24, 12, 1e-3, seed=1),
+        # k = 13: CTA per shot, vector in shared memory
+        "cta": random_near_clifford(14, 30, 14, 1e-3, seed=1),
+        # k = 14: CTA per shot; the FP64 vector (256 KB) lives in a global slot
+        "cta_global": random_near_clifford(14, 40, 20, 1e-3, seed=0),
+    }
+
+
+def _gpu_probs(text, shots, seed, precision, plain=False):
+    import paper_2607_28600_b300 as S
+    plan = S.symft_compile(text)
+    info = plan.info
+    W = (shots + 63) // 64
+    meas = torch.zeros((max(1, info["n_records"]), W), dtype=torch.int64, device="cuda")
+    prob = torch.full((max(1, info["n_causal"]), shots), float("nan"), dtype=torch.float64, device="cuda")
+    S.symft_sample_ex(plan, shots, seed, meas_out=meas, precision=precision, check=True,
+                      prob_out=prob, plain=plain)
+    torch.cuda.synchronize()
+    recs = unpack(meas.cpu().numpy().view(np.uint64)[: info["n_records"]], shots)
+    return plan, recs, prob.cpu().numpy()[: info["n_causal"]]
+
+
+def _sv_probs(text, seed, shots, active_t):
+    c = oparse(text)
+    noise = NoiseSampler(c, seed)
+    probs = np.zeros((len(active_t), shots))
+    for r in range(shots):
+        log = []
+        osv.sample_shot(c, seed, r, noise, prob_log=log)
+        p = dict(log)
+        probs[:, r] = [p[t] for t in active_t]
+    return probs
+
+
+@pytest.mark.parametrize("case", ["reg", "warp", "cta", "cta_global"])
+def test_branch_probabilities_vs_statevector(case):
+    text = _cases()[case]
+    shots = {"reg": 500, "warp": 300, "cta": 120, "cta_global": 120}[case]
+    seed = 21
+    plan, rec64, p64 = _gpu_probs(text, shots, seed, precision=1)
+    _, rec32, p32 = _gpu_probs(text, shots, seed, precision=0)
+    act = plan.active_meas()
+    k = plan.info["k_max"]
+    assert {"reg": k <= 5, "warp": k == 10, "cta": k == 13, "cta_global": k == 14}[case]
+    ref = _sv_probs(text, seed, shots, act)
+    # FP64: every active measurement of every shot
+    assert np.isfinite(p64).all()
+    assert np.abs(p64 - ref).max() <= 1e-9
+    o = oracle_sample(text, seed, range(shots), kind="sv")
+    np.testing.assert_array_equal(rec64, o["records"])
+    # FP32: prefixes up to and including the first flip
+    flips, worst = 0, 0.0
+    for r in range(shots):
+        for j, t in enumerate(act):
+            u = meas_uniform(seed, t, r)
+            worst = max(worst, abs(p32[j, r] - ref[j, r]))
+            if outcome_from(p32[j, r], u) != outcome_from(ref[j, r], u):
+                flips += 1
+                break
+        else:
+            np.testing.assert_array_equal(rec32[r], o["records"][r])
+    assert worst <= 1e-5, worst
+    assert flips <= max(1, shots // 50)
+
+
+def test_plain_form_reports_the_same_probabilities():
+    text = _cases()["warp"]
+    _, r1, p1 = _gpu_probs(text, 64, 5, precision=1)
+    _, r2, p2 = _gpu_probs(text, 64, 5, precision=1, plain=True)
+    np.testing.assert_array_equal(r1, r2)
+    assert np.abs(p1 - p2).max() <= 1e-12
+
+
+@pytest.mark.parametrize("rot", [False, True])
+def test_listed_postselection_bit_exact(rot):
+    text = rotated_surface_code_memory(3, 3, 2e-2, t_on_data0_after_round=0 if rot else None)
+    n_dets = oparse(text).num_dets
+    listed = sorted(random.Random(8).sample(range(n_dets), n_dets // 3))
+    shots = 900
+    plan, meas, det, obs, disc = gpu_sample(text, shots, 3, precision=1, postselect=2, post_dets=listed)
+    o = oracle_sample(text, 3, range(shots), postselect=2, post_dets=listed)
+    g = {"records": unpack(meas, shots), "dets": unpack(det, shots), "obs": unpack(obs, shots),
+         "discard": unpack(disc.reshape(1, -1), shots)[:, 0]}
+    for key in ("discard", "records", "dets", "obs"):
+        np.testing.assert_array_equal(g[key], o[key], err_msg=key)
+    assert 0.02 < g["discard"].mean() < 0.98
+    # the plain per-shot form applies the same rule
+    import paper_2607_28600_b300 as S
+    W = (shots + 63) // 64
+    d2 = torch.zeros((n_dets, W), dtype=torch.int64, device="cuda")
+    x2 = torch.zeros((W,), dtype=torch.int64, device="cuda")
+    S.symft_sample_ex(plan, shots, 3, det_out=d2, discard_out=x2, precision=1, plain=True, check=True)
+    np.testing.assert_array_equal(d2.cpu().numpy().view(np.uint64), det)
+    np.testing.assert_array_equal(x2.cpu().numpy().view(np.uint64), disc)
+
+
+def _popcounts(obs, disc, shots):
+    o = unpack(obs, shots)
+    d = unpack(disc.reshape(1, -1), shots)[:, 0]
+    kept = d == 0
+    return [int(kept.sum()), int((~kept).sum())] + [int(o[kept, j].sum()) for j in range(o.shape[1])]
+
+
+def test_counts_match_the_output_columns():
+    import paper_2607_28600_b300 as S
+    text = rotated_surface_code_memory(3, 3, 2e-2)
+    shots = 5000
+    plan, meas, det, obs, disc = gpu_sample(text, shots, 4, postselect=1)
+    want = _popcounts(obs, disc, shots)
+    n = 2 + plan.info["n_obs"]
+    # device counts, every output requested
+    c = torch.zeros((n,), dtype=torch.int64, device="cuda")
+    W = (shots + 63) // 64
+    ob = torch.zeros((plan.info["n_obs"], W), dtype=torch.int64, device="cuda")
+    dc = torch.zeros((W,), dtype=torch.int64, device="cuda")
+    S.symft_sample_ex(plan, shots, 4, obs_out=ob, discard_out=dc, counts_out=c, check=True)
+    assert c.cpu().tolist() == want
+    # counts alone: the library keeps the observable and discard columns itself
+    c.zero_()
+    S.symft_sample_ex(plan, shots, 4, counts_out=c, check=True)
+    assert c.cpu().tolist() == want
+    # host counts
+    hc = np.zeros((n,), dtype=np.uint64)
+    S.symft_sample_ex(plan, shots, 4, counts_out=hc, out_location=S.OUT_HOST)
+    assert hc.tolist() == want
+    # without postselection every shot is kept
+    plan2 = S.symft_compile(text)
+    c2 = torch.zeros((n,), dtype=torch.int64, device="cuda")
+    ob2 = torch.zeros((plan2.info["n_obs"], W), dtype=torch.int64, device="cuda")
+    S.symft_sample_ex(plan2, shots, 4, obs_out=ob2, counts_out=c2, check=True)
+    got = c2.cpu().tolist()
+    assert got[:2] == [shots, 0]
+    assert got[2] == int(unpack(ob2.cpu().numpy().view(np.uint64), shots)[:, 0].sum())
+
+
+def test_batch_job_counts():
+    import paper_2607_28600_b300 as S
+    text = rotated_surface_code_memory(3, 3, 2e-2)
+    plan = S.symft_compile(text, postselect=1)
+    shots = 3000
+    W = (shots + 63) // 64
+    n = 2 + plan.info["n_obs"]
+    cs = [torch.zeros((n,), dtype=torch.int64, device="cuda") for _ in range(2)]
+    ob = torch.zeros((plan.info["n_obs"], W), dtype=torch.int64, device="cuda")
+    dc = torch.zeros((W,), dtype=torch.int64, device="cuda")
+    jobs = [{"plan": 0, "shots": shots, "seed": 6, "counts_out": cs[0]},
+            {"plan": 0, "shots": shots, "seed": 6, "obs_out": ob, "discard_out": dc,
+             "counts_out": cs[1]}]
+    S.symft_sample_batch([plan], jobs)
+    torch.cuda.synchronize()
+    want = _popcounts(ob.cpu().numpy().view(np.uint64), dc.cpu().numpy().view(np.uint64), shots)
+    assert cs[0].cpu().tolist() == want and cs[1].cpu().tolist() == want
