@@ -100,7 +100,8 @@ typedef struct {
 typedef struct {
   uint64_t shots;          /* number of shots (>= 1) */
   uint64_t seed;           /* Philox key */
-  uint64_t shot_offset;    /* absolute index of the first shot; multiple of 128 */
+  uint64_t shot_offset;    /* absolute index of the first shot; multiple of 512 (the
+                              noise block of the random-stream specification) */
   uint64_t* meas_out;      /* n_records * W words */
   uint64_t* det_out;       /* n_dets * W words */
   uint64_t* obs_out;       /* n_obs * W words */
@@ -189,7 +190,7 @@ int symft_sample(const symft_plan* plan, uint64_t shots, uint64_t seed,
 int symft_sample_ex(const symft_plan* plan, const symft_sample_args* args);
 
 /* Pick the plan's launch shapes for one precision by timing candidates
- * (noise blocks per sign-kernel CTA, executor grid sizes, warps per CTA) on
+ * (resident sign-kernel CTAs per SM, executor grid sizes, warps per CTA) on
  * `shots` shots with throw-away outputs; later calls on the plan use the
  * winner.  Runs synchronously on `cuda_stream`; allocates probe buffers. */
 int symft_autotune(symft_plan* plan, uint64_t shots, int precision, void* cuda_stream);

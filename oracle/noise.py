@@ -1,7 +1,7 @@
 """Per-shot Pauli noise drawn from the shared stream specification (oracle side).
 
 Test infrastructure only.  For each noise channel of a parsed circuit and each
-128-shot block, the word-geometric process of ``oracle.streams`` yields the
+512-shot block, the block-geometric process of ``oracle.streams`` yields the
 (lane, cell) fire list; this module turns it into "shot r applies Pauli cell k
 of channel c".  The Pauli noise channel itself is the one of Sec. 2
 (N(rho) = sum_j p_j N_j rho N_j): a fired cell k applies N_k, no fire applies I.

@@ -10,14 +10,17 @@ independently on each side:
 Key      Philox key = (seed & 0xffffffff, seed >> 32).
 
 Noise    Channel ordinal c (circuit order, after REPEAT unrolling), shot block
-         b = shot >> 7 (NOISE_BLOCK = 128 shots, lanes 0..127).
+         b = shot >> 9 (NOISE_BLOCK = 512 shots, lanes 0..511).
          head draw          = Philox(c >> 2, b, 0, TAG_HEAD)[c & 3]
          tail draw i (>= 0) = Philox(c, b, i >> 2, TAG_TAIL)[i & 3]
-         Word-geometric process: L = 0, u = head draw;
-           j* = min{ j in [0, 127 - L] : u < THETA_j }, stop if none;
+         Block-geometric process: L = 0, u = head draw;
+           j* = min{ j in [0, 511 - L] : u < THETA_j }, stop if none;
            the channel fires on lane L + j*; if it has more than one Pauli
            cell the next tail draw v picks cell min{ k : v < PHI_k };
-           L = L + j* + 1 (stop at 128); u = next tail draw; repeat.
+           L = L + j* + 1 (stop at 512); u = next tail draw; repeat.
+         The block length is a choice of this specification (the paper
+         samples sparse noise by geometric gaps, Sec. 6, and fixes no block):
+         512 lanes make one head draw cover ~0.5 expected fires at q = 1e-3.
          THETA_j = min(floor((1 - r^(j+1)) * 2^32), 2^32 - 1), r = 1 - q,
          r^(j+1) by repeated multiplication in FP64; q = the channel's total
          error probability.  PHI_k = min(floor(W_k / W * 2^32), 2^32 - 1)
@@ -45,11 +48,13 @@ at the boundary cases (Pr = 1/2, 0, 1).
 """
 from __future__ import annotations
 
+from bisect import bisect_right
+
 import numpy as np
 
 from .philox import philox4x32, seed_key
 
-NOISE_BLOCK = 128
+NOISE_BLOCK = 512
 TAG_HEAD = 1
 TAG_TAIL = 2
 TAG_MBIT = 3
@@ -58,7 +63,7 @@ TWO32 = 4294967296.0
 
 
 def theta_table(q: float) -> list[int]:
-    """THETA_j, j = 0..127, for a channel with total error probability q."""
+    """THETA_j, j = 0..NOISE_BLOCK-1, for a channel with total error probability q."""
     r = 1.0 - float(q)
     out = []
     rp = r
@@ -102,9 +107,12 @@ def tail_draw(seed: int, c: int, b: int, i: int) -> int:
 
 
 def channel_block_fires(seed: int, c: int, b: int, theta, phi):
-    """Run the word-geometric process for channel c on shot block b.
+    """Run the block-geometric process for channel c on shot block b.
 
-    Returns a list of (lane, cell) pairs in increasing lane order.
+    Returns a list of (lane, cell) pairs in increasing lane order.  The first
+    index j with u < THETA_j is found by bisection: THETA is non-decreasing,
+    so it is the number of entries <= u (the linear scan of the definition
+    gives the same index).
     """
     fires = []
     if theta[NOISE_BLOCK - 1] == 0:
@@ -113,12 +121,8 @@ def channel_block_fires(seed: int, c: int, b: int, theta, phi):
     u = head_draw(seed, c, b)
     i = 0
     while True:
-        jstar = -1
-        for j in range(0, NOISE_BLOCK - L):
-            if u < theta[j]:
-                jstar = j
-                break
-        if jstar < 0:
+        jstar = bisect_right(theta, u)
+        if jstar > NOISE_BLOCK - 1 - L:
             break
         lane = L + jstar
         cell = 0

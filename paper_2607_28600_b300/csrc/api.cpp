@@ -222,7 +222,7 @@ struct Prep {
   double* prob = nullptr;
   uint64_t* counts = nullptr;
   int* status = nullptr;
-  int sign_nb = 0, sign_grid = 0;
+  int sign_grid = 0;
   int dense_kind = 0;   // 0 none, 1 register, 2 warp, 3 CTA per shot
   int dense_grid = 0, dense_wpb = 0, dense_use_smem = 0;
   size_t dense_smem = 0;
@@ -233,7 +233,8 @@ struct Prep {
 
 int validate(const symft_sample_args* a) {
   if (a->shots == 0) return set_error(SYMFT_E_ARG, "shots must be >= 1");
-  if (a->shot_offset % kNoiseBlock) return set_error(SYMFT_E_ARG, "shot_offset must be a multiple of 128");
+  if (a->shot_offset % kNoiseBlock)
+    return set_error(SYMFT_E_ARG, "shot_offset must be a multiple of " + std::to_string(kNoiseBlock));
   if (a->shots + a->shot_offset > (1ull << 39)) return set_error(SYMFT_E_ARG, "shot index beyond 2^39");
   if (a->precision != SYMFT_FP32 && a->precision != SYMFT_FP64) return set_error(SYMFT_E_ARG, "bad precision");
   if (a->out_location != SYMFT_OUT_DEVICE && a->out_location != SYMFT_OUT_HOST)
@@ -301,16 +302,14 @@ int prepare(symft_plan* P, const symft_sample_args* a, uint64_t* meas, uint64_t*
     o->m3 = static_cast<uint64_t*>(P->m3.ptr);
   }
   if (h.n_slots > 0) {
-    const int nb = t.sign_nb ? t.sign_nb : sign_blocks_per_cta(P->dp);
-    if (sign_smem_bytes(P->dp, nb) > 220 * 1024)
+    if (sign_smem_bytes(P->dp) > 220 * 1024)
       return set_error(SYMFT_E_CAPACITY, "too many bit-packed slots for shared memory (" +
                                              std::to_string(h.n_slots) + ")");
     int per_sm = 1;
-    CUDA_TRY(sign_occupancy(P->dp, nb, &per_sm));
-    const uint64_t chunks = (o->nblk + nb - 1) / nb;
+    CUDA_TRY(sign_occupancy(P->dp, &per_sm));
+    if (t.sign_ctas_per_sm > 0) per_sm = std::min(per_sm, t.sign_ctas_per_sm);
     const uint64_t cap = static_cast<uint64_t>(P->sm_count) * std::max(1, per_sm);
-    o->sign_nb = nb;
-    o->sign_grid = static_cast<int>(std::max<uint64_t>(1, std::min(chunks, cap)));
+    o->sign_grid = static_cast<int>(std::max<uint64_t>(1, std::min(o->nblk, cap)));
   }
   if (G) {
     const size_t amp = o->fp64 ? 16 : 8;
@@ -400,6 +399,7 @@ int enqueue(symft_plan* P, const symft_sample_args* a, const Prep& o, cudaStream
     SignArgs s{};
     s.p = P->dp;
     s.seed = a->seed;
+    s.keys = make_philox_keys(a->seed);
     s.block0 = a->shot_offset / kNoiseBlock;
     s.n_blocks = o.nblk;
     s.W = W;
@@ -409,7 +409,7 @@ int enqueue(symft_plan* P, const symft_sample_args* a, const Prep& o, cudaStream
     s.obs = o.obs;
     s.signs = o.signs;
     s.status = o.status;
-    CUDA_TRY(launch_sign(s, o.sign_nb, o.sign_grid, st));
+    CUDA_TRY(launch_sign(s, o.sign_grid, st));
     ++*launches;
   }
   if (o.dense_kind) {
@@ -534,12 +534,11 @@ int autotune_impl(symft_plan* P, uint64_t shots, int precision, cudaStream_t st)
   float best = 0.0f;
   Tune base = t;
   rc = time_cfg(&best);
-  // sign kernel: noise blocks per CTA
+  // sign kernel: resident CTAs per SM
   if (rc == SYMFT_OK && h.n_slots > 0) {
-    for (int nb : {2, 4}) {
-      if (sign_smem_bytes(P->dp, nb) > 200 * 1024) continue;
+    for (int cps : {2, 3, 4}) {
       Tune cand = base;
-      cand.sign_nb = nb;
+      cand.sign_ctas_per_sm = cps;
       t = cand;
       float ms = 0.0f;
       rc = time_cfg(&ms);

@@ -6,6 +6,7 @@
 #include <string>
 #include <vector>
 
+#include "plan_dev.hpp"
 #include "symft.h"
 
 namespace symft {
@@ -66,7 +67,6 @@ enum InstrKind : int {
   I_RANDOM_MEAS = 3, I_DET_MEAS = 4, I_ACTIVE_DIAG_MEAS = 5, I_ACTIVE_PAIR_MEAS = 6
 };
 
-constexpr int kNoiseBlock = 128;     // shots per noise block (stream spec)
 constexpr int kMaxActive = 24;       // build limit on k_max
 
 // One dense-state instruction (the sign is target sign_target + causal list).

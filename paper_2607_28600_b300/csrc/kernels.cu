@@ -36,34 +36,38 @@ __device__ __forceinline__ uint4 xor4(uint4 a, uint4 b) {
   return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
 }
 
-// smallest j in [0,128) with u < theta[j] (128 if none).  A guess from the
-// logarithm of the geometric law is corrected by exact integer comparisons
-// against the threshold table, so the result is the table's own answer.
+// smallest j in [0, kNoiseBlock) with u < theta[j] (kNoiseBlock if none).  A
+// guess from the logarithm of the geometric law is corrected by exact integer
+// comparisons against the threshold table, so the result is the table's own
+// answer.
 __device__ __forceinline__ int first_above(const uint32_t* th, float inv_log1m_q, uint32_t u) {
   int j = 0;
   if (inv_log1m_q != 0.0f) {
     const float x = (float)u * 2.3283064365386963e-10f;          // u / 2^32
     const float est = log1pf(-x) * inv_log1m_q;                  // ~ j*
-    j = est < 0.0f ? 0 : (est > 127.0f ? 127 : (int)est);
+    j = est < 0.0f ? 0 : (est > (float)(kNoiseBlock - 1) ? kNoiseBlock - 1 : (int)est);
   }
   while (j > 0 && u < th[j - 1]) --j;
-  while (j < 128 && u >= th[j]) ++j;
+  while (j < kNoiseBlock && u >= th[j]) ++j;
   return j;
 }
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
+// 128-lane sub-blocks of a noise block; a slot holds one uint4 per sub-block
+constexpr int kSub = kNoiseBlock / 128;
+
 struct SignLayout {
   size_t q_off, qi_off, c_off, slot_off, qa_off, qb_off, cnt_off, total;
 };
 
-__host__ __device__ inline SignLayout sign_layout(uint32_t n_qtab, uint32_t n_ctab, uint32_t n_slots, int nb) {
+__host__ __device__ inline SignLayout sign_layout(uint32_t n_qtab, uint32_t n_ctab, uint32_t n_slots) {
   SignLayout L;
   L.q_off = 0;
-  L.qi_off = align16((size_t)n_qtab * 128 * 4);
+  L.qi_off = align16((size_t)n_qtab * kNoiseBlock * 4);
   L.c_off = L.qi_off + align16((size_t)n_qtab * 4);
   L.slot_off = L.c_off + align16((size_t)n_ctab * sizeof(CellTableDev));
-  L.qa_off = L.slot_off + (size_t)n_slots * nb * 16;
+  L.qa_off = L.slot_off + (size_t)n_slots * kSub * 16;
   L.qb_off = L.qa_off + (size_t)kSignWarps * kQueue * 16;
   L.cnt_off = L.qb_off + (size_t)kSignWarps * kQueue * 4;
   L.total = L.cnt_off + 64;
@@ -72,19 +76,18 @@ __host__ __device__ inline SignLayout sign_layout(uint32_t n_qtab, uint32_t n_ct
 
 }  // namespace
 
-// One CTA samples NB consecutive 128-shot noise blocks (128*NB shots, 2*NB
-// 64-shot words per column).  Shared memory: the noise tables, then
-//   slots  n_slots x NB x uint4  (lane l of block b: bit l&31 of word l>>5)
-//   queue  kSignWarps x kQueue x {uint4 ((b << 28) | c, u, L | draw << 8, qtab | ctab << 16),
+// One CTA iteration samples one noise block (kNoiseBlock = 512 consecutive
+// shots, 8 words of 64 shots per column).  Shared memory: the noise tables,
+// then
+//   slots  n_slots x kSub x uint4  (lane l: bit l&31 of word l>>5 of the slot)
+//   queue  kSignWarps x kQueue x {uint4 (c, u, L | draw << 9, qtab | ctab << 16),
 //                                 uint32 first component}
-template <int NB>
 __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const uint32_t NT = A.p.n_slots;
-  const uint32_t k0 = (uint32_t)A.seed, k1 = (uint32_t)(A.seed >> 32);
-  const SignLayout Lay = sign_layout(A.p.n_qtab, A.p.n_ctab, NT, NB);
+  const SignLayout Lay = sign_layout(A.p.n_qtab, A.p.n_ctab, NT);
   uint32_t* sq = reinterpret_cast<uint32_t*>(smem_raw + Lay.q_off);
   float* sqi = reinterpret_cast<float*>(smem_raw + Lay.qi_off);
   CellTableDev* sc = reinterpret_cast<CellTableDev*>(smem_raw + Lay.c_off);
@@ -93,64 +96,63 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
   uint32_t* qb = reinterpret_cast<uint32_t*>(smem_raw + Lay.qb_off) + warp * kQueue;
   uint32_t* sqn = reinterpret_cast<uint32_t*>(smem_raw + Lay.cnt_off);
 
-  for (uint32_t i = threadIdx.x; i < A.p.n_qtab * 128; i += blockDim.x) sq[i] = __ldg(A.p.qtheta + i);
+  for (uint32_t i = threadIdx.x; i < A.p.n_qtab * kNoiseBlock; i += blockDim.x) sq[i] = __ldg(A.p.qtheta + i);
   for (uint32_t i = threadIdx.x; i < A.p.n_qtab; i += blockDim.x) sqi[i] = __ldg(A.p.qinv + i);
   for (uint32_t i = threadIdx.x; i < A.p.n_ctab; i += blockDim.x) sc[i] = A.p.ctabs[i];
   __syncthreads();
 
   const uint32_t n_groups = (A.p.n_channels + 3) >> 2;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  const uint64_t n_chunks = (A.n_blocks + NB - 1) / NB;
   const uint32_t R = A.p.n_records, DO = A.p.n_dets + A.p.n_obs;
+  uint32_t* sw = reinterpret_cast<uint32_t*>(slots);
 
-  for (uint64_t chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x) {
-    const uint64_t b0 = chunk * NB;                       // first local block
-    const uint32_t nb = (uint32_t)min((uint64_t)NB, A.n_blocks - b0);
+  for (uint64_t blk = blockIdx.x; blk < A.n_blocks; blk += gridDim.x) {
+    const uint32_t gblk = (uint32_t)(A.block0 + blk);      // global noise block
+    const uint64_t sub0 = blk * kSub;                       // local 128-shot sub-block
+    const uint32_t nsub = (uint32_t)min((uint64_t)kSub, (A.shots + 127) / 128 - sub0);
     // 1. constants
-    for (uint32_t i = threadIdx.x; i < NT * NB; i += blockDim.x) {
-      const uint32_t v = A.p.slot_const[i / NB] ? ~0u : 0u;
+    for (uint32_t i = threadIdx.x; i < NT * kSub; i += blockDim.x) {
+      const uint32_t v = A.p.slot_const[i / kSub] ? ~0u : 0u;
       slots[i] = make_uint4(v, v, v, v);
     }
     __syncthreads();
-    // 2. random-measurement bits m1: one Philox block = the 128 bits of a block
-    for (uint32_t it = threadIdx.x; it < nb * A.p.n_m1; it += blockDim.x) {
+    // 2. random-measurement bits m1: one Philox block = the 128 bits of a
+    //    sub-block (64-shot words 2s and 2s+1 of global sub-block s)
+    for (uint32_t it = threadIdx.x; it < nsub * A.p.n_m1; it += blockDim.x) {
       const uint32_t b = it / A.p.n_m1, j = it - b * A.p.n_m1;
-      const uint4 o = philox(make_uint4(__ldg(A.p.m1_t + j), (uint32_t)(A.block0 + b0 + b), 0u, kTagMbit), k0, k1);
+      const uint64_t gs = (uint64_t)gblk * kSub + b;
+      const uint4 o = philox(make_uint4(__ldg(A.p.m1_t + j), (uint32_t)gs, (uint32_t)(gs >> 32), kTagMbit), A.keys);
       const uint32_t e = __ldg(A.p.m1_off + j + 1);
       for (uint32_t q = __ldg(A.p.m1_off + j); q < e; ++q) {
-        uint32_t* t = reinterpret_cast<uint32_t*>(slots + (size_t)__ldg(A.p.m1_tgt + q) * NB + b);
+        uint32_t* t = reinterpret_cast<uint32_t*>(slots + (size_t)__ldg(A.p.m1_tgt + q) * kSub + b);
         atomicXor(t + 0, o.x);
         atomicXor(t + 1, o.y);
         atomicXor(t + 2, o.z);
         atomicXor(t + 3, o.w);
       }
     }
-    // 3. noise.  Phase A: each lane draws the head uniforms of four channels of
-    //    one block (one Philox block) and queues the channels that fire in it.
-    //    Phase B: each lane takes one queued (channel, block, u, L, draw index)
-    //    state, resolves exactly one fire -- lane L + j*, its Pauli cell and the
+    // 3. noise.  Phase A: each lane draws the head uniforms of four channels
+    //    (one Philox block) and queues the channels that fire in this block.
+    //    Phase B: each lane takes one queued (channel, u, L, draw index) state,
+    //    resolves exactly one fire -- lane L + j*, its Pauli cell and the
     //    scatter of its components -- and re-queues the channel if its
-    //    word-geometric process continues, so every step costs the same.
+    //    block-geometric process continues, so every step costs the same.
     uint32_t qn = 0;
-    // resolve the fire of one queued state; returns true (and the next state)
-    // if the channel's word-geometric process continues
     // Resolve the fire of one queued state (whose uniform is known to fire):
-    // lane, Pauli cell, and the (slot word, bit) pairs of its components,
-    // appended to `pairs` (one pair per incidence).  The next uniform is tested
-    // here; returns true (and the next state) only if the channel fires again.
+    // lane, Pauli cell, and the slot words of its components (`pw`, all-ones
+    // for none) with the lane's bit.  The next uniform is tested here; returns
+    // true (and the next state) only if the channel fires again.
     auto fire_step = [&](uint4 ent, uint32_t comp0, uint4& next, uint32_t (&pw)[8], uint32_t& bit) -> bool {
-      const uint32_t c = ent.x & 0x0FFFFFFFu, b = ent.x >> 28;
-      const uint32_t gb = (uint32_t)(A.block0 + b0 + b);
-      const int L = (int)(ent.z & 0xFFu);
-      uint32_t ti = ent.z >> 8;
+      const uint32_t c = ent.x;
+      const int L = (int)(ent.z & 0x1FFu);
+      uint32_t ti = ent.z >> 9;
       const uint32_t qt = ent.w & 0xFFFFu;
-      const uint32_t* th = sq + (size_t)qt * 128;
-      const float qi = sqi[qt];
+      const uint32_t* th = sq + (size_t)qt * kNoiseBlock;
       const CellTableDev* ct = sc + (ent.w >> 16);
-      const int lanebit = L + first_above(th, qi, ent.y);     // <= 127 by construction
+      const int lanebit = L + first_above(th, sqi[qt], ent.y);   // <= kNoiseBlock-1 by construction
       const uint32_t ncell = ct->ncell;
       // the draws of one fire (cell, next u) lie in one Philox block
-      const uint4 tail = philox(make_uint4(c, gb, ti >> 2, kTagTail), k0, k1);
+      const uint4 tail = philox(make_uint4(c, gblk, ti >> 2, kTagTail), A.keys);
       uint32_t cell = 0;
       if (ncell > 1) {
         const uint32_t v = pick(tail, ti & 3);
@@ -162,7 +164,7 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
         cell = (uint32_t)cc;
       }
       const uint32_t mask = ct->mask[cell];
-      const uint32_t wbase = b * 4 + ((uint32_t)lanebit >> 5);   // word offset inside a slot
+      const uint32_t wbase = (uint32_t)lanebit >> 5;     // word offset inside a slot
       bit = 1u << (lanebit & 31);
       // up to four components with up to two inline slots each; longer lists
       // are applied here directly
@@ -174,21 +176,20 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
           const uint32_t rng = __ldg(A.p.comp_rng + comp0 + bp);
           if (rng & 0x80000000u) {
             const uint32_t n = (rng >> 28) & 3u;
-            if (n > 0) pw[2 * bp] = (rng & 0x3FFFu) * (NB * 4) + wbase;
-            if (n > 1) pw[2 * bp + 1] = ((rng >> 14) & 0x3FFFu) * (NB * 4) + wbase;
+            if (n > 0) pw[2 * bp] = (rng & 0x3FFFu) * (kSub * 4) + wbase;
+            if (n > 1) pw[2 * bp + 1] = ((rng >> 14) & 0x3FFFu) * (kSub * 4) + wbase;
           } else {
-            uint32_t* sw = reinterpret_cast<uint32_t*>(slots);
             const uint32_t q0 = rng >> 8, qe = q0 + (rng & 0xFFu);
             for (uint32_t q = q0; q < qe; ++q)
-              atomicXor(sw + (uint32_t)__ldg(A.p.comp_tgt + q) * (NB * 4) + wbase, bit);
+              atomicXor(sw + (uint32_t)__ldg(A.p.comp_tgt + q) * (kSub * 4) + wbase, bit);
           }
         }
       }
-      if (lanebit >= 127) return false;
+      if (lanebit >= kNoiseBlock - 1) return false;
       const uint32_t u2 = pick(tail, ti & 3);        // next uniform, draw index ti
       const int L2 = lanebit + 1;
-      if (u2 >= th[127 - L2]) return false;          // no further fire in lanes L2..127
-      next = make_uint4(ent.x, u2, (uint32_t)L2 | ((ti + 1) << 8), ent.w);
+      if (u2 >= th[kNoiseBlock - 1 - L2]) return false;   // no further fire in lanes L2..end
+      next = make_uint4(c, u2, (uint32_t)L2 | ((ti + 1) << 9), ent.w);
       return true;
     };
     // full-warp drain of the first 32 queued states; continuing channels are re-queued
@@ -200,7 +201,6 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
       uint32_t pw[8];
       uint32_t bit = 0;
       const bool more = fire_step(ent, comp0, next, pw, bit);
-      uint32_t* sw = reinterpret_cast<uint32_t*>(slots);
 #pragma unroll
       for (int k = 0; k < 8; ++k)
         if (pw[k] != 0xFFFFFFFFu) atomicXor(sw + pw[k], bit);
@@ -229,20 +229,14 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
       qn = rest + __popc(bal);
       __syncwarp();
     };
-    const uint32_t items = nb * n_groups;
-    for (uint32_t base = warp * 32; base < items; base += kSignWarps * 32) {
-      const uint32_t it = base + lane;
-      const bool valid = it < items;
-      uint32_t b = 0, g = it;
-      while (g >= n_groups && b + 1 < (uint32_t)NB) {
-        g -= n_groups;
-        ++b;
-      }
+    for (uint32_t base = warp * 32; base < n_groups; base += kSignWarps * 32) {
+      const uint32_t g = base + lane;
+      const bool valid = g < n_groups;
       uint4 head = make_uint4(0u, 0u, 0u, 0u), th4 = make_uint4(0u, 0u, 0u, 0u);
       if (valid) {
         th4 = __ldg(A.p.theta4 + g);
         if (th4.x | th4.y | th4.z | th4.w)
-          head = philox(make_uint4(g, (uint32_t)(A.block0 + b0 + b), 0u, kTagHead), k0, k1);
+          head = philox(make_uint4(g, gblk, 0u, kTagHead), A.keys);
       }
       // queue the firing channels, two channel slots at a time (<= 64 new states)
 #pragma unroll
@@ -257,14 +251,14 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
           if (f0) {
             const uint32_t c = 4 * g + h2;
             const uint4 raw = __ldg(reinterpret_cast<const uint4*>(A.p.ch) + c);
-            qa[pos] = make_uint4((b << 28) | c, pick(head, h2), 0u, raw.y);
+            qa[pos] = make_uint4(c, pick(head, h2), 0u, raw.y);
             qb[pos] = raw.z;
             ++pos;
           }
           if (f1) {
             const uint32_t c = 4 * g + h2 + 1;
             const uint4 raw = __ldg(reinterpret_cast<const uint4*>(A.p.ch) + c);
-            qa[pos] = make_uint4((b << 28) | c, pick(head, h2 + 1), 0u, raw.y);
+            qa[pos] = make_uint4(c, pick(head, h2 + 1), 0u, raw.y);
             qb[pos] = raw.z;
           }
           qn += __popc(b0m) + __popc(b1m);
@@ -302,8 +296,7 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
     for (uint32_t x = threadIdx.x; x < total; x += blockDim.x) {
       uint4 ent = pool_a[x];
       const uint32_t comp0 = pool_b[x];
-      uint32_t* sw = reinterpret_cast<uint32_t*>(slots);
-      for (int guard = 0; guard < 128; ++guard) {
+      for (int guard = 0; guard < kNoiseBlock; ++guard) {
         uint4 next;
         uint32_t pw[8];
         uint32_t bit = 0;
@@ -319,23 +312,23 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
     // 4. records: XOR in the parent records level by level (exo_r = delta_r ^ parents)
     for (uint32_t L = 1; L <= A.p.n_levels; ++L) {
       const uint32_t lo = __ldg(A.p.lvl_off + L - 1), hi = __ldg(A.p.lvl_off + L);
-      for (uint32_t x = threadIdx.x; x < (hi - lo) * NB; x += blockDim.x) {
-        const uint32_t r = __ldg(A.p.lvl_rec + lo + x / NB), b = x % NB;
-        uint4 acc = slots[(size_t)r * NB + b];
+      for (uint32_t x = threadIdx.x; x < (hi - lo) * kSub; x += blockDim.x) {
+        const uint32_t r = __ldg(A.p.lvl_rec + lo + x / kSub), b = x % kSub;
+        uint4 acc = slots[(size_t)r * kSub + b];
         const uint32_t pe = __ldg(A.p.par_off + r + 1);
         for (uint32_t q = __ldg(A.p.par_off + r); q < pe; ++q)
-          acc = xor4(acc, slots[(size_t)__ldg(A.p.par + q) * NB + b]);
-        slots[(size_t)r * NB + b] = acc;
+          acc = xor4(acc, slots[(size_t)__ldg(A.p.par + q) * kSub + b]);
+        slots[(size_t)r * kSub + b] = acc;
       }
       __syncthreads();
     }
     // 5. write the columns (records, gathered detectors / observables, dense
-    //    signs): NB pieces of 16 bytes per column, consecutive threads writing
-    //    consecutive pieces of one column; padding bits cleared
+    //    signs): kSub pieces of 16 bytes per column, consecutive threads
+    //    writing consecutive pieces of one column; padding bits cleared
     const uint32_t n_out = R + DO + (NT - R);
-    for (uint32_t x = threadIdx.x; x < n_out * NB; x += blockDim.x) {
-      const uint32_t i = x / NB, b = x % NB;
-      if (b >= nb) continue;
+    for (uint32_t x = threadIdx.x; x < n_out * kSub; x += blockDim.x) {
+      const uint32_t i = x / kSub, b = x % kSub;
+      if (b >= nsub) continue;
       uint64_t* col;
       uint64_t idx;
       uint4 v;
@@ -343,7 +336,7 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
         col = A.meas;
         idx = i;
         if (col == nullptr) continue;
-        v = slots[(size_t)i * NB + b];
+        v = slots[(size_t)i * kSub + b];
       } else if (i < R + DO) {
         const uint32_t j = i - R;
         if (j < A.p.n_dets) { col = A.det; idx = j; }
@@ -352,16 +345,16 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
         v = make_uint4(0u, 0u, 0u, 0u);
         const uint32_t ge = __ldg(A.p.gat_off + j + 1);
         for (uint32_t q = __ldg(A.p.gat_off + j); q < ge; ++q)
-          v = xor4(v, slots[(size_t)__ldg(A.p.gat_rec + q) * NB + b]);
+          v = xor4(v, slots[(size_t)__ldg(A.p.gat_rec + q) * kSub + b]);
       } else {
         const uint32_t g = i - R - DO;
         col = A.signs;
         idx = g;
         if (col == nullptr) continue;
-        v = slots[(size_t)(R + g) * NB + b];
+        v = slots[(size_t)(R + g) * kSub + b];
       }
       uint64_t v0 = ((uint64_t)v.y << 32) | v.x, v1 = ((uint64_t)v.w << 32) | v.z;
-      const uint64_t wa = 2 * (b0 + b), wb = wa + 1;
+      const uint64_t wa = 2 * (sub0 + b), wb = wa + 1;
       if (wa >= A.W) continue;
       const uint64_t la = A.shots - 64 * wa;            // shots covered by word wa (>= 1)
       if (la < 64) v0 &= (1ull << la) - 1;
@@ -1040,7 +1033,7 @@ __host__ __device__ inline PlainLayout plain_layout(const DevPlan& p, uint32_t k
 }
 
 __device__ __forceinline__ int first_above_global(const uint32_t* __restrict__ th, uint32_t u) {
-  int lo = 0, hi = 128;
+  int lo = 0, hi = kNoiseBlock;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
     if (u < __ldg(th + mid)) hi = mid;
@@ -1091,7 +1084,7 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs A) {
 
   for (uint64_t r = blockIdx.x; r < A.shots; r += gridDim.x) {
     const uint64_t rg = A.shot0 + r;
-    const uint32_t gb = (uint32_t)(rg >> 7), my_lane = (uint32_t)(rg & 127);
+    const uint32_t gb = (uint32_t)(rg / kNoiseBlock), my_lane = (uint32_t)(rg % kNoiseBlock);
     const uint64_t w = r >> 6;
     const uint64_t bitmask = 1ull << (r & 63);
     for (uint32_t i = tid; i < (P.n_comp + 31) / 32; i += blockDim.x) fired[i] = 0u;
@@ -1109,14 +1102,14 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs A) {
         uint32_t u = pick(head, s2);
         if (u >= pick(th4, s2)) continue;
         const uint4 raw = __ldg(reinterpret_cast<const uint4*>(P.ch) + c);
-        const uint32_t* th = P.qtheta + (size_t)(raw.y & 0xFFFFu) * 128;
+        const uint32_t* th = P.qtheta + (size_t)(raw.y & 0xFFFFu) * kNoiseBlock;
         const CellTableDev* ct = P.ctabs + (raw.y >> 16);
         const uint32_t ncell = ct->ncell;
         uint32_t ti = 0;
         int L = 0;
-        for (int guard = 0; guard < 129; ++guard) {
+        for (int guard = 0; guard <= kNoiseBlock; ++guard) {
           const int j = first_above_global(th, u);
-          if (j > 127 - L) break;
+          if (j > kNoiseBlock - 1 - L) break;
           const int lanebit = L + j;
           if ((uint32_t)lanebit > my_lane) break;
           uint32_t cell = 0;
@@ -1138,7 +1131,7 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs A) {
             break;
           }
           L = lanebit + 1;
-          if (L >= 128) break;
+          if (L >= kNoiseBlock) break;
           const uint4 t4 = philox(make_uint4(c, gb, ti >> 2, kTagTail), k0, k1);
           u = pick(t4, ti & 3);
           ++ti;
@@ -1439,30 +1432,19 @@ __global__ void count_kernel(CountArgs A) {
 // ---------------------------------------------------------------------------
 cudaError_t set_smem_limits();
 
-// 512-shot CTAs when their slots fit comfortably, else 256-shot CTAs
-int sign_blocks_per_cta(const DevPlan& p) { return (size_t)p.n_slots * 4 * 16 <= 40 * 1024 ? 4 : 2; }
+size_t sign_smem_bytes(const DevPlan& p) { return sign_layout(p.n_qtab, p.n_ctab, p.n_slots).total; }
 
-size_t sign_smem_bytes(const DevPlan& p, int nb) {
-  return sign_layout(p.n_qtab, p.n_ctab, p.n_slots, nb).total;
-}
-
-static const void* sign_fn(int nb) {
-  return nb == 4 ? (const void*)sign_kernel<4> : (const void*)sign_kernel<2>;
-}
-
-cudaError_t sign_occupancy(const DevPlan& p, int nb, int* ctas_per_sm) {
-  const size_t smem = sign_smem_bytes(p, nb);
+cudaError_t sign_occupancy(const DevPlan& p, int* ctas_per_sm) {
+  const size_t smem = sign_smem_bytes(p);
   cudaError_t e = set_smem_limits();
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(sign_fn(nb), cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  e = cudaFuncSetAttribute((const void*)sign_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, sign_fn(nb), kSignWarps * 32, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, sign_kernel, kSignWarps * 32, smem);
 }
 
-cudaError_t launch_sign(const SignArgs& a, int nb, int grid, cudaStream_t st) {
-  const size_t smem = sign_smem_bytes(a.p, nb);
-  if (nb == 4) sign_kernel<4><<<grid, kSignWarps * 32, smem, st>>>(a);
-  else sign_kernel<2><<<grid, kSignWarps * 32, smem, st>>>(a);
+cudaError_t launch_sign(const SignArgs& a, int grid, cudaStream_t st) {
+  sign_kernel<<<grid, kSignWarps * 32, sign_smem_bytes(a.p), st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1510,7 +1492,7 @@ cudaError_t set_smem_limits() {
   static bool done = false;
   if (done) return cudaSuccess;
   const int lim = 227 * 1024;
-  const void* fns[] = {(const void*)sign_kernel<2>, (const void*)sign_kernel<4>,
+  const void* fns[] = {(const void*)sign_kernel,
                        (const void*)dense_kernel<float>, (const void*)dense_kernel<double>,
                        (const void*)dense_reg_kernel<float>, (const void*)dense_reg_kernel<double>,
                        (const void*)dense_cta_kernel<float>, (const void*)dense_cta_kernel<double>,

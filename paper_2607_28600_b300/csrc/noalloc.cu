@@ -77,7 +77,8 @@ extern "C" int symft_sample_noalloc(const symft_plan* plan, uint64_t shots, uint
   g_noalloc_error.clear();
   if (!plan) return fail(SYMFT_E_ARG, "null plan");
   if (shots == 0) return fail(SYMFT_E_ARG, "shots must be >= 1");
-  if (shot_offset % kNoiseBlock) return fail(SYMFT_E_ARG, "shot_offset must be a multiple of 128");
+  if (shot_offset % kNoiseBlock)
+    return fail(SYMFT_E_ARG, "shot_offset must be a multiple of " + std::to_string(kNoiseBlock));
   if (shots + shot_offset > (1ull << 39)) return fail(SYMFT_E_ARG, "shot index beyond 2^39");
   if (precision != SYMFT_FP32 && precision != SYMFT_FP64) return fail(SYMFT_E_ARG, "bad precision");
   const HostPlan& h = plan->hp;
@@ -147,6 +148,7 @@ extern "C" int symft_sample_noalloc(const symft_plan* plan, uint64_t shots, uint
     SignArgs s{};
     s.p = dp;
     s.seed = seed;
+    s.keys = make_philox_keys(seed);
     s.block0 = shot_offset / kNoiseBlock;
     s.n_blocks = nblk;
     s.W = W;
@@ -156,14 +158,12 @@ extern "C" int symft_sample_noalloc(const symft_plan* plan, uint64_t shots, uint
     s.obs = obs_out;
     s.signs = signs;
     s.status = status;
-    const int nb_cta = sign_blocks_per_cta(dp);
-    if (sign_smem_bytes(dp, nb_cta) > 220 * 1024) return fail(SYMFT_E_CAPACITY, "too many bit-packed slots");
+    if (sign_smem_bytes(dp) > 220 * 1024) return fail(SYMFT_E_CAPACITY, "too many bit-packed slots");
     int per_sm = 1;
-    e = sign_occupancy(dp, nb_cta, &per_sm);
+    e = sign_occupancy(dp, &per_sm);
     if (e != cudaSuccess) return fail(SYMFT_E_CUDA, cudaGetErrorString(e));
-    const uint64_t chunks = (nblk + nb_cta - 1) / nb_cta;
     const uint64_t cap = static_cast<uint64_t>(sms) * std::max(1, per_sm);
-    e = launch_sign(s, nb_cta, static_cast<int>(std::max<uint64_t>(1, std::min(chunks, cap))), st);
+    e = launch_sign(s, static_cast<int>(std::max<uint64_t>(1, std::min(nblk, cap))), st);
     if (e != cudaSuccess) return fail(SYMFT_E_CUDA, cudaGetErrorString(e));
   }
   if (G) {

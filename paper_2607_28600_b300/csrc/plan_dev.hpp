@@ -10,6 +10,12 @@ namespace symft {
 // stream tags (counter word 3)
 constexpr uint32_t kTagHead = 1, kTagTail = 2, kTagMbit = 3, kTagMfrac = 4;
 
+// shots per noise block of the stream specification: a channel's head draw
+// and its block-geometric process cover lanes 0..kNoiseBlock-1 of one block
+constexpr int kNoiseBlock = 512;
+// shots per packed random-measurement Philox block (two 64-shot words)
+constexpr int kWordPair = 128;
+
 struct ChannelDev {        // 16 bytes, one per noise channel
   uint32_t theta_last;     // THETA_127: u >= this means no fire in the block
   uint16_t qtab, ctab;
@@ -44,7 +50,7 @@ struct DevPlan {
   const ChannelDev* ch;
   const uint4* theta4;          // THETA_127 of channels 4g..4g+3 (0 = never fires)
   uint32_t n_qtab, n_ctab;
-  const uint32_t* qtheta;       // [n_qtab][128]
+  const uint32_t* qtheta;       // [n_qtab][kNoiseBlock]
   const float* qinv;            // [n_qtab] 1 / log(1 - q)
   const CellTableDev* ctabs;
   // per component: bit 31 set -> inline list: count in bits 28-29, slots in
@@ -87,11 +93,31 @@ struct DevPlan {
 };
 
 
+// Philox4x32-10 round keys of a seed: k[2r] = k0 + r * 0x9E3779B9,
+// k[2r+1] = k1 + r * 0xBB67AE85 (mod 2^32), r = 0..9, with (k0, k1) the low
+// and high words of the seed.  Kernels read them from the launch parameters.
+struct PhiloxKeys {
+  uint32_t k[20];
+};
+
+inline PhiloxKeys make_philox_keys(uint64_t seed) {
+  PhiloxKeys K;
+  uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    K.k[2 * r] = k0;
+    K.k[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return K;
+}
+
 struct SignArgs {
   DevPlan p;
+  PhiloxKeys keys;        // round keys of `seed`
   uint64_t seed;
-  uint64_t block0;        // global index of the first 128-shot block
-  uint64_t n_blocks;      // local blocks
+  uint64_t block0;        // global index of the first noise block (kNoiseBlock shots)
+  uint64_t n_blocks;      // local noise blocks
   uint64_t W;             // words per column
   uint64_t shots;
   uint64_t* meas;         // may be null

@@ -36,10 +36,9 @@ struct BlobOffsets {
   size_t plc, plo, pls;
 };
 
-cudaError_t launch_sign(const SignArgs& a, int nb, int grid, cudaStream_t st);
-int sign_blocks_per_cta(const DevPlan& p);
-size_t sign_smem_bytes(const DevPlan& p, int nb);
-cudaError_t sign_occupancy(const DevPlan& p, int nb, int* ctas_per_sm);
+cudaError_t launch_sign(const SignArgs& a, int grid, cudaStream_t st);
+size_t sign_smem_bytes(const DevPlan& p);
+cudaError_t sign_occupancy(const DevPlan& p, int* ctas_per_sm);
 cudaError_t launch_dense(const DenseArgs& a, bool fp64, int warps_per_block, int grid, size_t smem,
                          cudaStream_t st);
 cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t st);
@@ -55,7 +54,7 @@ cudaError_t launch_plain(const PlainArgs& a, bool fp64, int grid, cudaStream_t s
 // Launch shapes chosen by symft_autotune (0 = built-in heuristic).
 struct Tune {
   bool tuned = false;
-  int sign_nb = 0;           // 128-shot noise blocks per sign-kernel CTA
+  int sign_ctas_per_sm = 0;  // sign kernel: resident CTAs per SM (0 = occupancy limit)
   int dense_grid_mult = 8;   // register / warp executors: CTAs per SM
   int dense_wpb = 0;         // warp executor: warps (shots) per CTA
   int cta_grid_mult = 2;     // CTA executor with global vectors: CTAs per SM

@@ -75,6 +75,9 @@ def test_sample_argument_errors_before_any_device_work():
         S.symft_sample_ex(p, 10, 1, shot_offset=64)
     assert ei.value.code == -3
     with pytest.raises(S.SymftError) as ei:
+        S.symft_sample_ex(p, 10, 1, shot_offset=256)    # not a whole 512-shot noise block
+    assert ei.value.code == -3 and "512" in str(ei.value)
+    with pytest.raises(S.SymftError) as ei:
         S.symft_sample_ex(p, 10, 1, precision=7)
     assert ei.value.code == -3
 

@@ -12,7 +12,7 @@ def test_theta_table_is_the_geometric_cdf():
         th = S.theta_table(q)
         assert len(th) == S.NOISE_BLOCK
         assert all(th[i] <= th[i + 1] for i in range(len(th) - 1))
-        for j in (0, 1, 63, 127):
+        for j in (0, 1, 63, 127, 511):
             exact = (1.0 - (1.0 - q) ** (j + 1)) * 2.0 ** 32
             assert abs(th[j] - exact) <= 2.0 + 1e-9 * exact
     assert S.theta_table(0.0) == [0] * S.NOISE_BLOCK
@@ -58,6 +58,7 @@ def test_lane_marginals_bernoulli():
     # every lane, not only early ones
     per_lane = hits.mean(axis=0)
     assert abs(per_lane[:64].mean() - per_lane[64:].mean()) < 0.02
+    assert abs(per_lane[448:].mean() - q) < 0.012
 
 
 def test_lane_pairs_independent_and_cells_uniform():
@@ -75,7 +76,7 @@ def test_process_stops_and_orders_lanes():
     th, ph = S.theta_table(0.5), S.phi_table([1, 1, 1])
     fires = S.channel_block_fires(1, 3, 9, th, ph)
     lanes = [l for l, _ in fires]
-    assert lanes == sorted(set(lanes)) and all(0 <= l < 128 for l in lanes)
+    assert lanes == sorted(set(lanes)) and all(0 <= l < S.NOISE_BLOCK for l in lanes)
     assert S.channel_block_fires(1, 3, 9, S.theta_table(0.0), []) == []
 
 
@@ -96,3 +97,17 @@ def test_mbit_words_vector_matches_scalar():
     v = S.mbit_words(7, 11, 1000, 9)
     for i in range(9):
         assert int(v[i]) == S.mbit_word(7, 11, 1000 + i)
+
+
+def test_bisection_equals_the_linear_first_index():
+    """The bisection in the process returns the linear scan's min{j : u < THETA_j}."""
+    import random
+    from bisect import bisect_right
+    rng = random.Random(3)
+    for q in (1e-3, 0.02, 0.4):
+        th = S.theta_table(q)
+        for _ in range(300):
+            u = rng.choice([rng.getrandbits(32), th[rng.randrange(S.NOISE_BLOCK)],
+                            max(0, th[rng.randrange(S.NOISE_BLOCK)] - 1)])
+            lin = next((j for j in range(S.NOISE_BLOCK) if u < th[j]), S.NOISE_BLOCK)
+            assert bisect_right(th, u) == lin
