@@ -51,7 +51,7 @@ void build_blob(symft_plan* P) {
   const HostPlan& h = P->hp;
   std::vector<ChannelDev> ch(h.n_channels);
   for (uint32_t c = 0; c < h.n_channels; ++c)
-    ch[c] = ChannelDev{h.ch_theta_last[c], h.ch_qtab[c], h.ch_ctab[c], h.ch_comp0[c], h.ch_ncomp[c]};
+    ch[c] = ChannelDev{h.ch_theta_last[c], h.ch_qtab[c], h.ch_ctab[c], h.ch_comp0[c], h.ch_cell0[c]};
   std::vector<uint32_t> theta4(((h.n_channels + 3) / 4) * 4, 0u);
   for (uint32_t c = 0; c < h.n_channels; ++c) theta4[c] = h.ch_theta_last[c];
   std::vector<uint32_t> qtheta;
@@ -93,27 +93,29 @@ void build_blob(symft_plan* P) {
   P->off.ct = push(blob, ct);
   P->off.t4 = push(blob, theta4);
   P->off.qi = push(blob, qinv);
-  // packed incidence lists (16-bit targets, 24-bit offsets, 8-bit counts)
   if (h.n_slots >= 65536) throw Error(SYMFT_E_CAPACITY, "more than 65535 bit-packed slots");
-  if (h.comp_tgt.size() >= (1u << 24)) throw Error(SYMFT_E_CAPACITY, "too many sign incidences");
   if (h.n_channels >= (1u << 28)) throw Error(SYMFT_E_CAPACITY, "too many noise channels");
-  std::vector<uint32_t> comp_rng(h.n_comp);
-  for (uint32_t k = 0; k < h.n_comp; ++k) {
-    const uint32_t off = h.comp_off[k], n = h.comp_off[k + 1] - off;
-    bool inl = n <= 2;
-    for (uint32_t j = 0; j < n && inl; ++j) inl = h.comp_tgt[off + j] < 16384;
+  // (channel, cell) target entries: up to 7 word offsets inline, else a list
+  const size_t n_cells = h.cell_off.size() - 1;
+  std::vector<uint4> cellt(std::max<size_t>(1, n_cells));
+  std::vector<uint32_t> cell_ovf;
+  for (size_t e = 0; e < n_cells; ++e) {
+    const uint32_t off = h.cell_off[e], n = h.cell_off[e + 1] - off;
+    bool inl = n <= 7;
+    for (uint32_t j = 0; j < n && inl; ++j) inl = h.cell_tgt[off + j] < 4096;
+    uint16_t f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (inl) {
-      uint32_t t0 = n > 0 ? h.comp_tgt[off] : 0, t1 = n > 1 ? h.comp_tgt[off + 1] : 0;
-      comp_rng[k] = 0x80000000u | (n << 28) | (t1 << 14) | t0;
+      f[0] = static_cast<uint16_t>(n);
+      for (uint32_t j = 0; j < n; ++j) f[1 + j] = static_cast<uint16_t>(h.cell_tgt[off + j] * 16);
+      std::memcpy(&cellt[e], f, 16);
     } else {
-      if (n >= 256) throw Error(SYMFT_E_CAPACITY, "a noise component reaches more than 255 targets");
-      if (off >= (1u << 23)) throw Error(SYMFT_E_CAPACITY, "too many sign incidences");
-      comp_rng[k] = (off << 8) | n;
+      cellt[e] = make_uint4(0xFFFFu, static_cast<uint32_t>(cell_ovf.size()), n, 0u);
+      for (uint32_t j = 0; j < n; ++j) cell_ovf.push_back(h.cell_tgt[off + j] * 16);
     }
   }
-  std::vector<uint16_t> comp_tgt(h.comp_tgt.begin(), h.comp_tgt.end());
-  P->off.co = push(blob, comp_rng);
-  P->off.ctg = push(blob, comp_tgt);
+  if (cell_ovf.empty()) cell_ovf.push_back(0);
+  P->off.clt = push(blob, cellt);
+  P->off.clo = push(blob, cell_ovf);
   P->off.m1t = push(blob, h.m1_t);
   P->off.m1o = push(blob, h.m1_off);
   P->off.m1g = push(blob, h.m1_tgt);
@@ -146,8 +148,8 @@ void bind_plan(const symft_plan* P, unsigned char* base, DevPlan* dptr) {
   d.qtheta = reinterpret_cast<const uint32_t*>(at(P->off.q));
   d.qinv = reinterpret_cast<const float*>(at(P->off.qi));
   d.ctabs = reinterpret_cast<const CellTableDev*>(at(P->off.ct));
-  d.comp_rng = reinterpret_cast<const uint32_t*>(at(P->off.co));
-  d.comp_tgt = reinterpret_cast<const uint16_t*>(at(P->off.ctg));
+  d.cellt = reinterpret_cast<const CellTargetsDev*>(at(P->off.clt));
+  d.cell_ovf = reinterpret_cast<const uint32_t*>(at(P->off.clo));
   d.n_m1 = static_cast<uint32_t>(h.m1_t.size());
   d.m1_t = reinterpret_cast<const uint32_t*>(at(P->off.m1t));
   d.m1_off = reinterpret_cast<const uint32_t*>(at(P->off.m1o));

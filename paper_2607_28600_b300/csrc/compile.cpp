@@ -897,6 +897,31 @@ void Compiler::lower(HostPlan& P) {
     P.ch_theta_last[op.channel] = live ? P.qtabs[qi].theta[kNoiseBlock - 1] : 0;
   }
 
+  // targets of each (channel, cell): a fired cell applies all its components
+  // at once, so the sampler flips the XOR of their target sets
+  P.ch_cell0.assign(c_.n_channels, 0);
+  P.cell_off.assign(1, 0);
+  for (uint32_t ch = 0; ch < c_.n_channels; ++ch) {
+    P.ch_cell0[ch] = static_cast<uint32_t>(P.cell_off.size() - 1);
+    const CellTable& ct = P.ctabs[P.ch_ctab[ch]];
+    for (uint32_t k = 0; k < ct.ncell; ++k) {
+      std::vector<uint32_t> t;
+      for (int bp = 0; bp < 4; ++bp) {
+        if (!((ct.mask[k] >> bp) & 1)) continue;
+        const uint32_t comp = chan_comp0_[ch] + bp;
+        t.insert(t.end(), P.comp_tgt.begin() + P.comp_off[comp], P.comp_tgt.begin() + P.comp_off[comp + 1]);
+      }
+      std::sort(t.begin(), t.end());
+      for (size_t i = 0; i < t.size();) {
+        size_t j = i;
+        while (j < t.size() && t[j] == t[i]) ++j;
+        if ((j - i) & 1) P.cell_tgt.push_back(t[i]);
+        i = j;
+      }
+      P.cell_off.push_back(static_cast<uint32_t>(P.cell_tgt.size()));
+    }
+  }
+
   // postselection event order (Sec. 6, detector postselection): which
   // detectors reject a shot, and where each sits among the records
   std::vector<uint8_t> post(c_.n_dets, 0);

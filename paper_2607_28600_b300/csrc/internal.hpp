@@ -109,12 +109,16 @@ struct HostPlan {
   std::vector<uint16_t> ch_qtab, ch_ctab;
   std::vector<uint32_t> ch_comp0;        // first component id
   std::vector<uint8_t> ch_ncomp;
+  std::vector<uint32_t> ch_cell0;        // first (channel, cell) entry of cell_off
   std::vector<QTable> qtabs;
   std::vector<CellTable> ctabs;
 
   // component -> targets (CSR)
   uint32_t n_comp = 0;
   std::vector<uint32_t> comp_off, comp_tgt;
+  // (channel, Pauli cell) -> targets (CSR): the slots a fired cell flips, i.e.
+  // the XOR of its components' target sets (pairs that cancel removed)
+  std::vector<uint32_t> cell_off, cell_tgt;
 
   // random measurements (m1): ordinal and targets (CSR)
   std::vector<uint32_t> m1_t, m1_off, m1_tgt;

@@ -54,6 +54,17 @@ __device__ __forceinline__ int first_above(const uint32_t* th, float inv_log1m_q
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
+// XOR `bit` into word `wb` of the first n (<= 7) slots of a cell target entry
+__device__ __forceinline__ void scatter7(uint32_t* sw, uint4 tg, uint32_t n, uint32_t wb, uint32_t bit) {
+  const uint32_t f[7] = {tg.x >> 16, tg.y & 0xFFFFu, tg.y >> 16, tg.z & 0xFFFFu, tg.z >> 16,
+                         tg.w & 0xFFFFu, tg.w >> 16};
+#pragma unroll
+  for (uint32_t k = 0; k < 7; ++k) {
+    if (k >= n) break;
+    atomicXor(sw + f[k] + wb, bit);
+  }
+}
+
 // 128-lane sub-blocks of a noise block; a slot holds one uint4 per sub-block
 constexpr int kSub = kNoiseBlock / 128;
 
@@ -81,7 +92,7 @@ __host__ __device__ inline SignLayout sign_layout(uint32_t n_qtab, uint32_t n_ct
 // then
 //   slots  n_slots x kSub x uint4  (lane l: bit l&31 of word l>>5 of the slot)
 //   queue  kSignWarps x kQueue x {uint4 (c, u, L | draw << 9, qtab | ctab << 16),
-//                                 uint32 first component}
+//                                 uint32 first (channel, cell) target entry}
 __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
@@ -139,10 +150,10 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
     //    block-geometric process continues, so every step costs the same.
     uint32_t qn = 0;
     // Resolve the fire of one queued state (whose uniform is known to fire):
-    // lane, Pauli cell, and the slot words of its components (`pw`, all-ones
-    // for none) with the lane's bit.  The next uniform is tested here; returns
+    // its lane, its Pauli cell, and the XOR of the lane's bit into the slots
+    // of the cell's target entry.  The next uniform is tested here; returns
     // true (and the next state) only if the channel fires again.
-    auto fire_step = [&](uint4 ent, uint32_t comp0, uint4& next, uint32_t (&pw)[8], uint32_t& bit) -> bool {
+    auto fire_step = [&](uint4 ent, uint32_t cell0, uint4& next) -> bool {
       const uint32_t c = ent.x;
       const int L = (int)(ent.z & 0x1FFu);
       uint32_t ti = ent.z >> 9;
@@ -163,30 +174,17 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
         while (cc < (int)ncell - 1 && v >= ct->phi[cc]) ++cc;
         cell = (uint32_t)cc;
       }
-      const uint32_t mask = ct->mask[cell];
-      const uint32_t wbase = (uint32_t)lanebit >> 5;     // word offset inside a slot
-      bit = 1u << (lanebit & 31);
-      // up to four components with up to two inline slots each; longer lists
-      // are applied here directly
-#pragma unroll
-      for (int bp = 0; bp < 4; ++bp) {
-        pw[2 * bp] = 0xFFFFFFFFu;
-        pw[2 * bp + 1] = 0xFFFFFFFFu;
-        if ((mask >> bp) & 1u) {
-          const uint32_t rng = __ldg(A.p.comp_rng + comp0 + bp);
-          if (rng & 0x80000000u) {
-            const uint32_t n = (rng >> 28) & 3u;
-            if (n > 0) pw[2 * bp] = (rng & 0x3FFFu) * (kSub * 4) + wbase;
-            if (n > 1) pw[2 * bp + 1] = ((rng >> 14) & 0x3FFFu) * (kSub * 4) + wbase;
-          } else {
-            const uint32_t q0 = rng >> 8, qe = q0 + (rng & 0xFFu);
-            for (uint32_t q = q0; q < qe; ++q)
-              atomicXor(sw + (uint32_t)__ldg(A.p.comp_tgt + q) * (kSub * 4) + wbase, bit);
-          }
-        }
+      const uint32_t u2 = pick(tail, ti & 3);        // next uniform, draw index ti
+      const uint32_t wb = (uint32_t)lanebit >> 5;    // word offset inside a slot
+      const uint32_t bit = 1u << (lanebit & 31);
+      const uint4 tg = __ldg(A.p.cellt + cell0 + cell);
+      const uint32_t ntg = tg.x & 0xFFFFu;
+      if (ntg == 0xFFFFu) {
+        for (uint32_t q = tg.y; q < tg.y + tg.z; ++q) atomicXor(sw + __ldg(A.p.cell_ovf + q) + wb, bit);
+      } else {
+        scatter7(sw, tg, ntg, wb, bit);
       }
       if (lanebit >= kNoiseBlock - 1) return false;
-      const uint32_t u2 = pick(tail, ti & 3);        // next uniform, draw index ti
       const int L2 = lanebit + 1;
       if (u2 >= th[kNoiseBlock - 1 - L2]) return false;   // no further fire in lanes L2..end
       next = make_uint4(c, u2, (uint32_t)L2 | ((ti + 1) << 9), ent.w);
@@ -195,15 +193,10 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
     // full-warp drain of the first 32 queued states; continuing channels are re-queued
     auto drain32 = [&]() {
       const uint4 ent = qa[lane];
-      const uint32_t comp0 = qb[lane];
+      const uint32_t cell0 = qb[lane];
       __syncwarp();
       uint4 next = make_uint4(0u, 0u, 0u, 0u);
-      uint32_t pw[8];
-      uint32_t bit = 0;
-      const bool more = fire_step(ent, comp0, next, pw, bit);
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-        if (pw[k] != 0xFFFFFFFFu) atomicXor(sw + pw[k], bit);
+      const bool more = fire_step(ent, cell0, next);
       const uint32_t rest = qn - 32;          // < 64: move [32, qn) to [0, rest)
       for (uint32_t i0 = 0; i0 < rest; i0 += 32) {
         uint4 mv = make_uint4(0u, 0u, 0u, 0u);
@@ -224,7 +217,7 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
       if (more) {
         const uint32_t pos = rest + __popc(bal & lt_mask);
         qa[pos] = next;
-        qb[pos] = comp0;
+        qb[pos] = cell0;
       }
       qn = rest + __popc(bal);
       __syncwarp();
@@ -252,14 +245,14 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
             const uint32_t c = 4 * g + h2;
             const uint4 raw = __ldg(reinterpret_cast<const uint4*>(A.p.ch) + c);
             qa[pos] = make_uint4(c, pick(head, h2), 0u, raw.y);
-            qb[pos] = raw.z;
+            qb[pos] = raw.w;
             ++pos;
           }
           if (f1) {
             const uint32_t c = 4 * g + h2 + 1;
             const uint4 raw = __ldg(reinterpret_cast<const uint4*>(A.p.ch) + c);
             qa[pos] = make_uint4(c, pick(head, h2 + 1), 0u, raw.y);
-            qb[pos] = raw.z;
+            qb[pos] = raw.w;
           }
           qn += __popc(b0m) + __popc(b1m);
           __syncwarp();
@@ -295,15 +288,10 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
     __syncthreads();
     for (uint32_t x = threadIdx.x; x < total; x += blockDim.x) {
       uint4 ent = pool_a[x];
-      const uint32_t comp0 = pool_b[x];
+      const uint32_t cell0 = pool_b[x];
       for (int guard = 0; guard < kNoiseBlock; ++guard) {
         uint4 next;
-        uint32_t pw[8];
-        uint32_t bit = 0;
-        const bool more = fire_step(ent, comp0, next, pw, bit);
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if (pw[k] != 0xFFFFFFFFu) atomicXor(sw + pw[k], bit);
+        const bool more = fire_step(ent, cell0, next);
         if (!more) break;
         ent = next;
       }
@@ -323,52 +311,44 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
       __syncthreads();
     }
     // 5. write the columns (records, gathered detectors / observables, dense
-    //    signs): kSub pieces of 16 bytes per column, consecutive threads
-    //    writing consecutive pieces of one column; padding bits cleared
-    const uint32_t n_out = R + DO + (NT - R);
-    for (uint32_t x = threadIdx.x; x < n_out * kSub; x += blockDim.x) {
-      const uint32_t i = x / kSub, b = x % kSub;
-      if (b >= nsub) continue;
-      uint64_t* col;
-      uint64_t idx;
-      uint4 v;
-      if (i < R) {
-        col = A.meas;
-        idx = i;
-        if (col == nullptr) continue;
-        v = slots[(size_t)i * kSub + b];
-      } else if (i < R + DO) {
-        const uint32_t j = i - R;
-        if (j < A.p.n_dets) { col = A.det; idx = j; }
-        else { col = A.obs; idx = j - A.p.n_dets; }
-        if (col == nullptr) continue;
-        v = make_uint4(0u, 0u, 0u, 0u);
-        const uint32_t ge = __ldg(A.p.gat_off + j + 1);
-        for (uint32_t q = __ldg(A.p.gat_off + j); q < ge; ++q)
-          v = xor4(v, slots[(size_t)__ldg(A.p.gat_rec + q) * kSub + b]);
-      } else {
-        const uint32_t g = i - R - DO;
-        col = A.signs;
-        idx = g;
-        if (col == nullptr) continue;
-        v = slots[(size_t)(R + g) * kSub + b];
-      }
-      uint64_t v0 = ((uint64_t)v.y << 32) | v.x, v1 = ((uint64_t)v.w << 32) | v.z;
-      const uint64_t wa = 2 * (sub0 + b), wb = wa + 1;
-      if (wa >= A.W) continue;
-      const uint64_t la = A.shots - 64 * wa;            // shots covered by word wa (>= 1)
-      if (la < 64) v0 &= (1ull << la) - 1;
-      const bool hb = wb < A.W;
-      if (hb) {
-        const uint64_t lbits = A.shots - 64 * wb;
-        if (lbits < 64) v1 &= (1ull << lbits) - 1;
-      }
-      uint64_t* d = col + idx * A.W + wa;
-      if (hb && ((reinterpret_cast<uintptr_t>(d) & 15) == 0)) {
-        *reinterpret_cast<ulonglong2*>(d) = make_ulonglong2(v0, v1);
-      } else {
-        d[0] = v0;
-        if (hb) d[1] = v1;
+    //    signs): 16-byte pieces, thread t writing sub-block t % kSub of every
+    //    (blockDim / kSub)-th column, so consecutive threads cover consecutive
+    //    pieces of one column and the padding masks are per thread
+    {
+      const uint32_t b = threadIdx.x % kSub;
+      const uint32_t step = blockDim.x / kSub;
+      const uint32_t i0 = threadIdx.x / kSub;
+      const uint64_t wa = 2 * (sub0 + b);                 // first 64-shot word of the piece
+      if (b < nsub) {
+        const uint64_t la = A.shots - 64 * wa;            // shots in word wa (>= 1)
+        const uint64_t m0 = la < 64 ? (1ull << la) - 1 : ~0ull;
+        const bool hb = wa + 1 < A.W;                     // the piece has a second word
+        const uint64_t lb = hb ? A.shots - 64 * (wa + 1) : 0;
+        const uint64_t m1 = !hb ? 0ull : (lb < 64 ? (1ull << lb) - 1 : ~0ull);
+        auto put = [&](uint64_t* d, uint4 v) {
+          const uint64_t v0 = (((uint64_t)v.y << 32) | v.x) & m0, v1 = (((uint64_t)v.w << 32) | v.z) & m1;
+          if (hb && ((reinterpret_cast<uintptr_t>(d) & 15) == 0)) {
+            *reinterpret_cast<ulonglong2*>(d) = make_ulonglong2(v0, v1);
+          } else {
+            d[0] = v0;
+            if (hb) d[1] = v1;
+          }
+        };
+        if (A.meas)
+          for (uint32_t i = i0; i < R; i += step) put(A.meas + (uint64_t)i * A.W + wa, slots[(size_t)i * kSub + b]);
+        for (uint32_t j = i0; j < DO; j += step) {
+          uint64_t* col = j < A.p.n_dets ? (A.det ? A.det + (uint64_t)j * A.W : nullptr)
+                                         : (A.obs ? A.obs + (uint64_t)(j - A.p.n_dets) * A.W : nullptr);
+          if (col == nullptr) continue;
+          uint4 v = make_uint4(0u, 0u, 0u, 0u);
+          const uint32_t ge = __ldg(A.p.gat_off + j + 1);
+          for (uint32_t q = __ldg(A.p.gat_off + j); q < ge; ++q)
+            v = xor4(v, slots[(size_t)__ldg(A.p.gat_rec + q) * kSub + b]);
+          put(col + wa, v);
+        }
+        if (A.signs)
+          for (uint32_t g = i0; g < NT - R; g += step)
+            put(A.signs + (uint64_t)g * A.W + wa, slots[(size_t)(R + g) * kSub + b]);
       }
     }
     __syncthreads();

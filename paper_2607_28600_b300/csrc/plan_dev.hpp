@@ -17,11 +17,16 @@ constexpr int kNoiseBlock = 512;
 constexpr int kWordPair = 128;
 
 struct ChannelDev {        // 16 bytes, one per noise channel
-  uint32_t theta_last;     // THETA_127: u >= this means no fire in the block
+  uint32_t theta_last;     // THETA_{kNoiseBlock-1}: u >= this means no fire in the block
   uint16_t qtab, ctab;
-  uint32_t comp0;
-  uint32_t ncomp;
+  uint32_t comp0;          // first noise component (plain form)
+  uint32_t cell0;          // first (channel, cell) target entry (sign kernel)
 };
+
+// Targets of one (channel, Pauli cell), 16 bytes as eight 16-bit fields:
+// f0 = n <= 7 and f1..f(n) = slot * 16 (the slot's first 32-bit word); or
+// f0 = 0xFFFF and (y, z) = (offset, count) of a list of slot * 16 in cell_ovf.
+using CellTargetsDev = uint4;
 
 struct CellTableDev {
   uint32_t ncell;
@@ -53,10 +58,8 @@ struct DevPlan {
   const uint32_t* qtheta;       // [n_qtab][kNoiseBlock]
   const float* qinv;            // [n_qtab] 1 / log(1 - q)
   const CellTableDev* ctabs;
-  // per component: bit 31 set -> inline list: count in bits 28-29, slots in
-  // bits 0-13 and 14-27; else (first incidence << 8) | count into comp_tgt
-  const uint32_t* comp_rng;
-  const uint16_t* comp_tgt;     // incidence -> target slot
+  const CellTargetsDev* cellt;  // per (channel, cell)
+  const uint32_t* cell_ovf;     // long target lists (slot * 16)
   uint32_t n_m1;
   const uint32_t* m1_t;
   const uint32_t* m1_off;

@@ -32,8 +32,9 @@ struct DevBuf {
 
 // Byte offsets of the plan arrays inside the device blob.
 struct BlobOffsets {
-  size_t ch, q, ct, t4, qi, co, ctg, m1t, m1o, m1g, tco, tca, sc, po, pa, lo, lr, go, gr, pe, dn, dc;
+  size_t ch, q, ct, t4, qi, m1t, m1o, m1g, tco, tca, sc, po, pa, lo, lr, go, gr, pe, dn, dc;
   size_t plc, plo, pls;
+  size_t clt, clo;
 };
 
 cudaError_t launch_sign(const SignArgs& a, int grid, cudaStream_t st);
