@@ -122,12 +122,37 @@ void build_blob(symft_plan* P) {
   P->off.tco = push(blob, h.tgt_causal_off);
   P->off.tca = push(blob, h.tgt_causal);
   P->off.sc = push(blob, h.slot_const);
-  P->off.po = push(blob, h.par_off);
-  P->off.pa = push(blob, h.par);
-  P->off.lo = push(blob, h.lvl_off);
-  P->off.lr = push(blob, h.lvl_rec);
-  P->off.go = push(blob, h.gat_off);
-  P->off.gr = push(blob, h.gat_rec);
+  // level items: record and up to four parents, 16 bits each
+  std::vector<uint4> lvl_item(std::max<size_t>(1, h.lvl_rec.size()));
+  for (size_t x = 0; x < h.lvl_rec.size(); ++x) {
+    const uint32_t r = h.lvl_rec[x], p0 = h.par_off[r], np = h.par_off[r + 1] - p0;
+    if (np > 4) throw Error(SYMFT_E_DEVICE, "internal: more than four parent records");
+    uint32_t pp[4] = {0, 0, 0, 0};
+    for (uint32_t q = 0; q < np; ++q) pp[q] = h.par[p0 + q];
+    lvl_item[x] = make_uint4(r | (np << 16), pp[0] | (pp[1] << 16), pp[2] | (pp[3] << 16), 0u);
+  }
+  if (h.lvl_off.size() > static_cast<size_t>(kMaxLevels) + 1)
+    throw Error(SYMFT_E_DEVICE, "internal: record chains deeper than the level limit");
+  // detector / observable gathers: up to seven records inline, else a list
+  const size_t n_gat = h.gat_off.size() - 1;
+  std::vector<uint4> gat_item(std::max<size_t>(1, n_gat));
+  std::vector<uint32_t> gat_ovf;
+  for (size_t j = 0; j < n_gat; ++j) {
+    const uint32_t off = h.gat_off[j], n = h.gat_off[j + 1] - off;
+    uint16_t f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (n <= 7) {
+      f[0] = static_cast<uint16_t>(n);
+      for (uint32_t q = 0; q < n; ++q) f[1 + q] = static_cast<uint16_t>(h.gat_rec[off + q]);
+      std::memcpy(&gat_item[j], f, 16);
+    } else {
+      gat_item[j] = make_uint4(0xFFFFu, static_cast<uint32_t>(gat_ovf.size()), n, 0u);
+      for (uint32_t q = 0; q < n; ++q) gat_ovf.push_back(h.gat_rec[off + q]);
+    }
+  }
+  if (gat_ovf.empty()) gat_ovf.push_back(0);
+  P->off.li = push(blob, lvl_item);
+  P->off.gi = push(blob, gat_item);
+  P->off.gv = push(blob, gat_ovf);
   P->off.pe = push(blob, h.post_events);
   P->off.dn = push(blob, dn);
   P->off.dc = push(blob, h.dense_causal);
@@ -160,13 +185,10 @@ void bind_plan(const symft_plan* P, unsigned char* base, DevPlan* dptr) {
   d.tgt_sign0 = h.tgt_sign0;
   d.n_slots = h.n_slots;
   d.slot_const = reinterpret_cast<const uint8_t*>(at(P->off.sc));
-  d.par_off = reinterpret_cast<const uint32_t*>(at(P->off.po));
-  d.par = reinterpret_cast<const uint32_t*>(at(P->off.pa));
   d.n_levels = h.lvl_off.empty() ? 0 : static_cast<uint32_t>(h.lvl_off.size() - 1);
-  d.lvl_off = reinterpret_cast<const uint32_t*>(at(P->off.lo));
-  d.lvl_rec = reinterpret_cast<const uint32_t*>(at(P->off.lr));
-  d.gat_off = reinterpret_cast<const uint32_t*>(at(P->off.go));
-  d.gat_rec = reinterpret_cast<const uint32_t*>(at(P->off.gr));
+  d.lvl_item = reinterpret_cast<const uint4*>(at(P->off.li));
+  d.gat_item = reinterpret_cast<const uint4*>(at(P->off.gi));
+  d.gat_ovf = reinterpret_cast<const uint32_t*>(at(P->off.gv));
   d.tgt_causal_off = reinterpret_cast<const uint32_t*>(at(P->off.tco));
   d.tgt_causal = reinterpret_cast<const uint32_t*>(at(P->off.tca));
   d.n_post_events = static_cast<uint32_t>(h.post_events.size());
@@ -402,6 +424,7 @@ int enqueue(symft_plan* P, const symft_sample_args* a, const Prep& o, cudaStream
     s.p = P->dp;
     s.seed = a->seed;
     s.keys = make_philox_keys(a->seed);
+    set_levels(h, &s);
     s.block0 = a->shot_offset / kNoiseBlock;
     s.n_blocks = o.nblk;
     s.W = W;

@@ -709,6 +709,10 @@ void Compiler::lower(HostPlan& P) {
   constexpr uint64_t kParentGain = 20;
   constexpr int kMaxParents = 4;
   constexpr size_t kMaxCand = 96;
+  // chains are cut at depth kMaxLevels: the sign kernel resolves records
+  // level by level, one CTA barrier per level
+  constexpr uint32_t kMaxLevel = kMaxLevels;
+  std::vector<uint32_t> level(R, 0);
   std::vector<uint32_t> seen_mark(R, 0xFFFFFFFFu);
   for (uint32_t r = 0; r < R; ++r) {
     Expr resid = exo[r];
@@ -721,6 +725,7 @@ void Compiler::lower(HostPlan& P) {
         const auto& lst = inv[sidx];
         for (size_t j = lst.size(); j-- > 0 && cand.size() < kMaxCand;) {
           uint32_t p = lst[j];
+          if (level[p] >= kMaxLevel) continue;
           if (seen_mark[p] != r * 8 + it) {
             seen_mark[p] = r * 8 + it;
             cand.push_back(p);
@@ -742,16 +747,13 @@ void Compiler::lower(HostPlan& P) {
       ea_.xor_into(resid, exo[best]);
       cres = best_c;
       parents[r].push_back(static_cast<uint32_t>(best));
+      level[r] = std::max(level[r], level[best] + 1);
     }
     delta[r] = std::move(resid);
     ea_.for_each(exo[r], 0, NS, [&](uint32_t sidx) { inv[sidx].push_back(r); });
   }
-  std::vector<uint32_t> level(R, 0);
   uint32_t max_level = 0;
-  for (uint32_t r = 0; r < R; ++r) {
-    for (uint32_t p : parents[r]) level[r] = std::max(level[r], level[p] + 1);
-    max_level = std::max(max_level, level[r]);
-  }
+  for (uint32_t r = 0; r < R; ++r) max_level = std::max(max_level, level[r]);
   P.par_off.assign(R + 1, 0);
   for (uint32_t r = 0; r < R; ++r) {
     P.par.insert(P.par.end(), parents[r].begin(), parents[r].end());

@@ -25,7 +25,7 @@ namespace symft {
 
 namespace {
 
-constexpr int kQueue = 96;          // per-warp queue of (channel, block) fire states
+constexpr int kQueue = 96;          // per-warp ring of fire states (< 32 + 64 live)
 constexpr int kSignWarps = 8;       // warps per CTA
 
 __device__ __forceinline__ uint32_t pick(uint4 v, uint32_t s) {
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
     //    resolves exactly one fire -- lane L + j*, its Pauli cell and the
     //    scatter of its components -- and re-queues the channel if its
     //    block-geometric process continues, so every step costs the same.
-    uint32_t qn = 0;
+    uint32_t qn = 0, qh = 0;     // ring buffer: entries (qh + i) % kQueue, i < qn
     // Resolve the fire of one queued state (whose uniform is known to fire):
     // its lane, its Pauli cell, and the XOR of the lane's bit into the slots
     // of the cell's target entry.  The next uniform is tested here; returns
@@ -190,36 +190,24 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
       next = make_uint4(c, u2, (uint32_t)L2 | ((ti + 1) << 9), ent.w);
       return true;
     };
-    // full-warp drain of the first 32 queued states; continuing channels are re-queued
+    // full-warp drain of the 32 oldest queued states; continuing channels are
+    // re-queued at the back of the ring
     auto drain32 = [&]() {
-      const uint4 ent = qa[lane];
-      const uint32_t cell0 = qb[lane];
+      const uint32_t src = (qh + lane) % kQueue;
+      const uint4 ent = qa[src];
+      const uint32_t cell0 = qb[src];
       __syncwarp();
+      qh = (qh + 32) % kQueue;
+      qn -= 32;
       uint4 next = make_uint4(0u, 0u, 0u, 0u);
       const bool more = fire_step(ent, cell0, next);
-      const uint32_t rest = qn - 32;          // < 64: move [32, qn) to [0, rest)
-      for (uint32_t i0 = 0; i0 < rest; i0 += 32) {
-        uint4 mv = make_uint4(0u, 0u, 0u, 0u);
-        uint32_t mvb = 0;
-        const uint32_t i = i0 + lane;
-        if (i < rest) {
-          mv = qa[32 + i];
-          mvb = qb[32 + i];
-        }
-        __syncwarp();
-        if (i < rest) {
-          qa[i] = mv;
-          qb[i] = mvb;
-        }
-        __syncwarp();
-      }
       const uint32_t bal = __ballot_sync(0xffffffffu, more);
       if (more) {
-        const uint32_t pos = rest + __popc(bal & lt_mask);
+        const uint32_t pos = (qh + qn + __popc(bal & lt_mask)) % kQueue;
         qa[pos] = next;
         qb[pos] = cell0;
       }
-      qn = rest + __popc(bal);
+      qn += __popc(bal);
       __syncwarp();
     };
     for (uint32_t base = warp * 32; base < n_groups; base += kSignWarps * 32) {
@@ -240,13 +228,13 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
         if (b0m | b1m) {
           // slot order: lane-major pairs; position = entries of lower lanes + own
           const uint32_t lower = __popc(b0m & lt_mask) + __popc(b1m & lt_mask);
-          uint32_t pos = qn + lower;
+          uint32_t pos = (qh + qn + lower) % kQueue;
           if (f0) {
             const uint32_t c = 4 * g + h2;
             const uint4 raw = __ldg(reinterpret_cast<const uint4*>(A.p.ch) + c);
             qa[pos] = make_uint4(c, pick(head, h2), 0u, raw.y);
             qb[pos] = raw.w;
-            ++pos;
+            pos = pos + 1 == kQueue ? 0 : pos + 1;
           }
           if (f1) {
             const uint32_t c = 4 * g + h2 + 1;
@@ -275,8 +263,8 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
     uint4 mine = make_uint4(0u, 0u, 0u, 0u);
     uint32_t mineb = 0;
     if ((uint32_t)lane < qn) {
-      mine = qa[lane];
-      mineb = qb[lane];
+      mine = qa[(qh + lane) % kQueue];
+      mineb = qb[(qh + lane) % kQueue];
     }
     __syncthreads();
     uint4* pool_a = reinterpret_cast<uint4*>(smem_raw + Lay.qa_off);
@@ -298,15 +286,19 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
     }
     __syncthreads();
     // 4. records: XOR in the parent records level by level (exo_r = delta_r ^ parents)
-    for (uint32_t L = 1; L <= A.p.n_levels; ++L) {
-      const uint32_t lo = __ldg(A.p.lvl_off + L - 1), hi = __ldg(A.p.lvl_off + L);
-      for (uint32_t x = threadIdx.x; x < (hi - lo) * kSub; x += blockDim.x) {
-        const uint32_t r = __ldg(A.p.lvl_rec + lo + x / kSub), b = x % kSub;
-        uint4 acc = slots[(size_t)r * kSub + b];
-        const uint32_t pe = __ldg(A.p.par_off + r + 1);
-        for (uint32_t q = __ldg(A.p.par_off + r); q < pe; ++q)
-          acc = xor4(acc, slots[(size_t)__ldg(A.p.par + q) * kSub + b]);
-        slots[(size_t)r * kSub + b] = acc;
+    for (uint32_t L = 0; L < A.p.n_levels; ++L) {
+      const uint32_t hi = A.lvl[L + 1] * kSub;
+      for (uint32_t x = A.lvl[L] * kSub + threadIdx.x; x < hi; x += blockDim.x) {
+        const uint4 it = __ldg(A.p.lvl_item + x / kSub);
+        const uint32_t b = x % kSub, np = it.x >> 16;
+        const uint32_t pr[4] = {it.y & 0xFFFFu, it.y >> 16, it.z & 0xFFFFu, it.z >> 16};
+        uint4 acc = slots[(it.x & 0xFFFFu) * kSub + b];
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+          if (k >= np) break;
+          acc = xor4(acc, slots[pr[k] * kSub + b]);
+        }
+        slots[(it.x & 0xFFFFu) * kSub + b] = acc;
       }
       __syncthreads();
     }
@@ -341,9 +333,19 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
                                          : (A.obs ? A.obs + (uint64_t)(j - A.p.n_dets) * A.W : nullptr);
           if (col == nullptr) continue;
           uint4 v = make_uint4(0u, 0u, 0u, 0u);
-          const uint32_t ge = __ldg(A.p.gat_off + j + 1);
-          for (uint32_t q = __ldg(A.p.gat_off + j); q < ge; ++q)
-            v = xor4(v, slots[(size_t)__ldg(A.p.gat_rec + q) * kSub + b]);
+          const uint4 gi = __ldg(A.p.gat_item + j);
+          const uint32_t n = gi.x & 0xFFFFu;
+          if (n == 0xFFFFu) {
+            for (uint32_t q = gi.y; q < gi.y + gi.z; ++q) v = xor4(v, slots[__ldg(A.p.gat_ovf + q) * kSub + b]);
+          } else {
+            const uint32_t f[7] = {gi.x >> 16, gi.y & 0xFFFFu, gi.y >> 16, gi.z & 0xFFFFu, gi.z >> 16,
+                                   gi.w & 0xFFFFu, gi.w >> 16};
+#pragma unroll
+            for (uint32_t k = 0; k < 7; ++k) {
+              if (k >= n) break;
+              v = xor4(v, slots[f[k] * kSub + b]);
+            }
+          }
           put(col + wa, v);
         }
         if (A.signs)

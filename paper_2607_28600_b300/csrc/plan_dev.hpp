@@ -15,6 +15,8 @@ constexpr uint32_t kTagHead = 1, kTagTail = 2, kTagMbit = 3, kTagMfrac = 4;
 constexpr int kNoiseBlock = 512;
 // shots per packed random-measurement Philox block (two 64-shot words)
 constexpr int kWordPair = 128;
+// levels of the record chains (the compile step cuts chains at this depth)
+constexpr int kMaxLevels = 16;
 
 struct ChannelDev {        // 16 bytes, one per noise channel
   uint32_t theta_last;     // THETA_{kNoiseBlock-1}: u >= this means no fire in the block
@@ -71,13 +73,14 @@ struct DevPlan {
   // sign-kernel slots [records][dense signs]
   uint32_t n_slots;
   const uint8_t* slot_const;
-  const uint32_t* par_off;      // record -> parents (CSR)
-  const uint32_t* par;
+  // records with parents in level order, one 16-byte item each: x = record |
+  // (parents << 16), y = p0 | p1 << 16, z = p2 | p3 << 16
   uint32_t n_levels;
-  const uint32_t* lvl_off;      // n_levels + 1 offsets into lvl_rec
-  const uint32_t* lvl_rec;
-  const uint32_t* gat_off;      // det / obs -> records (CSR)
-  const uint32_t* gat_rec;
+  const uint4* lvl_item;
+  // det / obs -> records: f0 = n <= 7 and f1..f(n) = records, or f0 = 0xFFFF
+  // and (y, z) = (offset, count) of a record list in gat_ovf
+  const uint4* gat_item;
+  const uint32_t* gat_ovf;
   // postselection walk in circuit order: record r as r (>= 0), detector i as
   // -1 - (2 i + p) with p = 1 when detector i is postselected
   uint32_t n_post_events;
@@ -118,6 +121,7 @@ inline PhiloxKeys make_philox_keys(uint64_t seed) {
 struct SignArgs {
   DevPlan p;
   PhiloxKeys keys;        // round keys of `seed`
+  uint32_t lvl[kMaxLevels + 1];   // level L holds lvl_item[lvl[L] .. lvl[L+1])
   uint64_t seed;
   uint64_t block0;        // global index of the first noise block (kNoiseBlock shots)
   uint64_t n_blocks;      // local noise blocks

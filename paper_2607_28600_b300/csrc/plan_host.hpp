@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -32,7 +33,7 @@ struct DevBuf {
 
 // Byte offsets of the plan arrays inside the device blob.
 struct BlobOffsets {
-  size_t ch, q, ct, t4, qi, m1t, m1o, m1g, tco, tca, sc, po, pa, lo, lr, go, gr, pe, dn, dc;
+  size_t ch, q, ct, t4, qi, m1t, m1o, m1g, tco, tca, sc, li, gi, gv, pe, dn, dc;
   size_t plc, plo, pls;
   size_t clt, clo;
 };
@@ -83,6 +84,12 @@ struct symft_plan {
 };
 
 namespace symft {
+// Level boundaries of the record chains into the sign kernel's parameters.
+inline void set_levels(const HostPlan& h, SignArgs* s) {
+  for (int L = 0; L <= kMaxLevels; ++L)
+    s->lvl[L] = h.lvl_off.empty() ? 0 : h.lvl_off[std::min<size_t>(L, h.lvl_off.size() - 1)];
+}
+
 // Build the device image of a compiled plan (throws Error on capacity limits).
 void build_blob(symft_plan* P);
 // Point the DevPlan arrays into a copy of the blob at `base` (device address).
