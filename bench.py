@@ -32,6 +32,25 @@ WORKLOADS = {
 HEADLINE = "surface_d7_r7"
 
 
+# DRAM traffic of one sign-kernel launch on the headline workload, from the ncu
+# capture summarised in profiles/sign_kernel_surface_d7_r7.md
+# (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel
+# source it was taken on: reported as null once kernels.cu changes.
+SIGN_TRAFFIC = {"kernels_cu_sha256": "b1604487f8cd080ab596d58ad1dd62001dc05c311bb39a4f108cfeb4a915c4aa",
+                "bytes_per_launch": 21496832 + 865686016}
+
+
+def _sign_traffic():
+    import hashlib
+    path = os.path.join(ROOT, "paper_2607_28600_b300", "csrc", "kernels.cu")
+    try:
+        with open(path, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    return SIGN_TRAFFIC["bytes_per_launch"] if sha == SIGN_TRAFFIC["kernels_cu_sha256"] else None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -503,7 +522,7 @@ def main():
                    "parallelism": f"shot ranges x{world}"},
         "per_circuit": per_circuit,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": _sign_traffic() if shots == SHOTS else None,
                      "kernel": "sign_kernel", "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": h["out_bytes"]},
         "e2e": {"value": e2e_val, "unit": "shots/s", "h2d_bytes_per_step": 0,

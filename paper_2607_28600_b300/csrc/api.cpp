@@ -150,6 +150,7 @@ void build_blob(symft_plan* P) {
     }
   }
   if (gat_ovf.empty()) gat_ovf.push_back(0);
+  P->off.m3t = push(blob, h.m3_t);
   P->off.li = push(blob, lvl_item);
   P->off.gi = push(blob, gat_item);
   P->off.gv = push(blob, gat_ovf);
@@ -187,6 +188,7 @@ void bind_plan(const symft_plan* P, unsigned char* base, DevPlan* dptr) {
   d.slot_const = reinterpret_cast<const uint8_t*>(at(P->off.sc));
   d.n_levels = h.lvl_off.empty() ? 0 : static_cast<uint32_t>(h.lvl_off.size() - 1);
   d.lvl_item = reinterpret_cast<const uint4*>(at(P->off.li));
+  d.m3_t = reinterpret_cast<const uint32_t*>(at(P->off.m3t));
   d.gat_item = reinterpret_cast<const uint4*>(at(P->off.gi));
   d.gat_ovf = reinterpret_cast<const uint32_t*>(at(P->off.gv));
   d.tgt_causal_off = reinterpret_cast<const uint32_t*>(at(P->off.tco));
@@ -442,6 +444,7 @@ int enqueue(symft_plan* P, const symft_sample_args* a, const Prep& o, cudaStream
     DenseArgs d{};
     d.p = P->dp;
     d.seed = a->seed;
+    d.keys = make_philox_keys(a->seed);
     d.shot0 = a->shot_offset;
     d.shots = a->shots;
     d.W = W;

@@ -390,16 +390,31 @@ __device__ __forceinline__ double norm2(Cplx<Real> v) {
 }
 
 // U = u * 2^53 of the shared measurement rule: an integer below 2^53
-__device__ __forceinline__ uint64_t meas_U(uint64_t seed, uint32_t t, uint64_t r) {
-  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+__device__ __forceinline__ uint64_t meas_U(const PhiloxKeys& K, uint32_t t, uint64_t r) {
   const uint64_t w = r >> 6;
-  const uint4 ob = philox(make_uint4(t, (uint32_t)(w >> 1), (uint32_t)(w >> 33), kTagMbit), k0, k1);
+  const uint4 ob = philox(make_uint4(t, (uint32_t)(w >> 1), (uint32_t)(w >> 33), kTagMbit), K);
   const uint64_t word = (w & 1) ? ((uint64_t)ob.z | ((uint64_t)ob.w << 32)) : ((uint64_t)ob.x | ((uint64_t)ob.y << 32));
   const uint64_t bit = (word >> (r & 63)) & 1ull;
-  const uint4 of = philox(make_uint4(t, (uint32_t)(r >> 1), (uint32_t)(r >> 33), kTagMfrac), k0, k1);
+  const uint4 of = philox(make_uint4(t, (uint32_t)(r >> 1), (uint32_t)(r >> 33), kTagMfrac), K);
   const uint64_t fw = (r & 1) ? ((uint64_t)of.z | ((uint64_t)of.w << 32)) : ((uint64_t)of.x | ((uint64_t)of.y << 32));
   return (bit << 52) + (fw >> 12);
 }
+
+// The uniforms of a shot's active measurements, 32 at a time: lane l holds U
+// of active measurement 32 c + l for the current chunk c; a measurement reads
+// its value by a shuffle and moves to the next chunk when it leaves this one.
+struct ShotUniforms {
+  uint64_t uc = 0;
+  uint32_t chunk = 0xFFFFFFFFu;
+  __device__ __forceinline__ uint64_t get(const DenseArgs& A, uint32_t j, uint64_t rg, int lane) {
+    if ((j >> 5) != chunk) {
+      chunk = j >> 5;
+      const uint32_t jj = (chunk << 5) + (uint32_t)lane;
+      uc = jj < A.p.n_m3 ? meas_U(A.keys, __ldg(A.p.m3_t + jj), rg) : 0ull;
+    }
+    return __shfl_sync(0xffffffffu, uc, (int)(j & 31));
+  }
+};
 
 // recorded bit: 0 iff u < p0, i.e. U < p0 * 2^53 (both sides exact in FP64)
 __device__ __forceinline__ uint32_t decide64(uint64_t U, double p0) {
@@ -487,6 +502,7 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
     const uint64_t w = r >> 6;
     const uint64_t bitmask = 1ull << (r & 63);
     for (uint32_t i = lane; i < m3w; i += 32) m3bits[i] = 0u;
+    ShotUniforms su;
     if (lane == 0) {
       vec[0].re = (Real)1;
       vec[0].im = (Real)0;
@@ -584,9 +600,10 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
             double S0 = 0.0, S1 = 0.0;
             branch_sums<Real, double>(vec, I, n, lane, 32, mcr, mci, S0, S1);
             warp_sum2(S0, S1);
+            const uint64_t U = su.get(A, (uint32_t)I.m3, rg, lane);
             if (lane == 0) {
               const double p0 = (l0 ? S1 : S0) / (S0 + S1);
-              m = decide64(meas_U(A.seed, I.t, rg), p0);
+              m = decide64(U, p0);
               if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = p0;
             }
             m = __shfl_sync(0xffffffffu, m, 0);
@@ -595,9 +612,10 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
             float S0 = 0.0f, S1 = 0.0f;
             branch_sums<Real, float>(vec, I, n, lane, 32, mcr, mci, S0, S1);
             warp_sum2(S0, S1);
+            const uint64_t U = su.get(A, (uint32_t)I.m3, rg, lane);
             if (lane == 0) {
               const float p0 = (l0 ? S1 : S0) / (S0 + S1);
-              m = decide32(meas_U(A.seed, I.t, rg), p0);
+              m = decide32(U, p0);
               if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = (double)p0;
             }
             m = __shfl_sync(0xffffffffu, m, 0);
@@ -693,6 +711,7 @@ __global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) 
     }
     for (uint32_t i = lane; i < m3w; i += 32) m3b[i] = 0u;
     __syncwarp();
+    ShotUniforms su;
     Real re = lane == 0 ? (Real)1 : (Real)0, im = (Real)0;
     uint32_t k = 0;
     for (uint32_t g = 0; g < G; ++g) {
@@ -775,8 +794,8 @@ __global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) 
         warp_sum2(s0, s1);
         const uint32_t l0 = I.kind == 5 ? (lam ^ (uint32_t)I.eta) : lam;
         uint32_t m = 0;
+        const uint64_t U = su.get(A, (uint32_t)I.m3, rg, lane);
         if (lane == 0) {
-          const uint64_t U = meas_U(A.seed, I.t, rg);
           double pd;
           if (sizeof(Real) == 8) {
             pd = (double)(l0 ? s1 : s0) / (double)(s0 + s1);
@@ -942,7 +961,7 @@ __global__ void __launch_bounds__(kCtaThreads) dense_cta_kernel(DenseArgs A) {
         }
         if (tid == 0) {
           const double p0 = (l0 ? S1 : S0) / (S0 + S1);
-          const uint32_t m = decide64(meas_U(A.seed, I.t, rg), p0);
+          const uint32_t m = decide64(meas_U(A.keys, I.t, rg), p0);
           if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = p0;
           bcast[1] = (int)m;
           if (m) {

@@ -176,6 +176,7 @@ extern "C" int symft_sample_noalloc(const symft_plan* plan, uint64_t shots, uint
     DenseArgs d{};
     d.p = dp;
     d.seed = seed;
+    d.keys = make_philox_keys(seed);
     d.shot0 = shot_offset;
     d.shots = shots;
     d.W = W;

@@ -89,6 +89,7 @@ struct DevPlan {
   const DenseInstrDev* dense;
   const uint32_t* dense_causal;
   uint32_t n_m3;
+  const uint32_t* m3_t;         // measurement ordinal of each active measurement
   uint32_t n_records, n_dets, n_obs;
   int postselect;               // non-zero when any detector is postselected
   // plain (per-shot) form
@@ -136,6 +137,7 @@ struct SignArgs {
 
 struct DenseArgs {
   DevPlan p;
+  PhiloxKeys keys;        // round keys of `seed`
   uint64_t seed;
   uint64_t shot0;         // absolute index of local shot 0
   uint64_t shots;
