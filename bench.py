@@ -34,21 +34,28 @@ HEADLINE = "surface_d7_r7"
 
 # DRAM traffic of one sign-kernel launch on the headline workload, from the ncu
 # capture summarised in profiles/sign_kernel_surface_d7_r7.md
-# (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel
-# source it was taken on: reported as null once kernels.cu changes.
-SIGN_TRAFFIC = {"kernels_cu_sha256": "b1604487f8cd080ab596d58ad1dd62001dc05c311bb39a4f108cfeb4a915c4aa",
-                "bytes_per_launch": 21496832 + 865686016}
+# (dram__bytes_read.sum + dram__bytes_write.sum).  Valid only for the kernel
+# source it was taken on (sign.cu and the headers it includes): reported as
+# null once any of them changes.
+SIGN_TRAFFIC = {"source_sha256": None, "bytes_per_launch": None}
+SIGN_SOURCES = ("sign.cu", "device.cuh", "plan_dev.hpp")
+
+
+def sign_source_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for name in SIGN_SOURCES:
+        with open(os.path.join(ROOT, "paper_2607_28600_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def _sign_traffic():
-    import hashlib
-    path = os.path.join(ROOT, "paper_2607_28600_b300", "csrc", "kernels.cu")
     try:
-        with open(path, "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
+        sha = sign_source_sha256()
     except OSError:
         return None
-    return SIGN_TRAFFIC["bytes_per_launch"] if sha == SIGN_TRAFFIC["kernels_cu_sha256"] else None
+    return SIGN_TRAFFIC["bytes_per_launch"] if sha == SIGN_TRAFFIC["source_sha256"] else None
 
 
 def _peaks():
