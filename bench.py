@@ -397,7 +397,8 @@ def main():
     stream = torch.cuda.current_stream(dev)
     shots = args.shots
     W = (shots + 63) // 64
-    offset = rank * ((shots + 127) // 128) * 128
+    from paper_2607_28600_b300.sharding import weak_offset
+    offset = weak_offset(shots, rank)
     if args.only in ("near_clifford", "mixed_batch"):
         fn = measure_near_clifford if args.only == "near_clifford" else measure_mixed_batch
         res = fn(S, torch, dev, stream, steps=args.steps, warmup=args.warmup)

@@ -56,6 +56,11 @@ typedef enum {
   SYMFT_E_DEVICE = -8        /* device-side check failed (status word) */
 } symft_status;
 
+/* Shot offsets (symft_sample_args.shot_offset) are multiples of this: the
+ * noise block of the random-stream specification.  Shards of one sample set
+ * over several calls or GPUs start on such boundaries. */
+#define SYMFT_SHOT_ALIGN 512
+
 enum { SYMFT_POSTSELECT_NONE = 0, SYMFT_POSTSELECT_ALL = 1, SYMFT_POSTSELECT_LISTED = 2 };
 enum { SYMFT_FP32 = 0, SYMFT_FP64 = 1 };
 enum { SYMFT_OUT_DEVICE = 0, SYMFT_OUT_HOST = 1 };
@@ -100,8 +105,8 @@ typedef struct {
 typedef struct {
   uint64_t shots;          /* number of shots (>= 1) */
   uint64_t seed;           /* Philox key */
-  uint64_t shot_offset;    /* absolute index of the first shot; multiple of 512 (the
-                              noise block of the random-stream specification) */
+  uint64_t shot_offset;    /* absolute index of the first shot; a multiple of
+                              SYMFT_SHOT_ALIGN */
   uint64_t* meas_out;      /* n_records * W words */
   uint64_t* det_out;       /* n_dets * W words */
   uint64_t* obs_out;       /* n_obs * W words */

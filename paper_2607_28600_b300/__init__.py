@@ -15,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsymft.so")
 
 SYMFT_OK = 0
+SHOT_ALIGN = 512          # SYMFT_SHOT_ALIGN: shot offsets are multiples of this
 POSTSELECT_NONE, POSTSELECT_ALL, POSTSELECT_LISTED = 0, 1, 2
 FP32, FP64 = 0, 1
 OUT_DEVICE, OUT_HOST = 0, 1

@@ -47,6 +47,8 @@ size_t push(std::vector<unsigned char>& blob, const std::vector<T>& v) {
 
 namespace symft {
 
+static_assert(kNoiseBlock == SYMFT_SHOT_ALIGN, "shot alignment is the noise block");
+
 void build_blob(symft_plan* P) {
   const HostPlan& h = P->hp;
   std::vector<ChannelDev> ch(h.n_channels);

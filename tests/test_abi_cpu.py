@@ -119,6 +119,7 @@ def test_struct_layouts_match_the_header(tmp_path):
         lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
         for fname, _ in py._fields_:
             lines.append(f'  printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append('  printf("SHOT_ALIGN %d\\n", SYMFT_SHOT_ALIGN);')
     lines.append("  return 0;\n}")
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines))
@@ -126,6 +127,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
                                                    text=True).stdout.splitlines())
+    assert int(got["SHOT_ALIGN"]) == S.SHOT_ALIGN
     for cname, py in structs.items():
         assert int(got[cname]) == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
