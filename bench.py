@@ -193,6 +193,11 @@ NEAR_CLIFFORD = {
     "c3_cultivation_d3_to_d9": ("cultivation", 1, 10_000_000),
     "c4_distill_15to1_encoded": ("distill_encoded", 1, 10_000_000),
     "c4_distill_15to1_literal": ("distill_literal", 1, 1_000_000),
+    # coherent over-rotations R_Z(0.02) on surface codes (k_max 4, 8, 12, 24)
+    "coherent_d3_r1": ("coherent_3_1", 1, 10_000_000),
+    "coherent_d3_r3": ("coherent_3_3", 1, 1_000_000),
+    "coherent_d5_r1": ("coherent_5_1", 1, 100_000),
+    "coherent_d5_r5": ("coherent_5_5", 1, 64),
 }
 
 
@@ -205,6 +210,10 @@ def _near_clifford_text(kind):
         return cultivation_shaped(1e-3)
     if kind == "distill_encoded":
         return distillation_15_to_1(1e-3, "encoded")
+    if kind.startswith("coherent_"):
+        from paper_2607_28600_b300.workloads import coherent_surface_code_memory
+        _, d, r = kind.split("_")
+        return coherent_surface_code_memory(int(d), int(r), 1e-3, 0.02)
     return distillation_15_to_1(1e-3, "literal")
 
 
@@ -249,6 +258,8 @@ def measure_near_clifford(S, torch, dev, stream, steps, warmup, scale=1.0):
                                            ("PromoteRot", "ActiveDiagRot", "ActivePairRot",
                                             "ActiveDiagMeas", "ActivePairMeas")),
                  "postselect": bool(post)}
+        # per-shot work of the widest configs is large: fewer repetitions
+        st_w, st_n = (1, 1) if shots0 < 1000 else (warmup, steps)
         for mode, prec, plain in (("fp32_batched", S.FP32, False), ("fp64_batched", S.FP64, False),
                                   ("fp64_plain", S.FP64, True)):
             shots = max(128, int(shots0 * scale * (0.1 if plain else 1.0)))
@@ -262,7 +273,7 @@ def measure_near_clifford(S, torch, dev, stream, steps, warmup, scale=1.0):
                 S.symft_sample_ex(plan, shots, 100 + i, meas_out=meas, det_out=det, obs_out=obs,
                                   discard_out=disc, precision=prec, plain=plain, stream=stream)
             try:
-                for i in range(warmup):
+                for i in range(st_w):
                     step(i)
             except S.SymftError as e:
                 entry[mode] = {"unavailable": str(e)}
@@ -270,18 +281,18 @@ def measure_near_clifford(S, torch, dev, stream, steps, warmup, scale=1.0):
             torch.cuda.synchronize(dev)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for i in range(steps):
-                step(warmup + i)
+            for i in range(st_n):
+                step(st_w + i)
             e1.record(stream)
             torch.cuda.synchronize(dev)
-            ms = e0.elapsed_time(e1) / steps
+            ms = e0.elapsed_time(e1) / st_n
             import numpy as np
             words = disc.cpu().numpy().view(np.uint64)
             entry[mode] = {"shots_per_step": shots, "ms_per_step": ms,
                            "shots_per_s": shots / (ms / 1e3),
                            "discard_rate": int(np.bitwise_count(words).sum()) / shots,
                            "launches_per_step": S.symft_last_launch_count()}
-        entry["fp32_vs_fp64"] = fp32_accuracy(S, torch, plan, dev, stream)
+        entry["fp32_vs_fp64"] = fp32_accuracy(S, torch, plan, dev, stream, shots=min(1 << 16, shots0))
         if "shots_per_s" in entry.get("fp64_plain", {}) and "shots_per_s" in entry.get("fp32_batched", {}):
             entry["fp32_batched_over_fp64_plain"] = (entry["fp32_batched"]["shots_per_s"] /
                                                      entry["fp64_plain"]["shots_per_s"])

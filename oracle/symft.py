@@ -436,6 +436,17 @@ def compile_plan(circuit):
 # ---------------------------------------------------------------------------
 
 
+def _parity_vec(v):
+    """Parity of each entry of an integer array."""
+    return (np.bitwise_count(v) & 1).astype(np.int64)
+
+
+def _insert_bit_vec(z, h, delta):
+    """_insert_bit over an array of z."""
+    low = z & ((1 << h) - 1)
+    return low | (delta << h) | ((z >> h) << (h + 1))
+
+
 def _insert_bit(z, h, delta):
     low = z & ((1 << h) - 1)
     return low | (delta << h) | ((z >> h) << (h + 1))
@@ -489,34 +500,31 @@ def sample_shot(plan: Plan, seed: int, r: int, noise: NoiseSampler, prob_log=Non
             th = ins["theta"]
             mu = 1.0 if ins["mu"] == 0 else -1.0
             sgn = -1.0 if lam else 1.0
-            x = np.arange(1 << k)
-            par = np.array([_parity(int(v) & ins["b"]) for v in x])
+            x = np.arange(1 << k, dtype=np.int64)
+            par = _parity_vec(x & ins["b"])
             ang = -sgn * th * mu * np.where(par == 1, -1.0, 1.0) / 2.0
             alpha = np.exp(1j * ang) * alpha
             continue
         elif op == "ActivePairRot":
+            # alpha'_x = cos(th/2) alpha_x - i sgn sin(th/2) mu (-1)^{b.(x^a)} alpha_{x^a}
             th = ins["theta"]
             mu = 1j ** ins["mu"]
             sgn = -1.0 if lam else 1.0
             a, b = ins["a"], ins["b"]
-            new = np.empty_like(alpha)
-            for x in range(1 << k):
-                xa = x ^ a
-                ph = -1.0 if _parity(xa & b) else 1.0
-                new[x] = (math.cos(th / 2) * alpha[x]
-                          - 1j * sgn * math.sin(th / 2) * mu * ph * alpha[xa])
-            alpha = new
+            x = np.arange(1 << k, dtype=np.int64)
+            xa = x ^ a
+            ph = np.where(_parity_vec(xa & b) == 1, -1.0, 1.0)
+            alpha = (math.cos(th / 2) * alpha
+                     - 1j * sgn * math.sin(th / 2) * mu * ph * alpha[xa])
             continue
         elif op == "ActiveDiagMeas":
             b, h, eta = ins["b"], ins["h"], ins["eta"]
 
-            def xmap(u):
-                rest = u & ~(1 << h)
-                return u ^ (_parity(rest & b) << h)
-
             def branch(delta):
-                return np.array([alpha[xmap(_insert_bit(z, h, delta))]
-                                 for z in range(1 << (k - 1))])
+                # alpha at x(b, u(z, delta)): bit h of u(z, delta) corrected
+                # by the parity of b over the other bits
+                u = _insert_bit_vec(np.arange(1 << (k - 1), dtype=np.int64), h, delta)
+                return alpha[u ^ (_parity_vec(u & ~(1 << h) & b) << h)]
             v0 = branch(0 ^ lam ^ eta)
             p0 = float(np.vdot(v0, v0).real)
             t = ins["t"]
@@ -532,12 +540,10 @@ def sample_shot(plan: Plan, seed: int, r: int, noise: NoiseSampler, prob_log=Non
             muc = np.conj(1j ** ins["mu"])
 
             def beta(y):
-                outv = np.empty(1 << (k - 1), dtype=np.complex128)
-                for z in range(1 << (k - 1)):
-                    u0 = _insert_bit(z, h, 0)
-                    ph = -1.0 if (_parity(b & u0) ^ y) else 1.0
-                    outv[z] = (alpha[u0] + muc * ph * alpha[u0 ^ a]) / math.sqrt(2.0)
-                return outv
+                # beta_z(y) = (alpha_{u0} + conj(mu) (-1)^{b.u0 + y} alpha_{u0^a}) / sqrt(2)
+                u0 = _insert_bit_vec(np.arange(1 << (k - 1), dtype=np.int64), h, 0)
+                ph = np.where((_parity_vec(b & u0) ^ y) == 1, -1.0, 1.0)
+                return (alpha[u0] + muc * ph * alpha[u0 ^ a]) / math.sqrt(2.0)
             v0 = beta(0 ^ lam)
             p0 = float(np.vdot(v0, v0).real)
             t = ins["t"]

@@ -88,6 +88,7 @@ void build_blob(symft_plan* P) {
     o.causal_n = d.causal_n;
     o.t = d.t;
   }
+  P->dense_host = dn;
   std::vector<unsigned char>& blob = P->blob;
   blob.clear();
   P->off.ch = push(blob, ch);
@@ -239,6 +240,8 @@ cudaError_t upload(symft_plan* P) {
                        std::string(#expr) + ": " + cudaGetErrorString(_e));              \
   } while (0)
 
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
 // Launch shapes and workspace pointers of one sampling request.  prepare()
 // allocates and decides everything on the host; enqueue() only issues
 // memsets and kernel launches, so it can also run inside a stream capture.
@@ -251,12 +254,21 @@ struct Prep {
   uint64_t* counts = nullptr;
   int* status = nullptr;
   int sign_grid = 0;
-  int dense_kind = 0;   // 0 none, 1 register, 2 warp, 3 CTA per shot
+  int dense_kind = 0;   // 0 none, 1 register, 2 warp, 3 CTA per shot, 4 wide (HBM)
   int dense_grid = 0, dense_wpb = 0, dense_use_smem = 0;
   size_t dense_smem = 0;
   void* gvec = nullptr;
   uint64_t gvec_stride = 0;
   int plain_grid = 0;
+  // wide executor: batch size and workspace pieces
+  uint32_t wide_nb = 0;
+  void* wide_vec[2] = {nullptr, nullptr};
+  uint32_t* wide_m3b = nullptr;
+  uint8_t* wide_lam = nullptr;
+  double* wide_sums = nullptr;
+  double* wide_scale = nullptr;
+  float* wide_scalef = nullptr;
+  uint8_t* wide_lab = nullptr;
 };
 
 int validate(const symft_sample_args* a) {
@@ -359,23 +371,38 @@ int prepare(symft_plan* P, const symft_sample_args* a, uint64_t* meas, uint64_t*
       const uint64_t want = (a->shots + wpb - 1) / wpb;
       const uint64_t cap = static_cast<uint64_t>(P->sm_count) * t.dense_grid_mult * 2;
       o->dense_grid = static_cast<int>(std::max<uint64_t>(1, std::min(want, cap)));
-    } else {
-      o->dense_kind = 3;   // CTA per shot, vector in shared memory or a global slot
-      const bool in_smem = dense_cta_smem_bytes(P->dp, vec_bytes, true) <= 200 * 1024;
-      o->dense_smem = dense_cta_smem_bytes(P->dp, vec_bytes, in_smem);
-      o->dense_use_smem = in_smem ? 1 : 0;
-      int grid = P->sm_count * (in_smem ? 1 : t.cta_grid_mult);
-      if (!in_smem) {
-        // bound the global slots to ~8 GB
-        const uint64_t max_slots = std::max<uint64_t>(1, (8ull << 30) / vec_bytes);
-        grid = static_cast<int>(std::min<uint64_t>(grid, max_slots));
-      }
+    } else if (dense_cta_smem_bytes(P->dp, vec_bytes, true) <= 200 * 1024) {
+      o->dense_kind = 3;   // CTA per shot, vector in shared memory
+      o->dense_smem = dense_cta_smem_bytes(P->dp, vec_bytes, true);
+      o->dense_use_smem = 1;
+      const int grid = P->sm_count * t.cta_grid_mult;
       o->dense_grid = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(a->shots, grid)));
-      if (!in_smem) {
-        o->gvec_stride = static_cast<uint64_t>(1) << h.k_max;
-        CUDA_TRY(P->gvec.ensure(static_cast<size_t>(o->dense_grid) * vec_bytes));
-        o->gvec = P->gvec.ptr;
-      }
+    } else {
+      // wide executor: batches of shots with their vectors in HBM (two
+      // buffers each), instruction by instruction; ~8 GB of vectors
+      o->dense_kind = 4;
+      const uint64_t per_shot = 2 * vec_bytes;
+      const uint64_t nb = std::min<uint64_t>({a->shots, std::max<uint64_t>(1, (8ull << 30) / per_shot), 65535});
+      o->wide_nb = static_cast<uint32_t>(nb);
+      const size_t m3w = (h.n_m3 + 31) / 32;
+      const size_t off_m3b = 2 * nb * vec_bytes;
+      const size_t off_lam = align_up(off_m3b + nb * m3w * 4, 256);
+      const size_t off_sums = align_up(off_lam + std::max<size_t>(1, G) * nb, 256);
+      const size_t off_scale = off_sums + nb * 16;
+      const size_t off_scalef = off_scale + nb * 8;
+      const size_t off_lab = off_scalef + nb * 4;
+      const size_t total = off_lab + nb;
+      CUDA_TRY(P->wide.ensure(total));
+      unsigned char* base = static_cast<unsigned char*>(P->wide.ptr);
+      o->wide_vec[0] = base;
+      o->wide_vec[1] = base + nb * vec_bytes;
+      o->wide_m3b = reinterpret_cast<uint32_t*>(base + off_m3b);
+      o->wide_lam = base + off_lam;
+      o->wide_sums = reinterpret_cast<double*>(base + off_sums);
+      o->wide_scale = reinterpret_cast<double*>(base + off_scale);
+      o->wide_scalef = reinterpret_cast<float*>(base + off_scalef);
+      o->wide_lab = base + off_lab;
+      o->gvec_stride = static_cast<uint64_t>(1) << h.k_max;
     }
   }
   return SYMFT_OK;
@@ -458,7 +485,35 @@ int enqueue(symft_plan* P, const symft_sample_args* a, const Prep& o, cudaStream
     d.gvec = o.gvec;
     d.gvec_stride = o.gvec_stride;
     d.prob = o.prob;
-    if (o.dense_kind == 1) CUDA_TRY(launch_dense_reg(d, o.fp64, o.dense_grid, st));
+    if (o.dense_kind == 4) {
+      WideArgs wa{};
+      wa.p = P->dp;
+      wa.keys = d.keys;
+      wa.shots = a->shots;
+      wa.W = W;
+      wa.stride = o.gvec_stride;
+      wa.vec[0] = o.wide_vec[0];
+      wa.vec[1] = o.wide_vec[1];
+      wa.signs = o.signs;
+      wa.m3_out = o.m3;
+      wa.prob = o.prob;
+      wa.m3b = o.wide_m3b;
+      wa.lam = o.wide_lam;
+      wa.sums = o.wide_sums;
+      wa.scale = o.wide_scale;
+      wa.scalef = o.wide_scalef;
+      wa.lab = o.wide_lab;
+      for (uint64_t s0 = 0; s0 < a->shots; s0 += o.wide_nb) {
+        wa.shot0 = a->shot_offset + s0;
+        wa.r0 = s0;
+        wa.nb = static_cast<uint32_t>(std::min<uint64_t>(o.wide_nb, a->shots - s0));
+        wa.cur = 0;
+        int l = 0;
+        CUDA_TRY(launch_wide_batch(wa, P->dense_host.data(), o.fp64, P->sm_count, st, &l));
+        *launches += l;
+      }
+      --*launches;   // counted once below
+    } else if (o.dense_kind == 1) CUDA_TRY(launch_dense_reg(d, o.fp64, o.dense_grid, st));
     else if (o.dense_kind == 2) CUDA_TRY(launch_dense(d, o.fp64, o.dense_wpb, o.dense_grid, o.dense_smem, st));
     else CUDA_TRY(launch_dense_cta(d, o.fp64, o.dense_grid, o.dense_smem, st));
     ++*launches;
@@ -820,6 +875,7 @@ void symft_plan_free(symft_plan* p) {
   p->h_prob.release();
   p->h_counts.release();
   p->gvec.release();
+  p->wide.release();
   p->status.release();
   p->h_meas.release();
   p->h_det.release();

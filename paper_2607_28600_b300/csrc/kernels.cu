@@ -124,23 +124,38 @@ template <typename Real, typename Acc>
 __device__ __forceinline__ void branch_sums(const Cplx<Real>* vec, const DenseInstrDev& I, uint32_t n,
                                             uint32_t start, uint32_t stride, Real mcr, Real mci,
                                             Acc& S0, Acc& S1) {
+  // terms in the vector's precision, summed in runs of 16 in that precision
+  // and the runs in Acc (one Acc add per run keeps FP64 work off the
+  // per-element path of FP32 vectors)
+  constexpr uint32_t kRun = 16;
   const Real inv_sqrt2 = (Real)0.70710678118654752440;
   if (I.kind == 5) {
-    for (uint32_t x = start; x < n; x += stride) {
-      const Cplx<Real> a = vec[x];
-      const Acc v = (Acc)a.re * (Acc)a.re + (Acc)a.im * (Acc)a.im;
-      if (__popc(x & I.b) & 1) S1 += v; else S0 += v;
+    for (uint32_t x0 = start; x0 < n; x0 += stride * kRun) {
+      Real r0 = 0, r1 = 0;
+      for (uint32_t j = 0, x = x0; j < kRun && x < n; ++j, x += stride) {
+        const Cplx<Real> a = vec[x];
+        const Real v = a.re * a.re + a.im * a.im;
+        if (__popc(x & I.b) & 1) r1 += v; else r0 += v;
+      }
+      S0 += (Acc)r0;
+      S1 += (Acc)r1;
     }
   } else {
-    for (uint32_t z = start; z < (n >> 1); z += stride) {
-      const uint32_t u0 = insert_bit(z, I.h, 0u);
-      const Cplx<Real> a0 = vec[u0], a1 = vec[u0 ^ I.a];
-      const Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
-      const Real tr = sb * (mcr * a1.re - mci * a1.im), ti = sb * (mcr * a1.im + mci * a1.re);
-      const Real b0r = (a0.re + tr) * inv_sqrt2, b0i = (a0.im + ti) * inv_sqrt2;
-      const Real b1r = (a0.re - tr) * inv_sqrt2, b1i = (a0.im - ti) * inv_sqrt2;
-      S0 += (Acc)b0r * (Acc)b0r + (Acc)b0i * (Acc)b0i;
-      S1 += (Acc)b1r * (Acc)b1r + (Acc)b1i * (Acc)b1i;
+    const uint32_t half = n >> 1;
+    for (uint32_t z0 = start; z0 < half; z0 += stride * kRun) {
+      Real r0 = 0, r1 = 0;
+      for (uint32_t j = 0, z = z0; j < kRun && z < half; ++j, z += stride) {
+        const uint32_t u0 = insert_bit(z, I.h, 0u);
+        const Cplx<Real> a0 = vec[u0], a1 = vec[u0 ^ I.a];
+        const Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
+        const Real tr = sb * (mcr * a1.re - mci * a1.im), ti = sb * (mcr * a1.im + mci * a1.re);
+        const Real b0r = (a0.re + tr) * inv_sqrt2, b0i = (a0.im + ti) * inv_sqrt2;
+        const Real b1r = (a0.re - tr) * inv_sqrt2, b1i = (a0.im - ti) * inv_sqrt2;
+        r0 += b0r * b0r + b0i * b0i;
+        r1 += b1r * b1r + b1i * b1i;
+      }
+      S0 += (Acc)r0;
+      S1 += (Acc)r1;
     }
   }
 }

@@ -152,6 +152,29 @@ struct DenseArgs {
   double* prob;           // Pr(m = 0) per active measurement and shot (n_m3 x shots) or null
 };
 
+// One batch of the wide (instruction-major) dense executor.
+struct WideArgs {
+  DevPlan p;
+  PhiloxKeys keys;        // round keys of the seed
+  uint64_t shot0;         // absolute index of batch shot 0
+  uint64_t r0;            // request-local index of batch shot 0
+  uint64_t shots;         // shots of the whole request (prob_out row length)
+  uint64_t W;             // words per output column of the request
+  uint32_t nb;            // shots in this batch
+  int cur;                // buffer holding the current vectors (0 or 1)
+  uint64_t stride;        // amplitudes per shot in a buffer (2^k_max)
+  void* vec[2];           // [nb][stride] amplitudes each
+  const uint64_t* signs;  // exogenous sign columns (n_dense x W)
+  uint64_t* m3_out;       // active outcomes (n_m3 x W), zeroed before the first batch
+  double* prob;           // Pr(m = 0) per active measurement and shot, or null
+  uint32_t* m3b;          // [nb][ceil(n_m3 / 32)] active outcomes of each shot
+  uint8_t* lam;           // [n_dense][nb] sign of each dense instruction
+  double* sums;           // [nb][2] branch sums of the current measurement
+  double* scale;          // [nb] renormalisation after the current measurement
+  float* scalef;          // [nb] the same, rounded to FP32 (FP32 vectors)
+  uint8_t* lab;           // [nb] kept branch label
+};
+
 struct PlainArgs {
   DevPlan p;
   uint64_t seed;

@@ -52,6 +52,10 @@ size_t dense_cta_smem_bytes(const DevPlan& p, size_t vec_bytes, bool vec_in_smem
 cudaError_t launch_dense_cta(const DenseArgs& a, bool fp64, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_dense_reg(const DenseArgs& a, bool fp64, int grid, cudaStream_t st);
 cudaError_t launch_plain(const PlainArgs& a, bool fp64, int grid, cudaStream_t st);
+// all dense instructions for one batch of the wide executor (host_dense: the
+// plan's instruction stream in host memory, for the per-instruction launches)
+cudaError_t launch_wide_batch(const WideArgs& a, const DenseInstrDev* host_dense, bool fp64, int sm_count,
+                              cudaStream_t st, int* launches);
 
 // Launch shapes chosen by symft_autotune (0 = built-in heuristic).
 struct Tune {
@@ -74,7 +78,8 @@ struct symft_plan {
   int device = -1;
   symft::DevBuf plan_buf;
   symft::DevPlan dp{};
-  symft::DevBuf signs, m3, det_scratch, gvec, status;
+  symft::DevBuf signs, m3, det_scratch, gvec, status, wide;
+  std::vector<symft::DenseInstrDev> dense_host;   // host copy of the instruction stream
   symft::DevBuf obs_scratch, disc_scratch;      // tallies without obs / discard outputs
   symft::DevBuf h_meas, h_det, h_obs, h_disc;   // staging for host outputs
   symft::DevBuf h_prob, h_counts;

@@ -1,0 +1,415 @@
+// Wide dense executor: the dense-state instructions of Sec. 4 for active
+// widths whose vectors do not fit on chip (2^k amplitudes per shot above
+// ~200 KB).  Work is instruction-major: a batch of shots keeps its vectors in
+// HBM ([shot][2^k_max] amplitudes, two buffers), and every dense instruction
+// is one or three grid-wide passes over all shots of the batch, so each pass
+// streams whole vectors with full memory-level parallelism.
+//
+//   rotations    one pass, in place (PromoteRot writes the upper half,
+//                ActivePairRot updates disjoint pairs (x0, x0 ^ a))
+//   measurements branch sums per shot (block partials added into FP64
+//                accumulators), a per-shot decision (shared uniform rule,
+//                record / causal bits, renormalisation, signs of the
+//                following instructions), and compaction into the other
+//                buffer
+//
+// A shot's signs lam(g) = exogenous bit ^ causal residual (Sec. 5) are
+// evaluated per shot whenever its active outcomes change: at the start of the
+// batch for the instructions up to the first measurement, and by each
+// measurement's decision for those up to the next one.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "device.cuh"
+
+namespace symft {
+
+namespace {
+
+constexpr int kWideThreads = 256;
+constexpr int kWideItems = 4;     // elements per thread per block-pass
+
+template <typename Real>
+struct Amp {
+  Real re, im;
+};
+
+__device__ __forceinline__ uint32_t wide_insert_bit(uint32_t z, int h, uint32_t d) {
+  const uint32_t low = z & ((1u << h) - 1u);
+  return low | (d << h) | ((z >> h) << (h + 1));
+}
+
+__device__ __forceinline__ uint64_t wide_meas_U(const PhiloxKeys& K, uint32_t t, uint64_t r) {
+  const uint64_t w = r >> 6;
+  const uint4 ob = philox(make_uint4(t, (uint32_t)(w >> 1), (uint32_t)(w >> 33), kTagMbit), K);
+  const uint64_t word = (w & 1) ? ((uint64_t)ob.z | ((uint64_t)ob.w << 32)) : ((uint64_t)ob.x | ((uint64_t)ob.y << 32));
+  const uint64_t bit = (word >> (r & 63)) & 1ull;
+  const uint4 of = philox(make_uint4(t, (uint32_t)(r >> 1), (uint32_t)(r >> 33), kTagMfrac), K);
+  const uint64_t fw = (r & 1) ? ((uint64_t)of.z | ((uint64_t)of.w << 32)) : ((uint64_t)of.x | ((uint64_t)of.y << 32));
+  return (bit << 52) + (fw >> 12);
+}
+
+// signs of instructions g0, g0+1, ... up to and including the next active
+// measurement, for shot b (whose active outcomes so far are in m3b)
+__device__ void wide_signs_from(const WideArgs& A, uint32_t b, uint32_t g0) {
+  const uint64_t r = A.r0 + b;
+  const uint32_t m3w = (A.p.n_m3 + 31) / 32;
+  const uint32_t* mb = A.m3b + (size_t)b * m3w;
+  for (uint32_t g = g0; g < A.p.n_dense; ++g) {
+    const DenseInstrDev I = A.p.dense[g];
+    uint32_t lam = (uint32_t)((__ldg(A.signs + (uint64_t)I.sign_target_col * A.W + (r >> 6)) >> (r & 63)) & 1ull);
+    for (uint32_t q = 0; q < I.causal_n; ++q) {
+      const uint32_t j = __ldg(A.p.dense_causal + I.causal_off + q);
+      lam ^= (mb[j >> 5] >> (j & 31)) & 1u;
+    }
+    A.lam[(size_t)g * A.nb + b] = (uint8_t)lam;
+    if (I.kind == 5 || I.kind == 6) break;
+  }
+}
+
+}  // namespace
+
+template <typename Real>
+__global__ void wide_init_kernel(WideArgs A) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= A.nb) return;
+  Amp<Real>* v = reinterpret_cast<Amp<Real>*>(A.vec[A.cur]) + (size_t)b * A.stride;
+  v[0].re = (Real)1;
+  v[0].im = (Real)0;
+  const uint32_t m3w = (A.p.n_m3 + 31) / 32;
+  for (uint32_t i = 0; i < m3w; ++i) A.m3b[(size_t)b * m3w + i] = 0u;
+  A.sums[2 * b] = 0.0;
+  A.sums[2 * b + 1] = 0.0;
+  wide_signs_from(A, b, 0);
+}
+
+// PromoteRot / ActiveDiagRot / ActivePairRot of instruction g on every shot:
+// one flat index over (shot, element), element count 2^lg per shot
+template <typename Real>
+__global__ void __launch_bounds__(kWideThreads) wide_rot_kernel(WideArgs A, uint32_t g) {
+  const DenseInstrDev I = A.p.dense[g];
+  const uint32_t n = 1u << I.k;
+  const int lg = I.kind == 2 ? I.k - 1 : I.k;          // pairs for ActivePairRot
+  const uint64_t total = (uint64_t)A.nb << lg;
+  const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+  const Real c = (Real)I.c, s = (Real)I.s;
+  const uint8_t* lamg = A.lam + (size_t)g * A.nb;
+  Amp<Real>* vbase = reinterpret_cast<Amp<Real>*>(A.vec[A.cur]);
+  if (I.kind == 0) {                    // a'_x = c a_x, a'_{x+n} = -i sg s a_x
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += step) {
+      const uint32_t b = (uint32_t)(i >> lg), x = (uint32_t)i & (n - 1);
+      Amp<Real>* v = vbase + (size_t)b * A.stride;
+      const Real sgs = lamg[b] ? -s : s;
+      Amp<Real> a = v[x], hi;
+      hi.re = sgs * a.im;
+      hi.im = -sgs * a.re;
+      v[x + n] = hi;
+      a.re *= c;
+      a.im *= c;
+      v[x] = a;
+    }
+  } else if (I.kind == 1) {             // a_x *= c - i sg mu (-1)^{b.x} s
+    const Real mus = I.mu == 0 ? s : -s;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += step) {
+      const uint32_t b = (uint32_t)(i >> lg), x = (uint32_t)i & (n - 1);
+      Amp<Real>* v = vbase + (size_t)b * A.stride;
+      const Real f = (lamg[b] ? -mus : mus) * ((__popc(x & I.b) & 1) ? (Real)-1 : (Real)1);
+      const Amp<Real> a = v[x];
+      Amp<Real> o;
+      o.re = c * a.re + f * a.im;
+      o.im = c * a.im - f * a.re;
+      v[x] = o;
+    }
+  } else {                              // pairs (x0, x0 ^ a), coefficient -i mu sg s (-1)^{b.x}
+    const int pb = 31 - __clz(I.a);
+    Real cr0, ci0;
+    switch (I.mu & 3) {
+      case 0: cr0 = 0; ci0 = -1; break;
+      case 1: cr0 = 1; ci0 = 0; break;
+      case 2: cr0 = 0; ci0 = 1; break;
+      default: cr0 = -1; ci0 = 0; break;
+    }
+    const uint32_t half_mask = (n >> 1) - 1;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += step) {
+      const uint32_t b = (uint32_t)(i >> lg), z = (uint32_t)i & half_mask;
+      Amp<Real>* v = vbase + (size_t)b * A.stride;
+      const Real sgs = lamg[b] ? -s : s;
+      const Real cr = cr0 * sgs, ci = ci0 * sgs;
+      const uint32_t x0 = wide_insert_bit(z, pb, 0u), x1 = x0 ^ I.a;
+      const Amp<Real> v0 = v[x0], v1 = v[x1];
+      const Real s1 = (__popc(x1 & I.b) & 1) ? (Real)-1 : (Real)1;
+      const Real s0 = (__popc(x0 & I.b) & 1) ? (Real)-1 : (Real)1;
+      Amp<Real> o0, o1;
+      o0.re = c * v0.re + s1 * (cr * v1.re - ci * v1.im);
+      o0.im = c * v0.im + s1 * (cr * v1.im + ci * v1.re);
+      o1.re = c * v1.re + s0 * (cr * v0.re - ci * v0.im);
+      o1.im = c * v1.im + s0 * (cr * v0.im + ci * v0.re);
+      v[x0] = o0;
+      v[x1] = o1;
+    }
+  }
+}
+
+// conj(mu) of a pair measurement
+template <typename Real>
+__device__ __forceinline__ void wide_conj_mu(int mu, Real& mcr, Real& mci) {
+  switch (mu & 3) {
+    case 0: mcr = 1; mci = 0; break;
+    case 1: mcr = 0; mci = -1; break;
+    case 2: mcr = -1; mci = 0; break;
+    default: mcr = 0; mci = 1; break;
+  }
+}
+
+// outcome of measurement g for shot b from its branch sums: the shared
+// uniform rule on p0 = S_{label 0} / (S0 + S1), records, renormalisation,
+// and the signs of the following instructions; returns the kept label and
+// the scale
+template <typename Real>
+__device__ void wide_decide_one(const WideArgs& A, uint32_t g, uint32_t b, double S0, double S1,
+                                uint32_t& lab_out, double& scale_out) {
+  const DenseInstrDev I = A.p.dense[g];
+  const uint64_t r = A.r0 + b, rg = A.shot0 + b;
+  const uint32_t lam = A.lam[(size_t)g * A.nb + b];
+  const uint32_t l0 = I.kind == 5 ? (lam ^ (uint32_t)I.eta) : lam;
+  const uint64_t U = wide_meas_U(A.keys, I.t, rg);
+  double pd = (l0 ? S1 : S0) / (S0 + S1);
+  // FP32 vectors: p0 rounded to FP32; p0 * 2^53 is exact in FP64 either way,
+  // so the comparison below is the exact rule U < p0 * 2^53
+  if (sizeof(Real) == 4) pd = (double)(float)pd;
+  const uint32_t m = (double)U < pd * 9007199254740992.0 ? 0u : 1u;
+  if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = pd;
+  lab_out = l0 ^ m;
+  scale_out = 1.0 / sqrt(lab_out ? S1 : S0);
+  if (m) {
+    const uint32_t m3w = (A.p.n_m3 + 31) / 32;
+    A.m3b[(size_t)b * m3w + (I.m3 >> 5)] |= 1u << (I.m3 & 31);
+    atomicOr(reinterpret_cast<unsigned long long*>(A.m3_out) + (uint64_t)I.m3 * A.W + (r >> 6),
+             1ull << (r & 63));
+  }
+  wide_signs_from(A, b, g + 1);
+}
+
+template <typename Real>
+__global__ void wide_decide_kernel(WideArgs A, uint32_t g) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= A.nb) return;
+  uint32_t lab;
+  double scale;
+  wide_decide_one<Real>(A, g, b, A.sums[2 * b], A.sums[2 * b + 1], lab, scale);
+  A.lab[b] = (uint8_t)lab;
+  A.scale[b] = scale;
+  A.scalef[b] = (float)scale;
+  A.sums[2 * b] = 0.0;
+  A.sums[2 * b + 1] = 0.0;
+}
+
+// compaction of shot b's measurement g: element z of the kept half
+template <typename Real>
+__device__ __forceinline__ Amp<Real> wide_kept(const Amp<Real>* v, const DenseInstrDev& I, uint32_t z, uint32_t lab,
+                                               Real scale, Real mcr, Real mci) {
+  const int h = I.h;
+  Amp<Real> a;
+  if (I.kind == 5) {
+    const uint32_t u = wide_insert_bit(z, h, lab);
+    a = v[u ^ ((uint32_t)(__popc(u & I.b & ~(1u << h)) & 1) << h)];
+    a.re *= scale;
+    a.im *= scale;
+  } else {
+    const Real inv_sqrt2 = (Real)0.70710678118654752440;
+    const uint32_t u0 = wide_insert_bit(z, h, 0u);
+    const Amp<Real> a0 = v[u0], a1 = v[u0 ^ I.a];
+    Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
+    if (lab) sb = -sb;
+    const Real tr = sb * (mcr * a1.re - mci * a1.im), ti = sb * (mcr * a1.im + mci * a1.re);
+    a.re = (a0.re + tr) * inv_sqrt2 * scale;
+    a.im = (a0.im + ti) * inv_sqrt2 * scale;
+  }
+  return a;
+}
+
+// branch sums of shot b's measurement g over elements e0, e0+step, ...:
+// terms in the vector's precision, summed in runs of kWideRun terms in that
+// precision and the runs in FP64 (B300's FP64 rate is a small fraction of its
+// FP32 rate, so FP32 vectors keep FP64 work to one add per run)
+constexpr uint32_t kWideRun = 16;
+
+template <typename Real>
+__device__ __forceinline__ void wide_partial_sums(const Amp<Real>* v, const DenseInstrDev& I, uint32_t e0,
+                                                  uint32_t step, double& S0, double& S1) {
+  const uint32_t n = 1u << I.k;
+  if (I.kind == 5) {
+    for (uint32_t x0 = e0; x0 < n; x0 += step * kWideRun) {
+      Real r0 = 0, r1 = 0;
+      for (uint32_t j = 0, x = x0; j < kWideRun && x < n; ++j, x += step) {
+        const Amp<Real> a = v[x];
+        const Real w = a.re * a.re + a.im * a.im;
+        if (__popc(x & I.b) & 1) r1 += w; else r0 += w;
+      }
+      S0 += (double)r0;
+      S1 += (double)r1;
+    }
+  } else {
+    Real mcr, mci;
+    wide_conj_mu<Real>(I.mu, mcr, mci);
+    const Real inv_sqrt2 = (Real)0.70710678118654752440;
+    const uint32_t half = n >> 1;
+    for (uint32_t z0 = e0; z0 < half; z0 += step * kWideRun) {
+      Real r0 = 0, r1 = 0;
+      for (uint32_t j = 0, z = z0; j < kWideRun && z < half; ++j, z += step) {
+        const uint32_t u0 = wide_insert_bit(z, I.h, 0u);
+        const Amp<Real> a0 = v[u0], a1 = v[u0 ^ I.a];
+        const Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
+        const Real tr = sb * (mcr * a1.re - mci * a1.im), ti = sb * (mcr * a1.im + mci * a1.re);
+        const Real b0r = (a0.re + tr) * inv_sqrt2, b0i = (a0.im + ti) * inv_sqrt2;
+        const Real b1r = (a0.re - tr) * inv_sqrt2, b1i = (a0.im - ti) * inv_sqrt2;
+        r0 += b0r * b0r + b0i * b0i;
+        r1 += b1r * b1r + b1i * b1i;
+      }
+      S0 += (double)r0;
+      S1 += (double)r1;
+    }
+  }
+}
+
+// a whole measurement of a small vector (2^k <= kWideSmall): one warp per
+// shot computes the sums, decides, and compacts into the other buffer
+constexpr uint32_t kWideSmall = 4096;
+
+template <typename Real>
+__global__ void __launch_bounds__(kWideThreads) wide_meas_small_kernel(WideArgs A, uint32_t g) {
+  const uint32_t b = blockIdx.x * (kWideThreads / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= A.nb) return;                       // whole warps leave together
+  const DenseInstrDev I = A.p.dense[g];
+  const Amp<Real>* v = reinterpret_cast<const Amp<Real>*>(A.vec[A.cur]) + (size_t)b * A.stride;
+  Amp<Real>* o = reinterpret_cast<Amp<Real>*>(A.vec[A.cur ^ 1]) + (size_t)b * A.stride;
+  double S0 = 0.0, S1 = 0.0;
+  wide_partial_sums<Real>(v, I, (uint32_t)lane, 32u, S0, S1);
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    S0 += __shfl_xor_sync(0xffffffffu, S0, off);
+    S1 += __shfl_xor_sync(0xffffffffu, S1, off);
+  }
+  uint32_t lab = 0;
+  double scale = 0.0;
+  if (lane == 0) wide_decide_one<Real>(A, g, b, S0, S1, lab, scale);
+  lab = __shfl_sync(0xffffffffu, lab, 0);
+  scale = __shfl_sync(0xffffffffu, scale, 0);
+  Real mcr = 0, mci = 0;
+  if (I.kind == 6) wide_conj_mu<Real>(I.mu, mcr, mci);
+  const uint32_t half = 1u << (I.k - 1);
+  for (uint32_t z = (uint32_t)lane; z < half; z += 32) o[z] = wide_kept<Real>(v, I, z, lab, (Real)scale, mcr, mci);
+}
+
+// branch sums S0 (label 0) and S1 of measurement g, FP64 accumulation: a 2D
+// grid of (chunk, shot) blocks adding block partials into the shot's sums
+template <typename Real>
+__global__ void __launch_bounds__(kWideThreads) wide_sums_kernel(WideArgs A, uint32_t g) {
+  __shared__ double red[2][kWideThreads / 32];
+  const uint32_t b = blockIdx.y;
+  const DenseInstrDev I = A.p.dense[g];
+  const Amp<Real>* v = reinterpret_cast<const Amp<Real>*>(A.vec[A.cur]) + (size_t)b * A.stride;
+  double S0 = 0.0, S1 = 0.0;
+  wide_partial_sums<Real>(v, I, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, S0, S1);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    S0 += __shfl_xor_sync(0xffffffffu, S0, o);
+    S1 += __shfl_xor_sync(0xffffffffu, S1, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][warp] = S0;
+    red[1][warp] = S1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t0 = 0.0, t1 = 0.0;
+    for (int w = 0; w < kWideThreads / 32; ++w) {
+      t0 += red[0][w];
+      t1 += red[1][w];
+    }
+    atomicAdd(A.sums + 2 * b, t0);
+    atomicAdd(A.sums + 2 * b + 1, t1);
+  }
+}
+
+// compaction of measurement g into the other buffer (2^(k-1) amplitudes per
+// shot), one flat index over (shot, element)
+template <typename Real>
+__global__ void __launch_bounds__(kWideThreads) wide_compact_kernel(WideArgs A, uint32_t g) {
+  const DenseInstrDev I = A.p.dense[g];
+  const int lg = I.k - 1;
+  const uint64_t total = (uint64_t)A.nb << lg;
+  const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+  Real mcr = 0, mci = 0;
+  if (I.kind == 6) wide_conj_mu<Real>(I.mu, mcr, mci);
+  const Amp<Real>* vb = reinterpret_cast<const Amp<Real>*>(A.vec[A.cur]);
+  Amp<Real>* ob = reinterpret_cast<Amp<Real>*>(A.vec[A.cur ^ 1]);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += step) {
+    const uint32_t b = (uint32_t)(i >> lg), z = (uint32_t)i & ((1u << lg) - 1u);
+    const Real sc = sizeof(Real) == 4 ? (Real)A.scalef[b] : (Real)A.scale[b];
+    ob[(size_t)b * A.stride + z] = wide_kept<Real>(vb + (size_t)b * A.stride, I, z, A.lab[b], sc, mcr, mci);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host: one batch of shots through the whole dense instruction stream
+// ---------------------------------------------------------------------------
+// blocks of a flat pass over `total` elements: enough to fill the GPU
+static unsigned wide_flat_blocks(uint64_t total, int sm_count) {
+  const uint64_t want = (total + (uint64_t)kWideThreads * kWideItems - 1) / ((uint64_t)kWideThreads * kWideItems);
+  const uint64_t cap = (uint64_t)sm_count * 32;
+  uint64_t x = want < cap ? want : cap;
+  return (unsigned)(x < 1 ? 1 : x);
+}
+
+// chunks per shot of a 2D (chunk, shot) pass over `elems` elements per shot
+static unsigned wide_chunks(uint64_t elems, int sm_count, uint32_t nb) {
+  const uint64_t want = (elems + (uint64_t)kWideThreads * kWideItems - 1) / ((uint64_t)kWideThreads * kWideItems);
+  const uint64_t fill = ((uint64_t)sm_count * 16 + nb - 1) / nb;
+  uint64_t x = want < fill ? want : fill;
+  if (x < 1) x = 1;
+  if (x > 65535) x = 65535;
+  return (unsigned)x;
+}
+
+template <typename Real>
+static cudaError_t wide_batch_t(WideArgs A, const DenseInstrDev* host_dense, int sm_count, cudaStream_t st,
+                                int* launches) {
+  const unsigned nb_blocks = (A.nb + 127) / 128;
+  wide_init_kernel<Real><<<nb_blocks, 128, 0, st>>>(A);
+  ++*launches;
+  for (uint32_t g = 0; g < A.p.n_dense; ++g) {
+    const DenseInstrDev& I = host_dense[g];
+    const uint64_t n = 1ull << I.k;
+    if (I.kind <= 2) {
+      const uint64_t per_shot = I.kind == 2 ? n / 2 : n;
+      wide_rot_kernel<Real><<<wide_flat_blocks(per_shot * A.nb, sm_count), kWideThreads, 0, st>>>(A, g);
+      ++*launches;
+    } else if (n <= kWideSmall) {
+      wide_meas_small_kernel<Real><<<(A.nb + kWideThreads / 32 - 1) / (kWideThreads / 32), kWideThreads, 0, st>>>(A, g);
+      ++*launches;
+      A.cur ^= 1;
+    } else {
+      const uint64_t elems = I.kind == 5 ? n : n / 2;
+      wide_sums_kernel<Real><<<dim3(wide_chunks(elems, sm_count, A.nb), A.nb), kWideThreads, 0, st>>>(A, g);
+      wide_decide_kernel<Real><<<nb_blocks, 128, 0, st>>>(A, g);
+      wide_compact_kernel<Real><<<wide_flat_blocks((n / 2) * A.nb, sm_count), kWideThreads, 0, st>>>(A, g);
+      *launches += 3;
+      A.cur ^= 1;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_wide_batch(const WideArgs& a, const DenseInstrDev* host_dense, bool fp64, int sm_count,
+                              cudaStream_t st, int* launches) {
+  return fp64 ? wide_batch_t<double>(a, host_dense, sm_count, st, launches)
+              : wide_batch_t<float>(a, host_dense, sm_count, st, launches);
+}
+
+}  // namespace symft

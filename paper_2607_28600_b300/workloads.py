@@ -4,8 +4,9 @@ The paper's benchmark circuits live in an external repository that is not
 available here, so every workload is generated from a seed with the shapes of
 the paper's workloads (Sec. 7): rotated surface-code memory (Sec. 7.2:
 d=7,r=7 has 97 qubits and 336 detectors, d=9,r=9 has 161 qubits and 720
-detectors), a cultivation-shaped near-Clifford circuit, 15-to-1 distillation
-and random near-Clifford circuits.  Each generator returns circuit text in the
+detectors), surface-code memory with coherent over-rotations, a
+cultivation-shaped near-Clifford circuit, 15-to-1 distillation and random
+near-Clifford circuits.  Each generator returns circuit text in the
 Stim-like grammar accepted by ``symft_compile``.
 
 Noise model (the paper does not print one for its circuits): DEPOLARIZE1(p)
@@ -187,6 +188,24 @@ def random_near_clifford(n: int, layers: int, n_rot: int, p: float = 1e-3,
             e.raw(f"R_PAULI({th!r}) {prod}")
     e.measure(list(range(n)), "Z")
     return e.text()
+
+
+def coherent_surface_code_memory(d: int, rounds: int, p: float = 1e-3, eps: float = 0.02) -> str:
+    """Rotated surface-code Z memory with coherent over-rotations: after every
+    CX layer, R_Z(eps) = exp(-i eps Z / 2) on both qubits of each CX, on top of
+    the circuit-level noise of `rotated_surface_code_memory`.
+
+    This is the shape of the paper's coherent-noise workload (Sec. 7: a small
+    R_Z(0.02) over-rotation with circuit-level noise on distance-d surface-code
+    circuits over r rounds).  Its peak active width grows with d and r: 4, 8,
+    12 and 24 for (d, r) = (3, 1), (3, 3), (5, 1), (5, 5).
+    """
+    out = []
+    for line in rotated_surface_code_memory(d, rounds, p).splitlines():
+        out.append(line)
+        if line.startswith("CX "):
+            out.append(f"R_Z({eps!r}) " + " ".join(line.split()[1:]))
+    return "\n".join(out) + "\n"
 
 
 # ---------------------------------------------------------------------------
