@@ -247,10 +247,13 @@ def fp32_accuracy(S, torch, plan, dev, stream, shots=1 << 16, seed=77):
             "max_prob_err_unflipped": err, "n_active_meas": info["n_causal"]}
 
 
-def measure_near_clifford(S, torch, dev, stream, steps, warmup, scale=1.0):
+def measure_near_clifford(S, torch, dev, stream, steps, warmup, scale=1.0, only=None):
     """FP32-batched vs FP64-plain (and FP64-batched) shots/s per near-Clifford config."""
     out = {}
+    peak, peak_kind = _peaks()
     for name, (kind, post, shots0) in NEAR_CLIFFORD.items():
+        if only is not None and name != only:
+            continue
         plan = S.symft_compile(_near_clifford_text(kind), postselect=post)
         info = plan.info
         entry = {"k_max": info["k_max"], "n_qubits": info["n_qubits"],
@@ -293,6 +296,19 @@ def measure_near_clifford(S, torch, dev, stream, steps, warmup, scale=1.0):
                            "discard_rate": int(np.bitwise_count(words).sum()) / shots,
                            "launches_per_step": S.symft_last_launch_count()}
         entry["fp32_vs_fp64"] = fp32_accuracy(S, torch, plan, dev, stream, shots=min(1 << 16, shots0))
+        # vector traffic of the dense instructions as streaming passes; in HBM
+        # when the vector exceeds shared memory (wide executor)
+        amps = info["dense_amp_traffic"]
+        vt = {}
+        for mode, amp_bytes in (("fp32_batched", 8), ("fp64_batched", 16)):
+            sps = entry.get(mode, {}).get("shots_per_s")
+            if sps and amps:
+                in_hbm = (1 << info["k_max"]) * amp_bytes > 200 * 1024
+                gbs = sps * amps * amp_bytes / 1e9
+                vt[mode] = {"bytes_per_shot": amps * amp_bytes, "achieved_GBps": gbs,
+                            "where": "hbm" if in_hbm else "on-chip",
+                            "frac_of_hbm": gbs / peak if in_hbm else None}
+        entry["vector_traffic"] = vt
         if "shots_per_s" in entry.get("fp64_plain", {}) and "shots_per_s" in entry.get("fp32_batched", {}):
             entry["fp32_batched_over_fp64_plain"] = (entry["fp32_batched"]["shots_per_s"] /
                                                      entry["fp64_plain"]["shots_per_s"])
@@ -388,7 +404,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--only", default=None,
                     help="run one part (profiling): a surface-code workload name, "
-                         "near_clifford or mixed_batch")
+                         "near_clifford, a near-Clifford config name, or mixed_batch")
     ap.add_argument("--no-near-clifford", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -410,9 +426,12 @@ def main():
     W = (shots + 63) // 64
     from paper_2607_28600_b300.sharding import weak_offset
     offset = weak_offset(shots, rank)
-    if args.only in ("near_clifford", "mixed_batch"):
-        fn = measure_near_clifford if args.only == "near_clifford" else measure_mixed_batch
-        res = fn(S, torch, dev, stream, steps=args.steps, warmup=args.warmup)
+    if args.only in ("near_clifford", "mixed_batch") or args.only in NEAR_CLIFFORD:
+        if args.only == "mixed_batch":
+            res = measure_mixed_batch(S, torch, dev, stream, steps=args.steps, warmup=args.warmup)
+        else:
+            res = measure_near_clifford(S, torch, dev, stream, steps=args.steps, warmup=args.warmup,
+                                        only=None if args.only == "near_clifford" else args.only)
         if rank == 0:
             print(json.dumps({args.only: res}), flush=True)
         return

@@ -99,6 +99,11 @@ typedef struct {
   uint64_t sign_xor_terms;    /* total (symbol, target) incidences */
   float tuned_ns_per_shot[2]; /* GPU time per shot of the autotuned shape
                                  (FP32, FP64); 0 until symft_autotune ran */
+  uint64_t dense_amp_traffic;  /* amplitudes read + written per shot by the dense
+                                  instructions as streaming passes (rotation 2 * 2^k,
+                                  PromoteRot 3 * 2^k, measurement 2^k + 1.5 * 2^k);
+                                  times 8 B (FP32) or 16 B (FP64) = vector bytes
+                                  per shot when vectors live in HBM */
 } symft_info;
 
 /* One sampling request.  All pointers may be NULL to skip that output. */

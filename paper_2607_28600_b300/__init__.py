@@ -46,7 +46,8 @@ class _Info(ctypes.Structure):
                 ("k_max", ctypes.c_uint32), ("n_instr", ctypes.c_uint32 * 7),
                 ("max_expr_weight", ctypes.c_uint32), ("n_noise_components", ctypes.c_uint32),
                 ("n_targets", ctypes.c_uint32), ("n_causal", ctypes.c_uint32),
-                ("sign_xor_terms", ctypes.c_uint64), ("tuned_ns_per_shot", ctypes.c_float * 2)]
+                ("sign_xor_terms", ctypes.c_uint64), ("tuned_ns_per_shot", ctypes.c_float * 2),
+                ("dense_amp_traffic", ctypes.c_uint64)]
 
 
 class _SampleArgs(ctypes.Structure):

@@ -851,6 +851,14 @@ int symft_plan_info(const symft_plan* p, symft_info* info) {
   info->n_targets = h.n_slots;
   info->n_causal = h.n_m3;
   info->sign_xor_terms = h.sign_xor_terms;
+  uint64_t traffic = 0;
+  for (const DenseInstr& d : h.dense) {
+    const uint64_t n = 1ull << d.k;
+    if (d.kind == I_PROMOTE_ROT) traffic += 3 * n;
+    else if (d.kind == I_ACTIVE_DIAG_ROT || d.kind == I_ACTIVE_PAIR_ROT) traffic += 2 * n;
+    else traffic += n + n + n / 2;
+  }
+  info->dense_amp_traffic = traffic;
   for (int i = 0; i < 2; ++i)
     info->tuned_ns_per_shot[i] = p->tune[i].tuned ? p->tune[i].best_ms_per_shot * 1e6f : 0.0f;
   return SYMFT_OK;
