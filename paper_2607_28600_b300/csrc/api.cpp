@@ -362,12 +362,13 @@ int prepare(symft_plan* P, const symft_sample_args* a, uint64_t* meas, uint64_t*
       o->dense_grid = static_cast<int>(std::max<uint64_t>(1, std::min(want, cap)));
     } else if (vec_bytes + m3bytes <= 48 * 1024) {
       o->dense_kind = 2;   // warp per shot, vector in shared memory
+      const size_t bk = dense_warp_smem_bytes(P->dp, 1, 0, false);
       int wpb = t.dense_wpb ? t.dense_wpb
-                            : static_cast<int>(std::min<size_t>(8, std::max<size_t>(1, (160 * 1024) / (vec_bytes + m3bytes + 16))));
-      while (wpb > 1 && ((wpb * m3bytes + 15) & ~size_t(15)) + wpb * vec_bytes > 200 * 1024) --wpb;
+                            : static_cast<int>(std::min<size_t>(8, std::max<size_t>(1, (160 * 1024) / (vec_bytes + bk + 16))));
+      while (wpb > 1 && dense_warp_smem_bytes(P->dp, wpb, vec_bytes, true) > 200 * 1024) --wpb;
       o->dense_wpb = wpb;
       o->dense_use_smem = 1;
-      o->dense_smem = ((wpb * m3bytes + 15) & ~size_t(15)) + wpb * vec_bytes;
+      o->dense_smem = dense_warp_smem_bytes(P->dp, wpb, vec_bytes, true);
       const uint64_t want = (a->shots + wpb - 1) / wpb;
       const uint64_t cap = static_cast<uint64_t>(P->sm_count) * t.dense_grid_mult * 2;
       o->dense_grid = static_cast<int>(std::max<uint64_t>(1, std::min(want, cap)));

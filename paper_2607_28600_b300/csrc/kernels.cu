@@ -168,11 +168,14 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
   const int wpb = blockDim.x >> 5;
   const uint32_t S = 1u << A.kmax;
   const uint32_t m3w = (A.p.n_m3 + 31) / 32;
-  uint32_t* m3bits = reinterpret_cast<uint32_t*>(dsm) + (size_t)wib * m3w;
+  const uint32_t G = A.p.n_dense;
+  const uint32_t bkw = m3w + (G + 31) / 32;     // per-warp words: m3 bits, then sign bits
+  uint32_t* m3bits = reinterpret_cast<uint32_t*>(dsm) + (size_t)wib * bkw;
+  uint32_t* sgn = m3bits + m3w;
   Cplx<Real>* vec;
   const uint64_t warp_global = (uint64_t)blockIdx.x * wpb + wib;
   if (A.use_smem) {
-    size_t off = ((size_t)wpb * m3w * 4 + 15) & ~(size_t)15;
+    size_t off = ((size_t)wpb * bkw * 4 + 15) & ~(size_t)15;
     vec = reinterpret_cast<Cplx<Real>*>(dsm + off) + (size_t)wib * S;
   } else {
     vec = reinterpret_cast<Cplx<Real>*>(A.gvec) + warp_global * A.gvec_stride;
@@ -183,6 +186,15 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
     const uint64_t w = r >> 6;
     const uint64_t bitmask = 1ull << (r & 63);
     for (uint32_t i = lane; i < m3w; i += 32) m3bits[i] = 0u;
+    // the shot's exogenous sign bits, 32 instructions per ballot, fetched
+    // together before the instruction loop
+    for (uint32_t base = 0; base < G; base += 32) {
+      const uint32_t g = base + lane;
+      bool bit = false;
+      if (g < G) bit = (__ldg(A.signs + (uint64_t)A.p.dense[g].sign_target_col * A.W + w) & bitmask) != 0;
+      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+      if (lane == 0) sgn[base >> 5] = bal;
+    }
     ShotUniforms su;
     if (lane == 0) {
       vec[0].re = (Real)1;
@@ -190,18 +202,14 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
     }
     __syncwarp();
     uint32_t k = 0;
-    for (uint32_t g = 0; g < A.p.n_dense; ++g) {
+    for (uint32_t g = 0; g < G; ++g) {
       const DenseInstrDev I = A.p.dense[g];
       // sign: exogenous bit xor causal residual over m3 bits of this shot
-      uint32_t lam = 0;
-      if (lane == 0) {
-        lam = (uint32_t)((__ldg(A.signs + (uint64_t)I.sign_target_col * A.W + w) & bitmask) != 0);
-        for (uint32_t q = 0; q < I.causal_n; ++q) {
-          uint32_t j = __ldg(A.p.dense_causal + I.causal_off + q);
-          lam ^= (m3bits[j >> 5] >> (j & 31)) & 1u;
-        }
+      uint32_t lam = (sgn[g >> 5] >> (g & 31)) & 1u;
+      for (uint32_t q = 0; q < I.causal_n; ++q) {
+        const uint32_t j = __ldg(A.p.dense_causal + I.causal_off + q);
+        lam ^= (m3bits[j >> 5] >> (j & 31)) & 1u;
       }
-      lam = __shfl_sync(0xffffffffu, lam, 0);
       const Real sg = lam ? (Real)-1 : (Real)1;
       const Real c = (Real)I.c, s = (Real)I.s;
       const uint32_t n = 1u << k;
@@ -1129,6 +1137,11 @@ cudaError_t launch_dense_cta(const DenseArgs& a, bool fp64, int grid, size_t sme
   if (fp64) dense_cta_kernel<double><<<grid, kCtaThreads, smem, st>>>(a);
   else dense_cta_kernel<float><<<grid, kCtaThreads, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+size_t dense_warp_smem_bytes(const DevPlan& p, int wpb, size_t vec_bytes, bool vec_in_smem) {
+  const size_t bk = ((size_t)(p.n_m3 + 31) / 32 + (p.n_dense + 31) / 32) * 4;   // per warp
+  return (((size_t)wpb * bk + 15) & ~(size_t)15) + (vec_in_smem ? (size_t)wpb * vec_bytes : 0);
 }
 
 size_t dense_reg_smem_bytes(const DevPlan& p) {

@@ -188,10 +188,10 @@ extern "C" int symft_sample_noalloc(const symft_plan* plan, uint64_t shots, uint
     uint64_t cap = static_cast<uint64_t>(sms) * (dense_smem ? 16 : 8);
     if (dense_smem) {
       d.use_smem = 1;
-      smem = ((dense_wpb * m3bytes + 15) & ~size_t(15)) + dense_wpb * vec_bytes;
+      smem = dense_warp_smem_bytes(dp, dense_wpb, vec_bytes, true);
     } else {
       d.use_smem = 0;
-      smem = dense_wpb * m3bytes + 16;
+      smem = dense_warp_smem_bytes(dp, dense_wpb, vec_bytes, false);
       cap = std::min<uint64_t>(cap, std::max<uint64_t>(1, dense_grid_cap));
       d.gvec = base + o_vec;
       d.gvec_stride = static_cast<uint64_t>(1) << h.k_max;
