@@ -125,6 +125,32 @@ void build_blob(symft_plan* P) {
   P->off.tco = push(blob, h.tgt_causal_off);
   P->off.tca = push(blob, h.tgt_causal);
   P->off.sc = push(blob, h.slot_const);
+  // slot -> constant and random-measurement sources (inverse of the m1 lists)
+  {
+    std::vector<std::vector<uint32_t>> src(h.n_slots);
+    for (size_t j = 0; j < h.m1_t.size(); ++j)
+      for (uint32_t q = h.m1_off[j]; q < h.m1_off[j + 1]; ++q) src[h.m1_tgt[q]].push_back(static_cast<uint32_t>(j));
+    std::vector<uint4> sm1(std::max<size_t>(1, h.n_slots));
+    std::vector<uint32_t> ovf;
+    for (uint32_t i = 0; i < h.n_slots; ++i) {
+      const uint32_t cbit = h.slot_const[i] ? 0x8000u : 0u;
+      const auto& v = src[i];
+      bool inl = v.size() <= 7;
+      for (uint32_t j : v) inl = inl && j < 65536;
+      uint16_t f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      if (inl) {
+        f[0] = static_cast<uint16_t>(v.size() | cbit);
+        for (size_t q = 0; q < v.size(); ++q) f[1 + q] = static_cast<uint16_t>(v[q]);
+        std::memcpy(&sm1[i], f, 16);
+      } else {
+        sm1[i] = make_uint4(0x7FFFu | cbit, static_cast<uint32_t>(ovf.size()), static_cast<uint32_t>(v.size()), 0u);
+        ovf.insert(ovf.end(), v.begin(), v.end());
+      }
+    }
+    if (ovf.empty()) ovf.push_back(0);
+    P->off.sm1 = push(blob, sm1);
+    P->off.sm1o = push(blob, ovf);
+  }
   // level items: record and up to four parents, 16 bits each
   std::vector<uint4> lvl_item(std::max<size_t>(1, h.lvl_rec.size()));
   for (size_t x = 0; x < h.lvl_rec.size(); ++x) {
@@ -189,6 +215,8 @@ void bind_plan(const symft_plan* P, unsigned char* base, DevPlan* dptr) {
   d.tgt_sign0 = h.tgt_sign0;
   d.n_slots = h.n_slots;
   d.slot_const = reinterpret_cast<const uint8_t*>(at(P->off.sc));
+  d.slot_m1 = reinterpret_cast<const uint4*>(at(P->off.sm1));
+  d.slot_m1_ovf = reinterpret_cast<const uint32_t*>(at(P->off.sm1o));
   d.n_levels = h.lvl_off.empty() ? 0 : static_cast<uint32_t>(h.lvl_off.size() - 1);
   d.lvl_item = reinterpret_cast<const uint4*>(at(P->off.li));
   d.m3_t = reinterpret_cast<const uint32_t*>(at(P->off.m3t));

@@ -73,6 +73,11 @@ struct DevPlan {
   // sign-kernel slots [records][dense signs]
   uint32_t n_slots;
   const uint8_t* slot_const;
+  // per slot: its constant and its random-measurement sources, 16 bytes as
+  // eight 16-bit fields: f0 = n | const << 15 with n <= 7 and f1..f(n) = m1
+  // indices, or n = 0x7FFF and (y, z) = (offset, count) of a list in slot_m1_ovf
+  const uint4* slot_m1;
+  const uint32_t* slot_m1_ovf;
   // records with parents in level order, one 16-byte item each: x = record |
   // (parents << 16), y = p0 | p1 << 16, z = p2 | p3 << 16
   uint32_t n_levels;

@@ -101,25 +101,59 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
     const uint32_t gblk = (uint32_t)(A.block0 + blk);      // global noise block
     const uint64_t sub0 = blk * kSub;                       // local 128-shot sub-block
     const uint32_t nsub = (uint32_t)min((uint64_t)kSub, (A.shots + 127) / 128 - sub0);
-    // 1. constants
-    for (uint32_t i = threadIdx.x; i < NT * kSub; i += blockDim.x) {
-      const uint32_t v = A.p.slot_const[i / kSub] ? ~0u : 0u;
-      slots[i] = make_uint4(v, v, v, v);
-    }
-    __syncthreads();
-    // 2. random-measurement bits m1: one Philox block = the 128 bits of a
-    //    sub-block (64-shot words 2s and 2s+1 of global sub-block s)
-    for (uint32_t it = threadIdx.x; it < nsub * A.p.n_m1; it += blockDim.x) {
-      const uint32_t b = it / A.p.n_m1, j = it - b * A.p.n_m1;
-      const uint64_t gs = (uint64_t)gblk * kSub + b;
-      const uint4 o = philox(make_uint4(__ldg(A.p.m1_t + j), (uint32_t)gs, (uint32_t)(gs >> 32), kTagMbit), A.keys);
-      const uint32_t e = __ldg(A.p.m1_off + j + 1);
-      for (uint32_t q = __ldg(A.p.m1_off + j); q < e; ++q) {
-        uint32_t* t = reinterpret_cast<uint32_t*>(slots + (size_t)__ldg(A.p.m1_tgt + q) * kSub + b);
-        atomicXor(t + 0, o.x);
-        atomicXor(t + 1, o.y);
-        atomicXor(t + 2, o.z);
-        atomicXor(t + 3, o.w);
+    // 1+2. constants and random-measurement bits m1: one Philox block = the
+    //    128 bits of a sub-block (64-shot words 2s and 2s+1 of global
+    //    sub-block s).  With few m1 symbols their words are staged in the
+    //    (still unused) queue area and every slot gathers its own sources;
+    //    otherwise the words are scattered into the slots with atomics.
+    if ((size_t)A.p.n_m1 * kSub * 16 <= (size_t)kSignWarps * kQueue * 16) {
+      uint4* mw = reinterpret_cast<uint4*>(smem_raw + Lay.qa_off);    // [n_m1][kSub]
+      for (uint32_t it = threadIdx.x; it < nsub * A.p.n_m1; it += blockDim.x) {
+        const uint32_t b = it / A.p.n_m1, j = it - b * A.p.n_m1;
+        const uint64_t gs = (uint64_t)gblk * kSub + b;
+        mw[j * kSub + b] = philox(make_uint4(__ldg(A.p.m1_t + j), (uint32_t)gs, (uint32_t)(gs >> 32), kTagMbit), A.keys);
+      }
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < NT * kSub; i += blockDim.x) {
+        const uint32_t b = i % kSub;
+        const uint4 e = __ldg(A.p.slot_m1 + i / kSub);
+        const uint32_t c = (e.x & 0x8000u) ? ~0u : 0u;
+        uint4 v = make_uint4(c, c, c, c);
+        const uint32_t n = e.x & 0x7FFFu;
+        if (b < nsub) {
+          if (n == 0x7FFFu) {
+            for (uint32_t q = e.y; q < e.y + e.z; ++q) v = xor4(v, mw[__ldg(A.p.slot_m1_ovf + q) * kSub + b]);
+          } else {
+            const uint32_t f[7] = {e.x >> 16, e.y & 0xFFFFu, e.y >> 16, e.z & 0xFFFFu, e.z >> 16,
+                                   e.w & 0xFFFFu, e.w >> 16};
+#pragma unroll
+            for (uint32_t k = 0; k < 7; ++k) {
+              if (k >= n) break;
+              v = xor4(v, mw[f[k] * kSub + b]);
+            }
+          }
+        }
+        slots[i] = v;
+      }
+      __syncthreads();
+    } else {
+      for (uint32_t i = threadIdx.x; i < NT * kSub; i += blockDim.x) {
+        const uint32_t v = A.p.slot_const[i / kSub] ? ~0u : 0u;
+        slots[i] = make_uint4(v, v, v, v);
+      }
+      __syncthreads();
+      for (uint32_t it = threadIdx.x; it < nsub * A.p.n_m1; it += blockDim.x) {
+        const uint32_t b = it / A.p.n_m1, j = it - b * A.p.n_m1;
+        const uint64_t gs = (uint64_t)gblk * kSub + b;
+        const uint4 o = philox(make_uint4(__ldg(A.p.m1_t + j), (uint32_t)gs, (uint32_t)(gs >> 32), kTagMbit), A.keys);
+        const uint32_t e = __ldg(A.p.m1_off + j + 1);
+        for (uint32_t q = __ldg(A.p.m1_off + j); q < e; ++q) {
+          uint32_t* t = reinterpret_cast<uint32_t*>(slots + (size_t)__ldg(A.p.m1_tgt + q) * kSub + b);
+          atomicXor(t + 0, o.x);
+          atomicXor(t + 1, o.y);
+          atomicXor(t + 2, o.z);
+          atomicXor(t + 3, o.w);
+        }
       }
     }
     // 3. noise.  Phase A: each lane draws the head uniforms of four channels
