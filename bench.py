@@ -37,8 +37,8 @@ HEADLINE = "surface_d7_r7"
 # (dram__bytes_read.sum + dram__bytes_write.sum).  Valid only for the kernel
 # source it was taken on (sign.cu and the headers it includes): reported as
 # null once any of them changes.
-SIGN_TRAFFIC = {"source_sha256": "9af6f08a4adc2faa78df25e6c3c1e16ccce805d7887a2e05144fee723de8a351",
-                "bytes_per_launch": 21191424 + 865432576}
+SIGN_TRAFFIC = {"source_sha256": "f7f062978446cd24cf457722b0b2568bad65c8edd5e190a065808e136e62006a",
+                "bytes_per_launch": 20266496 + 863651584}
 SIGN_SOURCES = ("sign.cu", "device.cuh", "plan_dev.hpp")
 
 
