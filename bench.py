@@ -37,8 +37,8 @@ HEADLINE = "surface_d7_r7"
 # (dram__bytes_read.sum + dram__bytes_write.sum).  Valid only for the kernel
 # source it was taken on (sign.cu and the headers it includes): reported as
 # null once any of them changes.
-SIGN_TRAFFIC = {"source_sha256": "f7f062978446cd24cf457722b0b2568bad65c8edd5e190a065808e136e62006a",
-                "bytes_per_launch": 20266496 + 863651584}
+SIGN_TRAFFIC = {"source_sha256": "5255b56e3dbe84d0c353084e05032e7357a9a3b7b6c185dbf620c3bfaddce1cf",
+                "bytes_per_launch": 20831232 + 863956224}
 SIGN_SOURCES = ("sign.cu", "device.cuh", "plan_dev.hpp")
 
 

@@ -87,6 +87,23 @@ void build_blob(symft_plan* P) {
     o.causal_off = d.causal_off;
     o.causal_n = d.causal_n;
     o.t = d.t;
+    o.post_grp = kNoGroup;
+    o.pad = 0;
+  }
+  // early exit only where it can pay: after an active measurement whose
+  // detector group is not empty and with at least kEarlyExitWork amplitudes
+  // of dense work still to come (below that the check costs more than it saves)
+  {
+    constexpr uint64_t kEarlyExitWork = 1024;
+    std::vector<uint64_t> rest(dn.size() + 1, 0);
+    for (size_t g = dn.size(); g-- > 0;) rest[g] = rest[g + 1] + (1ull << dn[g].k);
+    const bool ps = h.postselect && !h.post_chk.empty();
+    for (size_t g = 0; g < dn.size(); ++g) {
+      if (!ps || (dn[g].kind != I_ACTIVE_DIAG_MEAS && dn[g].kind != I_ACTIVE_PAIR_MEAS)) continue;
+      const uint32_t q = static_cast<uint32_t>(dn[g].m3) + 1;
+      if (h.post_chk_off[q + 1] > h.post_chk_off[q] && rest[g + 1] >= kEarlyExitWork) dn[g].post_grp = q;
+    }
+    P->post_grp0 = (ps && h.post_chk_off[1] > h.post_chk_off[0] && rest[0] >= kEarlyExitWork) ? 0u : kNoGroup;
   }
   P->dense_host = dn;
   std::vector<unsigned char>& blob = P->blob;
@@ -180,6 +197,8 @@ void build_blob(symft_plan* P) {
   }
   if (gat_ovf.empty()) gat_ovf.push_back(0);
   P->off.m3t = push(blob, h.m3_t);
+  P->off.pco = push(blob, h.post_chk_off);
+  P->off.pch = push(blob, h.post_chk);
   P->off.li = push(blob, lvl_item);
   P->off.gi = push(blob, gat_item);
   P->off.gv = push(blob, gat_ovf);
@@ -220,6 +239,10 @@ void bind_plan(const symft_plan* P, unsigned char* base, DevPlan* dptr) {
   d.n_levels = h.lvl_off.empty() ? 0 : static_cast<uint32_t>(h.lvl_off.size() - 1);
   d.lvl_item = reinterpret_cast<const uint4*>(at(P->off.li));
   d.m3_t = reinterpret_cast<const uint32_t*>(at(P->off.m3t));
+  const bool early = h.postselect && !h.post_chk.empty();
+  d.post_chk_off = early ? reinterpret_cast<const uint32_t*>(at(P->off.pco)) : nullptr;
+  d.post_chk = early ? reinterpret_cast<const uint32_t*>(at(P->off.pch)) : nullptr;
+  d.post_grp0 = P->post_grp0;
   d.gat_item = reinterpret_cast<const uint4*>(at(P->off.gi));
   d.gat_ovf = reinterpret_cast<const uint32_t*>(at(P->off.gv));
   d.tgt_causal_off = reinterpret_cast<const uint32_t*>(at(P->off.tco));
@@ -297,6 +320,7 @@ struct Prep {
   double* wide_scale = nullptr;
   float* wide_scalef = nullptr;
   uint8_t* wide_lab = nullptr;
+  uint8_t* wide_alive = nullptr;
 };
 
 int validate(const symft_sample_args* a) {
@@ -420,7 +444,8 @@ int prepare(symft_plan* P, const symft_sample_args* a, uint64_t* meas, uint64_t*
       const size_t off_scale = off_sums + nb * 16;
       const size_t off_scalef = off_scale + nb * 8;
       const size_t off_lab = off_scalef + nb * 4;
-      const size_t total = off_lab + nb;
+      const size_t off_alive = off_lab + nb;
+      const size_t total = off_alive + nb;
       CUDA_TRY(P->wide.ensure(total));
       unsigned char* base = static_cast<unsigned char*>(P->wide.ptr);
       o->wide_vec[0] = base;
@@ -431,6 +456,7 @@ int prepare(symft_plan* P, const symft_sample_args* a, uint64_t* meas, uint64_t*
       o->wide_scale = reinterpret_cast<double*>(base + off_scale);
       o->wide_scalef = reinterpret_cast<float*>(base + off_scalef);
       o->wide_lab = base + off_lab;
+      o->wide_alive = base + off_alive;
       o->gvec_stride = static_cast<uint64_t>(1) << h.k_max;
     }
   }
@@ -514,6 +540,9 @@ int enqueue(symft_plan* P, const symft_sample_args* a, const Prep& o, cudaStream
     d.gvec = o.gvec;
     d.gvec_stride = o.gvec_stride;
     d.prob = o.prob;
+    // early exit under postselection reads the detector columns the sign
+    // kernel has just written
+    d.det_exo = P->dp.post_chk_off ? o.det : nullptr;
     if (o.dense_kind == 4) {
       WideArgs wa{};
       wa.p = P->dp;
@@ -531,6 +560,8 @@ int enqueue(symft_plan* P, const symft_sample_args* a, const Prep& o, cudaStream
       wa.sums = o.wide_sums;
       wa.scale = o.wide_scale;
       wa.scalef = o.wide_scalef;
+      wa.det_exo = d.det_exo;
+      wa.alive = o.wide_alive;
       wa.lab = o.wide_lab;
       for (uint64_t s0 = 0; s0 < a->shots; s0 += o.wide_nb) {
         wa.shot0 = a->shot_offset + s0;

@@ -941,6 +941,24 @@ void Compiler::lower(HostPlan& P) {
       P.post_events.push_back(-1 - static_cast<int32_t>(2 * op.index + post[op.index]));
     }
   }
+  // early exit: postselected detectors grouped by the number of active
+  // measurements that precede them in circuit order.  Once the dense
+  // executor has decided active measurement j, every record and detector up
+  // to the detectors of group j + 1 is final, so a shot whose first fired
+  // postselected detector lies there needs no further dense work.
+  P.post_chk_off.assign(P.n_m3 + 2, 0);
+  if (P.postselect && P.n_m3 > 0) {
+    std::vector<std::vector<uint32_t>> grp(P.n_m3 + 1);
+    uint32_t seen = 0;
+    for (const Op& op : c_.ops) {
+      if (op.kind == OP_MEAS && cls[op.t] == 3) ++seen;
+      else if (op.kind == OP_DET && post[op.index]) grp[seen].push_back(op.index);
+    }
+    for (uint32_t q = 0; q <= P.n_m3; ++q) {
+      P.post_chk.insert(P.post_chk.end(), grp[q].begin(), grp[q].end());
+      P.post_chk_off[q + 1] = static_cast<uint32_t>(P.post_chk.size());
+    }
+  }
 }
 
 }  // namespace

@@ -46,4 +46,27 @@ __device__ __forceinline__ uint4 philox(uint4 c, const PhiloxKeys& K) {
   return c;
 }
 
+// Early exit under postselection (Sec. 6, detector postselection): whether a
+// postselected detector of group q fires for request-local shot r.  Group q
+// holds the postselected detectors that follow exactly q active measurements
+// in circuit order, in annotation order; their values are the sign kernel's
+// exogenous columns XOR the shot's active outcomes (bit j of m3bits), all of
+// which are decided once active measurement q - 1 is.
+__device__ __forceinline__ bool group_rejects(const DevPlan& p, const uint64_t* det_exo, uint64_t W, uint64_t r,
+                                              uint32_t q, const uint32_t* m3bits) {
+  const uint32_t e1 = __ldg(p.post_chk_off + q + 1);
+  for (uint32_t e = __ldg(p.post_chk_off + q); e < e1; ++e) {
+    const uint32_t d = __ldg(p.post_chk + e);
+    uint32_t v = (uint32_t)((__ldg(det_exo + (uint64_t)d * W + (r >> 6)) >> (r & 63)) & 1ull);
+    const uint32_t i = p.tgt_det0 + d;
+    const uint32_t ce = __ldg(p.tgt_causal_off + i + 1);
+    for (uint32_t c = __ldg(p.tgt_causal_off + i); c < ce; ++c) {
+      const uint32_t j = __ldg(p.tgt_causal + c);
+      v ^= (m3bits[j >> 5] >> (j & 31)) & 1u;
+    }
+    if (v) return true;
+  }
+  return false;
+}
+
 }  // namespace symft

@@ -144,6 +144,9 @@ struct HostPlan {
   // postselection order: events in circuit order, record r (>= 0) or
   // detector i (-1 - (2 i + p), p = 1 when detector i is postselected)
   std::vector<int32_t> post_events;
+  // postselected detectors grouped by the active measurements before them:
+  // group q (q = 0 .. n_m3) = post_chk[post_chk_off[q] .. post_chk_off[q+1])
+  std::vector<uint32_t> post_chk_off, post_chk;
 
   // dense executor
   std::vector<DenseInstr> dense;

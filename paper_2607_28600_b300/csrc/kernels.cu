@@ -201,6 +201,10 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
       vec[0].im = (Real)0;
     }
     __syncwarp();
+    // a shot rejected before any active measurement needs no dense work
+    const bool dead0 = A.det_exo && A.p.post_grp0 == 0 && group_rejects(A.p, A.det_exo, A.W, r, 0, m3bits);
+    __syncwarp();
+    if (dead0) continue;
     uint32_t k = 0;
     for (uint32_t g = 0; g < G; ++g) {
       const DenseInstrDev I = A.p.dense[g];
@@ -354,6 +358,11 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
           break;
       }
       __syncwarp();
+      if (A.det_exo && I.post_grp != kNoGroup) {           // early exit once rejected
+        const bool dead = group_rejects(A.p, A.det_exo, A.W, r, I.post_grp, m3bits);
+        __syncwarp();
+        if (dead) break;
+      }
     }
   }
 }
@@ -400,6 +409,10 @@ __global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) 
     }
     for (uint32_t i = lane; i < m3w; i += 32) m3b[i] = 0u;
     __syncwarp();
+    // a shot rejected before any active measurement needs no dense work
+    const bool dead0 = A.det_exo && A.p.post_grp0 == 0 && group_rejects(A.p, A.det_exo, A.W, r, 0, m3b);
+    __syncwarp();
+    if (dead0) continue;
     ShotUniforms su;
     Real re = lane == 0 ? (Real)1 : (Real)0, im = (Real)0;
     uint32_t k = 0;
@@ -517,6 +530,11 @@ __global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) 
                    1ull << bitpos);
         }
         __syncwarp();
+        if (A.det_exo && I.post_grp != kNoGroup) {   // early exit once rejected
+          const bool dead = group_rejects(A.p, A.det_exo, A.W, r, I.post_grp, m3b);
+          __syncwarp();
+          if (dead) break;
+        }
       }
     }
     __syncwarp();
@@ -552,6 +570,10 @@ __global__ void __launch_bounds__(kCtaThreads) dense_cta_kernel(DenseArgs A) {
       vec[0].im = (Real)0;
     }
     __syncthreads();
+    // a shot rejected before any active measurement needs no dense work
+    const bool dead0 = A.det_exo && A.p.post_grp0 == 0 && group_rejects(A.p, A.det_exo, A.W, r, 0, m3b);
+    __syncthreads();
+    if (dead0) continue;
     uint32_t k = 0;
     for (uint32_t g = 0; g < G; ++g) {
       const DenseInstrDev I = A.p.dense[g];
@@ -690,6 +712,11 @@ __global__ void __launch_bounds__(kCtaThreads) dense_cta_kernel(DenseArgs A) {
           __syncthreads();
         }
         --k;
+        if (A.det_exo && I.post_grp != kNoGroup) {   // early exit once rejected
+          const bool dead = group_rejects(A.p, A.det_exo, A.W, r, I.post_grp, m3b);
+          __syncthreads();
+          if (dead) break;
+        }
       }
       __syncthreads();
     }

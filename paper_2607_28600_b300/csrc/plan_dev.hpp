@@ -50,7 +50,12 @@ struct DenseInstrDev {
   uint32_t sign_target_col;   // column of the exogenous sign in the scratch
   uint32_t causal_off, causal_n;
   uint32_t t;
+  uint32_t post_grp;          // active measurement: detector group to check for early
+                              // exit after it, or kNoGroup
+  uint32_t pad;
 };
+
+constexpr uint32_t kNoGroup = 0xFFFFFFFFu;
 
 struct DevPlan {
   uint32_t n_channels;
@@ -90,6 +95,12 @@ struct DevPlan {
   // -1 - (2 i + p) with p = 1 when detector i is postselected
   uint32_t n_post_events;
   const int32_t* post_events;
+  // early exit of the dense executors: postselected detectors grouped by the
+  // number of active measurements before them (n_m3 + 2 offsets; group q is
+  // final once active measurement q - 1 is decided); null without postselection
+  const uint32_t* post_chk_off;
+  const uint32_t* post_chk;
+  uint32_t post_grp0;           // 0: check group 0 before a shot's dense work; else kNoGroup
   uint32_t n_dense;
   const DenseInstrDev* dense;
   const uint32_t* dense_causal;
@@ -155,6 +166,8 @@ struct DenseArgs {
   int use_smem;
   int* status;
   double* prob;           // Pr(m = 0) per active measurement and shot (n_m3 x shots) or null
+  const uint64_t* det_exo;   // detector columns from the sign kernel (exogenous parts), or
+                             // null: no early exit
 };
 
 // One batch of the wide (instruction-major) dense executor.
@@ -178,6 +191,8 @@ struct WideArgs {
   double* scale;          // [nb] renormalisation after the current measurement
   float* scalef;          // [nb] the same, rounded to FP32 (FP32 vectors)
   uint8_t* lab;           // [nb] kept branch label
+  const uint64_t* det_exo;   // as in DenseArgs (early exit), or null
+  uint8_t* alive;         // [nb] 0 once the shot is rejected by postselection
 };
 
 struct PlainArgs {

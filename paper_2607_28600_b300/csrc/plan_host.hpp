@@ -33,7 +33,7 @@ struct DevBuf {
 
 // Byte offsets of the plan arrays inside the device blob.
 struct BlobOffsets {
-  size_t ch, q, ct, t4, qi, m1t, m1o, m1g, tco, tca, sc, li, gi, gv, pe, dn, dc, m3t, sm1, sm1o;
+  size_t ch, q, ct, t4, qi, m1t, m1o, m1g, tco, tca, sc, li, gi, gv, pe, dn, dc, m3t, sm1, sm1o, pco, pch;
   size_t plc, plo, pls;
   size_t clt, clo;
 };
@@ -81,6 +81,7 @@ struct symft_plan {
   symft::DevPlan dp{};
   symft::DevBuf signs, m3, det_scratch, gvec, status, wide;
   std::vector<symft::DenseInstrDev> dense_host;   // host copy of the instruction stream
+  uint32_t post_grp0 = 0xFFFFFFFFu;                // early-exit check before any dense work
   symft::DevBuf obs_scratch, disc_scratch;      // tallies without obs / discard outputs
   symft::DevBuf h_meas, h_det, h_obs, h_disc;   // staging for host outputs
   symft::DevBuf h_prob, h_counts;

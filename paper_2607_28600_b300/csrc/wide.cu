@@ -82,6 +82,9 @@ __global__ void wide_init_kernel(WideArgs A) {
   A.sums[2 * b] = 0.0;
   A.sums[2 * b + 1] = 0.0;
   wide_signs_from(A, b, 0);
+  // early exit: a shot rejected before any active measurement is skipped
+  A.alive[b] = (A.det_exo && A.p.post_grp0 == 0 &&
+                group_rejects(A.p, A.det_exo, A.W, A.r0 + b, 0, A.m3b + (size_t)b * m3w)) ? 0 : 1;
 }
 
 // PromoteRot / ActiveDiagRot / ActivePairRot of instruction g on every shot:
@@ -99,6 +102,7 @@ __global__ void __launch_bounds__(kWideThreads) wide_rot_kernel(WideArgs A, uint
   if (I.kind == 0) {                    // a'_x = c a_x, a'_{x+n} = -i sg s a_x
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += step) {
       const uint32_t b = (uint32_t)(i >> lg), x = (uint32_t)i & (n - 1);
+      if (!A.alive[b]) continue;
       Amp<Real>* v = vbase + (size_t)b * A.stride;
       const Real sgs = lamg[b] ? -s : s;
       Amp<Real> a = v[x], hi;
@@ -113,6 +117,7 @@ __global__ void __launch_bounds__(kWideThreads) wide_rot_kernel(WideArgs A, uint
     const Real mus = I.mu == 0 ? s : -s;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += step) {
       const uint32_t b = (uint32_t)(i >> lg), x = (uint32_t)i & (n - 1);
+      if (!A.alive[b]) continue;
       Amp<Real>* v = vbase + (size_t)b * A.stride;
       const Real f = (lamg[b] ? -mus : mus) * ((__popc(x & I.b) & 1) ? (Real)-1 : (Real)1);
       const Amp<Real> a = v[x];
@@ -133,6 +138,7 @@ __global__ void __launch_bounds__(kWideThreads) wide_rot_kernel(WideArgs A, uint
     const uint32_t half_mask = (n >> 1) - 1;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += step) {
       const uint32_t b = (uint32_t)(i >> lg), z = (uint32_t)i & half_mask;
+      if (!A.alive[b]) continue;
       Amp<Real>* v = vbase + (size_t)b * A.stride;
       const Real sgs = lamg[b] ? -s : s;
       const Real cr = cr0 * sgs, ci = ci0 * sgs;
@@ -189,12 +195,17 @@ __device__ void wide_decide_one(const WideArgs& A, uint32_t g, uint32_t b, doubl
              1ull << (r & 63));
   }
   wide_signs_from(A, b, g + 1);
+  // early exit once a postselected detector that is now final fires
+  if (A.det_exo && I.post_grp != kNoGroup) {
+    const uint32_t m3w = (A.p.n_m3 + 31) / 32;
+    if (group_rejects(A.p, A.det_exo, A.W, r, I.post_grp, A.m3b + (size_t)b * m3w)) A.alive[b] = 0;
+  }
 }
 
 template <typename Real>
 __global__ void wide_decide_kernel(WideArgs A, uint32_t g) {
   const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= A.nb) return;
+  if (b >= A.nb || !A.alive[b]) return;
   uint32_t lab;
   double scale;
   wide_decide_one<Real>(A, g, b, A.sums[2 * b], A.sums[2 * b + 1], lab, scale);
@@ -281,7 +292,7 @@ template <typename Real>
 __global__ void __launch_bounds__(kWideThreads) wide_meas_small_kernel(WideArgs A, uint32_t g) {
   const uint32_t b = blockIdx.x * (kWideThreads / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  if (b >= A.nb) return;                       // whole warps leave together
+  if (b >= A.nb || !A.alive[b]) return;        // whole warps leave together
   const DenseInstrDev I = A.p.dense[g];
   const Amp<Real>* v = reinterpret_cast<const Amp<Real>*>(A.vec[A.cur]) + (size_t)b * A.stride;
   Amp<Real>* o = reinterpret_cast<Amp<Real>*>(A.vec[A.cur ^ 1]) + (size_t)b * A.stride;
@@ -309,6 +320,7 @@ template <typename Real>
 __global__ void __launch_bounds__(kWideThreads) wide_sums_kernel(WideArgs A, uint32_t g) {
   __shared__ double red[2][kWideThreads / 32];
   const uint32_t b = blockIdx.y;
+  if (!A.alive[b]) return;                     // the whole block leaves
   const DenseInstrDev I = A.p.dense[g];
   const Amp<Real>* v = reinterpret_cast<const Amp<Real>*>(A.vec[A.cur]) + (size_t)b * A.stride;
   double S0 = 0.0, S1 = 0.0;
@@ -349,6 +361,7 @@ __global__ void __launch_bounds__(kWideThreads) wide_compact_kernel(WideArgs A, 
   Amp<Real>* ob = reinterpret_cast<Amp<Real>*>(A.vec[A.cur ^ 1]);
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += step) {
     const uint32_t b = (uint32_t)(i >> lg), z = (uint32_t)i & ((1u << lg) - 1u);
+    if (!A.alive[b]) continue;
     const Real sc = sizeof(Real) == 4 ? (Real)A.scalef[b] : (Real)A.scale[b];
     ob[(size_t)b * A.stride + z] = wide_kept<Real>(vb + (size_t)b * A.stride, I, z, A.lab[b], sc, mcr, mci);
   }

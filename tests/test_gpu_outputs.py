@@ -185,3 +185,41 @@ def test_batch_job_counts():
     torch.cuda.synchronize()
     want = _popcounts(ob.cpu().numpy().view(np.uint64), dc.cpu().numpy().view(np.uint64), shots)
     assert cs[0].cpu().tolist() == want and cs[1].cpu().tolist() == want
+
+
+def _mask_by_postselection(text, rec, det, obs):
+    """Apply the postselection rule (reject at the first fired detector in
+    annotation order; later records and detectors and all observables read 0)
+    to unpostselected outputs, from the circuit's event order."""
+    c = oparse(text)
+    rec, det, obs = rec.copy(), det.copy(), obs.copy()
+    shots = rec.shape[0]
+    disc = np.zeros(shots, dtype=np.uint8)
+    cut = np.zeros(shots, dtype=bool)
+    for op in c.ops:
+        if op.kind == "meas" and op.rec >= 0:
+            rec[cut, op.rec] = 0
+        elif op.kind == "det":
+            det[cut, op.index] = 0
+            cut |= det[:, op.index] == 1
+    obs[cut] = 0
+    disc[cut] = 1
+    return rec, det, obs, disc
+
+
+@pytest.mark.parametrize("which,precision", [("literal", 0), ("literal", 1), ("coherent", 1)])
+def test_early_exit_matches_masked_full_run(which, precision):
+    """Shots rejected by a postselected detector stop their dense work early;
+    every output still equals the full (unpostselected) run with the
+    postselection rule applied afterwards."""
+    from paper_2607_28600_b300.workloads import coherent_surface_code_memory, distillation_15_to_1
+    text = (distillation_15_to_1(1e-3, "literal") if which == "literal"
+            else coherent_surface_code_memory(5, 1, 1e-3, 0.02))
+    shots = 3000 if which == "literal" else 1000
+    _, m0, d0, o0, _ = gpu_sample(text, shots, 13, precision=precision, postselect=0)
+    _, m1, d1, o1, x1 = gpu_sample(text, shots, 13, precision=precision, postselect=1)
+    want = _mask_by_postselection(text, unpack(m0, shots), unpack(d0, shots), unpack(o0, shots))
+    got = (unpack(m1, shots), unpack(d1, shots), unpack(o1, shots), unpack(x1.reshape(1, -1), shots)[:, 0])
+    for w, g, name in zip(want, got, ("records", "dets", "obs", "discard")):
+        np.testing.assert_array_equal(g, w, err_msg=name)
+    assert 0.05 < got[3].mean() < 0.99
