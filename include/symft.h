@@ -127,7 +127,10 @@ typedef struct {
                               the executor computed it (Sec. 4, Eqs. of
                               ActiveDiagMeas / ActivePairMeas), rounded from
                               FP32 when precision = FP32; for checking branch
-                              probabilities against an FP64 reference */
+                              probabilities against an FP64 reference.  Under
+                              postselection a rejected shot may stop its dense
+                              work early: entries of measurements it never
+                              reached are left unwritten */
   uint64_t* counts_out;    /* 2 + n_obs words: [0] kept shots, [1] discarded
                               shots, [2 + j] kept shots whose observable j is 1 */
 } symft_sample_args;
