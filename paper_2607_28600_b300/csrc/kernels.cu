@@ -879,9 +879,28 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs A) {
       vec[0].im = (Real)0;
     }
     __syncthreads();
-    // 4. dense instructions on the shot's vector
+    // early exit (this design ends a rejected shot at once): whether a
+    // postselected detector of group q fires, from the shot's unpacked
+    // exogenous detector values and its active outcomes so far
+    auto plain_rejects = [&](uint32_t q) -> bool {
+      if (!P.post_chk_off) return false;
+      const uint32_t e1 = __ldg(P.post_chk_off + q + 1);
+      for (uint32_t e = __ldg(P.post_chk_off + q); e < e1; ++e) {
+        const uint32_t i = R + __ldg(P.post_chk + e);     // the detector's output index
+        uint32_t v = val[i];
+        const uint32_t ce = __ldg(P.tgt_causal_off + i + 1);
+        for (uint32_t c = __ldg(P.tgt_causal_off + i); c < ce; ++c) {
+          const uint32_t j = __ldg(P.tgt_causal + c);
+          v ^= (m3b[j >> 5] >> (j & 31)) & 1u;
+        }
+        if (v) return true;
+      }
+      return false;
+    };
+    // 4. dense instructions on the shot's vector (skipped once rejected)
     uint32_t k = 0;
-    for (uint32_t g = 0; g < P.n_dense; ++g) {
+    const bool dead0 = plain_rejects(0);
+    for (uint32_t g = 0; g < P.n_dense && !dead0; ++g) {
       const DenseInstrDev I = P.dense[g];
       if (tid == 0) {
         uint32_t lam = val[NO + g];
@@ -1012,6 +1031,9 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs A) {
           __syncthreads();
         }
         --k;
+        const bool dead = plain_rejects((uint32_t)I.m3 + 1);
+        __syncthreads();
+        if (dead) break;
       }
       __syncthreads();
     }
