@@ -227,8 +227,10 @@ int symft_last_launch_count(void);
  * is an integration aid).  Some callers cannot let a library call cudaMalloc:
  * frameworks whose caching allocator owns the device heap, services with a
  * fixed memory budget, or code that samples while a stream is being captured.
- * This call runs the same kernels as symft_sample_ex on caller-owned DEVICE
- * outputs (same layout, same results), and takes every other byte it needs --
+ * This call runs the sampler's sign, warp-executor and finalize kernels on
+ * caller-owned DEVICE outputs (same layout and results as symft_sample_ex,
+ * up to the rare FP32 outcome flips the executors allow), and takes every
+ * other byte it needs --
  * the plan copy, dense-sign and active-outcome columns, the status word, any
  * global active vectors -- from one fixed 32 MiB __device__ array that the
  * library holds on every GPU that loads it until the process exits.

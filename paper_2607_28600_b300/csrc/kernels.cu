@@ -3,7 +3,7 @@
 //
 //  dense_reg_kernel  k_max <= 5: one warp per shot, lane x holds amplitude x
 //  dense_kernel      one warp per shot, active vector in shared memory
-//  dense_cta_kernel  one CTA per shot, vector in shared memory or a global slot
+//  dense_cta_kernel  one CTA per shot, vector in shared memory
 //                    -- all three run PromoteRot, ActiveDiagRot, ActivePairRot,
 //                    ActiveDiagMeas and ActivePairMeas (Sec. 4) on the shot's
 //                    active vector, completing each sign with the causal
@@ -542,9 +542,11 @@ __global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) 
 }
 
 // ---------------------------------------------------------------------------
-// CTA-per-shot dense executor for large k: the whole CTA works on one shot's
-// vector, held in shared memory when it fits and otherwise in a per-CTA slot
-// of a global workspace small enough to stay in L2 (one slot per resident CTA).
+// CTA-per-shot dense executor for vectors up to ~200 KB: the whole CTA works
+// on one shot's vector in shared memory.  (The kernel can also keep the vector
+// in a per-CTA global slot when use_smem is 0; the library sends vectors that
+// exceed shared memory to the wide executor instead, so it launches this
+// kernel with use_smem = 1 only.)
 // ---------------------------------------------------------------------------
 constexpr int kCtaThreads = 256;
 

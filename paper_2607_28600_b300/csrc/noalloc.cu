@@ -3,8 +3,9 @@
 // Some hosts of this library own the whole device heap (a framework with its
 // own caching allocator, a memory-budgeted service, code running while a
 // stream is being captured) and cannot let a library call cudaMalloc.  This
-// entry point runs the same kernels as symft_sample_ex but takes every byte
-// of device memory it needs beyond the caller's outputs -- the copy of the
+// entry point runs the sign, warp-executor and finalize kernels of
+// symft_sample_ex but takes every byte of device memory it needs beyond the
+// caller's outputs -- the copy of the
 // plan, the dense-sign columns, the active-outcome columns, the status word
 // and any global active vectors -- from one fixed array in this file.
 //
