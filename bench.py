@@ -30,11 +30,13 @@ WORKLOADS = {
     "surface_d5_r5": dict(d=5, rounds=5, p=1e-3),
 }
 HEADLINE = "surface_d7_r7"
+METRIC = "shots/s per circuit on 1 B300 (FP32-batched vs FP64-plain), % of roofline"
+HEADLINE_WORKLOAD = ("pure-Clifford rotated surface-code Z memory d=7, 7 rounds, "
+                     "depolarizing p=1e-3, bit-packed sign path")
 
 
-# DRAM traffic of one sign-kernel launch on the headline workload, from the ncu
-# capture summarised in profiles/sign_kernel_surface_d7_r7.md
-# (dram__bytes_read.sum + dram__bytes_write.sum).  Valid only for the kernel
+# DRAM traffic of one sign-kernel launch on the headline workload, from an ncu
+# capture of dram__bytes_read.sum + dram__bytes_write.sum.  Valid only for the kernel
 # source it was taken on (sign.cu and the headers it includes): reported as
 # null once any of them changes.
 SIGN_TRAFFIC = {"source_sha256": "5255b56e3dbe84d0c353084e05032e7357a9a3b7b6c185dbf620c3bfaddce1cf",
@@ -78,7 +80,8 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), f"symft_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -193,13 +196,13 @@ def run_reference(args):
         pool.join()
     per = sum(times) / len(times)
     val = sum(shots) / sum(times)
-    w = WORKLOADS[HEADLINE]
     line = {
-        "impl": "reference", "metric": "shots/s per circuit", "value": val, "unit": "shots/s",
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "shots/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": HEADLINE, "shots_per_step": sum(shots) // len(shots), **w},
+        "config": {"workload": HEADLINE_WORKLOAD, "shots_per_step": sum(shots) // len(shots),
+                   "shots_per_word": 64, "parallelism": "host processes"},
         "cpu_baseline": {"value": val, "unit": "shots/s", "cores": cores, "kind": "oracle",
                          "sample": f"about 3 s per step of {HEADLINE} through the "
                                    f"Aaronson-Gottesman tableau oracle on {cores} host processes"},
@@ -577,7 +580,7 @@ def main():
     peak, peak_kind = _peaks()
     achieved = h["out_bytes"] / (h["kernel_ms"] / 1e3) / 1e9
     line = {
-        "metric": "shots/s per circuit on 1 B300 (FP32-batched vs FP64-plain), % of roofline",
+        "metric": METRIC,
         "value": world * shots / (h["ms_step"] / 1e3),
         "unit": "shots/s",
         "n_gpus": world,
@@ -589,8 +592,7 @@ def main():
         "vs_baseline": None,
         "dtype": "u64",
         "data": "synthetic",
-        "config": {"workload": "pure-Clifford rotated surface-code Z memory d=7, 7 rounds, "
-                               "depolarizing p=1e-3, bit-packed sign path",
+        "config": {"workload": HEADLINE_WORKLOAD,
                    "shots_per_step": shots, "shots_per_word": 64,
                    "l2": "outputs (%.0f MB per step) exceed the 126 MB L2; no flush needed"
                          % (h["out_bytes"] / 1e6),

@@ -225,8 +225,8 @@ int symft_last_launch_count(void);
 
 /* Sampling without any device allocation (the paper has no counterpart; this
  * is an integration aid).  Some callers cannot let a library call cudaMalloc:
- * frameworks whose caching allocator owns the device heap, services with a
- * fixed memory budget, or code that samples while a stream is being captured.
+ * frameworks whose caching allocator owns the device heap, or services with a
+ * fixed memory budget.
  * This call runs the sampler's sign, warp-executor and finalize kernels on
  * caller-owned DEVICE outputs (same layout and results as symft_sample_ex,
  * up to the rare FP32 outcome flips the executors allow), and takes every
@@ -239,8 +239,10 @@ int symft_last_launch_count(void);
  *     32 MiB returns SYMFT_E_CAPACITY before any GPU work; sample fewer shots
  *     per call.
  *   - Set-up: the first call made with a device current looks up the array's
- *     device address (cudaGetSymbolAddress); make that first call before any
- *     stream capture.
+ *     device address (cudaGetSymbolAddress) and the device's SM count.  Every
+ *     call copies the plan image from host memory into the array
+ *     (cudaMemcpyAsync on `cuda_stream`), so the plan must stay alive until
+ *     the call's work on the stream is done.
  *   - Sharing: all calls share the array and it keeps the last call's
  *     contents; the call clears what must start at zero.  Calls that overlap
  *     on the GPU (other streams, other threads) race on it: serialise them.

@@ -306,13 +306,17 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
             branch_sums<Real, float>(vec, I, n, lane, 32, mcr, mci, S0, S1);
             warp_sum2(S0, S1);
             const uint64_t U = su.get(A, (uint32_t)I.m3, rg, lane);
+            // the renormalisation scale 1 / sqrt(S_m) in FP64 (one FP64 op per
+            // measurement, on one lane), rounded once to the vector's precision
+            float sc = 0.0f;
             if (lane == 0) {
               const float p0 = (l0 ? S1 : S0) / (S0 + S1);
               m = decide32(U, p0);
               if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = (double)p0;
+              sc = (float)(1.0 / sqrt((double)((l0 ^ m) ? S1 : S0)));
             }
             m = __shfl_sync(0xffffffffu, m, 0);
-            scale = (Real)rsqrtf((l0 ^ m) ? S1 : S0);
+            scale = (Real)__shfl_sync(0xffffffffu, sc, 0);
           }
           const uint32_t lab = l0 ^ m;
           // in-place compaction in increasing z order (sources are never below z)
@@ -497,6 +501,9 @@ __global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) 
         const uint32_t l0 = I.kind == 5 ? (lam ^ (uint32_t)I.eta) : lam;
         uint32_t m = 0;
         const uint64_t U = su.get(A, (uint32_t)I.m3, rg, lane);
+        // decision and the renormalisation scale 1 / sqrt(S_m), in FP64, on one
+        // lane; the scale is rounded once to the vector's precision
+        Real sc = 0;
         if (lane == 0) {
           double pd;
           if (sizeof(Real) == 8) {
@@ -508,11 +515,11 @@ __global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) 
             pd = (double)pf;
           }
           if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = pd;
+          sc = (Real)(1.0 / sqrt((double)((l0 ^ m) ? s1 : s0)));
         }
         m = __shfl_sync(0xffffffffu, m, 0);
         const uint32_t lab = l0 ^ m;
-        const Real scale = sizeof(Real) == 8 ? (Real)(1.0 / sqrt((double)(lab ? s1 : s0)))
-                                             : (Real)rsqrtf((float)(lab ? s1 : s0));
+        const Real scale = shfl_r(sc, 0);
         if (I.kind == 5) {
           const uint32_t u = insert_bit(z & (half - 1 + (half == 0)), h, lab);
           const uint32_t x = u ^ ((uint32_t)(__popc(u & I.b & ~(1u << h)) & 1) << h);

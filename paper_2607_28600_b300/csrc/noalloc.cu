@@ -1,8 +1,8 @@
 // symft_sample_noalloc: sampling for callers that cannot allocate device memory.
 //
 // Some hosts of this library own the whole device heap (a framework with its
-// own caching allocator, a memory-budgeted service, code running while a
-// stream is being captured) and cannot let a library call cudaMalloc.  This
+// own caching allocator, a service with a fixed memory budget) and cannot let
+// a library call cudaMalloc.  This
 // entry point runs the sign, warp-executor and finalize kernels of
 // symft_sample_ex but takes every byte of device memory it needs beyond the
 // caller's outputs -- the copy of the
@@ -185,6 +185,9 @@ extern "C" int symft_sample_noalloc(const symft_plan* plan, uint64_t shots, uint
     d.m3_out = m3 ? m3 : reinterpret_cast<uint64_t*>(base + o_m3);
     d.kmax = h.k_max;
     d.status = status;
+    // early exit under postselection reads the detector columns the sign
+    // kernel has just written (as symft_sample_ex does)
+    d.det_exo = dp.post_chk_off ? det : nullptr;
     size_t smem;
     uint64_t cap = static_cast<uint64_t>(sms) * (dense_smem ? 16 : 8);
     if (dense_smem) {

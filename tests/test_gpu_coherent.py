@@ -36,10 +36,15 @@ def test_coherent_fp64_bit_exact(d, r, shots, kind, kmax):
     np.testing.assert_array_equal(g32["dets"][~diff], o["dets"][~diff])
 
 
-def test_coherent_k24_sampled_shot_against_the_oracle():
+@pytest.mark.parametrize("precision", [1, 0])
+def test_coherent_k24_sampled_shot_against_the_oracle(precision):
     """d=5, 2 rounds reaches k_max = 24 (2^24 amplitudes per shot): one shot,
     every outcome and every active branch probability against the plain
-    SymFT oracle."""
+    SymFT oracle (FP64).  FP64 vectors: every probability within 1e-9 and
+    every record equal.  FP32 vectors (HBM-resident, FP64 branch sums): every
+    probability up to the shot's first outcome flip within 1e-5, and the
+    records equal if no flip occurs."""
+    from oracle.streams import meas_uniform, outcome_from
     import paper_2607_28600_b300 as S
     text = coherent_surface_code_memory(5, 2, 1e-3, 0.02)
     shot, seed = 3, 5
@@ -50,14 +55,26 @@ def test_coherent_k24_sampled_shot_against_the_oracle():
     info = plan.info
     meas = torch.zeros((info["n_records"], W), dtype=torch.int64, device="cuda")
     prob = torch.zeros((info["n_causal"], n), dtype=torch.float64, device="cuda")
-    S.symft_sample_ex(plan, n, seed, meas_out=meas, precision=S.FP64, prob_out=prob, check=True)
+    S.symft_sample_ex(plan, n, seed, meas_out=meas, precision=precision, prob_out=prob, check=True)
     torch.cuda.synchronize()
     g = unpack(meas.cpu().numpy().view(np.uint64), n)[shot]
     c = oparse(text)
     log = []
     o = osymft.sample_shot(osymft.Plan(c), seed, shot, NoiseSampler(c, seed), prob_log=log)
     want = np.array([o[op.t] for op in c.ops if op.kind == "meas" and op.rec >= 0], dtype=np.uint8)
-    np.testing.assert_array_equal(g, want)
     ref = dict(log)
     got = prob.cpu().numpy()[:, shot]
-    assert np.abs(got - np.array([ref[t] for t in plan.active_meas()])).max() <= 1e-9
+    act = plan.active_meas()
+    if precision == 1:
+        np.testing.assert_array_equal(g, want)
+        assert np.abs(got - np.array([ref[t] for t in act])).max() <= 1e-9
+        return
+    flipped = False
+    for j, t in enumerate(act):
+        assert abs(got[j] - ref[t]) <= 1e-5, (j, got[j], ref[t])
+        u = meas_uniform(seed, t, shot)
+        if outcome_from(got[j], u) != outcome_from(ref[t], u):
+            flipped = True
+            break
+    if not flipped:
+        np.testing.assert_array_equal(g, want)

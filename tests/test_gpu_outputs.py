@@ -98,6 +98,46 @@ def test_branch_probabilities_vs_statevector(case):
     assert flips <= max(1, shots // 50)
 
 
+def _fp32_prefix_check(p32, ref, rec32, want_rec, act, seed, shots):
+    """FP32 branch probabilities within 1e-5 of the reference on every active
+    measurement up to and including a shot's first flip; unflipped shots'
+    records bit-exact.  Returns (flips, worst error)."""
+    flips, worst = 0, 0.0
+    for r in range(shots):
+        for j, t in enumerate(act):
+            u = meas_uniform(seed, t, r)
+            worst = max(worst, abs(p32[j, r] - ref[j, r]))
+            if outcome_from(p32[j, r], u) != outcome_from(ref[j, r], u):
+                flips += 1
+                break
+        else:
+            np.testing.assert_array_equal(rec32[r], want_rec[r])
+    return flips, worst
+
+
+def test_wide_executor_fp32_branch_probabilities_k15():
+    """The literal 15-to-1 circuit (16 qubits, k_max = 15) runs on the wide
+    executor, whose FP32 vectors live in HBM: every branch probability up to a
+    shot's first flip within 1e-5 of the state vector's Pr(m = 0) (2^16
+    amplitudes, FP64), unflipped shots bit-exact, flips rare."""
+    from paper_2607_28600_b300.workloads import distillation_15_to_1
+    text = distillation_15_to_1(1e-3, "literal")
+    shots, seed = 40, 31
+    plan, rec32, p32 = _gpu_probs(text, shots, seed, precision=0)
+    assert plan.info["k_max"] == 15
+    act = plan.active_meas()
+    assert len(act) >= 14
+    ref = _sv_probs(text, seed, shots, act)
+    o = oracle_sample(text, seed, range(shots), kind="sv")
+    flips, worst = _fp32_prefix_check(p32, ref, rec32, o["records"], act, seed, shots)
+    assert worst <= 1e-5, worst
+    assert flips <= 1
+    # FP64 on the same executor: every probability to 1e-9, records bit-exact
+    _, rec64, p64 = _gpu_probs(text, shots, seed, precision=1)
+    assert np.abs(p64 - ref).max() <= 1e-9
+    np.testing.assert_array_equal(rec64, o["records"])
+
+
 def test_plain_form_reports_the_same_probabilities():
     text = _cases()["warp"]
     _, r1, p1 = _gpu_probs(text, 64, 5, precision=1)
