@@ -25,7 +25,7 @@ INSTR_NAMES = ("PromoteRot", "ActiveDiagRot", "ActivePairRot", "RandomMeas", "De
 EXPORTS = ("symft_compile", "symft_compile_ex", "symft_plan_info", "symft_plan_free",
            "symft_sample", "symft_sample_ex", "symft_last_error", "symft_last_launch_count",
            "symft_sample_noalloc", "symft_noalloc_last_error", "symft_autotune",
-           "symft_sample_batch", "symft_plan_active_meas")
+           "symft_sample_batch", "symft_plan_active_meas", "symft_measure_peaks")
 
 
 class SymftError(RuntimeError):
@@ -58,6 +58,13 @@ class _SampleArgs(ctypes.Structure):
                 ("out_location", ctypes.c_int), ("check", ctypes.c_int),
                 ("plain", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("prob_out", ctypes.c_void_p), ("counts_out", ctypes.c_void_p)]
+
+
+class _Peaks(ctypes.Structure):
+    _fields_ = [("sm_count", ctypes.c_int), ("sm_clock_mhz_attr", ctypes.c_double),
+                ("int32_lop3_per_s", ctypes.c_double), ("int32_imad_wide_per_s", ctypes.c_double),
+                ("philox_blocks_per_s", ctypes.c_double), ("fp32_fma_per_s", ctypes.c_double),
+                ("fp64_fma_per_s", ctypes.c_double), ("smem_bytes_per_s", ctypes.c_double)]
 
 
 class _Job(ctypes.Structure):
@@ -112,6 +119,8 @@ def lib():
     L.symft_sample_batch.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
                                      ctypes.POINTER(_Job), ctypes.c_int, ctypes.c_void_p]
     L.symft_sample_batch.restype = ctypes.c_int
+    L.symft_measure_peaks.argtypes = [ctypes.POINTER(_Peaks)]
+    L.symft_measure_peaks.restype = ctypes.c_int
     _LIB = L
     return L
 
@@ -267,6 +276,17 @@ def symft_sample_batch(plans, jobs, stream=None) -> None:
         J.plain = int(bool(j.get("plain", False)))
         J.counts_out = _ptr(j.get("counts_out"))
     _check(lib().symft_sample_batch(arr_p, len(plans), arr_j, len(jobs), _stream(stream)))
+
+
+def symft_measure_peaks() -> dict:
+    """Whole-GPU peak rates of the current device (integer LOP3 / IMAD.WIDE,
+    Philox blocks, FP32 / FP64 FMA, shared-memory loads), measured by the
+    library's microbenchmarks."""
+    p = _Peaks()
+    rc = lib().symft_measure_peaks(ctypes.byref(p))
+    if rc != SYMFT_OK:
+        raise SymftError(rc, "peak microbenchmarks failed")
+    return {name: getattr(p, name) for name, _ in _Peaks._fields_}
 
 
 def symft_last_launch_count() -> int:

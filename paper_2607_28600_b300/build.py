@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsymft.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["circuit.cpp", "compile.cpp", "api.cpp", "sign.cu", "kernels.cu", "wide.cu", "noalloc.cu"]
+SOURCES = ["circuit.cpp", "compile.cpp", "api.cpp", "sign.cu", "kernels.cu", "wide.cu", "noalloc.cu",
+           "peaks.cu"]
 HEADERS = ["internal.hpp", "plan_dev.hpp", "plan_host.hpp", "device.cuh"]
 
 
@@ -31,8 +32,9 @@ def _digest():
     for name in SOURCES + HEADERS:
         with open(os.path.join(CSRC, name), "rb") as f:
             h.update(f.read())
-    with open(os.path.join(INCLUDE, "symft.h"), "rb") as f:
-        h.update(f.read())
+    for hdr in ("symft.h", "symft_peaks.h"):
+        with open(os.path.join(INCLUDE, hdr), "rb") as f:
+            h.update(f.read())
     h.update(" ".join(ARCH).encode())
     return h.hexdigest()
 

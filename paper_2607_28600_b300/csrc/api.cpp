@@ -56,12 +56,21 @@ void build_blob(symft_plan* P) {
     ch[c] = ChannelDev{h.ch_theta_last[c], h.ch_qtab[c], h.ch_ctab[c], h.ch_comp0[c], h.ch_cell0[c]};
   std::vector<uint32_t> theta4(((h.n_channels + 3) / 4) * 4, 0u);
   for (uint32_t c = 0; c < h.n_channels; ++c) theta4[c] = h.ch_theta_last[c];
-  std::vector<uint32_t> qtheta;
-  std::vector<float> qinv;
+  std::vector<uint32_t> qtheta, qshift;
+  std::vector<uint16_t> qstart;
   for (auto& q : h.qtabs) {
     qtheta.insert(qtheta.end(), q.theta, q.theta + kNoiseBlock);
-    double l = std::log1p(-q.q);
-    qinv.push_back((q.q > 0.0 && q.q < 1.0) ? static_cast<float>(1.0 / l) : 0.0f);
+    // lane-search buckets (plan_dev.hpp, kQBuckets)
+    const uint32_t last = q.theta[kNoiseBlock - 1];
+    uint32_t sh = 0;
+    while (sh < 32 && (static_cast<uint64_t>(last) >> sh) >= static_cast<uint64_t>(kQBuckets)) ++sh;
+    qshift.push_back(sh);
+    uint32_t j = 0;
+    for (uint32_t i = 0; i < static_cast<uint32_t>(kQBuckets); ++i) {
+      const uint64_t lo = static_cast<uint64_t>(i) << sh;
+      while (j < static_cast<uint32_t>(kNoiseBlock) && q.theta[j] <= lo) ++j;
+      qstart.push_back(static_cast<uint16_t>(j));
+    }
   }
   std::vector<CellTableDev> ct(h.ctabs.size());
   for (size_t i = 0; i < h.ctabs.size(); ++i) {
@@ -112,7 +121,8 @@ void build_blob(symft_plan* P) {
   P->off.q = push(blob, qtheta);
   P->off.ct = push(blob, ct);
   P->off.t4 = push(blob, theta4);
-  P->off.qi = push(blob, qinv);
+  P->off.qi = push(blob, qshift);
+  P->off.qs = push(blob, qstart);
   if (h.n_slots >= 65536) throw Error(SYMFT_E_CAPACITY, "more than 65535 bit-packed slots");
   if (h.n_channels >= (1u << 28)) throw Error(SYMFT_E_CAPACITY, "too many noise channels");
   // (channel, cell) target entries: up to 7 word offsets inline, else a list
@@ -220,7 +230,8 @@ void bind_plan(const symft_plan* P, unsigned char* base, DevPlan* dptr) {
   d.n_qtab = static_cast<uint32_t>(h.qtabs.size());
   d.n_ctab = static_cast<uint32_t>(h.ctabs.size());
   d.qtheta = reinterpret_cast<const uint32_t*>(at(P->off.q));
-  d.qinv = reinterpret_cast<const float*>(at(P->off.qi));
+  d.qshift = reinterpret_cast<const uint32_t*>(at(P->off.qi));
+  d.qstart = reinterpret_cast<const uint16_t*>(at(P->off.qs));
   d.ctabs = reinterpret_cast<const CellTableDev*>(at(P->off.ct));
   d.cellt = reinterpret_cast<const CellTargetsDev*>(at(P->off.clt));
   d.cell_ovf = reinterpret_cast<const uint32_t*>(at(P->off.clo));

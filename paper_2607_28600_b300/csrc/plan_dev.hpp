@@ -36,11 +36,13 @@ struct CellTableDev {
   uint8_t mask[16];
 };
 
-// q-table acceleration: 1 / log(1 - q), used only to guess the fired lane
-// before the exact integer threshold comparisons
-struct QInvDev {
-  float inv_log1m_q;
-};
+// Lane-search buckets of a threshold table: with shift s the smallest value
+// such that THETA_{kNoiseBlock-1} >> s < kQBuckets, bucket i holds
+// min{j : THETA_j > i << s}, the first lane a uniform u with u >> s == i can
+// fire at.  The search starts there and steps up while u >= THETA_j, so its
+// answer is the table's own, and it takes kNoiseBlock / kQBuckets extra steps
+// on average for a uniform below THETA_{kNoiseBlock-1}.
+constexpr int kQBuckets = 512;
 
 struct DenseInstrDev {
   int32_t kind, k, h, mu;
@@ -60,10 +62,11 @@ constexpr uint32_t kNoGroup = 0xFFFFFFFFu;
 struct DevPlan {
   uint32_t n_channels;
   const ChannelDev* ch;
-  const uint4* theta4;          // THETA_127 of channels 4g..4g+3 (0 = never fires)
+  const uint4* theta4;          // THETA_{kNoiseBlock-1} of channels 4g..4g+3 (0 = never fires)
   uint32_t n_qtab, n_ctab;
   const uint32_t* qtheta;       // [n_qtab][kNoiseBlock]
-  const float* qinv;            // [n_qtab] 1 / log(1 - q)
+  const uint32_t* qshift;       // [n_qtab] bucket shift s
+  const uint16_t* qstart;       // [n_qtab][kQBuckets] first lane of each bucket
   const CellTableDev* ctabs;
   const CellTargetsDev* cellt;  // per (channel, cell)
   const uint32_t* cell_ovf;     // long target lists (slot * 16)

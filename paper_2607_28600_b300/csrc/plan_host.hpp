@@ -33,7 +33,7 @@ struct DevBuf {
 
 // Byte offsets of the plan arrays inside the device blob.
 struct BlobOffsets {
-  size_t ch, q, ct, t4, qi, m1t, m1o, m1g, tco, tca, sc, li, gi, gv, pe, dn, dc, m3t, sm1, sm1o, pco, pch;
+  size_t ch, q, ct, t4, qi, qs, m1t, m1o, m1g, tco, tca, sc, li, gi, gv, pe, dn, dc, m3t, sm1, sm1o, pco, pch;
   size_t plc, plo, pls;
   size_t clt, clo;
 };

@@ -18,19 +18,13 @@ namespace {
 constexpr int kQueue = 96;          // per-warp ring of fire states (< 32 + 64 live)
 constexpr int kSignWarps = 8;       // warps per CTA
 
-// smallest j in [0, kNoiseBlock) with u < theta[j] (kNoiseBlock if none).  A
-// guess from the logarithm of the geometric law is corrected by exact integer
-// comparisons against the threshold table, so the result is the table's own
-// answer.
-__device__ __forceinline__ int first_above(const uint32_t* th, float inv_log1m_q, uint32_t u) {
-  int j = 0;
-  if (inv_log1m_q != 0.0f) {
-    const float x = (float)u * 2.3283064365386963e-10f;          // u / 2^32
-    const float est = log1pf(-x) * inv_log1m_q;                  // ~ j*
-    j = est < 0.0f ? 0 : (est > (float)(kNoiseBlock - 1) ? kNoiseBlock - 1 : (int)est);
-  }
-  while (j > 0 && u < th[j - 1]) --j;
-  while (j < kNoiseBlock && u >= th[j]) ++j;
+// smallest j in [0, kNoiseBlock) with u < theta[j], for a u below
+// theta[kNoiseBlock-1]: the lane-search bucket of u (plan_dev.hpp, kQBuckets)
+// gives the first lane u can fire at, and exact integer comparisons step up
+// from there, so the result is the threshold table's own answer
+__device__ __forceinline__ int first_above(const uint32_t* th, const uint16_t* bk, uint32_t sh, uint32_t u) {
+  int j = bk[u >> sh];
+  while (j < kNoiseBlock - 1 && u >= th[j]) ++j;
   return j;
 }
 
@@ -49,14 +43,15 @@ __device__ __forceinline__ void scatter7(uint32_t* sw, uint4 tg, uint32_t n, uin
 constexpr int kSub = kNoiseBlock / 128;
 
 struct SignLayout {
-  size_t q_off, qi_off, c_off, slot_off, qa_off, qb_off, cnt_off, total;
+  size_t q_off, qs_off, qk_off, c_off, slot_off, qa_off, qb_off, cnt_off, total;
 };
 
 __host__ __device__ inline SignLayout sign_layout(uint32_t n_qtab, uint32_t n_ctab, uint32_t n_slots) {
   SignLayout L;
   L.q_off = 0;
-  L.qi_off = align16((size_t)n_qtab * kNoiseBlock * 4);
-  L.c_off = L.qi_off + align16((size_t)n_qtab * 4);
+  L.qs_off = align16((size_t)n_qtab * kNoiseBlock * 4);
+  L.qk_off = L.qs_off + align16((size_t)n_qtab * 4);
+  L.c_off = L.qk_off + align16((size_t)n_qtab * kQBuckets * 2);
   L.slot_off = L.c_off + align16((size_t)n_ctab * sizeof(CellTableDev));
   L.qa_off = L.slot_off + (size_t)n_slots * kSub * 16;
   L.qb_off = L.qa_off + (size_t)kSignWarps * kQueue * 16;
@@ -80,7 +75,8 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
   const uint32_t NT = A.p.n_slots;
   const SignLayout Lay = sign_layout(A.p.n_qtab, A.p.n_ctab, NT);
   uint32_t* sq = reinterpret_cast<uint32_t*>(smem_raw + Lay.q_off);
-  float* sqi = reinterpret_cast<float*>(smem_raw + Lay.qi_off);
+  uint32_t* sqs = reinterpret_cast<uint32_t*>(smem_raw + Lay.qs_off);
+  uint16_t* sqb = reinterpret_cast<uint16_t*>(smem_raw + Lay.qk_off);
   CellTableDev* sc = reinterpret_cast<CellTableDev*>(smem_raw + Lay.c_off);
   uint4* slots = reinterpret_cast<uint4*>(smem_raw + Lay.slot_off);
   uint4* qa = reinterpret_cast<uint4*>(smem_raw + Lay.qa_off) + warp * kQueue;
@@ -88,7 +84,8 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
   uint32_t* sqn = reinterpret_cast<uint32_t*>(smem_raw + Lay.cnt_off);
 
   for (uint32_t i = threadIdx.x; i < A.p.n_qtab * kNoiseBlock; i += blockDim.x) sq[i] = __ldg(A.p.qtheta + i);
-  for (uint32_t i = threadIdx.x; i < A.p.n_qtab; i += blockDim.x) sqi[i] = __ldg(A.p.qinv + i);
+  for (uint32_t i = threadIdx.x; i < A.p.n_qtab; i += blockDim.x) sqs[i] = __ldg(A.p.qshift + i);
+  for (uint32_t i = threadIdx.x; i < A.p.n_qtab * kQBuckets; i += blockDim.x) sqb[i] = __ldg(A.p.qstart + i);
   for (uint32_t i = threadIdx.x; i < A.p.n_ctab; i += blockDim.x) sc[i] = A.p.ctabs[i];
   __syncthreads();
 
@@ -174,7 +171,7 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
       const uint32_t qt = ent.w & 0xFFFFu;
       const uint32_t* th = sq + (size_t)qt * kNoiseBlock;
       const CellTableDev* ct = sc + (ent.w >> 16);
-      const int lanebit = L + first_above(th, sqi[qt], ent.y);   // <= kNoiseBlock-1 by construction
+      const int lanebit = L + first_above(th, sqb + qt * kQBuckets, sqs[qt], ent.y);   // <= kNoiseBlock-1 by construction
       const uint32_t ncell = ct->ncell;
       // the draws of one fire (cell, next u) lie in one Philox block
       const uint4 tail = philox(make_uint4(c, gblk, ti >> 2, kTagTail), A.keys);

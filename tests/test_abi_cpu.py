@@ -17,8 +17,11 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_library_exports_every_declared_symbol():
-    hdr = open(os.path.join(ROOT, "include", "symft.h")).read()
-    declared = set(re.findall(r"^\s*(?:int|void|const char\*)\s+(symft_\w+)\s*\(", hdr, re.M))
+    declared = set()
+    for name in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if name.endswith(".h"):
+            hdr = open(os.path.join(ROOT, "include", name)).read()
+            declared |= set(re.findall(r"^\s*(?:int|void|const char\*)\s+(symft_\w+)\s*\(", hdr, re.M))
     assert declared == set(S.EXPORTS)
     L = S.lib()
     for name in declared:
@@ -113,8 +116,9 @@ def test_struct_layouts_match_the_header(tmp_path):
     if shutil.which("gcc") is None:
         pytest.skip("no C compiler")
     structs = {"symft_options": S._Options, "symft_info": S._Info,
-               "symft_sample_args": S._SampleArgs, "symft_job": S._Job}
-    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "symft.h"', "int main(void) {"]
+               "symft_sample_args": S._SampleArgs, "symft_job": S._Job, "symft_peaks": S._Peaks}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "symft.h"', '#include "symft_peaks.h"',
+             "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
         for fname, _ in py._fields_:
