@@ -1,12 +1,14 @@
 // Wide dense executor: the dense-state instructions of Sec. 4 for active
 // widths whose vectors do not fit on chip (2^k amplitudes per shot above
 // ~200 KB).  Work is instruction-major: a batch of shots keeps its vectors in
-// HBM ([shot][2^k_max] amplitudes, two buffers), and every dense instruction
-// is one or three grid-wide passes over all shots of the batch, so each pass
-// streams whole vectors with full memory-level parallelism.
+// HBM ([shot][2^k_max] amplitudes, two buffers), and the dense instructions
+// run as grid-wide passes over all shots of the batch, so each pass streams
+// whole vectors with full memory-level parallelism.
 //
-//   rotations    one pass, in place (PromoteRot writes the upper half,
-//                ActivePairRot updates disjoint pairs (x0, x0 ^ a))
+//   rotations    a run of consecutive rotations whose pair and new bits fit
+//                a shared-memory tile is one fused pass (below); a lone
+//                rotation is one pass in place (PromoteRot writes the upper
+//                half, ActivePairRot updates disjoint pairs (x0, x0 ^ a))
 //   measurements branch sums per shot (block partials added into FP64
 //                accumulators), a per-shot decision (shared uniform rule,
 //                record / causal bits, renormalisation, signs of the
@@ -368,6 +370,199 @@ __global__ void __launch_bounds__(kWideThreads) wide_compact_kernel(WideArgs A, 
 }
 
 // ---------------------------------------------------------------------------
+// Fused rotation windows.  A run of consecutive PromoteRot / ActiveDiagRot /
+// ActivePairRot instructions whose pair bits (the bits of a), new bits (the
+// coordinate a PromoteRot adds) and the five lowest bits together number at
+// most T is applied in ONE pass over HBM: each CTA stages a tile of 2^T
+// amplitudes -- the "inner" bits vary inside the tile, the other ("outer")
+// bits are fixed per tile -- in shared memory, runs the whole window on it
+// and writes it back.  The five lowest bits are always inner, so a tile is
+// 2^(T-5) runs of 32 consecutive amplitudes (coalesced).  A diagonal phase
+// needs no pairing, so only pair and new bits constrain a window.  In tile
+// coordinates an instruction's masks are the inner parts of a and b gathered
+// onto the tile's bit positions; the outer part of b adds a parity that is
+// fixed per tile.
+// ---------------------------------------------------------------------------
+constexpr int kFuseMax = 48;        // instructions per window
+// tile bits: 2^12 FP32 / 2^11 FP64 amplitudes = 32 KB of shared memory (larger
+// tiles make the pass compute-bound before they save HBM traffic)
+constexpr uint32_t kFuseBitsF32 = 12, kFuseBitsF64 = 11;
+
+struct FuseInstr {
+  uint32_t b_out;      // b & outer bits (parity fixed per tile)
+  uint16_t a_loc;      // a gathered onto the tile bits (pair rotations)
+  uint16_t b_loc;      // b & inner bits gathered onto the tile bits
+  uint8_t kind;        // 0 PromoteRot, 1 ActiveDiagRot, 2 ActivePairRot
+  uint8_t p_loc;       // tile bit of the new coordinate (PromoteRot) or of a's pivot (pair)
+  uint16_t e_loc;      // tile bits of coordinates not yet promoted: elements with
+                       // any of them set do not exist yet (zero) and are skipped
+};
+
+struct WideFuse {
+  uint32_t g0, n;          // instructions g0 .. g0 + n - 1
+  uint32_t inner;          // inner (tile) bits, |inner| = T
+  uint32_t outer;          // outer bits: [0, k_start) without the inner bits
+  uint32_t T, kstart, kend;
+  uint32_t hi_shift;       // 5: inner bits 0..4 are the tile's low bits
+  FuseInstr ins[kFuseMax];
+};
+
+// x with the bits of v placed at the set positions of mask, lowest first
+__host__ __device__ __forceinline__ uint32_t deposit_bits(uint32_t v, uint32_t mask) {
+  uint32_t x = 0;
+  for (uint32_t m = mask; m; m &= m - 1) {
+    if (v & 1u) x |= m & (~m + 1u);
+    v >>= 1;
+  }
+  return x;
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(kWideThreads) wide_fused_rot_kernel(WideArgs A, WideFuse F) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  Amp<Real>* tile = reinterpret_cast<Amp<Real>*>(fsm);
+  uint32_t* hi_tab = reinterpret_cast<uint32_t*>(fsm + ((size_t)sizeof(Amp<Real>) << F.T));
+  const uint32_t n = 1u << F.T;
+  const uint32_t tid = threadIdx.x;
+  // global offsets of the tile's high inner index (i >> 5)
+  const uint32_t inner_hi = F.inner & ~31u;
+  for (uint32_t j = tid; j < (n >> 5); j += blockDim.x) hi_tab[j] = deposit_bits(j, inner_hi);
+  __syncthreads();
+  const uint32_t tiles = 1u << (F.kend - F.T);
+  const uint64_t total = (uint64_t)A.nb * tiles;
+  const uint32_t kst_mask = F.kstart >= 32 ? ~0u : (1u << F.kstart) - 1u;
+  for (uint64_t t = blockIdx.x; t < total; t += gridDim.x) {
+    const uint32_t b = (uint32_t)(t / tiles), o = (uint32_t)(t - (uint64_t)b * tiles);
+    if (!A.alive[b]) continue;                       // uniform over the CTA
+    const uint32_t off = deposit_bits(o, F.outer);
+    Amp<Real>* v = reinterpret_cast<Amp<Real>*>(A.vec[A.cur]) + (size_t)b * A.stride;
+    for (uint32_t i = tid; i < n; i += blockDim.x) {
+      const uint32_t x = off + hi_tab[i >> 5] + (i & 31u);
+      Amp<Real> a;
+      a.re = (Real)0;
+      a.im = (Real)0;
+      if ((x & ~kst_mask) == 0u) a = v[x];           // coordinates not yet promoted are 0
+      tile[i] = a;
+    }
+    __syncthreads();
+    for (uint32_t q = 0; q < F.n; ++q) {
+      const FuseInstr& L = F.ins[q];
+      const uint32_t g = F.g0 + q;
+      const DenseInstrDev& I = A.p.dense[g];
+      const Real c = (Real)I.c, s = (Real)I.s;
+      const Real sgs = A.lam[(size_t)g * A.nb + b] ? -s : s;
+      const uint32_t po = __popc(L.b_out & off) & 1u;
+      if (L.kind == 0) {                              // a'_x = c a_x, a'_{x+new} = -i sg s a_x
+        const uint32_t pb = 1u << L.p_loc;
+        for (uint32_t z = tid; z < (n >> 1); z += blockDim.x) {
+          const uint32_t i0 = wide_insert_bit(z, L.p_loc, 0u);
+          if (i0 & L.e_loc) continue;
+          Amp<Real> a = tile[i0], hi;
+          hi.re = sgs * a.im;
+          hi.im = -sgs * a.re;
+          a.re *= c;
+          a.im *= c;
+          tile[i0] = a;
+          tile[i0 | pb] = hi;
+        }
+      } else if (L.kind == 1) {                       // a_x *= c - i sg mu (-1)^{b.x} s
+        const Real mus = I.mu == 0 ? sgs : -sgs;
+        for (uint32_t i = tid; i < n; i += blockDim.x) {
+          if (i & L.e_loc) continue;
+          const Real f = ((__popc(i & L.b_loc) ^ po) & 1u) ? -mus : mus;
+          const Amp<Real> a = tile[i];
+          Amp<Real> r;
+          r.re = c * a.re + f * a.im;
+          r.im = c * a.im - f * a.re;
+          tile[i] = r;
+        }
+      } else {                                        // pairs (x0, x0 ^ a)
+        Real cr, ci;
+        switch (I.mu & 3) {
+          case 0: cr = 0; ci = -1; break;
+          case 1: cr = 1; ci = 0; break;
+          case 2: cr = 0; ci = 1; break;
+          default: cr = -1; ci = 0; break;
+        }
+        cr *= sgs;
+        ci *= sgs;
+        for (uint32_t z = tid; z < (n >> 1); z += blockDim.x) {
+          const uint32_t i0 = wide_insert_bit(z, L.p_loc, 0u), i1 = i0 ^ L.a_loc;
+          if (i0 & L.e_loc) continue;
+          const Amp<Real> v0 = tile[i0], v1 = tile[i1];
+          const Real s1 = ((__popc(i1 & L.b_loc) ^ po) & 1u) ? (Real)-1 : (Real)1;
+          const Real s0 = ((__popc(i0 & L.b_loc) ^ po) & 1u) ? (Real)-1 : (Real)1;
+          Amp<Real> o0, o1;
+          o0.re = c * v0.re + s1 * (cr * v1.re - ci * v1.im);
+          o0.im = c * v0.im + s1 * (cr * v1.im + ci * v1.re);
+          o1.re = c * v1.re + s0 * (cr * v0.re - ci * v0.im);
+          o1.im = c * v1.im + s0 * (cr * v0.im + ci * v0.re);
+          tile[i0] = o0;
+          tile[i1] = o1;
+        }
+      }
+      __syncthreads();
+    }
+    for (uint32_t i = tid; i < n; i += blockDim.x) v[off + hi_tab[i >> 5] + (i & 31u)] = tile[i];
+    __syncthreads();
+  }
+}
+
+// bit positions of mask, gathered: the index of each set bit of x & mask
+static uint32_t gather_bits(uint32_t x, uint32_t mask) {
+  uint32_t r = 0, k = 0;
+  for (uint32_t m = mask; m; m &= m - 1, ++k)
+    if (x & m & (~m + 1u)) r |= 1u << k;
+  return r;
+}
+
+// Greedy window from instruction g0 (a rotation): consecutive rotations while
+// the inner bits fit in T.  Returns the number of instructions taken.
+static uint32_t build_window(const DenseInstrDev* d, uint32_t G, uint32_t g0, uint32_t T, WideFuse* F) {
+  const uint32_t kstart = (uint32_t)d[g0].k;
+  uint32_t inner = 0u;
+  for (uint32_t j = 0; j < 5; ++j) inner |= 1u << j;
+  uint32_t g = g0, kend = kstart;
+  while (g < G && d[g].kind <= 2 && g - g0 < (uint32_t)kFuseMax) {
+    uint32_t need = 0u;
+    if (d[g].kind == 0) need = 1u << d[g].k;
+    else if (d[g].kind == 2) need = d[g].a;
+    const uint32_t nx = inner | need;
+    if ((uint32_t)__builtin_popcount(nx) > T) break;
+    inner = nx;
+    if (d[g].kind == 0) kend = (uint32_t)d[g].k + 1;
+    ++g;
+  }
+  const uint32_t n = g - g0;
+  // the tile: at most T bits of [0, kend); pad with the lowest free bits
+  const uint32_t Te = kend < T ? kend : T;
+  const uint32_t kmask = kend >= 32 ? ~0u : (1u << kend) - 1u;
+  inner &= kmask;
+  for (uint32_t j = 0; j < kend && (uint32_t)__builtin_popcount(inner) < Te; ++j) inner |= 1u << j;
+  F->g0 = g0;
+  F->n = n;
+  F->inner = inner;
+  F->T = (uint32_t)__builtin_popcount(inner);
+  F->kstart = kstart;
+  F->kend = kend;
+  F->outer = (kstart >= 32 ? ~0u : (1u << kstart) - 1u) & ~inner;
+  F->hi_shift = 5;
+  for (uint32_t q = 0; q < n; ++q) {
+    const DenseInstrDev& I = d[g0 + q];
+    FuseInstr& L = F->ins[q];
+    L.kind = (uint8_t)I.kind;
+    L.b_out = I.b & F->outer;
+    L.b_loc = (uint16_t)gather_bits(I.b, inner);
+    L.a_loc = (uint16_t)gather_bits(I.a, inner);
+    L.p_loc = 0;
+    if (I.kind == 0) L.p_loc = (uint8_t)__builtin_popcount(inner & ((1u << I.k) - 1u));
+    else if (I.kind == 2) L.p_loc = (uint8_t)(31 - __builtin_clz((uint32_t)L.a_loc));
+    L.e_loc = (uint16_t)gather_bits(~((1u << I.k) - 1u), inner);
+  }
+  return n;
+}
+
+// ---------------------------------------------------------------------------
 // host: one batch of shots through the whole dense instruction stream
 // ---------------------------------------------------------------------------
 // blocks of a flat pass over `total` elements: enough to fill the GPU
@@ -394,13 +589,34 @@ static cudaError_t wide_batch_t(WideArgs A, const DenseInstrDev* host_dense, int
   const unsigned nb_blocks = (A.nb + 127) / 128;
   wide_init_kernel<Real><<<nb_blocks, 128, 0, st>>>(A);
   ++*launches;
+  const uint32_t T = sizeof(Real) == 4 ? kFuseBitsF32 : kFuseBitsF64;
   for (uint32_t g = 0; g < A.p.n_dense; ++g) {
     const DenseInstrDev& I = host_dense[g];
     const uint64_t n = 1ull << I.k;
     if (I.kind <= 2) {
-      const uint64_t per_shot = I.kind == 2 ? n / 2 : n;
-      wide_rot_kernel<Real><<<wide_flat_blocks(per_shot * A.nb, sm_count), kWideThreads, 0, st>>>(A, g);
-      ++*launches;
+      WideFuse F;
+      const uint32_t nw = build_window(host_dense, A.p.n_dense, g, T, &F);
+      if (nw >= 2 && F.kend >= 5) {
+        // one pass over HBM for the whole window
+        const size_t smem = (sizeof(Amp<Real>) << F.T) + ((size_t)4 << (F.T - 5));
+        const uint64_t tiles = (uint64_t)A.nb << (F.kend - F.T);
+        const uint64_t cap = (uint64_t)sm_count * 8;
+        const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
+        static bool attr_set = false;
+        if (!attr_set) {
+          cudaError_t e = cudaFuncSetAttribute((const void*)wide_fused_rot_kernel<Real>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+          if (e != cudaSuccess) return e;
+          attr_set = true;
+        }
+        wide_fused_rot_kernel<Real><<<grid, kWideThreads, smem, st>>>(A, F);
+        ++*launches;
+        g += nw - 1;
+      } else {
+        const uint64_t per_shot = I.kind == 2 ? n / 2 : n;
+        wide_rot_kernel<Real><<<wide_flat_blocks(per_shot * A.nb, sm_count), kWideThreads, 0, st>>>(A, g);
+        ++*launches;
+      }
     } else if (n <= kWideSmall) {
       wide_meas_small_kernel<Real><<<(A.nb + kWideThreads / 32 - 1) / (kWideThreads / 32), kWideThreads, 0, st>>>(A, g);
       ++*launches;
