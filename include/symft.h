@@ -77,7 +77,11 @@ typedef struct {
                               0-based, duplicates allowed); caller-owned, read
                               only during symft_compile_ex; an index >= the
                               number of detectors is SYMFT_E_ARG */
-  int reserved[4];
+  int no_simplify;         /* non-zero: skip the commutation-aware
+                              simplification before planning (Sec. 6): same
+                              output distribution, possibly a wider active
+                              state and more dense instructions */
+  int reserved[3];
 } symft_options;
 
 /* Counts of a compiled plan (Sec. 5, sampling complexity). */
@@ -104,6 +108,11 @@ typedef struct {
                                   PromoteRot 3 * 2^k, measurement 2^k + 1.5 * 2^k);
                                   times 8 B (FP32) or 16 B (FP64) = vector bytes
                                   per shot when vectors live in HBM */
+  uint32_t simplified[3];     /* commutation-aware simplification (Sec. 6):
+                                 rotations merged into an earlier same-body
+                                 rotation, merged rotations removed (angle a
+                                 multiple of 2 pi), rotations removed as the
+                                 branch phase of a later same-body measurement */
 } symft_info;
 
 /* One sampling request.  All pointers may be NULL to skip that output. */

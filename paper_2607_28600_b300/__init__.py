@@ -36,7 +36,8 @@ class SymftError(RuntimeError):
 
 class _Options(ctypes.Structure):
     _fields_ = [("postselect", ctypes.c_int), ("n_post_dets", ctypes.c_uint32),
-                ("post_dets", ctypes.POINTER(ctypes.c_uint32)), ("reserved", ctypes.c_int * 4)]
+                ("post_dets", ctypes.POINTER(ctypes.c_uint32)), ("no_simplify", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 class _Info(ctypes.Structure):
@@ -47,7 +48,7 @@ class _Info(ctypes.Structure):
                 ("max_expr_weight", ctypes.c_uint32), ("n_noise_components", ctypes.c_uint32),
                 ("n_targets", ctypes.c_uint32), ("n_causal", ctypes.c_uint32),
                 ("sign_xor_terms", ctypes.c_uint64), ("tuned_ns_per_shot", ctypes.c_float * 2),
-                ("dense_amp_traffic", ctypes.c_uint64)]
+                ("dense_amp_traffic", ctypes.c_uint64), ("simplified", ctypes.c_uint32 * 3)]
 
 
 class _SampleArgs(ctypes.Structure):
@@ -181,12 +182,15 @@ class Plan:
         return symft_plan_active_meas(self)
 
 
-def symft_compile(circuit_text: str, postselect: int = POSTSELECT_NONE, post_dets=None) -> Plan:
+def symft_compile(circuit_text: str, postselect: int = POSTSELECT_NONE, post_dets=None,
+                  simplify: bool = True) -> Plan:
     """Compile circuit text.  postselect=POSTSELECT_LISTED rejects a shot only at
-    the detectors whose indices are listed in `post_dets`."""
+    the detectors whose indices are listed in `post_dets`; simplify=False skips
+    the commutation-aware simplification before planning."""
     h = ctypes.c_void_p()
     opt = _Options()
     opt.postselect = postselect
+    opt.no_simplify = 0 if simplify else 1
     if post_dets is not None:
         dets = [int(d) for d in post_dets]
         arr = (ctypes.c_uint32 * max(1, len(dets)))(*dets)
@@ -200,7 +204,9 @@ def symft_plan_info(plan: Plan) -> dict:
     info = _Info()
     _check(lib().symft_plan_info(plan.handle, ctypes.byref(info)))
     d = {name: getattr(info, name) for name, _ in _Info._fields_
-         if name not in ("n_instr", "tuned_ns_per_shot")}
+         if name not in ("n_instr", "tuned_ns_per_shot", "simplified")}
+    d["simplified"] = {"fused": int(info.simplified[0]), "cancelled": int(info.simplified[1]),
+                       "branch_phase": int(info.simplified[2])}
     d["tuned_ns_per_shot"] = [float(info.tuned_ns_per_shot[0]), float(info.tuned_ns_per_shot[1])]
     d["n_instr"] = {INSTR_NAMES[i]: int(info.n_instr[i]) for i in range(7)}
     return d

@@ -930,6 +930,9 @@ int symft_plan_info(const symft_plan* p, symft_info* info) {
     else traffic += n + n + n / 2;
   }
   info->dense_amp_traffic = traffic;
+  info->simplified[0] = h.n_fused;
+  info->simplified[1] = h.n_cancelled;
+  info->simplified[2] = h.n_branch_phase;
   for (int i = 0; i < 2; ++i)
     info->tuned_ns_per_shot[i] = p->tune[i].tuned ? p->tune[i].best_ms_per_shot * 1e6f : 0.0f;
   return SYMFT_OK;

@@ -183,6 +183,88 @@ class Compiler {
   uint32_t k_ = 0, kmax_ = 0;
   std::vector<RawInstr> instrs_;
 
+  // Factorized operator sequence (Sec. 3): rotations R_P(theta) and Pauli
+  // measurements with P pulled back through the Clifford frame and the sign
+  // lam from the noise and feedback terms of the Pauli frame; detectors and
+  // observables are segment boundaries.
+  struct FOp {
+    int kind;          // 0 rotation, 1 measurement, 2 detector / observable boundary
+    Pauli p;
+    double theta = 0.0;
+    uint32_t t = 0;
+    Expr lam;
+    bool dead = false;
+  };
+  uint32_t n_fused_ = 0, n_cancelled_ = 0, n_branch_phase_ = 0;
+
+  bool symbol_free(const Expr& e) const {
+    for (uint32_t w = 0; w < ea_.nw; ++w) {
+      uint64_t v = e.w[w];
+      if (w == (ea_.ns >> 6)) v &= ~(1ull << (ea_.ns & 63));
+      if (v) return false;
+    }
+    return true;
+  }
+
+  // Commutation-aware simplification before planning (Sec. 6): conservative
+  // local rewrites inside each segment between detector positions.
+  //  - Rotation fusion: a rotation whose Pauli body equals that of an earlier
+  //    rotation, with every operation in between commuting with it and with
+  //    signs that differ by a constant (lam_i ^ lam_j has no symbol), is
+  //    merged into the earlier one; the merged rotation is removed when its
+  //    angle is a multiple of 2 pi (the identity up to a global phase).
+  //  - Branch phase: a rotation followed, across operations that all commute
+  //    with it, by a measurement of the same Pauli body acts on each outcome's
+  //    eigenspace as a phase only, so it is removed.
+  // Measurements never move, so record order, detector boundaries and the
+  // measurement symbols every sign uses stay as they were.
+  void simplify(std::vector<FOp>& f) {
+    constexpr size_t kScan = 512;   // operations examined per rewrite search
+    for (size_t j = 0; j < f.size(); ++j) {
+      if (f[j].kind != 0 || f[j].dead) continue;
+      size_t steps = 0;
+      for (size_t i = j; i-- > 0 && steps < kScan; ++steps) {
+        FOp& o = f[i];
+        if (o.dead) continue;
+        if (o.kind == 2) break;
+        if (o.kind == 0 && pa_.same_support(o.p, f[j].p)) {
+          Expr d = o.lam;
+          ea_.xor_into(d, f[j].lam);
+          if (symbol_free(d)) {
+            // P_j = s P_i with s = +-1 from the phases; signed angles add
+            const int rel = (ea_.constant(d) ? 1 : 0) ^ ((((o.p.e - f[j].p.e) & 3) == 2) ? 1 : 0);
+            o.theta += rel ? -f[j].theta : f[j].theta;
+            f[j].dead = true;
+            ++n_fused_;
+            const double two_pi = 6.283185307179586;
+            const double r = std::fabs(std::remainder(o.theta, two_pi));
+            if (r < 1e-12) {
+              o.dead = true;
+              ++n_cancelled_;
+            }
+            break;
+          }
+        }
+        if (pa_.omega(o.p, f[j].p)) break;
+      }
+    }
+    for (size_t i = 0; i < f.size(); ++i) {
+      if (f[i].kind != 0 || f[i].dead) continue;
+      size_t steps = 0;
+      for (size_t j = i + 1; j < f.size() && steps < kScan; ++j, ++steps) {
+        const FOp& o = f[j];
+        if (o.dead) continue;
+        if (o.kind == 2) break;
+        if (o.kind == 1 && pa_.same_support(o.p, f[i].p)) {
+          f[i].dead = true;
+          ++n_branch_phase_;
+          break;
+        }
+        if (pa_.omega(o.p, f[i].p)) break;
+      }
+    }
+  }
+
   uint32_t msym(uint32_t t) const { return n_comp_ + t; }
 
   Pauli pull_back_local(const LocalPauli& lp, uint32_t qa, uint32_t qb) const {
@@ -482,6 +564,8 @@ HostPlan Compiler::run() {
   Ex_.assign(nq, ea_.zero());
   Ez_.assign(nq, ea_.zero());
 
+  // 1. factorization: the frame holds the noise and feedback terms only
+  std::vector<FOp> fops;
   for (const Op& op : c_.ops) {
     switch (op.kind) {
       case OP_CLIFF:
@@ -506,24 +590,52 @@ HostPlan Compiler::run() {
         break;
       }
       case OP_ROT: {
-        Pauli pp = pull_back(op.pauli);
-        Expr lam = frame_sign(pp);
-        plan_rotation(pp, op.theta, std::move(lam));
+        FOp f;
+        f.kind = 0;
+        f.p = pull_back(op.pauli);
+        f.lam = frame_sign(f.p);
+        f.theta = op.theta;
+        fops.push_back(std::move(f));
         break;
       }
       case OP_MEAS: {
-        Pauli pp = pull_back(op.pauli);
-        Expr lam = frame_sign(pp);
-        plan_measurement(pp, op.t, std::move(lam));
+        FOp f;
+        f.kind = 1;
+        f.p = pull_back(op.pauli);
+        f.lam = frame_sign(f.p);
+        f.t = op.t;
+        fops.push_back(std::move(f));
         break;
       }
       case OP_DET:
-      case OP_OBS:
+      case OP_OBS: {
+        FOp f;
+        f.kind = 2;
+        fops.push_back(std::move(f));
         break;
+      }
     }
+  }
+  // 2. commutation-aware simplification
+  if (!opt_.no_simplify) simplify(fops);
+  // 3. planning (Sec. 4): the frame now accumulates the planner's measurement
+  //    corrections, and an operation's sign is its factorized sign XOR theirs
+  for (uint32_t q = 0; q < nq; ++q) {
+    Ex_[q] = ea_.zero();
+    Ez_[q] = ea_.zero();
+  }
+  for (FOp& f : fops) {
+    if (f.dead || f.kind == 2) continue;
+    Expr lam = frame_sign(f.p);
+    ea_.xor_into(lam, f.lam);
+    if (f.kind == 0) plan_rotation(f.p, f.theta, std::move(lam));
+    else plan_measurement(f.p, f.t, std::move(lam));
   }
   HostPlan P;
   lower(P);
+  P.n_fused = n_fused_;
+  P.n_cancelled = n_cancelled_;
+  P.n_branch_phase = n_branch_phase_;
   return P;
 }
 

@@ -155,6 +155,10 @@ struct HostPlan {
   std::vector<uint32_t> m3_t;            // ordinal of each m3 symbol
 
   uint64_t sign_xor_terms = 0;
+  // commutation-aware simplification: rotations merged into an earlier one,
+  // merged rotations removed (angle a multiple of 2 pi), rotations removed as
+  // branch phases of a later same-body measurement
+  uint32_t n_fused = 0, n_cancelled = 0, n_branch_phase = 0;
 };
 
 HostPlan compile_plan(const Circuit& c, const symft_options& opt);
