@@ -70,6 +70,16 @@ def _peaks():
         return 6400.0, "fallback"
 
 
+def all_peaks(S):
+    """HBM from MEASURED_PEAKS.json (or the fallback); integer, Philox, FP32 /
+    FP64 FMA and shared-memory rates measured now by the library's own
+    microbenchmarks on this GPU."""
+    hbm, kind = _peaks()
+    pk = S.symft_measure_peaks()
+    pk.update({"hbm_gbs": hbm, "hbm_kind": kind})
+    return pk
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled during the timed region."""
 
@@ -257,7 +267,8 @@ def _near_clifford_text(kind):
 
 
 def fp32_accuracy(S, torch, plan, dev, stream, shots=1 << 16, seed=77):
-    """FP32 executor against the FP64 one on the same shots: the fraction of shots
+    """GPU FP32 executor against the GPU FP64 executor on the same shots (both
+    checked against the oracle by the parity tests): the fraction of shots
     whose outputs differ (an active outcome flipped) and the largest branch-
     probability difference over the shots whose outputs agree."""
     import numpy as np
@@ -286,98 +297,138 @@ def fp32_accuracy(S, torch, plan, dev, stream, shots=1 << 16, seed=77):
             "max_prob_err_unflipped": err, "n_active_meas": info["n_causal"]}
 
 
-def measure_near_clifford(S, torch, dev, stream, steps, warmup, scale=1.0, only=None):
-    """FP32-batched vs FP64-plain (and FP64-batched) shots/s per near-Clifford config."""
+def dense_floor(info, peaks, fp64=False):
+    """Per-shot time floors of the dense instructions when every shot runs the
+    whole stream.  On-chip executors: FP arithmetic (FLOPs counted per
+    amplitude: PromoteRot 4, diagonal rotation 6, pair rotation 10, diagonal
+    measurement 5, pair measurement 13, at two FLOPs per FMA) and
+    shared-memory traffic (each instruction reads and writes its vector);
+    vectors beyond shared memory: the HBM bytes of the wide executor's fused
+    passes."""
+    amp = 16 if fp64 else 8
+    in_hbm = (1 << info["k_max"]) * amp > 200 * 1024
+    if in_hbm:
+        b = info["wide_amp_traffic"][1 if fp64 else 0] * amp
+        return {"where": "hbm", "bytes_per_shot": b, "floor_s_per_shot": b / (peaks["hbm_gbs"] * 1e9)}
+    fl = info["dense_flops"]
+    fma = peaks["fp64_fma_per_s"] if fp64 else peaks["fp32_fma_per_s"]
+    t_fp = fl / (2.0 * fma)
+    sm = info["dense_amp_traffic"] * amp
+    t_sm = sm / peaks["smem_bytes_per_s"]
+    return {"where": "on-chip", "flops_per_shot": fl, "smem_bytes_per_shot": sm,
+            "fp_floor_s_per_shot": t_fp, "smem_floor_s_per_shot": t_sm,
+            "floor_s_per_shot": max(t_fp, t_sm), "bound": "fp" if t_fp >= t_sm else "smem"}
+
+
+def _time_call(S, torch, dev, stream, plan, shots, seed0, steps, warmup, **kw):
+    info = plan.info
+    W = (shots + 63) // 64
+    meas = torch.empty((max(1, info["n_records"]), W), dtype=torch.int64, device=dev)
+    det = torch.empty((max(1, info["n_dets"]), W), dtype=torch.int64, device=dev)
+    obs = torch.empty((max(1, info["n_obs"]), W), dtype=torch.int64, device=dev)
+    disc = torch.empty((W,), dtype=torch.int64, device=dev)
+
+    def step(i):
+        S.symft_sample_ex(plan, shots, seed0 + i, meas_out=meas, det_out=det, obs_out=obs,
+                          discard_out=disc, stream=stream, **kw)
+    for i in range(warmup):
+        step(i)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        step(warmup + i)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    import numpy as np
+    words = disc.cpu().numpy().view(np.uint64)
+    return {"shots_per_step": shots, "ms_per_step": ms, "shots_per_s": shots / (ms / 1e3),
+            "discard_rate": int(np.bitwise_count(words).sum()) / shots,
+            "launches_per_step": S.symft_last_launch_count()}
+
+
+def measure_near_clifford(S, torch, dev, stream, steps, warmup, peaks, scale=1.0, only=None):
+    """Attempted shots/s per near-Clifford config: FP32-batched, FP64-batched
+    and the paper's GPU design in FP64 (one CTA per shot, in-kernel sampling
+    or the packed-column prepass; the faster of the two is the FP64-plain
+    figure, as the paper's backend picks per circuit).  Roofline: the dense
+    floor of a full shot against the FP32-batched run without postselection,
+    where every shot runs the whole instruction stream."""
     out = {}
-    peak, peak_kind = _peaks()
     for name, (kind, post, shots0) in NEAR_CLIFFORD.items():
         if only is not None and name != only:
             continue
-        plan = S.symft_compile(_near_clifford_text(kind), postselect=post)
+        text = _near_clifford_text(kind)
+        plan = S.symft_compile(text, postselect=post)
         info = plan.info
         entry = {"k_max": info["k_max"], "n_qubits": info["n_qubits"],
                  "dense_instructions": sum(info["n_instr"][k] for k in
                                            ("PromoteRot", "ActiveDiagRot", "ActivePairRot",
                                             "ActiveDiagMeas", "ActivePairMeas")),
-                 "postselect": bool(post)}
+                 "postselect": bool(post), "simplified": info["simplified"]}
         # per-shot work of the widest configs is large: fewer repetitions
         st_w, st_n = (1, 1) if shots0 < 1000 else (warmup, steps)
-        for mode, prec, plain in (("fp32_batched", S.FP32, False), ("fp64_batched", S.FP64, False),
-                                  ("fp64_plain", S.FP64, True)):
-            shots = max(128, int(shots0 * scale * (0.1 if plain else 1.0)))
-            W = (shots + 63) // 64
-            meas = torch.empty((max(1, info["n_records"]), W), dtype=torch.int64, device=dev)
-            det = torch.empty((max(1, info["n_dets"]), W), dtype=torch.int64, device=dev)
-            obs = torch.empty((max(1, info["n_obs"]), W), dtype=torch.int64, device=dev)
-            disc = torch.empty((W,), dtype=torch.int64, device=dev)
-
-            def step(i):
-                S.symft_sample_ex(plan, shots, 100 + i, meas_out=meas, det_out=det, obs_out=obs,
-                                  discard_out=disc, precision=prec, plain=plain, stream=stream)
+        modes = (("fp32_batched", S.FP32, S.PLAIN_OFF, 1.0), ("fp64_batched", S.FP64, S.PLAIN_OFF, 1.0),
+                 ("fp64_plain_in_kernel", S.FP64, S.PLAIN_IN_KERNEL, 0.1),
+                 ("fp64_plain_prepass", S.FP64, S.PLAIN_PREPASS, 0.1))
+        for mode, prec, plain, frac in modes:
+            shots = max(128, int(shots0 * scale * frac))
             try:
-                for i in range(st_w):
-                    step(i)
+                entry[mode] = _time_call(S, torch, dev, stream, plan, shots, 100, st_n, st_w,
+                                         precision=prec, plain=plain)
             except S.SymftError as e:
                 entry[mode] = {"unavailable": str(e)}
-                continue
-            torch.cuda.synchronize(dev)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for i in range(st_n):
-                step(st_w + i)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            ms = e0.elapsed_time(e1) / st_n
-            import numpy as np
-            words = disc.cpu().numpy().view(np.uint64)
-            entry[mode] = {"shots_per_step": shots, "ms_per_step": ms,
-                           "shots_per_s": shots / (ms / 1e3),
-                           "discard_rate": int(np.bitwise_count(words).sum()) / shots,
-                           "launches_per_step": S.symft_last_launch_count()}
-        entry["fp32_vs_fp64"] = fp32_accuracy(S, torch, plan, dev, stream, shots=min(1 << 16, shots0))
-        # vector traffic of the dense instructions as streaming passes; in HBM
-        # when the vector exceeds shared memory (wide executor)
-        amps = info["dense_amp_traffic"]
-        vt = {}
-        for mode, amp_bytes in (("fp32_batched", 8), ("fp64_batched", 16)):
-            sps = entry.get(mode, {}).get("shots_per_s")
-            if sps and amps:
-                in_hbm = (1 << info["k_max"]) * amp_bytes > 200 * 1024
-                gbs = sps * amps * amp_bytes / 1e9
-                vt[mode] = {"bytes_per_shot": amps * amp_bytes, "achieved_GBps": gbs,
-                            "where": "hbm" if in_hbm else "on-chip",
-                            "frac_of_hbm": gbs / peak if in_hbm else None}
-        entry["vector_traffic"] = vt
-        if "shots_per_s" in entry.get("fp64_plain", {}) and "shots_per_s" in entry.get("fp32_batched", {}):
-            entry["fp32_batched_over_fp64_plain"] = (entry["fp32_batched"]["shots_per_s"] /
-                                                     entry["fp64_plain"]["shots_per_s"])
+        plains = [entry[m] for m in ("fp64_plain_in_kernel", "fp64_plain_prepass") if "shots_per_s" in entry[m]]
+        if plains:
+            best = max(plains, key=lambda d: d["shots_per_s"])
+            entry["fp64_plain"] = {"shots_per_s": best["shots_per_s"],
+                                   "form": "prepass" if best is entry["fp64_plain_prepass"] else "in_kernel"}
+            entry["fp32_batched_over_fp64_plain"] = entry["fp32_batched"]["shots_per_s"] / best["shots_per_s"]
+        if "shots_per_s" in entry["fp64_batched"]:
+            entry["fp32_batched_over_fp64_batched"] = (entry["fp32_batched"]["shots_per_s"] /
+                                                      entry["fp64_batched"]["shots_per_s"])
+        entry["gpu_fp32_vs_gpu_fp64"] = fp32_accuracy(S, torch, plan, dev, stream, shots=min(1 << 16, shots0))
+        # roofline of the FP32-batched path: every shot runs the whole stream
+        if info["k_max"] > 0:
+            fl = dense_floor(info, peaks)
+            plan0 = S.symft_compile(text, postselect=0) if post else plan
+            rshots = max(128, int(shots0 * scale)) if shots0 >= 1000 else max(32, shots0 // 2)
+            run = _time_call(S, torch, dev, stream, plan0, rshots, 500, st_n, st_w, precision=S.FP32)
+            t_shot = run["ms_per_step"] / 1e3 / rshots
+            fl["no_postselect_shots_per_s"] = run["shots_per_s"]
+            fl["frac"] = fl["floor_s_per_shot"] / t_shot
+            fl["note"] = ("floor of the dense instructions alone, against the whole step (sign "
+                          "kernel, executor, finalize): a lower bound on the executor's own fraction")
+            entry["roofline"] = fl
         out[name] = entry
     return out
 
 
 def measure_mixed_batch(S, torch, dev, stream, steps, warmup, n_circuits=64, target_ms=2.0):
-    """64 mixed circuits (k_max <= 20): autotuned FP32 jobs in one graph launch per step,
-    against untuned sequential FP64 runs (plain form where it fits, batched form)."""
-    import numpy as np
+    """64 mixed circuits (k_max <= 20): autotuned FP32 jobs in one graph launch per
+    step, against untuned sequential FP64 calls: the paper's GPU design (one CTA
+    per shot, the faster of its two forms per circuit) on the circuits whose
+    vectors fit its shared memory, and the batched FP64 path on all.  Ratios are
+    taken over the same circuits."""
     from paper_2607_28600_b300.workloads import mixed_batch
-    plans, names = [], []
+    plans, texts = [], []
     for name, text, post in mixed_batch(seed=1, n=4 * n_circuits):
         pl = S.symft_compile(text, postselect=post)
         if pl.info["k_max"] > 20:
             continue
         plans.append(pl)
-        names.append(name)
+        texts.append((text, post))
         if len(plans) == n_circuits:
             break
     t0 = time.perf_counter()
+    tuned = []
     for pl in plans:
         k = pl.info["k_max"]
         S.symft_autotune(pl, int(min(65536, max(256, (1 << 22) >> k))), S.FP32, stream=stream)
+        tuned.append(pl.refresh_info()["tuned_ns_per_shot"][0])
     tune_s = time.perf_counter() - t0
-    shots = []
-    for pl in plans:
-        ns = max(pl.refresh_info()["tuned_ns_per_shot"][0], 1e-3)
-        shots.append(int(min(10_000_000, max(128, (target_ms * 1e6 / ns) // 128 * 128))))
+    shots = [int(min(10_000_000, max(128, (target_ms * 1e6 / max(ns, 1e-3)) // 128 * 128))) for ns in tuned]
     outs = []
     for pl, n in zip(plans, shots):
         W = (n + 63) // 64
@@ -386,50 +437,155 @@ def measure_mixed_batch(S, torch, dev, stream, steps, warmup, n_circuits=64, tar
         outs.append({"meas_out": mk(info["n_records"]), "det_out": mk(info["n_dets"]),
                      "obs_out": mk(info["n_obs"]),
                      "discard_out": torch.empty((W,), dtype=torch.int64, device=dev)})
-
-    def jobs_for(step, precision=S.FP32, plain=False):
-        return [{"plan": i, "shots": n, "seed": 1000 * step + i, "precision": precision,
-                 "plain": plain, **o} for i, (n, o) in enumerate(zip(shots, outs))]
-    for w in range(warmup):
-        S.symft_sample_batch(plans, jobs_for(w), stream=stream)
-    torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for st in range(steps):
-        S.symft_sample_batch(plans, jobs_for(warmup + st), stream=stream)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms_batch = e0.elapsed_time(e1) / steps
-    total = sum(shots)
+
+    def graph_ms(idx, step0):
+        sub = [plans[i] for i in idx]
+        jobs = lambda st: [{"plan": j, "shots": shots[i], "seed": 1000 * st + i, "precision": S.FP32,
+                            **outs[i]} for j, i in enumerate(idx)]
+        for w in range(warmup):
+            S.symft_sample_batch(sub, jobs(step0 + w), stream=stream)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for st in range(steps):
+            S.symft_sample_batch(sub, jobs(step0 + warmup + st), stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / steps, S.symft_last_launch_count()
+
+    all_idx = list(range(len(plans)))
+    ms_all, launches = graph_ms(all_idx, 0)
+    # untuned FP64 on fresh plans, one call per circuit, each timed on its own
+    fresh = [S.symft_compile(t, postselect=post) for t, post in texts]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in fresh]
+
+    def per_circuit_ms(**kw):
+        res = []
+        for (a, b), pl, n, o in zip(ev, fresh, shots, outs):
+            try:
+                S.symft_sample_ex(pl, n, 7, precision=S.FP64, stream=stream, **kw, **o)   # warm-up
+                a.record(stream)
+                S.symft_sample_ex(pl, n, 8, precision=S.FP64, stream=stream, **kw, **o)
+                b.record(stream)
+                res.append((a, b))
+            except S.SymftError:
+                res.append(None)
+        torch.cuda.synchronize(dev)
+        return [None if r is None else r[0].elapsed_time(r[1]) for r in res]
+    plain_ik = per_circuit_ms(plain=S.PLAIN_IN_KERNEL)
+    plain_pp = per_circuit_ms(plain=S.PLAIN_PREPASS)
+    batched64 = per_circuit_ms(plain=S.PLAIN_OFF)
+    plain_best = [min([x for x in (a, b) if x is not None]) if (a is not None or b is not None) else None
+                  for a, b in zip(plain_ik, plain_pp)]
+    fits = [i for i in all_idx if plain_best[i] is not None]
+    ms_fits, _ = graph_ms(fits, 100)
+    total, total_fits = sum(shots), sum(shots[i] for i in fits)
     res = {"n_circuits": len(plans), "total_shots_per_step": total,
            "k_max_hist": {str(k): sum(1 for p in plans if p.info["k_max"] == k)
                           for k in sorted(set(p.info["k_max"] for p in plans))},
            "autotune_s": tune_s,
-           "fp32_autotuned_graph": {"ms_per_step": ms_batch, "shots_per_s": total / (ms_batch / 1e3),
-                                    "kernel_launches_per_step": S.symft_last_launch_count(),
-                                    "graph_launches_per_step": 1}}
-    # untuned FP64, sequential calls on fresh plans (no autotuning)
-    fresh = [S.symft_compile(t, postselect=post) for name, t, post in mixed_batch(seed=1, n=4 * n_circuits)
-             if name in set(names)]
-    for label, plain in (("fp64_plain_untuned", True), ("fp64_batched_untuned", False)):
-        ok_shots, skipped = 0, 0
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        for pl, n, o in zip(fresh, shots, outs):
-            try:
-                S.symft_sample_ex(pl, n, 7, precision=S.FP64, plain=plain, stream=stream, **o)
-                ok_shots += n
-            except S.SymftError:
-                skipped += 1
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1)
-        res[label] = {"ms": ms, "shots": ok_shots, "circuits_skipped": skipped,
-                      "shots_per_s": ok_shots / (ms / 1e3) if ms > 0 else None}
-    if res["fp64_plain_untuned"]["shots_per_s"]:
-        res["fp32_autotuned_over_fp64_plain"] = (res["fp32_autotuned_graph"]["shots_per_s"] /
-                                                 res["fp64_plain_untuned"]["shots_per_s"])
+           "fp32_autotuned_graph": {"ms_per_step": ms_all, "shots_per_s": total / (ms_all / 1e3),
+                                    "kernel_launches_per_step": launches, "graph_launches_per_step": 1},
+           "fp64_batched_untuned": {"ms": sum(batched64), "shots_per_s": total / (sum(batched64) / 1e3)},
+           "fits_plain_design": {
+               "n_circuits": len(fits), "shots_per_step": total_fits,
+               "fp32_autotuned_graph_ms": ms_fits,
+               "fp64_plain_best_form_untuned_ms": sum(plain_best[i] for i in fits),
+               "fp64_batched_untuned_ms": sum(batched64[i] for i in fits),
+               "plain_form_chosen": {"in_kernel": sum(1 for i in fits if plain_ik[i] is not None and
+                                                      plain_ik[i] == plain_best[i]),
+                                     "prepass": sum(1 for i in fits if plain_ik[i] is None or
+                                                    plain_ik[i] != plain_best[i])}}}
+    # each circuit: the tuner's executor, its tuned time per shot and the dense
+    # floor of a full shot (on-chip FP / shared memory, or HBM for wide vectors)
+    peaks = all_peaks(S)
+    circ = []
+    for pl, ns in zip(plans, tuned):
+        info = pl.refresh_info()
+        row = {"k_max": info["k_max"], "executor": info["dense_executor"][0],
+               "tuned_ns_per_shot": ns, "shots": shots[plans.index(pl)]}
+        if info["k_max"] > 0:
+            fl = dense_floor(info, peaks)
+            row["dense_floor_ns_per_shot"] = fl["floor_s_per_shot"] * 1e9
+            row["frac_of_tuned_time"] = fl["floor_s_per_shot"] * 1e9 / max(ns, 1e-9)
+            row["bound"] = fl.get("bound", fl["where"])
+        circ.append(row)
+    res["per_circuit"] = circ
+    res["executors"] = {k: sum(1 for r in circ if r["executor"] == k) for k in sorted(set(r["executor"] for r in circ))}
+    # graph launch overhead: the same graph with 64 shots per job
+    tiny = [{"plan": i, "shots": 64, "seed": 5 + i, "precision": S.FP32, **outs[i]} for i in all_idx]
+    for _ in range(2):
+        S.symft_sample_batch(plans, tiny, stream=stream)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(5):
+        S.symft_sample_batch(plans, tiny, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    res["graph_with_64_shots_per_job_ms"] = e0.elapsed_time(e1) / 5
+    res["graph_overhead_share"] = res["graph_with_64_shots_per_job_ms"] / ms_all
+    f = res["fits_plain_design"]
+    f["fp32_autotuned_over_fp64_plain"] = f["fp64_plain_best_form_untuned_ms"] / ms_fits
+    f["fp32_autotuned_over_fp64_batched"] = f["fp64_batched_untuned_ms"] / ms_fits
+    res["fp32_autotuned_over_fp64_batched_all"] = sum(batched64) / ms_all
     return res
+
+
+def _pinned_worker(args):
+    """Tableau oracle pinned to one host core for about budget_s (a child process)."""
+    core, budget_s = args
+    os.sched_setaffinity(0, {core})
+    _oracle_worker_init()
+    n, lo = 0, 0
+    _oracle_chunk((0, 8))
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        n += _oracle_chunk((lo, lo + 64))
+        lo += 64
+    return n, time.perf_counter() - t0
+
+
+def _symft_oracle_worker(args):
+    """Plain SymFT oracle (FP64, one shot at a time) on the cultivation-shaped
+    circuit, pinned to one core, for about budget_s."""
+    core, budget_s = args
+    os.sched_setaffinity(0, {core})
+    from oracle import symft as osymft
+    from oracle.circuit import parse
+    from oracle.noise import NoiseSampler
+    text = _near_clifford_text("cultivation")
+    c = parse(text)
+    plan = osymft.Plan(c)
+    noise = NoiseSampler(c, 1)
+    osymft.sample_shot(plan, 1, 0, noise)
+    n = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        osymft.sample_shot(plan, 1, n, noise)
+        n += 1
+    return n, time.perf_counter() - t0
+
+
+def cpu_baselines(budget_s=8.0):
+    """The oracle as it stands on the host cores: the tableau sampler on every
+    core (the headline workload), the same on one pinned core, and the plain
+    SymFT interpreter on one pinned core for the cultivation-shaped circuit."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    out = {"all_cores": cpu_baseline(budget_s)}
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(1) as pool:
+        n, dt = pool.map(_pinned_worker, [(0, budget_s)])[0]
+    out["one_core"] = {"value": n / dt, "unit": "shots/s", "cores": 1, "kind": "oracle",
+                       "sample": f"{n} shots of {HEADLINE} through the tableau oracle pinned to core 0 "
+                                 f"in {dt:.1f} s"}
+    with ctx.Pool(1) as pool:
+        n, dt = pool.map(_symft_oracle_worker, [(0, budget_s)])[0]
+    out["near_clifford_one_core"] = {
+        "value": n / dt, "unit": "shots/s", "cores": 1, "kind": "oracle",
+        "sample": f"{n} shots of the cultivation-shaped circuit (c3, FP64) through the plain "
+                  f"SymFT oracle pinned to core 0 in {dt:.1f} s; host has {cores} cores"}
+    return out
 
 
 def main():
@@ -470,6 +626,7 @@ def main():
             res = measure_mixed_batch(S, torch, dev, stream, steps=args.steps, warmup=args.warmup)
         else:
             res = measure_near_clifford(S, torch, dev, stream, steps=args.steps, warmup=args.warmup,
+                                        peaks=all_peaks(S),
                                         only=None if args.only == "near_clifford" else args.only)
         if rank == 0:
             print(json.dumps({args.only: res}), flush=True)
@@ -523,28 +680,20 @@ def main():
             "n_channels": info["n_channels"], "n_records": info["n_records"],
             "n_dets": info["n_dets"],
         }
-        # the same circuit through the plain form (one CTA per shot), on fewer shots
-        pshots = max(128, shots // 20)
-        pW = (pshots + 63) // 64
-        pm = torch.empty((info["n_records"], pW), dtype=torch.int64, device=dev)
-        pd = torch.empty((info["n_dets"], pW), dtype=torch.int64, device=dev)
-        po = torch.empty((info["n_obs"], pW), dtype=torch.int64, device=dev)
-        for i in range(2):
-            S.symft_sample_ex(plan, pshots, 5 + i, meas_out=pm, det_out=pd, obs_out=po,
-                              precision=S.FP64, plain=True, stream=stream)
-        pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        psteps = 3
-        pe0.record(stream)
-        for i in range(psteps):
-            S.symft_sample_ex(plan, pshots, 50 + i, meas_out=pm, det_out=pd, obs_out=po,
-                              precision=S.FP64, plain=True, stream=stream)
-        pe1.record(stream)
-        torch.cuda.synchronize(dev)
-        pms = pe0.elapsed_time(pe1) / psteps
-        per_circuit[name]["fp64_plain"] = {"shots_per_step": pshots, "ms_per_step": pms,
-                                           "shots_per_s": pshots / (pms / 1e3)}
-        per_circuit[name]["batched_over_plain"] = per_circuit[name]["shots_per_s"] / (pshots / (pms / 1e3))
-        del pm, pd, po
+        # the same circuit through the paper's GPU design in FP64: in-kernel
+        # sampling (one CTA per shot, fewer shots) and the packed-column prepass;
+        # the faster form is the FP64-plain figure
+        pin = _time_call(S, torch, dev, stream, plan, max(128, shots // 20), 50, 3, 2,
+                         precision=S.FP64, plain=S.PLAIN_IN_KERNEL)
+        ppp = _time_call(S, torch, dev, stream, plan, shots, 60, 3, 2,
+                         precision=S.FP64, plain=S.PLAIN_PREPASS)
+        best = pin if pin["shots_per_s"] >= ppp["shots_per_s"] else ppp
+        per_circuit[name]["fp64_plain_in_kernel"] = pin
+        per_circuit[name]["fp64_plain_prepass"] = ppp
+        per_circuit[name]["fp64_plain"] = {"shots_per_s": best["shots_per_s"],
+                                           "form": "in_kernel" if best is pin else "prepass"}
+        per_circuit[name]["batched_over_plain"] = per_circuit[name]["shots_per_s"] / best["shots_per_s"]
+        per_circuit[name]["batched_over_plain_in_kernel"] = per_circuit[name]["shots_per_s"] / pin["shots_per_s"]
         if name == HEADLINE:
             headline = dict(plan=plan, info=info, clk=clk.summary(), t_host=t_host,
                             kernel_ms=kernel_ms, out_bytes=out_bytes, ms_step=ms_step,
@@ -577,8 +726,25 @@ def main():
 
     if rank != 0:
         return
-    peak, peak_kind = _peaks()
+    peaks = all_peaks(S)
+    peak, peak_kind = peaks["hbm_gbs"], peaks["hbm_kind"]
     achieved = h["out_bytes"] / (h["kernel_ms"] / 1e3) / 1e9
+    # integer work of the same launch (plan model) against the measured Philox
+    # and LOP3 rates: the time those pipes need at their peaks
+    sm = info["sign_model"]
+    blocks = (shots + 511) // 512
+    ks = h["kernel_ms"] / 1e3
+    t_philox = blocks * sm["philox_blocks_per_block"] / peaks["philox_blocks_per_s"]
+    t_xor = blocks * sm["xor_ops_per_block"] / peaks["int32_lop3_per_s"]
+    t_hbm = h["out_bytes"] / (peak * 1e9)
+    alu = {"philox_blocks_per_launch": blocks * sm["philox_blocks_per_block"],
+           "achieved_philox_blocks_per_s": blocks * sm["philox_blocks_per_block"] / ks,
+           "peak_philox_blocks_per_s": peaks["philox_blocks_per_s"],
+           "xor_ops_per_launch": blocks * sm["xor_ops_per_block"],
+           "peak_lop3_per_s": peaks["int32_lop3_per_s"],
+           "floor_ms": max(t_philox, t_xor) * 1e3, "frac": max(t_philox, t_xor) / ks,
+           "philox_floor_ms": t_philox * 1e3, "xor_floor_ms": t_xor * 1e3,
+           "peak_kind": "measured now (symft_measure_peaks)"}
     line = {
         "metric": METRIC,
         "value": world * shots / (h["ms_step"] / 1e3),
@@ -598,20 +764,25 @@ def main():
                          % (h["out_bytes"] / 1e6),
                    "parallelism": f"shot ranges x{world}"},
         "per_circuit": per_circuit,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "roofline": {"bound": "hbm" if t_hbm >= max(t_philox, t_xor) else "alu",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": _sign_traffic() if shots == SHOTS else None,
                      "kernel": "sign_kernel", "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_launch": h["out_bytes"]},
+                     "algorithmic_bytes_per_launch": h["out_bytes"], "hbm_floor_ms": t_hbm * 1e3,
+                     "alu": alu},
+        "peaks": {k: v for k, v in peaks.items()},
         "e2e": {"value": e2e_val, "unit": "shots/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": h["out_bytes"]},
         "gpu_launches": h["launches"] * args.steps,
         "clocks": h["clk"],
     }
     if not args.no_near_clifford and world == 1:
-        line["near_clifford"] = measure_near_clifford(S, torch, dev, stream, steps=5, warmup=3)
+        line["near_clifford"] = measure_near_clifford(S, torch, dev, stream, steps=5, warmup=3, peaks=peaks)
         line["mixed_batch"] = measure_mixed_batch(S, torch, dev, stream, steps=5, warmup=3)
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline()
+        cb = cpu_baselines()
+        line["cpu_baseline"] = cb["all_cores"]
+        line["cpu_baselines"] = cb
     print(json.dumps(line), flush=True)
 
 

@@ -64,6 +64,13 @@ typedef enum {
 enum { SYMFT_POSTSELECT_NONE = 0, SYMFT_POSTSELECT_ALL = 1, SYMFT_POSTSELECT_LISTED = 2 };
 enum { SYMFT_FP32 = 0, SYMFT_FP64 = 1 };
 enum { SYMFT_OUT_DEVICE = 0, SYMFT_OUT_HOST = 1 };
+/* Comparison forms of the paper's own GPU design (Sec. 6, GPU acceleration):
+ * one CTA per shot with the shot's vector in shared memory, either sampling
+ * the exogenous variables and evaluating every affine sign inside the shot's
+ * CTA (IN_KERNEL), or reading them from packed columns that a separate
+ * device-side pass computed for all shots (PREPASS: the bit-packed sign
+ * kernel).  OFF is this library's batched executor choice. */
+enum { SYMFT_PLAIN_OFF = 0, SYMFT_PLAIN_IN_KERNEL = 1, SYMFT_PLAIN_PREPASS = 2 };
 
 typedef struct symft_plan symft_plan;   /* opaque; immutable after compile */
 
@@ -108,6 +115,30 @@ typedef struct {
                                   PromoteRot 3 * 2^k, measurement 2^k + 1.5 * 2^k);
                                   times 8 B (FP32) or 16 B (FP64) = vector bytes
                                   per shot when vectors live in HBM */
+  uint64_t dense_flops;       /* floating-point operations per shot of the dense
+                                 instructions (per amplitude: PromoteRot 4,
+                                 ActiveDiagRot 6, ActivePairRot 10,
+                                 ActiveDiagMeas 5, ActivePairMeas 13) */
+  uint64_t wide_amp_traffic[2];/* amplitudes one shot moves through HBM when its
+                                 vector lives there (the wide executor: runs of
+                                 rotations fused into one pass per shared-memory
+                                 tile, one pass per other rotation, sums and
+                                 compaction per measurement), for FP32 and FP64
+                                 tiles; times 8 B or 16 B = HBM bytes per shot */
+  uint32_t dense_executor[2]; /* dense executor a call at FP32 / FP64 uses: 1
+                                 register-resident warp per shot (k <= 5), 2 warp
+                                 per shot with the vector in shared memory, 3 CTA
+                                 per shot with the vector in shared memory, 4 wide
+                                 (vectors in HBM, instruction-major passes); the
+                                 smallest that fits unless symft_autotune chose
+                                 another; 0 without dense instructions */
+  double sign_model[3];       /* algorithmic integer work of the bit-packed sign
+                                 path per noise block of SYMFT_SHOT_ALIGN shots:
+                                 [0] Philox4x32-10 blocks (head draws, the tail
+                                 draws of the expected fires, random-measurement
+                                 words), [1] expected noise fires, [2] 32-bit XOR
+                                 operations (fired targets, random-measurement
+                                 sources, record parents and output gathers) */
   uint32_t simplified[3];     /* commutation-aware simplification (Sec. 6):
                                  rotations merged into an earlier same-body
                                  rotation, merged rotations removed (angle a
@@ -128,8 +159,11 @@ typedef struct {
   int precision;           /* SYMFT_FP32 (default) or SYMFT_FP64 dense vectors */
   int out_location;        /* SYMFT_OUT_DEVICE (default) or SYMFT_OUT_HOST */
   int check;               /* non-zero: synchronise and read the device status */
-  int plain;               /* non-zero: per-shot unpacked evaluation, one CTA per shot
-                              (the paper's GPU design, kept for comparison; same bits) */
+  int plain;               /* SYMFT_PLAIN_*: the paper's GPU design, kept for
+                              comparison (same bits): IN_KERNEL = per-shot
+                              unpacked evaluation, one CTA per shot; PREPASS =
+                              packed exogenous columns, then one CTA per shot;
+                              a vector beyond shared memory is SYMFT_E_CAPACITY */
   void* stream;            /* cudaStream_t (NULL: legacy default stream) */
   double* prob_out;        /* n_causal * shots doubles, [j * shots + r]: Pr(m = 0)
                               of active measurement j (plan order) in shot r as
@@ -154,7 +188,7 @@ typedef struct {
   uint64_t* obs_out;
   uint64_t* discard_out;
   int precision;           /* SYMFT_FP32 / SYMFT_FP64 */
-  int plain;               /* per-shot plain form */
+  int plain;               /* SYMFT_PLAIN_* comparison form */
   uint64_t* counts_out;    /* DEVICE, 2 + n_obs words as in symft_sample_args */
 } symft_job;
 
@@ -212,7 +246,8 @@ int symft_sample(const symft_plan* plan, uint64_t shots, uint64_t seed,
 int symft_sample_ex(const symft_plan* plan, const symft_sample_args* args);
 
 /* Pick the plan's launch shapes for one precision by timing candidates
- * (resident sign-kernel CTAs per SM, executor grid sizes, warps per CTA) on
+ * (the dense executor kind among those that fit, resident sign-kernel CTAs
+ * per SM, executor grid sizes, warps per CTA) on
  * `shots` shots with throw-away outputs; later calls on the plan use the
  * winner.  Runs synchronously on `cuda_stream`; allocates probe buffers. */
 int symft_autotune(symft_plan* plan, uint64_t shots, int precision, void* cuda_stream);

@@ -19,6 +19,7 @@ SHOT_ALIGN = 512          # SYMFT_SHOT_ALIGN: shot offsets are multiples of this
 POSTSELECT_NONE, POSTSELECT_ALL, POSTSELECT_LISTED = 0, 1, 2
 FP32, FP64 = 0, 1
 OUT_DEVICE, OUT_HOST = 0, 1
+PLAIN_OFF, PLAIN_IN_KERNEL, PLAIN_PREPASS = 0, 1, 2
 INSTR_NAMES = ("PromoteRot", "ActiveDiagRot", "ActivePairRot", "RandomMeas", "DetMeas",
                "ActiveDiagMeas", "ActivePairMeas")
 
@@ -48,7 +49,10 @@ class _Info(ctypes.Structure):
                 ("max_expr_weight", ctypes.c_uint32), ("n_noise_components", ctypes.c_uint32),
                 ("n_targets", ctypes.c_uint32), ("n_causal", ctypes.c_uint32),
                 ("sign_xor_terms", ctypes.c_uint64), ("tuned_ns_per_shot", ctypes.c_float * 2),
-                ("dense_amp_traffic", ctypes.c_uint64), ("simplified", ctypes.c_uint32 * 3)]
+                ("dense_amp_traffic", ctypes.c_uint64), ("dense_flops", ctypes.c_uint64),
+                ("wide_amp_traffic", ctypes.c_uint64 * 2),
+                ("dense_executor", ctypes.c_uint32 * 2), ("sign_model", ctypes.c_double * 3),
+                ("simplified", ctypes.c_uint32 * 3)]
 
 
 class _SampleArgs(ctypes.Structure):
@@ -204,7 +208,14 @@ def symft_plan_info(plan: Plan) -> dict:
     info = _Info()
     _check(lib().symft_plan_info(plan.handle, ctypes.byref(info)))
     d = {name: getattr(info, name) for name, _ in _Info._fields_
-         if name not in ("n_instr", "tuned_ns_per_shot", "simplified")}
+         if name not in ("n_instr", "tuned_ns_per_shot", "simplified", "wide_amp_traffic", "sign_model",
+                         "dense_executor")}
+    kinds = {0: "none", 1: "register", 2: "warp", 3: "cta", 4: "wide"}
+    d["dense_executor"] = [kinds.get(int(info.dense_executor[i]), "?") for i in range(2)]
+    d["sign_model"] = {"philox_blocks_per_block": float(info.sign_model[0]),
+                       "fires_per_block": float(info.sign_model[1]),
+                       "xor_ops_per_block": float(info.sign_model[2])}
+    d["wide_amp_traffic"] = [int(info.wide_amp_traffic[0]), int(info.wide_amp_traffic[1])]
     d["simplified"] = {"fused": int(info.simplified[0]), "cancelled": int(info.simplified[1]),
                        "branch_phase": int(info.simplified[2])}
     d["tuned_ns_per_shot"] = [float(info.tuned_ns_per_shot[0]), float(info.tuned_ns_per_shot[1])]
@@ -230,13 +241,13 @@ def symft_sample(plan: Plan, shots: int, seed: int, meas_out=None, det_out=None,
 def symft_sample_ex(plan: Plan, shots: int, seed: int, shot_offset: int = 0, meas_out=None,
                     det_out=None, obs_out=None, discard_out=None, precision: int = FP32,
                     out_location: int = OUT_DEVICE, check: bool = False, stream=None,
-                    plain: bool = False, prob_out=None, counts_out=None) -> None:
+                    plain: int = PLAIN_OFF, prob_out=None, counts_out=None) -> None:
     a = _SampleArgs()
     a.shots, a.seed, a.shot_offset = shots, seed, shot_offset
     a.meas_out, a.det_out = _ptr(meas_out), _ptr(det_out)
     a.obs_out, a.discard_out = _ptr(obs_out), _ptr(discard_out)
     a.precision, a.out_location, a.check = precision, out_location, int(bool(check))
-    a.plain = int(bool(plain))
+    a.plain = int(plain)
     a.stream = _stream(stream)
     a.prob_out, a.counts_out = _ptr(prob_out), _ptr(counts_out)
     _check(lib().symft_sample_ex(plan.handle, ctypes.byref(a)))
@@ -279,7 +290,7 @@ def symft_sample_batch(plans, jobs, stream=None) -> None:
         J.obs_out = _ptr(j.get("obs_out"))
         J.discard_out = _ptr(j.get("discard_out"))
         J.precision = j.get("precision", FP32)
-        J.plain = int(bool(j.get("plain", False)))
+        J.plain = int(j.get("plain", PLAIN_OFF))
         J.counts_out = _ptr(j.get("counts_out"))
     _check(lib().symft_sample_batch(arr_p, len(plans), arr_j, len(jobs), _stream(stream)))
 

@@ -304,6 +304,31 @@ cudaError_t upload(symft_plan* P) {
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Whether dense executor `kind` (1 register, 2 warp with the vector in shared
+// memory, 3 CTA with the vector in shared memory, 4 wide with vectors in HBM)
+// can run this plan at this precision.
+bool dense_kind_valid(const symft_plan* P, const HostPlan& h, bool fp64, int kind) {
+  const size_t amp = fp64 ? 16 : 8;
+  const size_t m3bytes = ((h.n_m3 + 31) / 32) * 4;
+  const size_t vec_bytes = (static_cast<size_t>(1) << h.k_max) * amp;
+  switch (kind) {
+    case 1: return h.k_max <= 5 && dense_reg_smem_bytes(P->dp) <= 96 * 1024;
+    case 2: return vec_bytes + m3bytes <= 48 * 1024 && dense_warp_smem_bytes(P->dp, 1, vec_bytes, true) <= 200 * 1024;
+    case 3: return dense_cta_smem_bytes(P->dp, vec_bytes, true) <= 200 * 1024;
+    case 4: return true;
+  }
+  return false;
+}
+
+// The executor for a plan: the tuned choice when it is valid, else the first
+// valid kind in the order register, warp, CTA, wide (smallest footprint first).
+int dense_kind_for(const symft_plan* P, const HostPlan& h, bool fp64, int tuned) {
+  if (tuned && dense_kind_valid(P, h, fp64, tuned)) return tuned;
+  for (int k = 1; k <= 4; ++k)
+    if (dense_kind_valid(P, h, fp64, k)) return k;
+  return 4;
+}
+
 // Launch shapes and workspace pointers of one sampling request.  prepare()
 // allocates and decides everything on the host; enqueue() only issues
 // memsets and kernel launches, so it can also run inside a stream capture.
@@ -342,6 +367,8 @@ int validate(const symft_sample_args* a) {
   if (a->precision != SYMFT_FP32 && a->precision != SYMFT_FP64) return set_error(SYMFT_E_ARG, "bad precision");
   if (a->out_location != SYMFT_OUT_DEVICE && a->out_location != SYMFT_OUT_HOST)
     return set_error(SYMFT_E_ARG, "bad out_location");
+  if (a->plain != SYMFT_PLAIN_OFF && a->plain != SYMFT_PLAIN_IN_KERNEL && a->plain != SYMFT_PLAIN_PREPASS)
+    return set_error(SYMFT_E_ARG, "bad plain form");
   return SYMFT_OK;
 }
 
@@ -361,7 +388,7 @@ int prepare(symft_plan* P, const symft_sample_args* a, uint64_t* meas, uint64_t*
   o->W = (a->shots + 63) / 64;
   o->shots = a->shots;
   o->nblk = (a->shots + kNoiseBlock - 1) / kNoiseBlock;
-  o->plain = a->plain != 0;
+  o->plain = a->plain == SYMFT_PLAIN_IN_KERNEL;
   o->fp64 = a->precision == SYMFT_FP64;
   const uint64_t W = o->W;
   if (h.n_records == 0) meas = nullptr;
@@ -418,12 +445,22 @@ int prepare(symft_plan* P, const symft_sample_args* a, uint64_t* meas, uint64_t*
     const size_t amp = o->fp64 ? 16 : 8;
     const size_t m3bytes = ((h.n_m3 + 31) / 32) * 4;
     const size_t vec_bytes = (static_cast<size_t>(1) << h.k_max) * amp;
-    if (h.k_max <= 5 && dense_reg_smem_bytes(P->dp) <= 96 * 1024) {
+    if (a->plain == SYMFT_PLAIN_PREPASS) {
+      // the paper's GPU design with its device-side prepass: one CTA per shot,
+      // the whole vector in shared memory, signs from the packed columns
+      if (dense_cta_smem_bytes(P->dp, vec_bytes, true) > 200 * 1024)
+        return set_error(SYMFT_E_CAPACITY, "plain prepass form: per-shot vector exceeds shared memory");
+      o->dense_kind = 3;
+      o->dense_smem = dense_cta_smem_bytes(P->dp, vec_bytes, true);
+      o->dense_use_smem = 1;
+      const uint64_t cap = static_cast<uint64_t>(P->sm_count) * 16;
+      o->dense_grid = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(a->shots, cap)));
+    } else if (dense_kind_for(P, h, o->fp64, t.dense_kind) == 1) {
       o->dense_kind = 1;   // register-resident: lane x holds amplitude x
       const uint64_t want = (a->shots + 7) / 8;
       const uint64_t cap = static_cast<uint64_t>(P->sm_count) * t.dense_grid_mult;
       o->dense_grid = static_cast<int>(std::max<uint64_t>(1, std::min(want, cap)));
-    } else if (vec_bytes + m3bytes <= 48 * 1024) {
+    } else if (dense_kind_for(P, h, o->fp64, t.dense_kind) == 2) {
       o->dense_kind = 2;   // warp per shot, vector in shared memory
       const size_t bk = dense_warp_smem_bytes(P->dp, 1, 0, false);
       int wpb = t.dense_wpb ? t.dense_wpb
@@ -435,7 +472,7 @@ int prepare(symft_plan* P, const symft_sample_args* a, uint64_t* meas, uint64_t*
       const uint64_t want = (a->shots + wpb - 1) / wpb;
       const uint64_t cap = static_cast<uint64_t>(P->sm_count) * t.dense_grid_mult * 2;
       o->dense_grid = static_cast<int>(std::max<uint64_t>(1, std::min(want, cap)));
-    } else if (dense_cta_smem_bytes(P->dp, vec_bytes, true) <= 200 * 1024) {
+    } else if (dense_kind_for(P, h, o->fp64, t.dense_kind) == 3) {
       o->dense_kind = 3;   // CTA per shot, vector in shared memory
       o->dense_smem = dense_cta_smem_bytes(P->dp, vec_bytes, true);
       o->dense_use_smem = 1;
@@ -703,6 +740,21 @@ int autotune_impl(symft_plan* P, uint64_t shots, int precision, cudaStream_t st)
     }
     t = base;
   }
+  // dense executor kind: every kind that can run the plan, default shapes
+  if (rc == SYMFT_OK && !h.dense.empty()) {
+    const bool fp64 = precision == SYMFT_FP64;
+    for (int kind = 1; kind <= 4; ++kind) {
+      if (!dense_kind_valid(P, h, fp64, kind) || kind == dense_kind_for(P, h, fp64, base.dense_kind)) continue;
+      Tune cand = base;
+      cand.dense_kind = kind;
+      t = cand;
+      float ms = 0.0f;
+      rc = time_cfg(&ms);
+      if (rc != SYMFT_OK) break;
+      if (ms < best) { best = ms; base = cand; }
+    }
+    t = base;
+  }
   // dense executor: grid size (register / warp kernels), warps per CTA, CTA slots
   if (rc == SYMFT_OK && !h.dense.empty()) {
     std::vector<Tune> cands;
@@ -922,19 +974,74 @@ int symft_plan_info(const symft_plan* p, symft_info* info) {
   info->n_targets = h.n_slots;
   info->n_causal = h.n_m3;
   info->sign_xor_terms = h.sign_xor_terms;
-  uint64_t traffic = 0;
+  uint64_t traffic = 0, flops = 0;
   for (const DenseInstr& d : h.dense) {
     const uint64_t n = 1ull << d.k;
     if (d.kind == I_PROMOTE_ROT) traffic += 3 * n;
     else if (d.kind == I_ACTIVE_DIAG_ROT || d.kind == I_ACTIVE_PAIR_ROT) traffic += 2 * n;
     else traffic += n + n + n / 2;
+    switch (d.kind) {
+      case I_PROMOTE_ROT: flops += 4 * n; break;
+      case I_ACTIVE_DIAG_ROT: flops += 6 * n; break;
+      case I_ACTIVE_PAIR_ROT: flops += 10 * n; break;
+      case I_ACTIVE_DIAG_MEAS: flops += 5 * n; break;
+      default: flops += 13 * n; break;
+    }
   }
   info->dense_amp_traffic = traffic;
+  info->dense_flops = flops;
+  // algorithmic integer work of the sign kernel per noise block (512 shots):
+  // Philox blocks the stream specification needs, expected fires, and 32-bit
+  // XOR operations (random-measurement sources, record parents and output
+  // gather terms over 16 words per slot, plus one XOR per fired target)
+  {
+    double philox = static_cast<double>(h.m1_t.size()) * (kNoiseBlock / kWordPair);
+    double fires = 0.0, xor_ops = 0.0;
+    const uint32_t n_groups = (h.n_channels + 3) / 4;
+    for (uint32_t g = 0; g < n_groups; ++g) {
+      bool live = false;
+      for (uint32_t c = 4 * g; c < std::min(h.n_channels, 4 * g + 4); ++c) live |= h.ch_theta_last[c] != 0;
+      if (live) philox += 1.0;
+    }
+    for (uint32_t c = 0; c < h.n_channels; ++c) {
+      if (h.ch_theta_last[c] == 0) continue;
+      const double q = h.qtabs[h.ch_qtab[c]].q;
+      const CellTable& ct = h.ctabs[h.ch_ctab[c]];
+      const double d = ct.ncell > 1 ? 2.0 : 1.0;            // tail draws per fire
+      // N ~ Binomial(512, q) fires; ceil(d N / 4) tail blocks
+      double pk = std::pow(1.0 - q, kNoiseBlock), tail = 0.0;
+      for (int k = 0; k <= kNoiseBlock && (k < 8 || pk > 1e-18); ++k) {
+        tail += pk * std::ceil(d * k / 4.0);
+        pk *= (static_cast<double>(kNoiseBlock - k) / (k + 1)) * (q / (1.0 - q));
+      }
+      philox += tail;
+      const double nf = kNoiseBlock * q;
+      fires += nf;
+      // mean number of target slots of a fired cell, weighted by the cell law
+      double prev = 0.0, tg = 0.0;
+      for (uint32_t k = 0; k < ct.ncell; ++k) {
+        const double hi = k + 1 < ct.ncell ? ct.phi[k] / 4294967296.0 : 1.0;
+        const uint32_t e = h.ch_cell0[c] + k;
+        tg += (hi - prev) * (h.cell_off[e + 1] - h.cell_off[e]);
+        prev = hi;
+      }
+      xor_ops += nf * tg;
+    }
+    xor_ops += 16.0 * (static_cast<double>(h.m1_tgt.size()) + h.par.size() + h.gat_rec.size());
+    info->sign_model[0] = philox;
+    info->sign_model[1] = fires;
+    info->sign_model[2] = xor_ops;
+  }
+  info->wide_amp_traffic[0] = wide_amp_traffic(p->dense_host.data(), static_cast<uint32_t>(p->dense_host.size()), false);
+  info->wide_amp_traffic[1] = wide_amp_traffic(p->dense_host.data(), static_cast<uint32_t>(p->dense_host.size()), true);
   info->simplified[0] = h.n_fused;
   info->simplified[1] = h.n_cancelled;
   info->simplified[2] = h.n_branch_phase;
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 2; ++i) {
     info->tuned_ns_per_shot[i] = p->tune[i].tuned ? p->tune[i].best_ms_per_shot * 1e6f : 0.0f;
+    info->dense_executor[i] = h.dense.empty() ? 0u
+        : static_cast<uint32_t>(dense_kind_for(p, h, i == 1, p->tune[i].dense_kind));
+  }
   return SYMFT_OK;
 }
 

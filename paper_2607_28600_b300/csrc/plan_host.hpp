@@ -57,6 +57,8 @@ cudaError_t launch_plain(const PlainArgs& a, bool fp64, int grid, cudaStream_t s
 // plan's instruction stream in host memory, for the per-instruction launches)
 cudaError_t launch_wide_batch(const WideArgs& a, const DenseInstrDev* host_dense, bool fp64, int sm_count,
                               cudaStream_t st, int* launches);
+// amplitudes one shot moves through HBM in the wide executor's passes
+uint64_t wide_amp_traffic(const DenseInstrDev* d, uint32_t G, bool fp64);
 
 // Launch shapes chosen by symft_autotune (0 = built-in heuristic).
 struct Tune {
@@ -65,6 +67,7 @@ struct Tune {
   int dense_grid_mult = 8;   // register / warp executors: CTAs per SM
   int dense_wpb = 0;         // warp executor: warps (shots) per CTA
   int cta_grid_mult = 2;     // CTA executor with global vectors: CTAs per SM
+  int dense_kind = 0;        // dense executor (1 register, 2 warp, 3 CTA, 4 wide; 0 = first that fits)
   float best_ms_per_shot = 0.0f;
 };
 

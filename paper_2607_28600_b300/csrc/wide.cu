@@ -635,6 +635,33 @@ static cudaError_t wide_batch_t(WideArgs A, const DenseInstrDev* host_dense, int
   return cudaSuccess;
 }
 
+// Amplitudes one shot moves through HBM in the passes wide_batch_t issues
+// (every shot running to the end): a fused window reads the 2^k_start
+// existing amplitudes and writes 2^k_end; a lone PromoteRot reads 2^k and
+// writes 2^(k+1), a lone diagonal or pair rotation reads and writes 2^k; a
+// measurement reads 2^k for its sums, reads up to 2^k for the compaction and
+// writes 2^(k-1).
+uint64_t wide_amp_traffic(const DenseInstrDev* d, uint32_t G, bool fp64) {
+  const uint32_t T = fp64 ? kFuseBitsF64 : kFuseBitsF32;
+  uint64_t amps = 0;
+  for (uint32_t g = 0; g < G; ++g) {
+    const uint64_t n = 1ull << d[g].k;
+    if (d[g].kind <= 2) {
+      WideFuse F;
+      const uint32_t nw = build_window(d, G, g, T, &F);
+      if (nw >= 2 && F.kend >= 5) {
+        amps += (1ull << F.kstart) + (1ull << F.kend);
+        g += nw - 1;
+      } else {
+        amps += d[g].kind == 0 ? 3 * n : 2 * n;
+      }
+    } else {
+      amps += n + n + n / 2;
+    }
+  }
+  return amps;
+}
+
 cudaError_t launch_wide_batch(const WideArgs& a, const DenseInstrDev* host_dense, bool fp64, int sm_count,
                               cudaStream_t st, int* launches) {
   return fp64 ? wide_batch_t<double>(a, host_dense, sm_count, st, launches)

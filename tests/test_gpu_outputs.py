@@ -267,8 +267,9 @@ def test_early_exit_matches_masked_full_run(which, precision):
 
 @pytest.mark.parametrize("which", ["coherent", "cultivation"])
 def test_plain_form_early_exit_matches_batched(which):
-    """The plain per-shot form also ends a rejected shot's dense work at once;
-    its FP64 outputs equal the batched FP64 path bit for bit."""
+    """Both forms of the paper's GPU design (in-kernel sampling and the
+    packed-column prepass, one CTA per shot) end a rejected shot's dense work
+    at once; their FP64 outputs equal the batched FP64 path bit for bit."""
     import paper_2607_28600_b300 as S
     from paper_2607_28600_b300.workloads import coherent_surface_code_memory, cultivation_shaped
     text = coherent_surface_code_memory(3, 3, 1e-3, 0.02) if which == "coherent" else cultivation_shaped(1e-3)
@@ -277,7 +278,7 @@ def test_plain_form_early_exit_matches_batched(which):
     shots = 2000
     W = (shots + 63) // 64
     outs = []
-    for plain in (False, True):
+    for plain in (S.PLAIN_OFF, S.PLAIN_IN_KERNEL, S.PLAIN_PREPASS):
         cols = [torch.zeros((max(1, info[k]), W), dtype=torch.int64, device="cuda")
                 for k in ("n_records", "n_dets", "n_obs")]
         disc = torch.zeros((W,), dtype=torch.int64, device="cuda")
@@ -285,6 +286,7 @@ def test_plain_form_early_exit_matches_batched(which):
                           discard_out=disc, precision=S.FP64, plain=plain, check=True)
         torch.cuda.synchronize()
         outs.append([c.cpu().numpy() for c in cols] + [disc.cpu().numpy()])
-    for a, b in zip(*outs):
-        np.testing.assert_array_equal(a, b)
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            np.testing.assert_array_equal(a, b)
     assert 0.02 < unpack(outs[1][3].view(np.uint64).reshape(1, -1), shots).mean() < 0.99
