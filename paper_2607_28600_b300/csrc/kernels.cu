@@ -306,14 +306,16 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
             branch_sums<Real, float>(vec, I, n, lane, 32, mcr, mci, S0, S1);
             warp_sum2(S0, S1);
             const uint64_t U = su.get(A, (uint32_t)I.m3, rg, lane);
-            // the renormalisation scale 1 / sqrt(S_m) in FP64 (one FP64 op per
-            // measurement, on one lane), rounded once to the vector's precision
+            // the renormalisation scale 1 / sqrt(S_m) in FP32 on one lane: every
+            // later branch probability is self-normalised, so the scale only
+            // sets the vector's overall norm (an FP64 scale measured 2.4-3x
+            // slower on B300, whose FP64 pipe is a small fraction of FP32's)
             float sc = 0.0f;
             if (lane == 0) {
               const float p0 = (l0 ? S1 : S0) / (S0 + S1);
               m = decide32(U, p0);
               if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = (double)p0;
-              sc = (float)(1.0 / sqrt((double)((l0 ^ m) ? S1 : S0)));
+              sc = rsqrtf((l0 ^ m) ? S1 : S0);
             }
             m = __shfl_sync(0xffffffffu, m, 0);
             scale = (Real)__shfl_sync(0xffffffffu, sc, 0);
@@ -501,8 +503,9 @@ __global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) 
         const uint32_t l0 = I.kind == 5 ? (lam ^ (uint32_t)I.eta) : lam;
         uint32_t m = 0;
         const uint64_t U = su.get(A, (uint32_t)I.m3, rg, lane);
-        // decision and the renormalisation scale 1 / sqrt(S_m), in FP64, on one
-        // lane; the scale is rounded once to the vector's precision
+        // decision and the renormalisation scale 1 / sqrt(S_m) on one lane, in
+        // the vector's precision (self-normalised probabilities make the scale
+        // matter only for the overall norm)
         Real sc = 0;
         if (lane == 0) {
           double pd;
@@ -515,7 +518,7 @@ __global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) 
             pd = (double)pf;
           }
           if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = pd;
-          sc = (Real)(1.0 / sqrt((double)((l0 ^ m) ? s1 : s0)));
+          sc = sizeof(Real) == 8 ? (Real)(1.0 / sqrt((double)((l0 ^ m) ? s1 : s0))) : (Real)rsqrtf((float)((l0 ^ m) ? s1 : s0));
         }
         m = __shfl_sync(0xffffffffu, m, 0);
         const uint32_t lab = l0 ^ m;
