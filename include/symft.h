@@ -88,7 +88,10 @@ typedef struct {
                               simplification before planning (Sec. 6): same
                               output distribution, possibly a wider active
                               state and more dense instructions */
-  int reserved[3];
+  int no_product_components;  /* non-zero: never use the product-component
+                              representation (Sec. 6); by default it is used
+                              when its cost model predicts a clear benefit */
+  int reserved[2];
 } symft_options;
 
 /* Counts of a compiled plan (Sec. 5, sampling complexity). */
@@ -129,9 +132,17 @@ typedef struct {
                                  register-resident warp per shot (k <= 5), 2 warp
                                  per shot with the vector in shared memory, 3 CTA
                                  per shot with the vector in shared memory, 4 wide
-                                 (vectors in HBM, instruction-major passes); the
-                                 smallest that fits unless symft_autotune chose
+                                 (vectors in HBM, instruction-major passes), 5
+                                 warp per shot on the product-component program;
+                                 the product components when selected, else the
+                                 smallest that fits, unless symft_autotune chose
                                  another; 0 without dense instructions */
+  uint32_t pc_capacity;       /* product-component representation (Sec. 6):
+                                 workspace amplitudes per shot */
+  uint32_t pc_selected;       /* 1 when its cost model selected it (at most half
+                                 the monolithic vector work, k_max > 5) */
+  uint64_t pc_work[2];        /* amplitudes touched per shot: [0] product
+                                 components (merges included), [1] monolithic */
   double sign_model[3];       /* algorithmic integer work of the bit-packed sign
                                  path per noise block of SYMFT_SHOT_ALIGN shots:
                                  [0] Philox4x32-10 blocks (head draws, the tail

@@ -37,8 +37,8 @@ class SymftError(RuntimeError):
 
 class _Options(ctypes.Structure):
     _fields_ = [("postselect", ctypes.c_int), ("n_post_dets", ctypes.c_uint32),
-                ("post_dets", ctypes.POINTER(ctypes.c_uint32)), ("no_simplify", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                 ("post_dets", ctypes.POINTER(ctypes.c_uint32)), ("no_simplify", ctypes.c_int),
+                ("no_product_components", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class _Info(ctypes.Structure):
@@ -51,7 +51,9 @@ class _Info(ctypes.Structure):
                 ("sign_xor_terms", ctypes.c_uint64), ("tuned_ns_per_shot", ctypes.c_float * 2),
                 ("dense_amp_traffic", ctypes.c_uint64), ("dense_flops", ctypes.c_uint64),
                 ("wide_amp_traffic", ctypes.c_uint64 * 2),
-                ("dense_executor", ctypes.c_uint32 * 2), ("sign_model", ctypes.c_double * 3),
+                ("dense_executor", ctypes.c_uint32 * 2), ("pc_capacity", ctypes.c_uint32),
+                ("pc_selected", ctypes.c_uint32), ("pc_work", ctypes.c_uint64 * 2),
+                ("sign_model", ctypes.c_double * 3),
                 ("simplified", ctypes.c_uint32 * 3)]
 
 
@@ -187,7 +189,7 @@ class Plan:
 
 
 def symft_compile(circuit_text: str, postselect: int = POSTSELECT_NONE, post_dets=None,
-                  simplify: bool = True) -> Plan:
+                  simplify: bool = True, product_components: bool = True) -> Plan:
     """Compile circuit text.  postselect=POSTSELECT_LISTED rejects a shot only at
     the detectors whose indices are listed in `post_dets`; simplify=False skips
     the commutation-aware simplification before planning."""
@@ -195,6 +197,7 @@ def symft_compile(circuit_text: str, postselect: int = POSTSELECT_NONE, post_det
     opt = _Options()
     opt.postselect = postselect
     opt.no_simplify = 0 if simplify else 1
+    opt.no_product_components = 0 if product_components else 1
     if post_dets is not None:
         dets = [int(d) for d in post_dets]
         arr = (ctypes.c_uint32 * max(1, len(dets)))(*dets)
@@ -209,8 +212,9 @@ def symft_plan_info(plan: Plan) -> dict:
     _check(lib().symft_plan_info(plan.handle, ctypes.byref(info)))
     d = {name: getattr(info, name) for name, _ in _Info._fields_
          if name not in ("n_instr", "tuned_ns_per_shot", "simplified", "wide_amp_traffic", "sign_model",
-                         "dense_executor")}
-    kinds = {0: "none", 1: "register", 2: "warp", 3: "cta", 4: "wide"}
+                         "dense_executor", "pc_work")}
+    d["pc_work"] = [int(info.pc_work[0]), int(info.pc_work[1])]
+    kinds = {0: "none", 1: "register", 2: "warp", 3: "cta", 4: "wide", 5: "components"}
     d["dense_executor"] = [kinds.get(int(info.dense_executor[i]), "?") for i in range(2)]
     d["sign_model"] = {"philox_blocks_per_block": float(info.sign_model[0]),
                        "fires_per_block": float(info.sign_model[1]),

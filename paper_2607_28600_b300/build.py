@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsymft.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["circuit.cpp", "compile.cpp", "api.cpp", "sign.cu", "kernels.cu", "wide.cu", "noalloc.cu",
+SOURCES = ["circuit.cpp", "compile.cpp", "components.cpp", "api.cpp", "sign.cu", "kernels.cu", "wide.cu", "noalloc.cu",
            "peaks.cu"]
 HEADERS = ["internal.hpp", "plan_dev.hpp", "plan_host.hpp", "device.cuh"]
 

@@ -214,6 +214,7 @@ void build_blob(symft_plan* P) {
   P->off.gv = push(blob, gat_ovf);
   P->off.pe = push(blob, h.post_events);
   P->off.dn = push(blob, dn);
+  P->off.pc = push(blob, h.pc.ops);
   P->off.dc = push(blob, h.dense_causal);
   P->off.plc = push(blob, h.plain_const);
   P->off.plo = push(blob, h.plain_off);
@@ -262,6 +263,9 @@ void bind_plan(const symft_plan* P, unsigned char* base, DevPlan* dptr) {
   d.post_events = reinterpret_cast<const int32_t*>(at(P->off.pe));
   d.n_dense = static_cast<uint32_t>(h.dense.size());
   d.dense = reinterpret_cast<const DenseInstrDev*>(at(P->off.dn));
+  d.n_pc = static_cast<uint32_t>(h.pc.ops.size());
+  d.pc = reinterpret_cast<const PCOp*>(at(P->off.pc));
+  d.pc_capacity = h.pc.capacity;
   d.dense_causal = reinterpret_cast<const uint32_t*>(at(P->off.dc));
   d.n_m3 = h.n_m3;
   d.n_records = h.n_records;
@@ -305,8 +309,9 @@ cudaError_t upload(symft_plan* P) {
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Whether dense executor `kind` (1 register, 2 warp with the vector in shared
-// memory, 3 CTA with the vector in shared memory, 4 wide with vectors in HBM)
-// can run this plan at this precision.
+// memory, 3 CTA with the vector in shared memory, 4 wide with vectors in HBM,
+// 5 warp running the product-component program) can run this plan at this
+// precision.
 bool dense_kind_valid(const symft_plan* P, const HostPlan& h, bool fp64, int kind) {
   const size_t amp = fp64 ? 16 : 8;
   const size_t m3bytes = ((h.n_m3 + 31) / 32) * 4;
@@ -316,14 +321,17 @@ bool dense_kind_valid(const symft_plan* P, const HostPlan& h, bool fp64, int kin
     case 2: return vec_bytes + m3bytes <= 48 * 1024 && dense_warp_smem_bytes(P->dp, 1, vec_bytes, true) <= 200 * 1024;
     case 3: return dense_cta_smem_bytes(P->dp, vec_bytes, true) <= 200 * 1024;
     case 4: return true;
+    case 5: return !h.pc.ops.empty() && h.pc.capacity <= (1u << 22);
   }
   return false;
 }
 
-// The executor for a plan: the tuned choice when it is valid, else the first
+// The executor for a plan: the tuned choice when it is valid, else the
+// product-component executor when its cost model selected it, else the first
 // valid kind in the order register, warp, CTA, wide (smallest footprint first).
 int dense_kind_for(const symft_plan* P, const HostPlan& h, bool fp64, int tuned) {
   if (tuned && dense_kind_valid(P, h, fp64, tuned)) return tuned;
+  if (h.pc.use && dense_kind_valid(P, h, fp64, 5)) return 5;
   for (int k = 1; k <= 4; ++k)
     if (dense_kind_valid(P, h, fp64, k)) return k;
   return 4;
@@ -455,6 +463,34 @@ int prepare(symft_plan* P, const symft_sample_args* a, uint64_t* meas, uint64_t*
       o->dense_use_smem = 1;
       const uint64_t cap = static_cast<uint64_t>(P->sm_count) * 16;
       o->dense_grid = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(a->shots, cap)));
+    } else if (dense_kind_for(P, h, o->fp64, t.dense_kind) == 5) {
+      // product components: one warp per shot, the component workspace in
+      // shared memory when it fits, else in a global slot per resident warp
+      o->dense_kind = 5;
+      const size_t ws_bytes = static_cast<size_t>(h.pc.capacity) * amp;
+      const size_t bk = dense_warp_smem_bytes(P->dp, 1, 0, false);
+      if (ws_bytes + m3bytes <= 48 * 1024) {
+        int wpb = t.dense_wpb ? t.dense_wpb
+                              : static_cast<int>(std::min<size_t>(8, std::max<size_t>(1, (160 * 1024) / (ws_bytes + bk + 16))));
+        while (wpb > 1 && dense_warp_smem_bytes(P->dp, wpb, ws_bytes, true) > 200 * 1024) --wpb;
+        o->dense_wpb = wpb;
+        o->dense_use_smem = 1;
+        o->dense_smem = dense_warp_smem_bytes(P->dp, wpb, ws_bytes, true);
+        const uint64_t want = (a->shots + wpb - 1) / wpb;
+        const uint64_t cap = static_cast<uint64_t>(P->sm_count) * t.dense_grid_mult * 2;
+        o->dense_grid = static_cast<int>(std::max<uint64_t>(1, std::min(want, cap)));
+      } else {
+        const int wpb = 4;
+        o->dense_wpb = wpb;
+        o->dense_use_smem = 0;
+        o->dense_smem = dense_warp_smem_bytes(P->dp, wpb, 0, false);
+        const uint64_t want = (a->shots + wpb - 1) / wpb;
+        const uint64_t cap = static_cast<uint64_t>(P->sm_count) * t.dense_grid_mult * 2;
+        o->dense_grid = static_cast<int>(std::max<uint64_t>(1, std::min(want, cap)));
+        o->gvec_stride = h.pc.capacity;
+        CUDA_TRY(P->gvec.ensure(static_cast<size_t>(o->dense_grid) * wpb * ws_bytes));
+        o->gvec = P->gvec.ptr;
+      }
     } else if (dense_kind_for(P, h, o->fp64, t.dense_kind) == 1) {
       o->dense_kind = 1;   // register-resident: lane x holds amplitude x
       const uint64_t want = (a->shots + 7) / 8;
@@ -622,6 +658,7 @@ int enqueue(symft_plan* P, const symft_sample_args* a, const Prep& o, cudaStream
       }
       --*launches;   // counted once below
     } else if (o.dense_kind == 1) CUDA_TRY(launch_dense_reg(d, o.fp64, o.dense_grid, st));
+    else if (o.dense_kind == 5) CUDA_TRY(launch_dense_pc(d, o.fp64, o.dense_wpb, o.dense_grid, o.dense_smem, st));
     else if (o.dense_kind == 2) CUDA_TRY(launch_dense(d, o.fp64, o.dense_wpb, o.dense_grid, o.dense_smem, st));
     else CUDA_TRY(launch_dense_cta(d, o.fp64, o.dense_grid, o.dense_smem, st));
     ++*launches;
@@ -743,7 +780,7 @@ int autotune_impl(symft_plan* P, uint64_t shots, int precision, cudaStream_t st)
   // dense executor kind: every kind that can run the plan, default shapes
   if (rc == SYMFT_OK && !h.dense.empty()) {
     const bool fp64 = precision == SYMFT_FP64;
-    for (int kind = 1; kind <= 4; ++kind) {
+    for (int kind = 1; kind <= 5; ++kind) {
       if (!dense_kind_valid(P, h, fp64, kind) || kind == dense_kind_for(P, h, fp64, base.dense_kind)) continue;
       Tune cand = base;
       cand.dense_kind = kind;
@@ -1034,6 +1071,10 @@ int symft_plan_info(const symft_plan* p, symft_info* info) {
   }
   info->wide_amp_traffic[0] = wide_amp_traffic(p->dense_host.data(), static_cast<uint32_t>(p->dense_host.size()), false);
   info->wide_amp_traffic[1] = wide_amp_traffic(p->dense_host.data(), static_cast<uint32_t>(p->dense_host.size()), true);
+  info->pc_capacity = h.pc.capacity;
+  info->pc_selected = h.pc.use ? 1u : 0u;
+  info->pc_work[0] = h.pc.work_pc;
+  info->pc_work[1] = h.pc.work_mono;
   info->simplified[0] = h.n_fused;
   info->simplified[1] = h.n_cancelled;
   info->simplified[2] = h.n_branch_phase;

@@ -636,6 +636,8 @@ HostPlan Compiler::run() {
   P.n_fused = n_fused_;
   P.n_cancelled = n_cancelled_;
   P.n_branch_phase = n_branch_phase_;
+  P.pc = build_product_components(P.dense, P.k_max);
+  if (opt_.no_product_components) P.pc.use = false;
   return P;
 }
 

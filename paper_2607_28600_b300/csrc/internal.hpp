@@ -97,6 +97,16 @@ struct CellTable {
   uint8_t mask[16];          // component mask per cell
 };
 
+struct PCProgram {
+  std::vector<PCOp> ops;
+  uint32_t capacity = 0;      // workspace amplitudes per shot
+  uint64_t work_pc = 0;       // amplitudes touched per shot by the program
+  uint64_t work_mono = 0;     // amplitudes touched per shot by the monolithic vector
+  bool use = false;           // selected by the cost model
+};
+
+PCProgram build_product_components(const std::vector<DenseInstr>& dense, uint32_t k_max);
+
 struct HostPlan {
   uint32_t n_qubits = 0, n_meas = 0, n_records = 0, n_dets = 0, n_obs = 0, n_channels = 0;
   uint32_t k_max = 0;
@@ -159,6 +169,8 @@ struct HostPlan {
   // merged rotations removed (angle a multiple of 2 pi), rotations removed as
   // branch phases of a later same-body measurement
   uint32_t n_fused = 0, n_cancelled = 0, n_branch_phase = 0;
+  // product-component form of the dense instruction stream
+  PCProgram pc;
 };
 
 HostPlan compile_plan(const Circuit& c, const symft_options& opt);

@@ -160,6 +160,163 @@ __device__ __forceinline__ void branch_sums(const Cplx<Real>* vec, const DenseIn
   }
 }
 
+// One dense instruction (Sec. 4: PromoteRot, ActiveDiagRot, ActivePairRot,
+// ActiveDiagMeas, ActivePairMeas) on a vector of n = 2^k amplitudes held by
+// one warp (shared or global memory), with the instruction's sign lam; the
+// masks a, b and the pivot h of I are those of the vector's own bits.
+template <typename Real>
+__device__ __forceinline__ void warp_instr(const DenseArgs& A, Cplx<Real>* vec, uint32_t n, const DenseInstrDev& I,
+                                           uint32_t lam, uint64_t r, uint64_t rg, uint64_t w, uint64_t bitmask,
+                                           uint32_t* m3bits, ShotUniforms& su, int lane) {
+  const Real sg = lam ? (Real)-1 : (Real)1;
+  const Real c = (Real)I.c, s = (Real)I.s;
+
+  switch (I.kind) {
+    case 0: {  // PromoteRot: a'_{x} = c a_x, a'_{x+2^k} = -i sg s a_x
+      for (uint32_t x = lane; x < n; x += 32) {
+        Cplx<Real> v = vec[x];
+        Cplx<Real> hi;
+        hi.re = sg * s * v.im;
+        hi.im = -sg * s * v.re;
+        vec[x + n] = hi;
+        v.re *= c;
+        v.im *= c;
+        vec[x] = v;
+      }
+      break;
+    }
+    case 1: {  // ActiveDiagRot: a_x *= c - i sg mu (-1)^{b.x} s
+      const Real mu = I.mu == 0 ? (Real)1 : (Real)-1;
+      for (uint32_t x = lane; x < n; x += 32) {
+        Real f = sg * mu * s * ((__popc(x & I.b) & 1) ? (Real)-1 : (Real)1);
+        Cplx<Real> v = vec[x];
+        Cplx<Real> o;
+        o.re = c * v.re + f * v.im;
+        o.im = c * v.im - f * v.re;
+        vec[x] = o;
+      }
+      break;
+    }
+    case 2: {  // ActivePairRot on pairs (x0, x0 ^ a)
+      const int p = 31 - __clz(I.a);
+      // coefficient -i mu sg s (-1)^{b.x} for mu = i^mu
+      Real cr, ci;  // -i * i^mu
+      switch (I.mu & 3) {
+        case 0: cr = 0; ci = -1; break;
+        case 1: cr = 1; ci = 0; break;
+        case 2: cr = 0; ci = 1; break;
+        default: cr = -1; ci = 0; break;
+      }
+      cr *= sg * s;
+      ci *= sg * s;
+      for (uint32_t z = lane; z < (n >> 1); z += 32) {
+        uint32_t x0 = insert_bit(z, p, 0u);
+        uint32_t x1 = x0 ^ I.a;
+        Cplx<Real> v0 = vec[x0], v1 = vec[x1];
+        Real s1 = (__popc(x1 & I.b) & 1) ? (Real)-1 : (Real)1;   // applied to a_{x1} in a'_{x0}
+        Real s0 = (__popc(x0 & I.b) & 1) ? (Real)-1 : (Real)1;
+        Cplx<Real> o0, o1;
+        o0.re = c * v0.re + s1 * (cr * v1.re - ci * v1.im);
+        o0.im = c * v0.im + s1 * (cr * v1.im + ci * v1.re);
+        o1.re = c * v1.re + s0 * (cr * v0.re - ci * v0.im);
+        o1.im = c * v1.im + s0 * (cr * v0.im + ci * v0.re);
+        vec[x0] = o0;
+        vec[x1] = o1;
+      }
+      break;
+    }
+    case 5:
+    case 6: {  // active measurements
+      const int h = I.h;
+      const Real inv_sqrt2 = (Real)0.70710678118654752440;
+      Real mcr = 0, mci = 0;       // conj(mu)
+      if (I.kind == 6) {
+        switch (I.mu & 3) {
+          case 0: mcr = 1; mci = 0; break;
+          case 1: mcr = 0; mci = -1; break;
+          case 2: mcr = -1; mci = 0; break;
+          default: mcr = 0; mci = 1; break;
+        }
+      }
+      // label for m = 0: diag -> parity lam^eta ; pair -> y = lam
+      const uint32_t l0 = I.kind == 5 ? (lam ^ (uint32_t)I.eta) : lam;
+      uint32_t m = 0;
+      Real scale;
+      if (sizeof(Real) == 8 || n >= (1u << 14)) {      // FP64 sums
+        double S0 = 0.0, S1 = 0.0;
+        branch_sums<Real, double>(vec, I, n, lane, 32, mcr, mci, S0, S1);
+        warp_sum2(S0, S1);
+        const uint64_t U = su.get(A, (uint32_t)I.m3, rg, lane);
+        if (lane == 0) {
+          const double p0 = (l0 ? S1 : S0) / (S0 + S1);
+          m = decide64(U, p0);
+          if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = p0;
+        }
+        m = __shfl_sync(0xffffffffu, m, 0);
+        scale = (Real)(1.0 / sqrt((l0 ^ m) ? S1 : S0));
+      } else {                                         // FP32 sums below 2^14 terms
+        float S0 = 0.0f, S1 = 0.0f;
+        branch_sums<Real, float>(vec, I, n, lane, 32, mcr, mci, S0, S1);
+        warp_sum2(S0, S1);
+        const uint64_t U = su.get(A, (uint32_t)I.m3, rg, lane);
+        // the renormalisation scale 1 / sqrt(S_m) in FP32 on one lane: every
+        // later branch probability is self-normalised, so the scale only
+        // sets the vector's overall norm (an FP64 scale measured 2.4-3x
+        // slower on B300, whose FP64 pipe is a small fraction of FP32's)
+        float sc = 0.0f;
+        if (lane == 0) {
+          const float p0 = (l0 ? S1 : S0) / (S0 + S1);
+          m = decide32(U, p0);
+          if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = (double)p0;
+          sc = rsqrtf((l0 ^ m) ? S1 : S0);
+        }
+        m = __shfl_sync(0xffffffffu, m, 0);
+        scale = (Real)__shfl_sync(0xffffffffu, sc, 0);
+      }
+      const uint32_t lab = l0 ^ m;
+      // in-place compaction in increasing z order (sources are never below z)
+      const uint32_t half = n >> 1;
+      for (uint32_t z0 = 0; z0 < half; z0 += 32) {
+        uint32_t z = z0 + lane;
+        Cplx<Real> val;
+        val.re = 0; val.im = 0;
+        if (z < half) {
+          if (I.kind == 5) {
+            uint32_t u = insert_bit(z, h, lab);
+            uint32_t x = u ^ ((uint32_t)(__popc(u & I.b & ~(1u << h)) & 1) << h);
+            // x(b,u): bit h = u_h xor parity of b over the other bits
+            val = vec[x];
+          } else {
+            uint32_t u0 = insert_bit(z, h, 0u);
+            Cplx<Real> a0 = vec[u0], a1 = vec[u0 ^ I.a];
+            Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
+            if (lab) sb = -sb;
+            Real tr = sb * (mcr * a1.re - mci * a1.im), ti = sb * (mcr * a1.im + mci * a1.re);
+            val.re = (a0.re + tr) * inv_sqrt2;
+            val.im = (a0.im + ti) * inv_sqrt2;
+          }
+          val.re *= scale;
+          val.im *= scale;
+        }
+        __syncwarp();
+        if (z < half) vec[z] = val;
+        __syncwarp();
+      }
+      if (m) {
+        if (lane == 0) {
+          m3bits[I.m3 >> 5] |= 1u << (I.m3 & 31);
+          atomicOr(reinterpret_cast<unsigned long long*>(A.m3_out) + (uint64_t)I.m3 * A.W + w,
+                   (unsigned long long)bitmask);
+        }
+      }
+      break;
+    }
+    default:
+      if (lane == 0 && A.status) atomicExch(A.status, 1);
+      break;
+  }
+}
+
 template <typename Real>
 __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
   extern __shared__ unsigned char dsm[];
@@ -214,155 +371,104 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
         const uint32_t j = __ldg(A.p.dense_causal + I.causal_off + q);
         lam ^= (m3bits[j >> 5] >> (j & 31)) & 1u;
       }
-      const Real sg = lam ? (Real)-1 : (Real)1;
-      const Real c = (Real)I.c, s = (Real)I.s;
       const uint32_t n = 1u << k;
-      switch (I.kind) {
-        case 0: {  // PromoteRot: a'_{x} = c a_x, a'_{x+2^k} = -i sg s a_x
-          for (uint32_t x = lane; x < n; x += 32) {
-            Cplx<Real> v = vec[x];
-            Cplx<Real> hi;
-            hi.re = sg * s * v.im;
-            hi.im = -sg * s * v.re;
-            vec[x + n] = hi;
-            v.re *= c;
-            v.im *= c;
-            vec[x] = v;
-          }
-          ++k;
-          break;
-        }
-        case 1: {  // ActiveDiagRot: a_x *= c - i sg mu (-1)^{b.x} s
-          const Real mu = I.mu == 0 ? (Real)1 : (Real)-1;
-          for (uint32_t x = lane; x < n; x += 32) {
-            Real f = sg * mu * s * ((__popc(x & I.b) & 1) ? (Real)-1 : (Real)1);
-            Cplx<Real> v = vec[x];
-            Cplx<Real> o;
-            o.re = c * v.re + f * v.im;
-            o.im = c * v.im - f * v.re;
-            vec[x] = o;
-          }
-          break;
-        }
-        case 2: {  // ActivePairRot on pairs (x0, x0 ^ a)
-          const int p = 31 - __clz(I.a);
-          // coefficient -i mu sg s (-1)^{b.x} for mu = i^mu
-          Real cr, ci;  // -i * i^mu
-          switch (I.mu & 3) {
-            case 0: cr = 0; ci = -1; break;
-            case 1: cr = 1; ci = 0; break;
-            case 2: cr = 0; ci = 1; break;
-            default: cr = -1; ci = 0; break;
-          }
-          cr *= sg * s;
-          ci *= sg * s;
-          for (uint32_t z = lane; z < (n >> 1); z += 32) {
-            uint32_t x0 = insert_bit(z, p, 0u);
-            uint32_t x1 = x0 ^ I.a;
-            Cplx<Real> v0 = vec[x0], v1 = vec[x1];
-            Real s1 = (__popc(x1 & I.b) & 1) ? (Real)-1 : (Real)1;   // applied to a_{x1} in a'_{x0}
-            Real s0 = (__popc(x0 & I.b) & 1) ? (Real)-1 : (Real)1;
-            Cplx<Real> o0, o1;
-            o0.re = c * v0.re + s1 * (cr * v1.re - ci * v1.im);
-            o0.im = c * v0.im + s1 * (cr * v1.im + ci * v1.re);
-            o1.re = c * v1.re + s0 * (cr * v0.re - ci * v0.im);
-            o1.im = c * v1.im + s0 * (cr * v0.im + ci * v0.re);
-            vec[x0] = o0;
-            vec[x1] = o1;
-          }
-          break;
-        }
-        case 5:
-        case 6: {  // active measurements
-          const int h = I.h;
-          const Real inv_sqrt2 = (Real)0.70710678118654752440;
-          Real mcr = 0, mci = 0;       // conj(mu)
-          if (I.kind == 6) {
-            switch (I.mu & 3) {
-              case 0: mcr = 1; mci = 0; break;
-              case 1: mcr = 0; mci = -1; break;
-              case 2: mcr = -1; mci = 0; break;
-              default: mcr = 0; mci = 1; break;
-            }
-          }
-          // label for m = 0: diag -> parity lam^eta ; pair -> y = lam
-          const uint32_t l0 = I.kind == 5 ? (lam ^ (uint32_t)I.eta) : lam;
-          uint32_t m = 0;
-          Real scale;
-          if (sizeof(Real) == 8 || n >= (1u << 14)) {      // FP64 sums
-            double S0 = 0.0, S1 = 0.0;
-            branch_sums<Real, double>(vec, I, n, lane, 32, mcr, mci, S0, S1);
-            warp_sum2(S0, S1);
-            const uint64_t U = su.get(A, (uint32_t)I.m3, rg, lane);
-            if (lane == 0) {
-              const double p0 = (l0 ? S1 : S0) / (S0 + S1);
-              m = decide64(U, p0);
-              if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = p0;
-            }
-            m = __shfl_sync(0xffffffffu, m, 0);
-            scale = (Real)(1.0 / sqrt((l0 ^ m) ? S1 : S0));
-          } else {                                         // FP32 sums below 2^14 terms
-            float S0 = 0.0f, S1 = 0.0f;
-            branch_sums<Real, float>(vec, I, n, lane, 32, mcr, mci, S0, S1);
-            warp_sum2(S0, S1);
-            const uint64_t U = su.get(A, (uint32_t)I.m3, rg, lane);
-            // the renormalisation scale 1 / sqrt(S_m) in FP32 on one lane: every
-            // later branch probability is self-normalised, so the scale only
-            // sets the vector's overall norm (an FP64 scale measured 2.4-3x
-            // slower on B300, whose FP64 pipe is a small fraction of FP32's)
-            float sc = 0.0f;
-            if (lane == 0) {
-              const float p0 = (l0 ? S1 : S0) / (S0 + S1);
-              m = decide32(U, p0);
-              if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = (double)p0;
-              sc = rsqrtf((l0 ^ m) ? S1 : S0);
-            }
-            m = __shfl_sync(0xffffffffu, m, 0);
-            scale = (Real)__shfl_sync(0xffffffffu, sc, 0);
-          }
-          const uint32_t lab = l0 ^ m;
-          // in-place compaction in increasing z order (sources are never below z)
-          const uint32_t half = n >> 1;
-          for (uint32_t z0 = 0; z0 < half; z0 += 32) {
-            uint32_t z = z0 + lane;
-            Cplx<Real> val;
-            val.re = 0; val.im = 0;
-            if (z < half) {
-              if (I.kind == 5) {
-                uint32_t u = insert_bit(z, h, lab);
-                uint32_t x = u ^ ((uint32_t)(__popc(u & I.b & ~(1u << h)) & 1) << h);
-                // x(b,u): bit h = u_h xor parity of b over the other bits
-                val = vec[x];
-              } else {
-                uint32_t u0 = insert_bit(z, h, 0u);
-                Cplx<Real> a0 = vec[u0], a1 = vec[u0 ^ I.a];
-                Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
-                if (lab) sb = -sb;
-                Real tr = sb * (mcr * a1.re - mci * a1.im), ti = sb * (mcr * a1.im + mci * a1.re);
-                val.re = (a0.re + tr) * inv_sqrt2;
-                val.im = (a0.im + ti) * inv_sqrt2;
-              }
-              val.re *= scale;
-              val.im *= scale;
-            }
-            __syncwarp();
-            if (z < half) vec[z] = val;
-            __syncwarp();
-          }
-          --k;
-          if (m) {
-            if (lane == 0) {
-              m3bits[I.m3 >> 5] |= 1u << (I.m3 & 31);
-              atomicOr(reinterpret_cast<unsigned long long*>(A.m3_out) + (uint64_t)I.m3 * A.W + w,
-                       (unsigned long long)bitmask);
-            }
-          }
-          break;
-        }
-        default:
-          if (lane == 0 && A.status) atomicExch(A.status, 1);
-          break;
+      warp_instr<Real>(A, vec, n, I, lam, r, rg, w, bitmask, m3bits, su, lane);
+      if (I.kind == 0) ++k;
+      else if (I.kind == 5 || I.kind == 6) --k;
+      __syncwarp();
+      if (A.det_exo && I.post_grp != kNoGroup) {           // early exit once rejected
+        const bool dead = group_rejects(A.p, A.det_exo, A.W, r, I.post_grp, m3bits);
+        __syncwarp();
+        if (dead) break;
       }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Product-component executor (Sec. 6, adaptive product-component
+// representation): one warp per shot runs the plan's component program on a
+// workspace of pc_capacity amplitudes (shared memory, or a per-warp global
+// slot): INIT opens a one-coordinate component with the PromoteRot's factor
+// (c, -i sg s); MERGE writes the Kronecker product C[xA + 2^kA xB] =
+// A[xA] B[xB] into a fresh region; APPLY runs a dense instruction on one
+// component with local masks.  Signs, outcomes and early exit as in the
+// monolithic warp executor.
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void __launch_bounds__(256) dense_pc_kernel(DenseArgs A) {
+  extern __shared__ unsigned char dsm[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  const uint32_t m3w = (A.p.n_m3 + 31) / 32;
+  const uint32_t G = A.p.n_dense;
+  const uint32_t bkw = m3w + (G + 31) / 32;
+  uint32_t* m3bits = reinterpret_cast<uint32_t*>(dsm) + (size_t)wib * bkw;
+  uint32_t* sgn = m3bits + m3w;
+  const uint64_t warp_global = (uint64_t)blockIdx.x * wpb + wib;
+  Cplx<Real>* ws;
+  if (A.use_smem) {
+    const size_t off = ((size_t)wpb * bkw * 4 + 15) & ~(size_t)15;
+    ws = reinterpret_cast<Cplx<Real>*>(dsm + off) + (size_t)wib * A.p.pc_capacity;
+  } else {
+    ws = reinterpret_cast<Cplx<Real>*>(A.gvec) + warp_global * A.gvec_stride;
+  }
+  for (uint64_t r = warp_global; r < A.shots; r += (uint64_t)gridDim.x * wpb) {
+    const uint64_t rg = A.shot0 + r;
+    const uint64_t w = r >> 6;
+    const uint64_t bitmask = 1ull << (r & 63);
+    for (uint32_t i = lane; i < m3w; i += 32) m3bits[i] = 0u;
+    for (uint32_t base = 0; base < G; base += 32) {
+      const uint32_t g = base + lane;
+      bool bit = false;
+      if (g < G) bit = (__ldg(A.signs + (uint64_t)A.p.dense[g].sign_target_col * A.W + w) & bitmask) != 0;
+      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+      if (lane == 0) sgn[base >> 5] = bal;
+    }
+    ShotUniforms su;
+    __syncwarp();
+    const bool dead0 = A.det_exo && A.p.post_grp0 == 0 && group_rejects(A.p, A.det_exo, A.W, r, 0, m3bits);
+    __syncwarp();
+    if (dead0) continue;
+    for (uint32_t q = 0; q < A.p.n_pc; ++q) {
+      const PCOp O = A.p.pc[q];
+      if (O.op == PC_MERGE) {
+        const uint32_t na = 1u << O.kA, nc = 1u << (O.kA + O.kB);
+        const Cplx<Real>* pa = ws + O.offA;
+        const Cplx<Real>* pb = ws + O.offB;
+        Cplx<Real>* pc = ws + O.off;
+        for (uint32_t x = lane; x < nc; x += 32) {
+          const Cplx<Real> u = pa[x & (na - 1)], v = pb[x >> O.kA];
+          Cplx<Real> t;
+          t.re = u.re * v.re - u.im * v.im;
+          t.im = u.re * v.im + u.im * v.re;
+          pc[x] = t;
+        }
+        __syncwarp();
+        continue;
+      }
+      DenseInstrDev I = A.p.dense[O.g];
+      uint32_t lam = (sgn[O.g >> 5] >> (O.g & 31)) & 1u;
+      for (uint32_t c = 0; c < I.causal_n; ++c) {
+        const uint32_t j = __ldg(A.p.dense_causal + I.causal_off + c);
+        lam ^= (m3bits[j >> 5] >> (j & 31)) & 1u;
+      }
+      Cplx<Real>* vec = ws + O.off;
+      if (O.op == PC_INIT) {
+        if (lane == 0) {
+          vec[0].re = (Real)1;
+          vec[0].im = (Real)0;
+        }
+        __syncwarp();
+        warp_instr<Real>(A, vec, 1u, I, lam, r, rg, w, bitmask, m3bits, su, lane);
+        __syncwarp();
+        continue;
+      }
+      I.a = O.a;
+      I.b = O.b;
+      I.h = O.h;
+      warp_instr<Real>(A, vec, 1u << O.k, I, lam, r, rg, w, bitmask, m3bits, su, lane);
       __syncwarp();
       if (A.det_exo && I.post_grp != kNoGroup) {           // early exit once rejected
         const bool dead = group_rejects(A.p, A.det_exo, A.W, r, I.post_grp, m3bits);
@@ -1217,6 +1323,12 @@ cudaError_t launch_dense_reg(const DenseArgs& a, bool fp64, int grid, cudaStream
   return cudaGetLastError();
 }
 
+cudaError_t launch_dense_pc(const DenseArgs& a, bool fp64, int warps_per_block, int grid, size_t smem, cudaStream_t st) {
+  if (fp64) dense_pc_kernel<double><<<grid, warps_per_block * 32, smem, st>>>(a);
+  else dense_pc_kernel<float><<<grid, warps_per_block * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_dense(const DenseArgs& a, bool fp64, int warps_per_block, int grid, size_t smem, cudaStream_t st) {
   return fp64 ? launch_dense_t<double>(a, warps_per_block, grid, smem, st)
               : launch_dense_t<float>(a, warps_per_block, grid, smem, st);
@@ -1234,6 +1346,7 @@ cudaError_t set_smem_limits() {
   const int lim = 227 * 1024;
   const void* fns[] = {sign_kernel_fn(),
                        (const void*)dense_kernel<float>, (const void*)dense_kernel<double>,
+                       (const void*)dense_pc_kernel<float>, (const void*)dense_pc_kernel<double>,
                        (const void*)dense_reg_kernel<float>, (const void*)dense_reg_kernel<double>,
                        (const void*)dense_cta_kernel<float>, (const void*)dense_cta_kernel<double>,
                        (const void*)plain_kernel<float>, (const void*)plain_kernel<double>};

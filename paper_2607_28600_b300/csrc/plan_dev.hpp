@@ -59,6 +59,23 @@ struct DenseInstrDev {
 
 constexpr uint32_t kNoGroup = 0xFFFFFFFFu;
 
+// Product-component program (Sec. 6, adaptive product-component
+// representation): one op per component initialisation, Kronecker merge or
+// dense instruction, with the component's place in the per-shot workspace.
+enum PCOpKind : uint32_t { PC_INIT = 0, PC_MERGE = 1, PC_APPLY = 2 };
+
+struct PCOp {
+  uint32_t op;        // PCOpKind
+  uint32_t g;         // dense instruction (INIT: its PromoteRot; APPLY: the instruction)
+  uint32_t off;       // workspace offset (amplitudes) of the target component
+  uint32_t k;         // APPLY: the component's width before the instruction
+  uint32_t a, b;      // APPLY: masks in the component's local bits
+  int32_t h;          // APPLY (measurement): local pivot bit
+  uint32_t offA, kA;  // MERGE: first factor (its bits become the low bits)
+  uint32_t offB, kB;  // MERGE: second factor
+  uint32_t pad;
+};
+
 struct DevPlan {
   uint32_t n_channels;
   const ChannelDev* ch;
@@ -106,6 +123,9 @@ struct DevPlan {
   uint32_t post_grp0;           // 0: check group 0 before a shot's dense work; else kNoGroup
   uint32_t n_dense;
   const DenseInstrDev* dense;
+  uint32_t n_pc;                // product-component program (0: not built)
+  const PCOp* pc;
+  uint32_t pc_capacity;         // its workspace amplitudes per shot
   const uint32_t* dense_causal;
   uint32_t n_m3;
   const uint32_t* m3_t;         // measurement ordinal of each active measurement

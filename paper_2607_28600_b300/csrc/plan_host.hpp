@@ -33,7 +33,7 @@ struct DevBuf {
 
 // Byte offsets of the plan arrays inside the device blob.
 struct BlobOffsets {
-  size_t ch, q, ct, t4, qi, qs, m1t, m1o, m1g, tco, tca, sc, li, gi, gv, pe, dn, dc, m3t, sm1, sm1o, pco, pch;
+  size_t ch, q, ct, t4, qi, qs, pc, m1t, m1o, m1g, tco, tca, sc, li, gi, gv, pe, dn, dc, m3t, sm1, sm1o, pco, pch;
   size_t plc, plo, pls;
   size_t clt, clo;
 };
@@ -52,6 +52,8 @@ size_t dense_warp_smem_bytes(const DevPlan& p, int wpb, size_t vec_bytes, bool v
 size_t dense_cta_smem_bytes(const DevPlan& p, size_t vec_bytes, bool vec_in_smem);
 cudaError_t launch_dense_cta(const DenseArgs& a, bool fp64, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_dense_reg(const DenseArgs& a, bool fp64, int grid, cudaStream_t st);
+cudaError_t launch_dense_pc(const DenseArgs& a, bool fp64, int warps_per_block, int grid, size_t smem,
+                            cudaStream_t st);
 cudaError_t launch_plain(const PlainArgs& a, bool fp64, int grid, cudaStream_t st);
 // all dense instructions for one batch of the wide executor (host_dense: the
 // plan's instruction stream in host memory, for the per-instruction launches)
@@ -67,7 +69,8 @@ struct Tune {
   int dense_grid_mult = 8;   // register / warp executors: CTAs per SM
   int dense_wpb = 0;         // warp executor: warps (shots) per CTA
   int cta_grid_mult = 2;     // CTA executor with global vectors: CTAs per SM
-  int dense_kind = 0;        // dense executor (1 register, 2 warp, 3 CTA, 4 wide; 0 = first that fits)
+  int dense_kind = 0;        // dense executor (1 register, 2 warp, 3 CTA, 4 wide, 5 product
+                             // components; 0 = the cost model's choice)
   float best_ms_per_shot = 0.0f;
 };
 

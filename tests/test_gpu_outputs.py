@@ -41,9 +41,9 @@ def _cases():
     }
 
 
-def _gpu_probs(text, shots, seed, precision, plain=False):
+def _gpu_probs(text, shots, seed, precision, plain=False, product_components=True):
     import paper_2607_28600_b300 as S
-    plan = S.symft_compile(text)
+    plan = S.symft_compile(text, product_components=product_components)
     info = plan.info
     W = (shots + 63) // 64
     meas = torch.zeros((max(1, info["n_records"]), W), dtype=torch.int64, device="cuda")
@@ -123,8 +123,9 @@ def test_wide_executor_fp32_branch_probabilities_k15():
     from paper_2607_28600_b300.workloads import distillation_15_to_1
     text = distillation_15_to_1(1e-3, "literal")
     shots, seed = 40, 31
-    plan, rec32, p32 = _gpu_probs(text, shots, seed, precision=0)
-    assert plan.info["k_max"] == 15
+    # the monolithic vector (the product-component form is tested on its own)
+    plan, rec32, p32 = _gpu_probs(text, shots, seed, precision=0, product_components=False)
+    assert plan.info["k_max"] == 15 and plan.info["dense_executor"] == ["wide", "wide"]
     act = plan.active_meas()
     assert len(act) >= 14
     ref = _sv_probs(text, seed, shots, act)
@@ -133,7 +134,7 @@ def test_wide_executor_fp32_branch_probabilities_k15():
     assert worst <= 1e-5, worst
     assert flips <= 1
     # FP64 on the same executor: every probability to 1e-9, records bit-exact
-    _, rec64, p64 = _gpu_probs(text, shots, seed, precision=1)
+    _, rec64, p64 = _gpu_probs(text, shots, seed, precision=1, product_components=False)
     assert np.abs(p64 - ref).max() <= 1e-9
     np.testing.assert_array_equal(rec64, o["records"])
 
