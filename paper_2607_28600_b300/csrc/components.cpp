@@ -152,16 +152,28 @@ PCProgram build_product_components(const std::vector<DenseInstr>& dense, uint32_
     op.a = local_mask(C, I.a);
     op.b = local_mask(C, I.b);
     op.h = 0;
+    op.out = C.off;
     work_pc += 1ull << kc;
     if (I.kind == I_ACTIVE_DIAG_MEAS || I.kind == I_ACTIVE_PAIR_MEAS) {
       const auto hp = std::find(C.coords.begin(), C.coords.end(), static_cast<uint32_t>(I.h));
       op.h = static_cast<int>(hp - C.coords.begin());
+      // The compaction removes the pivot's local bit.  In place it reads every
+      // source at or above its destination only when the pivot is the highest
+      // local bit of a (the planner's choice in the monolithic order); a pair
+      // measurement whose pivot landed lower in the component writes its kept
+      // half to a fresh region instead.
+      const bool fresh = I.kind == I_ACTIVE_PAIR_MEAS && op.h != 31 - __builtin_clz(op.a);
+      if (fresh) {
+        op.out = pl.alloc(1u << (kc - 1));
+        pl.release(C.off, 1u << kc);
+        C.off = op.out;
+      } else {
+        op.out = C.off;
+        pl.release(C.off + (1u << (kc - 1)), 1u << (kc - 1));
+      }
       P.ops.push_back(op);
-      // the compaction removes the pivot's local bit; the upper half of the
-      // region is free again, and a component left without coordinates is a
-      // global phase
+      // a component left without coordinates is a global phase
       C.coords.erase(hp);
-      pl.release(C.off + (1u << (kc - 1)), 1u << (kc - 1));
       if (C.coords.empty()) {
         pl.release(C.off, 1);
         C.live = false;

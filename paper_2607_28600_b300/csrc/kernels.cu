@@ -163,11 +163,14 @@ __device__ __forceinline__ void branch_sums(const Cplx<Real>* vec, const DenseIn
 // One dense instruction (Sec. 4: PromoteRot, ActiveDiagRot, ActivePairRot,
 // ActiveDiagMeas, ActivePairMeas) on a vector of n = 2^k amplitudes held by
 // one warp (shared or global memory), with the instruction's sign lam; the
-// masks a, b and the pivot h of I are those of the vector's own bits.
+// masks a, b and the pivot h of I are those of the vector's own bits.  A
+// measurement writes the kept half to out: in place (out == vec) when h is
+// the highest bit of a (pair) or any bit of b (diagonal), else to a disjoint
+// region.
 template <typename Real>
-__device__ __forceinline__ void warp_instr(const DenseArgs& A, Cplx<Real>* vec, uint32_t n, const DenseInstrDev& I,
-                                           uint32_t lam, uint64_t r, uint64_t rg, uint64_t w, uint64_t bitmask,
-                                           uint32_t* m3bits, ShotUniforms& su, int lane) {
+__device__ __forceinline__ void warp_instr(const DenseArgs& A, Cplx<Real>* vec, Cplx<Real>* out, uint32_t n,
+                                           const DenseInstrDev& I, uint32_t lam, uint64_t r, uint64_t rg, uint64_t w,
+                                           uint64_t bitmask, uint32_t* m3bits, ShotUniforms& su, int lane) {
   const Real sg = lam ? (Real)-1 : (Real)1;
   const Real c = (Real)I.c, s = (Real)I.s;
 
@@ -274,7 +277,7 @@ __device__ __forceinline__ void warp_instr(const DenseArgs& A, Cplx<Real>* vec, 
         scale = (Real)__shfl_sync(0xffffffffu, sc, 0);
       }
       const uint32_t lab = l0 ^ m;
-      // in-place compaction in increasing z order (sources are never below z)
+      // compaction in increasing z order (in place, sources are never below z)
       const uint32_t half = n >> 1;
       for (uint32_t z0 = 0; z0 < half; z0 += 32) {
         uint32_t z = z0 + lane;
@@ -299,7 +302,7 @@ __device__ __forceinline__ void warp_instr(const DenseArgs& A, Cplx<Real>* vec, 
           val.im *= scale;
         }
         __syncwarp();
-        if (z < half) vec[z] = val;
+        if (z < half) out[z] = val;
         __syncwarp();
       }
       if (m) {
@@ -372,7 +375,7 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
         lam ^= (m3bits[j >> 5] >> (j & 31)) & 1u;
       }
       const uint32_t n = 1u << k;
-      warp_instr<Real>(A, vec, n, I, lam, r, rg, w, bitmask, m3bits, su, lane);
+      warp_instr<Real>(A, vec, vec, n, I, lam, r, rg, w, bitmask, m3bits, su, lane);
       if (I.kind == 0) ++k;
       else if (I.kind == 5 || I.kind == 6) --k;
       __syncwarp();
@@ -461,14 +464,14 @@ __global__ void __launch_bounds__(256) dense_pc_kernel(DenseArgs A) {
           vec[0].im = (Real)0;
         }
         __syncwarp();
-        warp_instr<Real>(A, vec, 1u, I, lam, r, rg, w, bitmask, m3bits, su, lane);
+        warp_instr<Real>(A, vec, vec, 1u, I, lam, r, rg, w, bitmask, m3bits, su, lane);
         __syncwarp();
         continue;
       }
       I.a = O.a;
       I.b = O.b;
       I.h = O.h;
-      warp_instr<Real>(A, vec, 1u << O.k, I, lam, r, rg, w, bitmask, m3bits, su, lane);
+      warp_instr<Real>(A, vec, ws + O.out, 1u << O.k, I, lam, r, rg, w, bitmask, m3bits, su, lane);
       __syncwarp();
       if (A.det_exo && I.post_grp != kNoGroup) {           // early exit once rejected
         const bool dead = group_rejects(A.p, A.det_exo, A.W, r, I.post_grp, m3bits);

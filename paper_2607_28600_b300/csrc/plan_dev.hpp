@@ -73,7 +73,7 @@ struct PCOp {
   int32_t h;          // APPLY (measurement): local pivot bit
   uint32_t offA, kA;  // MERGE: first factor (its bits become the low bits)
   uint32_t offB, kB;  // MERGE: second factor
-  uint32_t pad;
+  uint32_t out;       // APPLY (measurement): offset the kept half is written to (off: in place)
 };
 
 struct DevPlan {
