@@ -304,18 +304,24 @@ def dense_floor(info, peaks, fp64=False):
     measurement 5, pair measurement 13, at two FLOPs per FMA) and
     shared-memory traffic (each instruction reads and writes its vector);
     vectors beyond shared memory: the HBM bytes of the wide executor's fused
-    passes."""
+    passes.  Under the product-component executor the work is scaled by the
+    amplitudes its program touches over those of the monolithic vector."""
     amp = 16 if fp64 else 8
-    in_hbm = (1 << info["k_max"]) * amp > 200 * 1024
+    executor = info["dense_executor"][1 if fp64 else 0]
+    in_hbm = executor == "wide"
+    # the product-component executor touches pc_work[0] amplitudes per shot
+    # where the monolithic vector touches pc_work[1]
+    scale = info["pc_work"][0] / info["pc_work"][1] if executor == "components" and info["pc_work"][1] else 1.0
     if in_hbm:
         b = info["wide_amp_traffic"][1 if fp64 else 0] * amp
-        return {"where": "hbm", "bytes_per_shot": b, "floor_s_per_shot": b / (peaks["hbm_gbs"] * 1e9)}
-    fl = info["dense_flops"]
+        return {"where": "hbm", "executor": executor, "bytes_per_shot": b,
+                "floor_s_per_shot": b / (peaks["hbm_gbs"] * 1e9)}
+    fl = info["dense_flops"] * scale
     fma = peaks["fp64_fma_per_s"] if fp64 else peaks["fp32_fma_per_s"]
     t_fp = fl / (2.0 * fma)
-    sm = info["dense_amp_traffic"] * amp
+    sm = info["dense_amp_traffic"] * amp * scale
     t_sm = sm / peaks["smem_bytes_per_s"]
-    return {"where": "on-chip", "flops_per_shot": fl, "smem_bytes_per_shot": sm,
+    return {"where": "on-chip", "executor": executor, "flops_per_shot": fl, "smem_bytes_per_shot": sm,
             "fp_floor_s_per_shot": t_fp, "smem_floor_s_per_shot": t_sm,
             "floor_s_per_shot": max(t_fp, t_sm), "bound": "fp" if t_fp >= t_sm else "smem"}
 
