@@ -311,7 +311,8 @@ def dense_floor(info, peaks, fp64=False):
     in_hbm = executor == "wide"
     # the product-component executor touches pc_work[0] amplitudes per shot
     # where the monolithic vector touches pc_work[1]
-    scale = info["pc_work"][0] / info["pc_work"][1] if executor == "components" and info["pc_work"][1] else 1.0
+    scale = (info["pc_work"][0] / info["pc_work"][1]
+             if executor.startswith("components") and info["pc_work"][1] else 1.0)
     if in_hbm:
         b = info["wide_amp_traffic"][1 if fp64 else 0] * amp
         return {"where": "hbm", "executor": executor, "bytes_per_shot": b,

@@ -91,7 +91,13 @@ typedef struct {
   int no_product_components;  /* non-zero: never use the product-component
                               representation (Sec. 6); by default it is used
                               when its cost model predicts a clear benefit */
-  int reserved[2];
+  int executor;            /* dense executor preference, the numbering of
+                              symft_info.dense_executor (1 register, 2 warp,
+                              3 CTA, 4 wide, 5 / 6 product components on a warp
+                              / a CTA); used when it can run the plan, else the
+                              automatic choice; 0 = automatic.  symft_autotune
+                              replaces it with its own pick */
+  int reserved[1];
 } symft_options;
 
 /* Counts of a compiled plan (Sec. 5, sampling complexity). */
@@ -133,7 +139,8 @@ typedef struct {
                                  per shot with the vector in shared memory, 3 CTA
                                  per shot with the vector in shared memory, 4 wide
                                  (vectors in HBM, instruction-major passes), 5
-                                 warp per shot on the product-component program;
+                                 warp per shot on the product-component program,
+                                 6 CTA per shot on it (workspace in shared memory);
                                  the product components when selected, else the
                                  smallest that fits, unless symft_autotune chose
                                  another; 0 without dense instructions */

@@ -38,7 +38,8 @@ class SymftError(RuntimeError):
 class _Options(ctypes.Structure):
     _fields_ = [("postselect", ctypes.c_int), ("n_post_dets", ctypes.c_uint32),
                  ("post_dets", ctypes.POINTER(ctypes.c_uint32)), ("no_simplify", ctypes.c_int),
-                ("no_product_components", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("no_product_components", ctypes.c_int), ("executor", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1)]
 
 
 class _Info(ctypes.Structure):
@@ -188,8 +189,12 @@ class Plan:
         return symft_plan_active_meas(self)
 
 
+EXECUTORS = {"auto": 0, "register": 1, "warp": 2, "cta": 3, "wide": 4, "components_warp": 5,
+             "components_cta": 6}
+
+
 def symft_compile(circuit_text: str, postselect: int = POSTSELECT_NONE, post_dets=None,
-                  simplify: bool = True, product_components: bool = True) -> Plan:
+                  simplify: bool = True, product_components: bool = True, executor: str = "auto") -> Plan:
     """Compile circuit text.  postselect=POSTSELECT_LISTED rejects a shot only at
     the detectors whose indices are listed in `post_dets`; simplify=False skips
     the commutation-aware simplification before planning."""
@@ -198,6 +203,7 @@ def symft_compile(circuit_text: str, postselect: int = POSTSELECT_NONE, post_det
     opt.postselect = postselect
     opt.no_simplify = 0 if simplify else 1
     opt.no_product_components = 0 if product_components else 1
+    opt.executor = EXECUTORS[executor]
     if post_dets is not None:
         dets = [int(d) for d in post_dets]
         arr = (ctypes.c_uint32 * max(1, len(dets)))(*dets)
@@ -214,7 +220,8 @@ def symft_plan_info(plan: Plan) -> dict:
          if name not in ("n_instr", "tuned_ns_per_shot", "simplified", "wide_amp_traffic", "sign_model",
                          "dense_executor", "pc_work")}
     d["pc_work"] = [int(info.pc_work[0]), int(info.pc_work[1])]
-    kinds = {0: "none", 1: "register", 2: "warp", 3: "cta", 4: "wide", 5: "components"}
+    kinds = {0: "none", 1: "register", 2: "warp", 3: "cta", 4: "wide", 5: "components_warp",
+             6: "components_cta"}
     d["dense_executor"] = [kinds.get(int(info.dense_executor[i]), "?") for i in range(2)]
     d["sign_model"] = {"philox_blocks_per_block": float(info.sign_model[0]),
                        "fires_per_block": float(info.sign_model[1]),

@@ -310,8 +310,8 @@ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Whether dense executor `kind` (1 register, 2 warp with the vector in shared
 // memory, 3 CTA with the vector in shared memory, 4 wide with vectors in HBM,
-// 5 warp running the product-component program) can run this plan at this
-// precision.
+// 5 warp running the product-component program, 6 CTA running it with the
+// workspace in shared memory) can run this plan at this precision.
 bool dense_kind_valid(const symft_plan* P, const HostPlan& h, bool fp64, int kind) {
   const size_t amp = fp64 ? 16 : 8;
   const size_t m3bytes = ((h.n_m3 + 31) / 32) * 4;
@@ -322,15 +322,19 @@ bool dense_kind_valid(const symft_plan* P, const HostPlan& h, bool fp64, int kin
     case 3: return dense_cta_smem_bytes(P->dp, vec_bytes, true) <= 200 * 1024;
     case 4: return true;
     case 5: return !h.pc.ops.empty() && h.pc.capacity <= (1u << 22);
+    case 6: return !h.pc.ops.empty() &&
+                   dense_cta_smem_bytes(P->dp, static_cast<size_t>(h.pc.capacity) * amp, true) <= 200 * 1024;
   }
   return false;
 }
 
 // The executor for a plan: the tuned choice when it is valid, else the
-// product-component executor when its cost model selected it, else the first
+// product-component executor (CTA per shot when the workspace fits its shared
+// memory, else warp per shot) when its cost model selected it, else the first
 // valid kind in the order register, warp, CTA, wide (smallest footprint first).
 int dense_kind_for(const symft_plan* P, const HostPlan& h, bool fp64, int tuned) {
   if (tuned && dense_kind_valid(P, h, fp64, tuned)) return tuned;
+  if (h.pc.use && dense_kind_valid(P, h, fp64, 6)) return 6;
   if (h.pc.use && dense_kind_valid(P, h, fp64, 5)) return 5;
   for (int k = 1; k <= 4; ++k)
     if (dense_kind_valid(P, h, fp64, k)) return k;
@@ -462,6 +466,13 @@ int prepare(symft_plan* P, const symft_sample_args* a, uint64_t* meas, uint64_t*
       o->dense_smem = dense_cta_smem_bytes(P->dp, vec_bytes, true);
       o->dense_use_smem = 1;
       const uint64_t cap = static_cast<uint64_t>(P->sm_count) * 16;
+      o->dense_grid = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(a->shots, cap)));
+    } else if (dense_kind_for(P, h, o->fp64, t.dense_kind) == 6) {
+      // product components, one CTA per shot, workspace in shared memory
+      o->dense_kind = 6;
+      o->dense_smem = dense_cta_smem_bytes(P->dp, static_cast<size_t>(h.pc.capacity) * amp, true);
+      o->dense_use_smem = 1;
+      const uint64_t cap = static_cast<uint64_t>(P->sm_count) * 8 * t.cta_grid_mult;
       o->dense_grid = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(a->shots, cap)));
     } else if (dense_kind_for(P, h, o->fp64, t.dense_kind) == 5) {
       // product components: one warp per shot, the component workspace in
@@ -659,6 +670,7 @@ int enqueue(symft_plan* P, const symft_sample_args* a, const Prep& o, cudaStream
       --*launches;   // counted once below
     } else if (o.dense_kind == 1) CUDA_TRY(launch_dense_reg(d, o.fp64, o.dense_grid, st));
     else if (o.dense_kind == 5) CUDA_TRY(launch_dense_pc(d, o.fp64, o.dense_wpb, o.dense_grid, o.dense_smem, st));
+    else if (o.dense_kind == 6) CUDA_TRY(launch_dense_pc_cta(d, o.fp64, o.dense_grid, o.dense_smem, st));
     else if (o.dense_kind == 2) CUDA_TRY(launch_dense(d, o.fp64, o.dense_wpb, o.dense_grid, o.dense_smem, st));
     else CUDA_TRY(launch_dense_cta(d, o.fp64, o.dense_grid, o.dense_smem, st));
     ++*launches;
@@ -780,7 +792,7 @@ int autotune_impl(symft_plan* P, uint64_t shots, int precision, cudaStream_t st)
   // dense executor kind: every kind that can run the plan, default shapes
   if (rc == SYMFT_OK && !h.dense.empty()) {
     const bool fp64 = precision == SYMFT_FP64;
-    for (int kind = 1; kind <= 5; ++kind) {
+    for (int kind = 1; kind <= 6; ++kind) {
       if (!dense_kind_valid(P, h, fp64, kind) || kind == dense_kind_for(P, h, fp64, base.dense_kind)) continue;
       Tune cand = base;
       cand.dense_kind = kind;
@@ -973,10 +985,12 @@ int symft_compile_ex(const char* text, const symft_options* opt, symft_plan** ou
         if (o.post_dets[i] >= c.n_dets)
           return set_error(SYMFT_E_ARG, "postselect LISTED: detector " + std::to_string(o.post_dets[i]) +
                                             " out of range (" + std::to_string(c.n_dets) + " detectors)");
+    if (o.executor < 0 || o.executor > 6) return set_error(SYMFT_E_ARG, "bad executor preference");
     symft_plan* p = new symft_plan();
     try {
       p->hp = compile_plan(c, o);
       build_blob(p);
+      p->tune[0].dense_kind = p->tune[1].dense_kind = o.executor;
     } catch (...) {
       delete p;
       throw;

@@ -669,6 +669,141 @@ __global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) 
 // ---------------------------------------------------------------------------
 constexpr int kCtaThreads = 256;
 
+// One dense instruction on a vector of n = 2^k amplitudes held by a whole
+// CTA (shared or global memory), with the instruction's sign lam (the CTA
+// executor's body; red and bcast are the CTA's reduction and broadcast
+// scratch).  A measurement writes the kept half to out, in place when out ==
+// vec (pivot h the highest bit of a for a pair measurement), else to a
+// disjoint region.
+template <typename Real>
+__device__ __forceinline__ void cta_instr(const DenseArgs& A, Cplx<Real>* vec, Cplx<Real>* out, uint32_t n,
+                                          const DenseInstrDev& I, uint32_t lam, uint64_t rg, uint64_t r, uint64_t w,
+                                          uint64_t bitmask, uint32_t* m3b, double* red, int* bcast, uint32_t tid) {
+  const Real sg = lam ? (Real)-1 : (Real)1;
+  const Real c = (Real)I.c, s = (Real)I.s;
+  if (I.kind == 0) {
+    for (uint32_t x = tid; x < n; x += blockDim.x) {
+      Cplx<Real> v = vec[x], hi;
+      hi.re = sg * s * v.im;
+      hi.im = -sg * s * v.re;
+      vec[x + n] = hi;
+      v.re *= c;
+      v.im *= c;
+      vec[x] = v;
+    }
+  } else if (I.kind == 1) {
+    const Real mu = I.mu == 0 ? (Real)1 : (Real)-1;
+    for (uint32_t x = tid; x < n; x += blockDim.x) {
+      const Real f = sg * mu * s * ((__popc(x & I.b) & 1) ? (Real)-1 : (Real)1);
+      const Cplx<Real> v = vec[x];
+      Cplx<Real> o;
+      o.re = c * v.re + f * v.im;
+      o.im = c * v.im - f * v.re;
+      vec[x] = o;
+    }
+  } else if (I.kind == 2) {
+    const int pb = 31 - __clz(I.a);
+    Real cr, ci;
+    switch (I.mu & 3) {
+      case 0: cr = 0; ci = -1; break;
+      case 1: cr = 1; ci = 0; break;
+      case 2: cr = 0; ci = 1; break;
+      default: cr = -1; ci = 0; break;
+    }
+    cr *= sg * s;
+    ci *= sg * s;
+    for (uint32_t z = tid; z < (n >> 1); z += blockDim.x) {
+      const uint32_t x0 = insert_bit(z, pb, 0u), x1 = x0 ^ I.a;
+      const Cplx<Real> v0 = vec[x0], v1 = vec[x1];
+      const Real s1 = (__popc(x1 & I.b) & 1) ? (Real)-1 : (Real)1;
+      const Real s0 = (__popc(x0 & I.b) & 1) ? (Real)-1 : (Real)1;
+      Cplx<Real> o0, o1;
+      o0.re = c * v0.re + s1 * (cr * v1.re - ci * v1.im);
+      o0.im = c * v0.im + s1 * (cr * v1.im + ci * v1.re);
+      o1.re = c * v1.re + s0 * (cr * v0.re - ci * v0.im);
+      o1.im = c * v1.im + s0 * (cr * v0.im + ci * v0.re);
+      vec[x0] = o0;
+      vec[x1] = o1;
+    }
+  } else {
+    const int h = I.h;
+    const Real inv_sqrt2 = (Real)0.70710678118654752440;
+    Real mcr = 0, mci = 0;
+    if (I.kind == 6) {
+      switch (I.mu & 3) {
+        case 0: mcr = 1; mci = 0; break;
+        case 1: mcr = 0; mci = -1; break;
+        case 2: mcr = -1; mci = 0; break;
+        default: mcr = 0; mci = 1; break;
+      }
+    }
+    const uint32_t l0 = I.kind == 5 ? (lam ^ (uint32_t)I.eta) : lam;
+    double S0 = 0.0, S1 = 0.0;
+    if (sizeof(Real) == 8 || n >= (1u << 14)) {    // FP64 sums
+      branch_sums<Real, double>(vec, I, n, tid, blockDim.x, mcr, mci, S0, S1);
+      warp_sum2(S0, S1);
+    } else {                                       // FP32 sums below 2^14 terms
+      float F0 = 0.0f, F1 = 0.0f;
+      branch_sums<Real, float>(vec, I, n, tid, blockDim.x, mcr, mci, F0, F1);
+      warp_sum2(F0, F1);
+      S0 = F0;
+      S1 = F1;
+    }
+    if ((tid & 31) == 0) {
+      red[tid >> 5] = S0;
+      red[kCtaThreads / 32 + (tid >> 5)] = S1;
+    }
+    __syncthreads();
+    S0 = 0.0;
+    S1 = 0.0;
+    for (int w2 = 0; w2 < kCtaThreads / 32; ++w2) {
+      S0 += red[w2];
+      S1 += red[kCtaThreads / 32 + w2];
+    }
+    if (tid == 0) {
+      const double p0 = (l0 ? S1 : S0) / (S0 + S1);
+      const uint32_t m = decide64(meas_U(A.keys, I.t, rg), p0);
+      if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = p0;
+      bcast[1] = (int)m;
+      if (m) {
+        m3b[I.m3 >> 5] |= 1u << (I.m3 & 31);
+        atomicOr(reinterpret_cast<unsigned long long*>(A.m3_out) + (uint64_t)I.m3 * A.W + w,
+                 (unsigned long long)bitmask);
+      }
+    }
+    __syncthreads();
+    const uint32_t m = (uint32_t)bcast[1];
+    const uint32_t lab = l0 ^ m;
+    const Real scale = (Real)(1.0 / sqrt(lab ? S1 : S0));
+    const uint32_t half = n >> 1;
+    for (uint32_t z0 = 0; z0 < half; z0 += blockDim.x) {
+      const uint32_t z = z0 + tid;
+      Cplx<Real> v;
+      v.re = 0;
+      v.im = 0;
+      if (z < half) {
+        if (I.kind == 5) {
+          const uint32_t u = insert_bit(z, h, lab);
+          v = vec[u ^ ((uint32_t)(__popc(u & I.b & ~(1u << h)) & 1) << h)];
+        } else {
+          const uint32_t u0 = insert_bit(z, h, 0u);
+          const Cplx<Real> a0 = vec[u0], a1 = vec[u0 ^ I.a];
+          Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
+          if (lab) sb = -sb;
+          const Real tr = sb * (mcr * a1.re - mci * a1.im), tim = sb * (mcr * a1.im + mci * a1.re);
+          v.re = (a0.re + tr) * inv_sqrt2;
+          v.im = (a0.im + tim) * inv_sqrt2;
+        }
+        v.re *= scale;
+        v.im *= scale;
+      }
+      __syncthreads();
+      if (z < half) out[z] = v;
+      __syncthreads();
+    }
+  }
+}
+
 template <typename Real>
 __global__ void __launch_bounds__(kCtaThreads) dense_cta_kernel(DenseArgs A) {
   extern __shared__ __align__(16) unsigned char csm[];
@@ -708,131 +843,90 @@ __global__ void __launch_bounds__(kCtaThreads) dense_cta_kernel(DenseArgs A) {
       }
       __syncthreads();
       const uint32_t lam = (uint32_t)bcast[0];
-      const Real sg = lam ? (Real)-1 : (Real)1;
-      const Real c = (Real)I.c, s = (Real)I.s;
       const uint32_t n = 1u << k;
+      cta_instr<Real>(A, vec, vec, n, I, lam, rg, r, w, bitmask, m3b, red, bcast, tid);
       if (I.kind == 0) {
-        for (uint32_t x = tid; x < n; x += blockDim.x) {
-          Cplx<Real> v = vec[x], hi;
-          hi.re = sg * s * v.im;
-          hi.im = -sg * s * v.re;
-          vec[x + n] = hi;
-          v.re *= c;
-          v.im *= c;
-          vec[x] = v;
-        }
         ++k;
-      } else if (I.kind == 1) {
-        const Real mu = I.mu == 0 ? (Real)1 : (Real)-1;
-        for (uint32_t x = tid; x < n; x += blockDim.x) {
-          const Real f = sg * mu * s * ((__popc(x & I.b) & 1) ? (Real)-1 : (Real)1);
-          const Cplx<Real> v = vec[x];
-          Cplx<Real> o;
-          o.re = c * v.re + f * v.im;
-          o.im = c * v.im - f * v.re;
-          vec[x] = o;
-        }
-      } else if (I.kind == 2) {
-        const int pb = 31 - __clz(I.a);
-        Real cr, ci;
-        switch (I.mu & 3) {
-          case 0: cr = 0; ci = -1; break;
-          case 1: cr = 1; ci = 0; break;
-          case 2: cr = 0; ci = 1; break;
-          default: cr = -1; ci = 0; break;
-        }
-        cr *= sg * s;
-        ci *= sg * s;
-        for (uint32_t z = tid; z < (n >> 1); z += blockDim.x) {
-          const uint32_t x0 = insert_bit(z, pb, 0u), x1 = x0 ^ I.a;
-          const Cplx<Real> v0 = vec[x0], v1 = vec[x1];
-          const Real s1 = (__popc(x1 & I.b) & 1) ? (Real)-1 : (Real)1;
-          const Real s0 = (__popc(x0 & I.b) & 1) ? (Real)-1 : (Real)1;
-          Cplx<Real> o0, o1;
-          o0.re = c * v0.re + s1 * (cr * v1.re - ci * v1.im);
-          o0.im = c * v0.im + s1 * (cr * v1.im + ci * v1.re);
-          o1.re = c * v1.re + s0 * (cr * v0.re - ci * v0.im);
-          o1.im = c * v1.im + s0 * (cr * v0.im + ci * v0.re);
-          vec[x0] = o0;
-          vec[x1] = o1;
-        }
-      } else {
-        const int h = I.h;
-        const Real inv_sqrt2 = (Real)0.70710678118654752440;
-        Real mcr = 0, mci = 0;
-        if (I.kind == 6) {
-          switch (I.mu & 3) {
-            case 0: mcr = 1; mci = 0; break;
-            case 1: mcr = 0; mci = -1; break;
-            case 2: mcr = -1; mci = 0; break;
-            default: mcr = 0; mci = 1; break;
-          }
-        }
-        const uint32_t l0 = I.kind == 5 ? (lam ^ (uint32_t)I.eta) : lam;
-        double S0 = 0.0, S1 = 0.0;
-        if (sizeof(Real) == 8 || n >= (1u << 14)) {    // FP64 sums
-          branch_sums<Real, double>(vec, I, n, tid, blockDim.x, mcr, mci, S0, S1);
-          warp_sum2(S0, S1);
-        } else {                                       // FP32 sums below 2^14 terms
-          float F0 = 0.0f, F1 = 0.0f;
-          branch_sums<Real, float>(vec, I, n, tid, blockDim.x, mcr, mci, F0, F1);
-          warp_sum2(F0, F1);
-          S0 = F0;
-          S1 = F1;
-        }
-        if ((tid & 31) == 0) {
-          red[tid >> 5] = S0;
-          red[kCtaThreads / 32 + (tid >> 5)] = S1;
-        }
-        __syncthreads();
-        S0 = 0.0;
-        S1 = 0.0;
-        for (int w2 = 0; w2 < kCtaThreads / 32; ++w2) {
-          S0 += red[w2];
-          S1 += red[kCtaThreads / 32 + w2];
-        }
-        if (tid == 0) {
-          const double p0 = (l0 ? S1 : S0) / (S0 + S1);
-          const uint32_t m = decide64(meas_U(A.keys, I.t, rg), p0);
-          if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = p0;
-          bcast[1] = (int)m;
-          if (m) {
-            m3b[I.m3 >> 5] |= 1u << (I.m3 & 31);
-            atomicOr(reinterpret_cast<unsigned long long*>(A.m3_out) + (uint64_t)I.m3 * A.W + w,
-                     (unsigned long long)bitmask);
-          }
-        }
-        __syncthreads();
-        const uint32_t m = (uint32_t)bcast[1];
-        const uint32_t lab = l0 ^ m;
-        const Real scale = (Real)(1.0 / sqrt(lab ? S1 : S0));
-        const uint32_t half = n >> 1;
-        for (uint32_t z0 = 0; z0 < half; z0 += blockDim.x) {
-          const uint32_t z = z0 + tid;
-          Cplx<Real> v;
-          v.re = 0;
-          v.im = 0;
-          if (z < half) {
-            if (I.kind == 5) {
-              const uint32_t u = insert_bit(z, h, lab);
-              v = vec[u ^ ((uint32_t)(__popc(u & I.b & ~(1u << h)) & 1) << h)];
-            } else {
-              const uint32_t u0 = insert_bit(z, h, 0u);
-              const Cplx<Real> a0 = vec[u0], a1 = vec[u0 ^ I.a];
-              Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
-              if (lab) sb = -sb;
-              const Real tr = sb * (mcr * a1.re - mci * a1.im), tim = sb * (mcr * a1.im + mci * a1.re);
-              v.re = (a0.re + tr) * inv_sqrt2;
-              v.im = (a0.im + tim) * inv_sqrt2;
-            }
-            v.re *= scale;
-            v.im *= scale;
-          }
-          __syncthreads();
-          if (z < half) vec[z] = v;
-          __syncthreads();
-        }
+      } else if (I.kind == 5 || I.kind == 6) {
         --k;
+        if (A.det_exo && I.post_grp != kNoGroup) {   // early exit once rejected
+          const bool dead = group_rejects(A.p, A.det_exo, A.W, r, I.post_grp, m3b);
+          __syncthreads();
+          if (dead) break;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Product-component program on one CTA per shot: the component workspace
+// (pc_capacity amplitudes) in shared memory or a per-CTA global slot, every
+// INIT / MERGE / APPLY op executed by the whole CTA (for components of
+// thousands of amplitudes, where one warp per shot leaves the SM idle).
+template <typename Real>
+__global__ void __launch_bounds__(kCtaThreads) dense_pc_cta_kernel(DenseArgs A) {
+  extern __shared__ __align__(16) unsigned char csm[];
+  const uint32_t tid = threadIdx.x;
+  const uint32_t m3w = (A.p.n_m3 + 31) / 32;
+  uint32_t* m3b = reinterpret_cast<uint32_t*>(csm);
+  double* red = reinterpret_cast<double*>(csm + align16(m3w * 4 + 16));
+  int* bcast = reinterpret_cast<int*>(red + 2 * (kCtaThreads / 32));
+  Cplx<Real>* ws = A.use_smem
+                       ? reinterpret_cast<Cplx<Real>*>(csm + align16(m3w * 4 + 16) + align16(2 * (kCtaThreads / 32) * 8 + 16))
+                       : reinterpret_cast<Cplx<Real>*>(A.gvec) + (uint64_t)blockIdx.x * A.gvec_stride;
+  for (uint64_t r = blockIdx.x; r < A.shots; r += gridDim.x) {
+    const uint64_t rg = A.shot0 + r;
+    const uint64_t w = r >> 6;
+    const uint64_t bitmask = 1ull << (r & 63);
+    for (uint32_t i = tid; i < m3w; i += blockDim.x) m3b[i] = 0u;
+    __syncthreads();
+    const bool dead0 = A.det_exo && A.p.post_grp0 == 0 && group_rejects(A.p, A.det_exo, A.W, r, 0, m3b);
+    __syncthreads();
+    if (dead0) continue;
+    for (uint32_t q = 0; q < A.p.n_pc; ++q) {
+      const PCOp O = A.p.pc[q];
+      if (O.op == PC_MERGE) {
+        const uint32_t na = 1u << O.kA, nc = 1u << (O.kA + O.kB);
+        const Cplx<Real>* pa = ws + O.offA;
+        const Cplx<Real>* pb = ws + O.offB;
+        Cplx<Real>* pcv = ws + O.off;
+        for (uint32_t x = tid; x < nc; x += blockDim.x) {
+          const Cplx<Real> u = pa[x & (na - 1)], v = pb[x >> O.kA];
+          Cplx<Real> t;
+          t.re = u.re * v.re - u.im * v.im;
+          t.im = u.re * v.im + u.im * v.re;
+          pcv[x] = t;
+        }
+        __syncthreads();
+        continue;
+      }
+      DenseInstrDev I = A.p.dense[O.g];
+      if (tid == 0) {
+        uint32_t lam = (uint32_t)((__ldg(A.signs + (uint64_t)I.sign_target_col * A.W + w) & bitmask) != 0);
+        for (uint32_t c = 0; c < I.causal_n; ++c) {
+          const uint32_t j = __ldg(A.p.dense_causal + I.causal_off + c);
+          lam ^= (m3b[j >> 5] >> (j & 31)) & 1u;
+        }
+        bcast[0] = (int)lam;
+        if (O.op == PC_INIT) {
+          ws[O.off].re = (Real)1;
+          ws[O.off].im = (Real)0;
+        }
+      }
+      __syncthreads();
+      const uint32_t lam = (uint32_t)bcast[0];
+      Cplx<Real>* vec = ws + O.off;
+      if (O.op == PC_INIT) {
+        cta_instr<Real>(A, vec, vec, 1u, I, lam, rg, r, w, bitmask, m3b, red, bcast, tid);
+        __syncthreads();
+        continue;
+      }
+      I.a = O.a;
+      I.b = O.b;
+      I.h = O.h;
+      cta_instr<Real>(A, vec, ws + O.out, 1u << O.k, I, lam, rg, r, w, bitmask, m3b, red, bcast, tid);
+      if (I.kind == 5 || I.kind == 6) {
         if (A.det_exo && I.post_grp != kNoGroup) {   // early exit once rejected
           const bool dead = group_rejects(A.p, A.det_exo, A.W, r, I.post_grp, m3b);
           __syncthreads();
@@ -1332,6 +1426,12 @@ cudaError_t launch_dense_pc(const DenseArgs& a, bool fp64, int warps_per_block, 
   return cudaGetLastError();
 }
 
+cudaError_t launch_dense_pc_cta(const DenseArgs& a, bool fp64, int grid, size_t smem, cudaStream_t st) {
+  if (fp64) dense_pc_cta_kernel<double><<<grid, kCtaThreads, smem, st>>>(a);
+  else dense_pc_cta_kernel<float><<<grid, kCtaThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_dense(const DenseArgs& a, bool fp64, int warps_per_block, int grid, size_t smem, cudaStream_t st) {
   return fp64 ? launch_dense_t<double>(a, warps_per_block, grid, smem, st)
               : launch_dense_t<float>(a, warps_per_block, grid, smem, st);
@@ -1350,6 +1450,7 @@ cudaError_t set_smem_limits() {
   const void* fns[] = {sign_kernel_fn(),
                        (const void*)dense_kernel<float>, (const void*)dense_kernel<double>,
                        (const void*)dense_pc_kernel<float>, (const void*)dense_pc_kernel<double>,
+                       (const void*)dense_pc_cta_kernel<float>, (const void*)dense_pc_cta_kernel<double>,
                        (const void*)dense_reg_kernel<float>, (const void*)dense_reg_kernel<double>,
                        (const void*)dense_cta_kernel<float>, (const void*)dense_cta_kernel<double>,
                        (const void*)plain_kernel<float>, (const void*)plain_kernel<double>};

@@ -54,6 +54,7 @@ cudaError_t launch_dense_cta(const DenseArgs& a, bool fp64, int grid, size_t sme
 cudaError_t launch_dense_reg(const DenseArgs& a, bool fp64, int grid, cudaStream_t st);
 cudaError_t launch_dense_pc(const DenseArgs& a, bool fp64, int warps_per_block, int grid, size_t smem,
                             cudaStream_t st);
+cudaError_t launch_dense_pc_cta(const DenseArgs& a, bool fp64, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_plain(const PlainArgs& a, bool fp64, int grid, cudaStream_t st);
 // all dense instructions for one batch of the wide executor (host_dense: the
 // plan's instruction stream in host memory, for the per-instruction launches)
@@ -69,8 +70,8 @@ struct Tune {
   int dense_grid_mult = 8;   // register / warp executors: CTAs per SM
   int dense_wpb = 0;         // warp executor: warps (shots) per CTA
   int cta_grid_mult = 2;     // CTA executor with global vectors: CTAs per SM
-  int dense_kind = 0;        // dense executor (1 register, 2 warp, 3 CTA, 4 wide, 5 product
-                             // components; 0 = the cost model's choice)
+  int dense_kind = 0;        // dense executor (1 register, 2 warp, 3 CTA, 4 wide, 5 / 6 product
+                             // components on a warp / a CTA; 0 = the cost model's choice)
   float best_ms_per_shot = 0.0f;
 };
 

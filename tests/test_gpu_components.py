@@ -16,9 +16,10 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def _run(text, shots, seed, precision, product_components, postselect=0):
+def _run(text, shots, seed, precision, product_components, postselect=0, executor="auto"):
     import paper_2607_28600_b300 as S
-    plan = S.symft_compile(text, postselect=postselect, product_components=product_components)
+    plan = S.symft_compile(text, postselect=postselect, product_components=product_components,
+                           executor=executor)
     info = plan.info
     W = (shots + 63) // 64
     cols = [torch.zeros((max(1, info[k]), W), dtype=torch.int64, device="cuda")
@@ -40,7 +41,8 @@ def test_literal_distillation_components_vs_statevector():
     shots, seed = 48, 23
     plan, rec64, p64 = _gpu_probs(text, shots, seed, precision=1)
     info = plan.info
-    assert info["pc_selected"] == 1 and info["dense_executor"] == ["components", "components"]
+    assert info["pc_selected"] == 1
+    assert all(e.startswith("components") for e in info["dense_executor"])
     assert info["pc_capacity"] < (1 << info["k_max"])
     act = plan.active_meas()
     ref = _sv_probs(text, seed, shots, act)
@@ -54,17 +56,19 @@ def test_literal_distillation_components_vs_statevector():
 
 @pytest.mark.parametrize("which", ["literal", "coherent_d5_r1"])
 @pytest.mark.parametrize("precision", [1, 0])
-def test_components_equal_monolithic(which, precision):
-    """Same plan with and without the product components, postselection on
-    (early exit inside the component program): FP64 bit-exact, FP32 equal on
-    every shot without an outcome flip."""
+@pytest.mark.parametrize("executor", ["components_cta", "components_warp"])
+def test_components_equal_monolithic(which, precision, executor):
+    """Same plan with and without the product components (on one CTA or one
+    warp per shot), postselection on (early exit inside the component
+    program): FP64 bit-exact, FP32 equal on every shot without an outcome
+    flip."""
     text = (distillation_15_to_1(1e-3, "literal") if which == "literal"
             else coherent_surface_code_memory(5, 1, 1e-3, 0.02))
     shots, seed = (4000, 3) if which == "literal" else (600, 4)
-    p1, a = _run(text, shots, seed, precision, True, postselect=1)
+    p1, a = _run(text, shots, seed, precision, True, postselect=1, executor=executor)
     p0, b = _run(text, shots, seed, precision, False, postselect=1)
-    assert p1.info["dense_executor"][precision] == "components"
-    assert p0.info["dense_executor"][precision] != "components"
+    assert p1.info["dense_executor"][precision] == executor
+    assert not p0.info["dense_executor"][precision].startswith("components")
     if precision == 1:
         for x, y in zip(a, b):
             np.testing.assert_array_equal(x, y)
@@ -90,3 +94,21 @@ def test_components_random_circuits_vs_statevector(case):
     np.testing.assert_array_equal(g[0], m[0])
     if plan.info["k_max"] > 5:
         assert plan.info["pc_work"][0] <= plan.info["pc_work"][1] * 2
+
+
+@pytest.mark.parametrize("which", ["coherent_d3_r3", "random"])
+def test_every_executor_gives_the_same_bits(which):
+    """Every dense executor that can run a plan (warp, CTA, wide, product
+    components on a warp or a CTA; the autotuner may pick any of them)
+    samples the same FP64 bits."""
+    text = (coherent_surface_code_memory(3, 3, 1e-3, 0.02) if which == "coherent_d3_r3"
+            else random_near_clifford(14, 4, 12, 2e-3, seed=61))
+    shots, seed = 1500, 12
+    outs = {}
+    for ex in ("warp", "cta", "wide", "components_warp", "components_cta"):
+        plan, o = _run(text, shots, seed, 1, True, postselect=1, executor=ex)
+        assert plan.info["dense_executor"][1] == ex
+        outs[ex] = o
+    for ex, o in outs.items():
+        for x, y in zip(outs["warp"], o):
+            np.testing.assert_array_equal(x, y, err_msg=ex)
