@@ -329,12 +329,13 @@ bool dense_kind_valid(const symft_plan* P, const HostPlan& h, bool fp64, int kin
 }
 
 // The executor for a plan: the tuned choice when it is valid, else the
-// product-component executor (CTA per shot when the workspace fits its shared
-// memory, else warp per shot) when its cost model selected it, else the first
-// valid kind in the order register, warp, CTA, wide (smallest footprint first).
+// product-component executor on one warp per shot when its cost model
+// selected it (measured faster than one CTA per shot on the component
+// programs here: a CTA pays a barrier per op on mostly small components), else
+// the first valid kind in the order register, warp, CTA, wide (smallest
+// footprint first).
 int dense_kind_for(const symft_plan* P, const HostPlan& h, bool fp64, int tuned) {
   if (tuned && dense_kind_valid(P, h, fp64, tuned)) return tuned;
-  if (h.pc.use && dense_kind_valid(P, h, fp64, 6)) return 6;
   if (h.pc.use && dense_kind_valid(P, h, fp64, 5)) return 5;
   for (int k = 1; k <= 4; ++k)
     if (dense_kind_valid(P, h, fp64, k)) return k;
