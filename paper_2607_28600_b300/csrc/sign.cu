@@ -323,26 +323,32 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
       const uint32_t i0 = threadIdx.x / kSub;
       const uint64_t wa = 2 * (sub0 + b);                 // first 64-shot word of the piece
       if (b < nsub) {
+        // full pieces (both words hold only real shots, W even and the array
+        // 16-byte aligned, so every piece is too) are one 16-byte store; the
+        // request's last piece is masked
+        const bool full = 64 * (wa + 2) <= A.shots && (A.W & 1) == 0;
         const uint64_t la = A.shots - 64 * wa;            // shots in word wa (>= 1)
         const uint64_t m0 = la < 64 ? (1ull << la) - 1 : ~0ull;
         const bool hb = wa + 1 < A.W;                     // the piece has a second word
         const uint64_t lb = hb ? A.shots - 64 * (wa + 1) : 0;
         const uint64_t m1 = !hb ? 0ull : (lb < 64 ? (1ull << lb) - 1 : ~0ull);
-        auto put = [&](uint64_t* d, uint4 v) {
-          const uint64_t v0 = (((uint64_t)v.y << 32) | v.x) & m0, v1 = (((uint64_t)v.w << 32) | v.z) & m1;
-          if (hb && ((reinterpret_cast<uintptr_t>(d) & 15) == 0)) {
-            *reinterpret_cast<ulonglong2*>(d) = make_ulonglong2(v0, v1);
+        auto put = [&](uint64_t* d, uint4 v, bool al) {
+          if (full && al) {
+            *reinterpret_cast<uint4*>(d) = v;
           } else {
-            d[0] = v0;
-            if (hb) d[1] = v1;
+            d[0] = (((uint64_t)v.y << 32) | v.x) & m0;
+            if (hb) d[1] = (((uint64_t)v.w << 32) | v.z) & m1;
           }
         };
-        if (A.meas)
-          for (uint32_t i = i0; i < R; i += step) put(A.meas + (uint64_t)i * A.W + wa, slots[(size_t)i * kSub + b]);
-        for (uint32_t j = i0; j < DO; j += step) {
-          uint64_t* col = j < A.p.n_dets ? (A.det ? A.det + (uint64_t)j * A.W : nullptr)
-                                         : (A.obs ? A.obs + (uint64_t)(j - A.p.n_dets) * A.W : nullptr);
-          if (col == nullptr) continue;
+        const uint64_t cstep = (uint64_t)step * A.W;
+        if (A.meas) {
+          uint64_t* d = A.meas + (uint64_t)i0 * A.W + wa;
+          const uint4* sl = slots + (size_t)i0 * kSub + b;
+          const bool al = ((reinterpret_cast<uintptr_t>(A.meas) & 15) == 0);
+          for (uint32_t i = i0; i < R; i += step, d += cstep, sl += (size_t)step * kSub) put(d, *sl, al);
+        }
+        // detectors, then observables: XOR of the gathered records' slots
+        auto gather = [&](uint32_t j) {
           uint4 v = make_uint4(0u, 0u, 0u, 0u);
           const uint4 gi = __ldg(A.p.gat_item + j);
           const uint32_t n = gi.x & 0xFFFFu;
@@ -357,11 +363,24 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
               v = xor4(v, slots[f[k] * kSub + b]);
             }
           }
-          put(col + wa, v);
+          return v;
+        };
+        const uint32_t ND = A.p.n_dets;
+        if (A.det) {
+          uint64_t* d = A.det + (uint64_t)i0 * A.W + wa;
+          const bool al = ((reinterpret_cast<uintptr_t>(A.det) & 15) == 0);
+          for (uint32_t j = i0; j < ND; j += step, d += cstep) put(d, gather(j), al);
         }
-        if (A.signs)
-          for (uint32_t g = i0; g < NT - R; g += step)
-            put(A.signs + (uint64_t)g * A.W + wa, slots[(size_t)(R + g) * kSub + b]);
+        if (A.obs) {
+          uint64_t* d = A.obs + (uint64_t)i0 * A.W + wa;
+          const bool al = ((reinterpret_cast<uintptr_t>(A.obs) & 15) == 0);
+          for (uint32_t j = i0; j < DO - ND; j += step, d += cstep) put(d, gather(ND + j), al);
+        }
+        if (A.signs) {
+          uint64_t* d = A.signs + (uint64_t)i0 * A.W + wa;
+          const bool al = ((reinterpret_cast<uintptr_t>(A.signs) & 15) == 0);
+          for (uint32_t g = i0; g < NT - R; g += step, d += cstep) put(d, slots[(size_t)(R + g) * kSub + b], al);
+        }
       }
     }
     __syncthreads();
