@@ -28,6 +28,10 @@ __device__ __forceinline__ int first_above(const uint32_t* th, const uint16_t* b
   return j;
 }
 
+// x mod kQueue for x < 2 kQueue (every ring index sum below stays under that:
+// qh < kQueue, at most 64 entries live after a drain, lane / popc <= 32)
+__device__ __forceinline__ uint32_t ring(uint32_t x) { return x >= (uint32_t)kQueue ? x - kQueue : x; }
+
 // XOR `bit` into word `wb` of the first n (<= 7) slots of a cell target entry
 __device__ __forceinline__ void scatter7(uint32_t* sw, uint4 tg, uint32_t n, uint32_t wb, uint32_t bit) {
   const uint32_t f[7] = {tg.x >> 16, tg.y & 0xFFFFu, tg.y >> 16, tg.z & 0xFFFFu, tg.z >> 16,
@@ -204,17 +208,17 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
     // full-warp drain of the 32 oldest queued states; continuing channels are
     // re-queued at the back of the ring
     auto drain32 = [&]() {
-      const uint32_t src = (qh + lane) % kQueue;
+      const uint32_t src = ring(qh + lane);
       const uint4 ent = qa[src];
       const uint32_t cell0 = qb[src];
       __syncwarp();
-      qh = (qh + 32) % kQueue;
+      qh = ring(qh + 32);
       qn -= 32;
       uint4 next = make_uint4(0u, 0u, 0u, 0u);
       const bool more = fire_step(ent, cell0, next);
       const uint32_t bal = __ballot_sync(0xffffffffu, more);
       if (more) {
-        const uint32_t pos = (qh + qn + __popc(bal & lt_mask)) % kQueue;
+        const uint32_t pos = ring(qh + qn + __popc(bal & lt_mask));
         qa[pos] = next;
         qb[pos] = cell0;
       }
@@ -239,7 +243,7 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
         if (b0m | b1m) {
           // slot order: lane-major pairs; position = entries of lower lanes + own
           const uint32_t lower = __popc(b0m & lt_mask) + __popc(b1m & lt_mask);
-          uint32_t pos = (qh + qn + lower) % kQueue;
+          uint32_t pos = ring(qh + qn + lower);
           if (f0) {
             const uint32_t c = 4 * g + h2;
             const uint4 raw = __ldg(reinterpret_cast<const uint4*>(A.p.ch) + c);
@@ -274,8 +278,8 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
     uint4 mine = make_uint4(0u, 0u, 0u, 0u);
     uint32_t mineb = 0;
     if ((uint32_t)lane < qn) {
-      mine = qa[(qh + lane) % kQueue];
-      mineb = qb[(qh + lane) % kQueue];
+      mine = qa[ring(qh + lane)];
+      mineb = qb[ring(qh + lane)];
     }
     __syncthreads();
     uint4* pool_a = reinterpret_cast<uint4*>(smem_raw + Lay.qa_off);
