@@ -165,17 +165,17 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
     //    block-geometric process continues, so every step costs the same.
     uint32_t qn = 0, qh = 0;     // ring buffer: entries (qh + i) % kQueue, i < qn
     // Resolve the fire of one queued state (whose uniform is known to fire):
-    // its lane, its Pauli cell, and the XOR of the lane's bit into the slots
-    // of the cell's target entry.  The next uniform is tested here; returns
-    // true (and the next state) only if the channel fires again.
-    auto fire_step = [&](uint4 ent, uint32_t cell0, uint4& next) -> bool {
+    // its Pauli cell (whose target entry is loaded right away, so the load is
+    // in flight during the lane search and the re-queue), its lane, and the
+    // word and bit that scatter() XORs into the entry's slots.  The next
+    // uniform is tested here; returns true (and the next state) only if the
+    // channel fires again.
+    auto fire_step = [&](uint4 ent, uint32_t cell0, uint4& next, uint4& tg, uint32_t& wb, uint32_t& bit) -> bool {
       const uint32_t c = ent.x;
       const int L = (int)(ent.z & 0x1FFu);
       uint32_t ti = ent.z >> 9;
       const uint32_t qt = ent.w & 0xFFFFu;
-      const uint32_t* th = sq + (size_t)qt * kNoiseBlock;
       const CellTableDev* ct = sc + (ent.w >> 16);
-      const int lanebit = L + first_above(th, sqb + qt * kQBuckets, sqs[qt], ent.y);   // <= kNoiseBlock-1 by construction
       const uint32_t ncell = ct->ncell;
       // the draws of one fire (cell, next u) lie in one Philox block
       const uint4 tail = philox(make_uint4(c, gblk, ti >> 2, kTagTail), A.keys);
@@ -189,21 +189,25 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
         while (cc < (int)ncell - 1 && v >= ct->phi[cc]) ++cc;
         cell = (uint32_t)cc;
       }
+      tg = __ldg(A.p.cellt + cell0 + cell);
+      const uint32_t* th = sq + (size_t)qt * kNoiseBlock;
+      const int lanebit = L + first_above(th, sqb + qt * kQBuckets, sqs[qt], ent.y);   // <= kNoiseBlock-1 by construction
       const uint32_t u2 = pick(tail, ti & 3);        // next uniform, draw index ti
-      const uint32_t wb = (uint32_t)lanebit >> 5;    // word offset inside a slot
-      const uint32_t bit = 1u << (lanebit & 31);
-      const uint4 tg = __ldg(A.p.cellt + cell0 + cell);
+      wb = (uint32_t)lanebit >> 5;                   // word offset inside a slot
+      bit = 1u << (lanebit & 31);
+      if (lanebit >= kNoiseBlock - 1) return false;
+      const int L2 = lanebit + 1;
+      if (u2 >= th[kNoiseBlock - 1 - L2]) return false;   // no further fire in lanes L2..end
+      next = make_uint4(c, u2, (uint32_t)L2 | ((ti + 1) << 9), ent.w);
+      return true;
+    };
+    auto scatter = [&](uint4 tg, uint32_t wb, uint32_t bit) {
       const uint32_t ntg = tg.x & 0xFFFFu;
       if (ntg == 0xFFFFu) {
         for (uint32_t q = tg.y; q < tg.y + tg.z; ++q) atomicXor(sw + __ldg(A.p.cell_ovf + q) + wb, bit);
       } else {
         scatter7(sw, tg, ntg, wb, bit);
       }
-      if (lanebit >= kNoiseBlock - 1) return false;
-      const int L2 = lanebit + 1;
-      if (u2 >= th[kNoiseBlock - 1 - L2]) return false;   // no further fire in lanes L2..end
-      next = make_uint4(c, u2, (uint32_t)L2 | ((ti + 1) << 9), ent.w);
-      return true;
     };
     // full-warp drain of the 32 oldest queued states; continuing channels are
     // re-queued at the back of the ring
@@ -214,8 +218,9 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
       __syncwarp();
       qh = ring(qh + 32);
       qn -= 32;
-      uint4 next = make_uint4(0u, 0u, 0u, 0u);
-      const bool more = fire_step(ent, cell0, next);
+      uint4 next = make_uint4(0u, 0u, 0u, 0u), tg;
+      uint32_t wb, bit;
+      const bool more = fire_step(ent, cell0, next, tg, wb, bit);
       const uint32_t bal = __ballot_sync(0xffffffffu, more);
       if (more) {
         const uint32_t pos = ring(qh + qn + __popc(bal & lt_mask));
@@ -223,6 +228,7 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
         qb[pos] = cell0;
       }
       qn += __popc(bal);
+      scatter(tg, wb, bit);
       __syncwarp();
     };
     for (uint32_t base = warp * 32; base < n_groups; base += kSignWarps * 32) {
@@ -293,8 +299,10 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
       uint4 ent = pool_a[x];
       const uint32_t cell0 = pool_b[x];
       for (int guard = 0; guard < kNoiseBlock; ++guard) {
-        uint4 next;
-        const bool more = fire_step(ent, cell0, next);
+        uint4 next, tg;
+        uint32_t wb, bit;
+        const bool more = fire_step(ent, cell0, next, tg, wb, bit);
+        scatter(tg, wb, bit);
         if (!more) break;
         ent = next;
       }
