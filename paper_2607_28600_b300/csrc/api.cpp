@@ -476,29 +476,51 @@ int prepare(symft_plan* P, const symft_sample_args* a, uint64_t* meas, uint64_t*
       const uint64_t cap = static_cast<uint64_t>(P->sm_count) * 8 * t.cta_grid_mult;
       o->dense_grid = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(a->shots, cap)));
     } else if (dense_kind_for(P, h, o->fp64, t.dense_kind) == 5) {
-      // product components: one warp per shot, the component workspace in
-      // shared memory when it fits, else in a global slot per resident warp
+      // product components: one warp per shot, its component workspace in
+      // shared memory or in a global slot per warp, whichever keeps more
+      // warps resident per SM (the workspaces bound them in shared memory,
+      // registers in global memory, where the workspaces of the resident
+      // warps mostly stay in L2); a shot is a chain of dependent accesses,
+      // so resident warps are what hides their latency
       o->dense_kind = 5;
       const size_t ws_bytes = static_cast<size_t>(h.pc.capacity) * amp;
-      const size_t bk = dense_warp_smem_bytes(P->dp, 1, 0, false);
-      if (ws_bytes + m3bytes <= 48 * 1024) {
-        int wpb = t.dense_wpb ? t.dense_wpb
-                              : static_cast<int>(std::min<size_t>(8, std::max<size_t>(1, (160 * 1024) / (ws_bytes + bk + 16))));
-        while (wpb > 1 && dense_warp_smem_bytes(P->dp, wpb, ws_bytes, true) > 200 * 1024) --wpb;
-        o->dense_wpb = wpb;
-        o->dense_use_smem = 1;
-        o->dense_smem = dense_warp_smem_bytes(P->dp, wpb, ws_bytes, true);
-        const uint64_t want = (a->shots + wpb - 1) / wpb;
-        const uint64_t cap = static_cast<uint64_t>(P->sm_count) * t.dense_grid_mult * 2;
-        o->dense_grid = static_cast<int>(std::max<uint64_t>(1, std::min(want, cap)));
-      } else {
-        const int wpb = 4;
-        o->dense_wpb = wpb;
-        o->dense_use_smem = 0;
-        o->dense_smem = dense_warp_smem_bytes(P->dp, wpb, 0, false);
-        const uint64_t want = (a->shots + wpb - 1) / wpb;
-        const uint64_t cap = static_cast<uint64_t>(P->sm_count) * t.dense_grid_mult * 2;
-        o->dense_grid = static_cast<int>(std::max<uint64_t>(1, std::min(want, cap)));
+      const int pi = o->fp64 ? 1 : 0;
+      constexpr int kGlobalWpb = 4;
+      if (P->pc_wpb[pi] == 0) {
+        int best = 0, bw = 1, bc = 0;
+        for (int c = 1; c <= 8 && ws_bytes + m3bytes <= 227 * 1024; ++c) {
+          const size_t sm = dense_warp_smem_bytes(P->dp, c, ws_bytes, true);
+          if (sm > 227 * 1024) break;
+          int n = 0;
+          CUDA_TRY(dense_pc_occupancy(o->fp64, c, sm, &n));
+          if (n * c > best) {
+            best = n * c;
+            bw = c;
+            bc = n;
+          }
+        }
+        int ng = 0;
+        CUDA_TRY(dense_pc_occupancy(o->fp64, kGlobalWpb, dense_warp_smem_bytes(P->dp, kGlobalWpb, 0, false), &ng));
+        const bool sm = best > 0 && best >= ng * kGlobalWpb;
+        P->pc_smem[pi] = sm ? 1 : 0;
+        P->pc_wpb[pi] = sm ? bw : kGlobalWpb;
+        P->pc_cps[pi] = sm ? bc : ng;
+      }
+      const bool in_smem = P->pc_smem[pi] != 0;
+      int wpb = t.dense_wpb ? t.dense_wpb : P->pc_wpb[pi];
+      while (in_smem && wpb > 1 && dense_warp_smem_bytes(P->dp, wpb, ws_bytes, true) > 227 * 1024) --wpb;
+      o->dense_wpb = wpb;
+      o->dense_use_smem = in_smem ? 1 : 0;
+      o->dense_smem = dense_warp_smem_bytes(P->dp, wpb, in_smem ? ws_bytes : 0, in_smem);
+      int cps = P->pc_cps[pi];
+      if (wpb != P->pc_wpb[pi]) CUDA_TRY(dense_pc_occupancy(o->fp64, wpb, o->dense_smem, &cps));
+      // resident CTAs times dense_grid_mult / 8 waves: the default, 8, is one
+      // wave of persistent warps (four waves measured no faster, and would
+      // hold four times the global workspace slots)
+      const uint64_t want = (a->shots + wpb - 1) / wpb;
+      const uint64_t cap = static_cast<uint64_t>(P->sm_count) * std::max(1, cps) * std::max(1, t.dense_grid_mult / 8);
+      o->dense_grid = static_cast<int>(std::max<uint64_t>(1, std::min(want, cap)));
+      if (!in_smem) {
         o->gvec_stride = h.pc.capacity;
         CUDA_TRY(P->gvec.ensure(static_cast<size_t>(o->dense_grid) * wpb * ws_bytes));
         o->gvec = P->gvec.ptr;

@@ -160,6 +160,70 @@ __device__ __forceinline__ void branch_sums(const Cplx<Real>* vec, const DenseIn
   }
 }
 
+// Per-element arithmetic of the dense instructions, shared by the
+// per-element and the batched loops below.
+// PromoteRot: a'_x = c a_x, a'_{x+n} = -i sg s a_x
+template <typename Real>
+__device__ __forceinline__ void promote_elem(Cplx<Real>* vec, uint32_t x, uint32_t n, Cplx<Real> v, Real sg,
+                                             Real s, Real c) {
+  Cplx<Real> hi;
+  hi.re = sg * s * v.im;
+  hi.im = -sg * s * v.re;
+  vec[x + n] = hi;
+  v.re *= c;
+  v.im *= c;
+  vec[x] = v;
+}
+// ActiveDiagRot: a_x *= c - i f, f = sg mu s (-1)^{b.x}
+template <typename Real>
+__device__ __forceinline__ void diag_elem(Cplx<Real>* vec, uint32_t x, Cplx<Real> v, Real sgmus, uint32_t b, Real c) {
+  const Real f = sgmus * ((__popc(x & b) & 1) ? (Real)-1 : (Real)1);
+  Cplx<Real> o;
+  o.re = c * v.re + f * v.im;
+  o.im = c * v.im - f * v.re;
+  vec[x] = o;
+}
+// ActivePairRot on the pair (x0, x1 = x0 ^ a): coefficient (cr + i ci) on
+// the partner, with its sign (-1)^{b.partner}
+template <typename Real>
+__device__ __forceinline__ void pair_elem(Cplx<Real>* vec, uint32_t x0, uint32_t x1, Cplx<Real> v0, Cplx<Real> v1,
+                                          uint32_t b, Real c, Real cr, Real ci) {
+  const Real s1 = (__popc(x1 & b) & 1) ? (Real)-1 : (Real)1;   // applied to a_{x1} in a'_{x0}
+  const Real s0 = (__popc(x0 & b) & 1) ? (Real)-1 : (Real)1;
+  Cplx<Real> o0, o1;
+  o0.re = c * v0.re + s1 * (cr * v1.re - ci * v1.im);
+  o0.im = c * v0.im + s1 * (cr * v1.im + ci * v1.re);
+  o1.re = c * v1.re + s0 * (cr * v0.re - ci * v0.im);
+  o1.im = c * v1.im + s0 * (cr * v0.im + ci * v0.re);
+  vec[x0] = o0;
+  vec[x1] = o1;
+}
+// kept amplitude z of an active measurement with label lab, scaled
+template <typename Real>
+__device__ __forceinline__ Cplx<Real> kept_elem(const Cplx<Real>* vec, const DenseInstrDev& I, uint32_t z,
+                                                uint32_t lab, Real mcr, Real mci, Real scale) {
+  const Real inv_sqrt2 = (Real)0.70710678118654752440;
+  const int h = I.h;
+  Cplx<Real> val;
+  if (I.kind == 5) {
+    const uint32_t u = insert_bit(z, h, lab);
+    // x(b,u): bit h = u_h xor parity of b over the other bits
+    const uint32_t x = u ^ ((uint32_t)(__popc(u & I.b & ~(1u << h)) & 1) << h);
+    val = vec[x];
+  } else {
+    const uint32_t u0 = insert_bit(z, h, 0u);
+    const Cplx<Real> a0 = vec[u0], a1 = vec[u0 ^ I.a];
+    Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
+    if (lab) sb = -sb;
+    const Real tr = sb * (mcr * a1.re - mci * a1.im), ti = sb * (mcr * a1.im + mci * a1.re);
+    val.re = (a0.re + tr) * inv_sqrt2;
+    val.im = (a0.im + ti) * inv_sqrt2;
+  }
+  val.re *= scale;
+  val.im *= scale;
+  return val;
+}
+
 // One dense instruction (Sec. 4: PromoteRot, ActiveDiagRot, ActivePairRot,
 // ActiveDiagMeas, ActivePairMeas) on a vector of n = 2^k amplitudes held by
 // one warp (shared or global memory), with the instruction's sign lam; the
@@ -167,7 +231,15 @@ __device__ __forceinline__ void branch_sums(const Cplx<Real>* vec, const DenseIn
 // measurement writes the kept half to out: in place (out == vec) when h is
 // the highest bit of a (pair) or any bit of b (diagonal), else to a disjoint
 // region.
-template <typename Real>
+//
+// kBatch > 1: an instruction over at least 32 kBatch elements (amplitudes,
+// pairs or kept amplitudes) runs in steps of kBatch elements per lane whose
+// loads are all issued before the step's stores, so their shared-memory
+// latencies overlap; the elements of a step are disjoint, and a
+// measurement's in-place compaction reads every source of a step before any
+// of its writes (a source is never below its destination).  Batching costs
+// registers, so only executors whose occupancy is set by shared memory take it.
+template <typename Real, uint32_t kBatch>
 __device__ __forceinline__ void warp_instr(const DenseArgs& A, Cplx<Real>* vec, Cplx<Real>* out, uint32_t n,
                                            const DenseInstrDev& I, uint32_t lam, uint64_t r, uint64_t rg, uint64_t w,
                                            uint64_t bitmask, uint32_t* m3bits, ShotUniforms& su, int lane) {
@@ -176,27 +248,32 @@ __device__ __forceinline__ void warp_instr(const DenseArgs& A, Cplx<Real>* vec, 
 
   switch (I.kind) {
     case 0: {  // PromoteRot: a'_{x} = c a_x, a'_{x+2^k} = -i sg s a_x
-      for (uint32_t x = lane; x < n; x += 32) {
-        Cplx<Real> v = vec[x];
-        Cplx<Real> hi;
-        hi.re = sg * s * v.im;
-        hi.im = -sg * s * v.re;
-        vec[x + n] = hi;
-        v.re *= c;
-        v.im *= c;
-        vec[x] = v;
+      if (kBatch > 1 && n >= 32 * kBatch) {
+        for (uint32_t x0 = lane; x0 < n; x0 += 32 * kBatch) {
+          Cplx<Real> v[kBatch];
+#pragma unroll
+          for (uint32_t j = 0; j < kBatch; ++j) v[j] = vec[x0 + 32 * j];
+#pragma unroll
+          for (uint32_t j = 0; j < kBatch; ++j) promote_elem(vec, x0 + 32 * j, n, v[j], sg, s, c);
+        }
+      } else {
+        for (uint32_t x = lane; x < n; x += 32) promote_elem(vec, x, n, vec[x], sg, s, c);
       }
       break;
     }
     case 1: {  // ActiveDiagRot: a_x *= c - i sg mu (-1)^{b.x} s
       const Real mu = I.mu == 0 ? (Real)1 : (Real)-1;
-      for (uint32_t x = lane; x < n; x += 32) {
-        Real f = sg * mu * s * ((__popc(x & I.b) & 1) ? (Real)-1 : (Real)1);
-        Cplx<Real> v = vec[x];
-        Cplx<Real> o;
-        o.re = c * v.re + f * v.im;
-        o.im = c * v.im - f * v.re;
-        vec[x] = o;
+      const Real sgmus = sg * mu * s;
+      if (kBatch > 1 && n >= 32 * kBatch) {
+        for (uint32_t x0 = lane; x0 < n; x0 += 32 * kBatch) {
+          Cplx<Real> v[kBatch];
+#pragma unroll
+          for (uint32_t j = 0; j < kBatch; ++j) v[j] = vec[x0 + 32 * j];
+#pragma unroll
+          for (uint32_t j = 0; j < kBatch; ++j) diag_elem(vec, x0 + 32 * j, v[j], sgmus, I.b, c);
+        }
+      } else {
+        for (uint32_t x = lane; x < n; x += 32) diag_elem(vec, x, vec[x], sgmus, I.b, c);
       }
       break;
     }
@@ -212,26 +289,32 @@ __device__ __forceinline__ void warp_instr(const DenseArgs& A, Cplx<Real>* vec, 
       }
       cr *= sg * s;
       ci *= sg * s;
-      for (uint32_t z = lane; z < (n >> 1); z += 32) {
-        uint32_t x0 = insert_bit(z, p, 0u);
-        uint32_t x1 = x0 ^ I.a;
-        Cplx<Real> v0 = vec[x0], v1 = vec[x1];
-        Real s1 = (__popc(x1 & I.b) & 1) ? (Real)-1 : (Real)1;   // applied to a_{x1} in a'_{x0}
-        Real s0 = (__popc(x0 & I.b) & 1) ? (Real)-1 : (Real)1;
-        Cplx<Real> o0, o1;
-        o0.re = c * v0.re + s1 * (cr * v1.re - ci * v1.im);
-        o0.im = c * v0.im + s1 * (cr * v1.im + ci * v1.re);
-        o1.re = c * v1.re + s0 * (cr * v0.re - ci * v0.im);
-        o1.im = c * v1.im + s0 * (cr * v0.im + ci * v0.re);
-        vec[x0] = o0;
-        vec[x1] = o1;
+      const uint32_t nh = n >> 1;
+      if (kBatch > 1 && nh >= 32 * kBatch) {
+        for (uint32_t z0 = lane; z0 < nh; z0 += 32 * kBatch) {
+          Cplx<Real> v0[kBatch], v1[kBatch];
+#pragma unroll
+          for (uint32_t j = 0; j < kBatch; ++j) {
+            const uint32_t x0 = insert_bit(z0 + 32 * j, p, 0u);
+            v0[j] = vec[x0];
+            v1[j] = vec[x0 ^ I.a];
+          }
+#pragma unroll
+          for (uint32_t j = 0; j < kBatch; ++j) {
+            const uint32_t x0 = insert_bit(z0 + 32 * j, p, 0u);
+            pair_elem(vec, x0, x0 ^ I.a, v0[j], v1[j], I.b, c, cr, ci);
+          }
+        }
+      } else {
+        for (uint32_t z = lane; z < nh; z += 32) {
+          const uint32_t x0 = insert_bit(z, p, 0u), x1 = x0 ^ I.a;
+          pair_elem(vec, x0, x1, vec[x0], vec[x1], I.b, c, cr, ci);
+        }
       }
       break;
     }
     case 5:
     case 6: {  // active measurements
-      const int h = I.h;
-      const Real inv_sqrt2 = (Real)0.70710678118654752440;
       Real mcr = 0, mci = 0;       // conj(mu)
       if (I.kind == 6) {
         switch (I.mu & 3) {
@@ -279,31 +362,27 @@ __device__ __forceinline__ void warp_instr(const DenseArgs& A, Cplx<Real>* vec, 
       const uint32_t lab = l0 ^ m;
       // compaction in increasing z order (in place, sources are never below z)
       const uint32_t half = n >> 1;
-      for (uint32_t z0 = 0; z0 < half; z0 += 32) {
-        uint32_t z = z0 + lane;
-        Cplx<Real> val;
-        val.re = 0; val.im = 0;
-        if (z < half) {
-          if (I.kind == 5) {
-            uint32_t u = insert_bit(z, h, lab);
-            uint32_t x = u ^ ((uint32_t)(__popc(u & I.b & ~(1u << h)) & 1) << h);
-            // x(b,u): bit h = u_h xor parity of b over the other bits
-            val = vec[x];
-          } else {
-            uint32_t u0 = insert_bit(z, h, 0u);
-            Cplx<Real> a0 = vec[u0], a1 = vec[u0 ^ I.a];
-            Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
-            if (lab) sb = -sb;
-            Real tr = sb * (mcr * a1.re - mci * a1.im), ti = sb * (mcr * a1.im + mci * a1.re);
-            val.re = (a0.re + tr) * inv_sqrt2;
-            val.im = (a0.im + ti) * inv_sqrt2;
-          }
-          val.re *= scale;
-          val.im *= scale;
+      if (kBatch > 1 && half >= 32 * kBatch) {
+        for (uint32_t z0 = lane; z0 < half; z0 += 32 * kBatch) {
+          Cplx<Real> val[kBatch];
+#pragma unroll
+          for (uint32_t j = 0; j < kBatch; ++j) val[j] = kept_elem(vec, I, z0 + 32 * j, lab, mcr, mci, scale);
+          __syncwarp();
+#pragma unroll
+          for (uint32_t j = 0; j < kBatch; ++j) out[z0 + 32 * j] = val[j];
+          __syncwarp();
         }
-        __syncwarp();
-        if (z < half) out[z] = val;
-        __syncwarp();
+      } else {
+        for (uint32_t z0 = 0; z0 < half; z0 += 32) {
+          const uint32_t z = z0 + lane;
+          Cplx<Real> val;
+          val.re = 0;
+          val.im = 0;
+          if (z < half) val = kept_elem(vec, I, z, lab, mcr, mci, scale);
+          __syncwarp();
+          if (z < half) out[z] = val;
+          __syncwarp();
+        }
       }
       if (m) {
         if (lane == 0) {
@@ -375,7 +454,7 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
         lam ^= (m3bits[j >> 5] >> (j & 31)) & 1u;
       }
       const uint32_t n = 1u << k;
-      warp_instr<Real>(A, vec, vec, n, I, lam, r, rg, w, bitmask, m3bits, su, lane);
+      warp_instr<Real, 1>(A, vec, vec, n, I, lam, r, rg, w, bitmask, m3bits, su, lane);
       if (I.kind == 0) ++k;
       else if (I.kind == 5 || I.kind == 6) --k;
       __syncwarp();
@@ -400,6 +479,10 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
 // ---------------------------------------------------------------------------
 template <typename Real>
 __global__ void __launch_bounds__(256) dense_pc_kernel(DenseArgs A) {
+  // warp_instr's batch: a shot's steps are a chain of dependent
+  // shared-memory or L2 round trips, so 8 FP32 elements per lane and step
+  // (measured fastest); FP64 measured no faster batched
+  constexpr uint32_t kPcBatch = sizeof(Real) == 4 ? 8 : 1;
   extern __shared__ unsigned char dsm[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -441,12 +524,25 @@ __global__ void __launch_bounds__(256) dense_pc_kernel(DenseArgs A) {
         const Cplx<Real>* pa = ws + O.offA;
         const Cplx<Real>* pb = ws + O.offB;
         Cplx<Real>* pc = ws + O.off;
-        for (uint32_t x = lane; x < nc; x += 32) {
-          const Cplx<Real> u = pa[x & (na - 1)], v = pb[x >> O.kA];
+        auto kron = [&](uint32_t x, const Cplx<Real>& u, const Cplx<Real>& v) {
           Cplx<Real> t;
           t.re = u.re * v.re - u.im * v.im;
           t.im = u.re * v.im + u.im * v.re;
           pc[x] = t;
+        };
+        if (kPcBatch > 1 && nc >= 32 * kPcBatch) {     // fresh region: disjoint from both factors
+          for (uint32_t x0 = lane; x0 < nc; x0 += 32 * kPcBatch) {
+            Cplx<Real> u[kPcBatch], v[kPcBatch];
+#pragma unroll
+            for (uint32_t j = 0; j < kPcBatch; ++j) {
+              u[j] = pa[(x0 + 32 * j) & (na - 1)];
+              v[j] = pb[(x0 + 32 * j) >> O.kA];
+            }
+#pragma unroll
+            for (uint32_t j = 0; j < kPcBatch; ++j) kron(x0 + 32 * j, u[j], v[j]);
+          }
+        } else {
+          for (uint32_t x = lane; x < nc; x += 32) kron(x, pa[x & (na - 1)], pb[x >> O.kA]);
         }
         __syncwarp();
         continue;
@@ -464,14 +560,14 @@ __global__ void __launch_bounds__(256) dense_pc_kernel(DenseArgs A) {
           vec[0].im = (Real)0;
         }
         __syncwarp();
-        warp_instr<Real>(A, vec, vec, 1u, I, lam, r, rg, w, bitmask, m3bits, su, lane);
+        warp_instr<Real, kPcBatch>(A, vec, vec, 1u, I, lam, r, rg, w, bitmask, m3bits, su, lane);
         __syncwarp();
         continue;
       }
       I.a = O.a;
       I.b = O.b;
       I.h = O.h;
-      warp_instr<Real>(A, vec, ws + O.out, 1u << O.k, I, lam, r, rg, w, bitmask, m3bits, su, lane);
+      warp_instr<Real, kPcBatch>(A, vec, ws + O.out, 1u << O.k, I, lam, r, rg, w, bitmask, m3bits, su, lane);
       __syncwarp();
       if (A.det_exo && I.post_grp != kNoGroup) {           // early exit once rejected
         const bool dead = group_rejects(A.p, A.det_exo, A.W, r, I.post_grp, m3bits);
@@ -1010,7 +1106,7 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs A) {
   int* bcast = reinterpret_cast<int*>(red + 2 * kPlainThreads);
   const uint32_t tid = threadIdx.x;
   const uint32_t k0 = (uint32_t)A.seed, k1 = (uint32_t)(A.seed >> 32);
-  const uint32_t R = P.n_records, DO = P.n_dets + P.n_obs, NO = P.tgt_sign0;
+  const uint32_t R = P.n_records, NO = P.tgt_sign0;
   const uint32_t NTP = NO + P.n_dense;
   const uint32_t n_groups = (P.n_channels + 3) >> 2;
 
@@ -1424,6 +1520,13 @@ cudaError_t launch_dense_pc(const DenseArgs& a, bool fp64, int warps_per_block, 
   if (fp64) dense_pc_kernel<double><<<grid, warps_per_block * 32, smem, st>>>(a);
   else dense_pc_kernel<float><<<grid, warps_per_block * 32, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t dense_pc_occupancy(bool fp64, int warps_per_block, size_t smem, int* ctas_per_sm) {
+  cudaError_t e = set_smem_limits();
+  if (e != cudaSuccess) return e;
+  const void* f = fp64 ? (const void*)dense_pc_kernel<double> : (const void*)dense_pc_kernel<float>;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, f, warps_per_block * 32, smem);
 }
 
 cudaError_t launch_dense_pc_cta(const DenseArgs& a, bool fp64, int grid, size_t smem, cudaStream_t st) {

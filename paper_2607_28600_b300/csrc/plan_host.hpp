@@ -54,6 +54,8 @@ cudaError_t launch_dense_cta(const DenseArgs& a, bool fp64, int grid, size_t sme
 cudaError_t launch_dense_reg(const DenseArgs& a, bool fp64, int grid, cudaStream_t st);
 cudaError_t launch_dense_pc(const DenseArgs& a, bool fp64, int warps_per_block, int grid, size_t smem,
                             cudaStream_t st);
+// resident CTAs per SM of the product-component warp executor for a launch shape
+cudaError_t dense_pc_occupancy(bool fp64, int warps_per_block, size_t smem, int* ctas_per_sm);
 cudaError_t launch_dense_pc_cta(const DenseArgs& a, bool fp64, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_plain(const PlainArgs& a, bool fp64, int grid, cudaStream_t st);
 // all dense instructions for one batch of the wide executor (host_dense: the
@@ -95,6 +97,10 @@ struct symft_plan {
   symft::DevBuf t_meas, t_det, t_obs, t_disc;   // outputs of autotuning probes
   symft::Tune tune[2];                          // FP32, FP64
   int sm_count = 0;
+  // product-component warp executor (FP32, FP64): workspace in shared memory
+  // (1) or global memory (0), warps per CTA and resident CTAs per SM, chosen
+  // by occupancy (pc_wpb 0 = not yet chosen)
+  int pc_smem[2] = {0, 0}, pc_wpb[2] = {0, 0}, pc_cps[2] = {0, 0};
 };
 
 namespace symft {
