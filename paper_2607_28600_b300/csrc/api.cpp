@@ -92,6 +92,8 @@ void build_blob(symft_plan* P) {
     o.m3 = d.m3;
     o.c = d.c;
     o.s = d.s;
+    o.cf = static_cast<float>(d.c);
+    o.sf = static_cast<float>(d.s);
     o.sign_target_col = d.sign_target - h.n_records;
     o.causal_off = d.causal_off;
     o.causal_n = d.causal_n;
@@ -317,7 +319,7 @@ bool dense_kind_valid(const symft_plan* P, const HostPlan& h, bool fp64, int kin
   const size_t m3bytes = ((h.n_m3 + 31) / 32) * 4;
   const size_t vec_bytes = (static_cast<size_t>(1) << h.k_max) * amp;
   switch (kind) {
-    case 1: return h.k_max <= 5 && dense_reg_smem_bytes(P->dp) <= 96 * 1024;
+    case 1: return h.k_max >= 1 && h.k_max <= 5 && dense_reg_smem_bytes(P->dp) <= 96 * 1024;
     case 2: return vec_bytes + m3bytes <= 48 * 1024 && dense_warp_smem_bytes(P->dp, 1, vec_bytes, true) <= 200 * 1024;
     case 3: return dense_cta_smem_bytes(P->dp, vec_bytes, true) <= 200 * 1024;
     case 4: return true;
@@ -526,8 +528,10 @@ int prepare(symft_plan* P, const symft_sample_args* a, uint64_t* meas, uint64_t*
         o->gvec = P->gvec.ptr;
       }
     } else if (dense_kind_for(P, h, o->fp64, t.dense_kind) == 1) {
-      o->dense_kind = 1;   // register-resident: lane x holds amplitude x
-      const uint64_t want = (a->shots + 7) / 8;
+      o->dense_kind = 1;   // register-resident: 32 / 2^k_max shots per warp, lane x of a shot's
+                           // segment holds amplitude x
+      const uint64_t per_cta = 8ull * (32u >> h.k_max);
+      const uint64_t want = (a->shots + per_cta - 1) / per_cta;
       const uint64_t cap = static_cast<uint64_t>(P->sm_count) * t.dense_grid_mult;
       o->dense_grid = static_cast<int>(std::max<uint64_t>(1, std::min(want, cap)));
     } else if (dense_kind_for(P, h, o->fp64, t.dense_kind) == 2) {

@@ -66,19 +66,22 @@ __device__ __forceinline__ uint64_t meas_U(const PhiloxKeys& K, uint32_t t, uint
   return (bit << 52) + (fw >> 12);
 }
 
-// The uniforms of a shot's active measurements, 32 at a time: lane l holds U
-// of active measurement 32 c + l for the current chunk c; a measurement reads
-// its value by a shuffle and moves to the next chunk when it leaves this one.
+// The uniforms of a shot's active measurements, one chunk at a time: the
+// shot's lanes (a segment of 2^lw lanes from lane `base`; the whole warp when
+// lw = 5) hold U of active measurements (c << lw) + l for the current chunk c,
+// lane l holding one; a measurement reads its value by a shuffle and moves to
+// the next chunk when it leaves this one.
 struct ShotUniforms {
   uint64_t uc = 0;
   uint32_t chunk = 0xFFFFFFFFu;
-  __device__ __forceinline__ uint64_t get(const DenseArgs& A, uint32_t j, uint64_t rg, int lane) {
-    if ((j >> 5) != chunk) {
-      chunk = j >> 5;
-      const uint32_t jj = (chunk << 5) + (uint32_t)lane;
+  __device__ __forceinline__ uint64_t get(const DenseArgs& A, uint32_t j, uint64_t rg, int l, uint32_t lw = 5,
+                                          int base = 0) {
+    if ((j >> lw) != chunk) {
+      chunk = j >> lw;
+      const uint32_t jj = (chunk << lw) + (uint32_t)l;
       uc = jj < A.p.n_m3 ? meas_U(A.keys, __ldg(A.p.m3_t + jj), rg) : 0ull;
     }
-    return __shfl_sync(0xffffffffu, uc, (int)(j & 31));
+    return __shfl_sync(0xffffffffu, uc, base + (int)(j & ((1u << lw) - 1u)));
   }
 };
 
@@ -244,7 +247,7 @@ __device__ __forceinline__ void warp_instr(const DenseArgs& A, Cplx<Real>* vec, 
                                            const DenseInstrDev& I, uint32_t lam, uint64_t r, uint64_t rg, uint64_t w,
                                            uint64_t bitmask, uint32_t* m3bits, ShotUniforms& su, int lane) {
   const Real sg = lam ? (Real)-1 : (Real)1;
-  const Real c = (Real)I.c, s = (Real)I.s;
+  const Real c = coef_c<Real>(I), s = coef_s<Real>(I);
 
   switch (I.kind) {
     case 0: {  // PromoteRot: a'_{x} = c a_x, a'_{x+2^k} = -i sg s a_x
@@ -579,10 +582,13 @@ __global__ void __launch_bounds__(256) dense_pc_kernel(DenseArgs A) {
 }
 
 // ---------------------------------------------------------------------------
-// Register-resident dense executor for k_max <= 5: one warp per shot, lane x
-// holds amplitude alpha_x (zero beyond 2^k); PromoteRot, pair partners and
-// compaction sources are warp shuffles.  The instruction stream sits in shared
-// memory and each shot's exogenous sign bits are fetched in one coalesced pass.
+// Register-resident dense executor for k_max <= 5: a warp holds 32 / 2^k_max
+// shots, one per segment of 2^k_max lanes; lane x of a segment holds its
+// shot's amplitude alpha_x (zero beyond 2^k), and PromoteRot, pair partners,
+// compaction sources and branch sums are shuffles inside the segment.  The
+// instruction stream sits in shared memory and is decoded once for all the
+// warp's shots; each shot's exogenous sign bits come in one coalesced pass
+// (the warp's shots share one 32-shot half-word of every sign column).
 // ---------------------------------------------------------------------------
 constexpr int kRegWarps = 8;
 
@@ -591,66 +597,76 @@ __device__ __forceinline__ Real shfl_r(Real v, int src) {
   return __shfl_sync(0xffffffffu, v, src);
 }
 
-template <typename Real>
+template <typename Real, uint32_t kLw>
 __global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) {
   extern __shared__ __align__(16) unsigned char rsm[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const uint32_t G = A.p.n_dense;
-  const uint32_t sgw = (G + 31) / 32;
   const uint32_t m3w = (A.p.n_m3 + 31) / 32;
+  constexpr uint32_t lw = kLw;                       // log2 lanes per shot (= k_max)
+  constexpr uint32_t Wd = 1u << lw;
+  constexpr uint32_t S = 32u >> lw;                  // shots per warp
+  const uint32_t seg = (uint32_t)lane >> lw;         // this lane's shot
+  const uint32_t sl = (uint32_t)lane & (Wd - 1u);    // its amplitude index
+  const int base = (int)(seg << lw);                 // the segment's first lane
   DenseInstrDev* ins = reinterpret_cast<DenseInstrDev*>(rsm);
-  uint32_t* sgn = reinterpret_cast<uint32_t*>(rsm + (size_t)G * sizeof(DenseInstrDev)) + (size_t)warp * (sgw + m3w);
-  uint32_t* m3b = sgn + sgw;
+  uint32_t* sgw = reinterpret_cast<uint32_t*>(rsm + (size_t)G * sizeof(DenseInstrDev)) + (size_t)warp * (G + 32 * m3w);
+  uint32_t* m3b = sgw + G + (size_t)seg * m3w;       // this shot's active outcomes
   for (uint32_t i = threadIdx.x; i < G * (sizeof(DenseInstrDev) / 4); i += blockDim.x)
     reinterpret_cast<uint32_t*>(ins)[i] = reinterpret_cast<const uint32_t*>(A.p.dense)[i];
   __syncthreads();
 
-  for (uint64_t r = (uint64_t)blockIdx.x * kRegWarps + warp; r < A.shots; r += (uint64_t)gridDim.x * kRegWarps) {
-    const uint64_t rg = A.shot0 + r;
+  uint32_t lead_mask = 0u;                           // lane 0 of every segment
+  for (uint32_t q = 0; q < S; ++q) lead_mask |= 1u << (q << lw);
+  const uint64_t wstride = (uint64_t)gridDim.x * kRegWarps * S;
+  for (uint64_t r0 = ((uint64_t)blockIdx.x * kRegWarps + warp) * S; r0 < A.shots; r0 += wstride) {
+    const uint64_t r = r0 + seg;                     // request-local shot of this segment
+    const uint64_t rg = A.shot0 + r;                 // absolute shot index
     const uint64_t w = r >> 6;
-    const uint32_t bitpos = (uint32_t)(r & 63);
-    // exogenous sign bits of this shot, 32 instructions per ballot
-    for (uint32_t base = 0; base < G; base += 32) {
-      const uint32_t g = base + lane;
-      bool bit = false;
-      if (g < G) bit = (__ldg(A.signs + (uint64_t)ins[g].sign_target_col * A.W + w) >> bitpos) & 1ull;
-      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-      if (lane == 0) sgn[base >> 5] = bal;
-    }
-    for (uint32_t i = lane; i < m3w; i += 32) m3b[i] = 0u;
+    const uint32_t rb = (uint32_t)(r & 31);          // bit of the shot in its half-word
+    // exogenous sign bits: the 32-shot half-word of each sign column that
+    // holds all of the warp's shots (r0 is a multiple of S <= 32)
+    const uint32_t hw = (uint32_t)(r0 >> 5) & 1u;
+    for (uint32_t g = lane; g < G; g += 32)
+      sgw[g] = (uint32_t)(__ldg(A.signs + (uint64_t)ins[g].sign_target_col * A.W + (r0 >> 6)) >> (32 * hw));
+    for (uint32_t i = lane; i < S * m3w; i += 32) sgw[G + i] = 0u;
     __syncwarp();
-    // a shot rejected before any active measurement needs no dense work
-    const bool dead0 = A.det_exo && A.p.post_grp0 == 0 && group_rejects(A.p, A.det_exo, A.W, r, 0, m3b);
+    // segments past the request, or rejected before any active measurement,
+    // need no dense work; they step along masked while others run
+    bool dead = r >= A.shots;
+    if (!dead && sl == 0 && A.det_exo && A.p.post_grp0 == 0) dead = group_rejects(A.p, A.det_exo, A.W, r, 0, m3b);
+    uint32_t deadm = __ballot_sync(0xffffffffu, sl == 0 && dead);
+    dead = (deadm >> base) & 1u;
     __syncwarp();
-    if (dead0) continue;
+    if ((deadm & lead_mask) == lead_mask) continue;
     ShotUniforms su;
-    Real re = lane == 0 ? (Real)1 : (Real)0, im = (Real)0;
+    Real re = sl == 0 ? (Real)1 : (Real)0, im = (Real)0;
     uint32_t k = 0;
     for (uint32_t g = 0; g < G; ++g) {
       const DenseInstrDev& I = ins[g];
-      uint32_t lam = (sgn[g >> 5] >> (g & 31)) & 1u;
+      uint32_t lam = (sgw[g] >> rb) & 1u;
       for (uint32_t q = 0; q < I.causal_n; ++q) {
         const uint32_t j = __ldg(A.p.dense_causal + I.causal_off + q);
         lam ^= (m3b[j >> 5] >> (j & 31)) & 1u;
       }
       const Real sg = lam ? (Real)-1 : (Real)1;
-      const Real c = (Real)I.c, s = (Real)I.s;
+      const Real c = coef_c<Real>(I), s = coef_s<Real>(I);
       const uint32_t n = 1u << k;
       if (I.kind == 0) {                       // PromoteRot
-        const int src = lane >= (int)n ? lane - (int)n : lane;
+        const int src = base + (int)(sl >= n ? sl - n : sl);
         const Real ore = shfl_r(re, src), oim = shfl_r(im, src);
-        if ((uint32_t)lane < n) {
+        if (sl < n) {
           re *= c;
           im *= c;
-        } else if ((uint32_t)lane < 2 * n) {
+        } else if (sl < 2 * n) {
           re = sg * s * oim;                   // -i sg s alpha
           im = -sg * s * ore;
         }
         ++k;
       } else if (I.kind == 1) {                // ActiveDiagRot
         const Real mu = I.mu == 0 ? (Real)1 : (Real)-1;
-        const Real f = sg * mu * s * ((__popc((uint32_t)lane & I.b) & 1) ? (Real)-1 : (Real)1);
+        const Real f = sg * mu * s * ((__popc(sl & I.b) & 1) ? (Real)-1 : (Real)1);
         const Real nre = c * re + f * im, nim = c * im - f * re;
         re = nre;
         im = nim;
@@ -662,11 +678,11 @@ __global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) 
           case 2: cr = 0; ci = 1; break;
           default: cr = -1; ci = 0; break;
         }
-        const int partner = lane ^ (int)I.a;
-        const Real pre = shfl_r(re, partner & 31), pim = shfl_r(im, partner & 31);
-        const Real sp = ((__popc((uint32_t)partner & I.b) & 1) ? (Real)-1 : (Real)1) * sg * s;
+        const uint32_t partner = (sl ^ I.a) & (Wd - 1u);
+        const Real pre = shfl_r(re, base + (int)partner), pim = shfl_r(im, base + (int)partner);
+        const Real sp = ((__popc(partner & I.b) & 1) ? (Real)-1 : (Real)1) * sg * s;
         const Real nre = c * re + sp * (cr * pre - ci * pim), nim = c * im + sp * (cr * pim + ci * pre);
-        if ((uint32_t)lane < n) {
+        if (sl < n) {
           re = nre;
           im = nim;
         }
@@ -676,14 +692,14 @@ __global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) 
         const Real inv_sqrt2 = (Real)0.70710678118654752440;
         // diag: partition by parity(b.x); pair: beta_z(y) from (u0, u0^a)
         Real b0re = 0, b0im = 0, b1re = 0, b1im = 0;
-        const uint32_t z = (uint32_t)lane;
+        const uint32_t z = sl;
         const uint32_t u0 = insert_bit(z & (half - 1 + (half == 0)), h, 0u);
         Real mcr = 0, mci = 0;
         Real s0 = 0, s1 = 0;                   // this lane's share (one amplitude)
         if (I.kind == 5) {
-          if ((uint32_t)lane < n) {
+          if (sl < n) {
             const Real v = re * re + im * im;
-            if (__popc((uint32_t)lane & I.b) & 1) s1 = v; else s0 = v;
+            if (__popc(sl & I.b) & 1) s1 = v; else s0 = v;
           }
         } else {
           switch (I.mu & 3) {
@@ -692,8 +708,9 @@ __global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) 
             case 2: mcr = -1; mci = 0; break;
             default: mcr = 0; mci = 1; break;
           }
-          const Real a0re = shfl_r(re, (int)(u0 & 31)), a0im = shfl_r(im, (int)(u0 & 31));
-          const Real a1re = shfl_r(re, (int)((u0 ^ I.a) & 31)), a1im = shfl_r(im, (int)((u0 ^ I.a) & 31));
+          const int l0s = base + (int)(u0 & (Wd - 1u)), l1s = base + (int)((u0 ^ I.a) & (Wd - 1u));
+          const Real a0re = shfl_r(re, l0s), a0im = shfl_r(im, l0s);
+          const Real a1re = shfl_r(re, l1s), a1im = shfl_r(im, l1s);
           const Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
           const Real tr = sb * (mcr * a1re - mci * a1im), ti = sb * (mcr * a1im + mci * a1re);
           b0re = (a0re + tr) * inv_sqrt2; b0im = (a0im + ti) * inv_sqrt2;
@@ -703,35 +720,38 @@ __global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) 
             s1 = b1re * b1re + b1im * b1im;
           }
         }
-        // at most 32 terms: sums in the vector's own precision
-        warp_sum2(s0, s1);
+        // at most 32 terms, summed over the segment in the vector's own precision
+        for (uint32_t o = Wd >> 1; o; o >>= 1) {
+          s0 += __shfl_xor_sync(0xffffffffu, s0, (int)o);
+          s1 += __shfl_xor_sync(0xffffffffu, s1, (int)o);
+        }
         const uint32_t l0 = I.kind == 5 ? (lam ^ (uint32_t)I.eta) : lam;
         uint32_t m = 0;
-        const uint64_t U = su.get(A, (uint32_t)I.m3, rg, lane);
-        // decision and the renormalisation scale 1 / sqrt(S_m) on one lane, in
-        // the vector's precision (self-normalised probabilities make the scale
-        // matter only for the overall norm)
+        const uint64_t U = su.get(A, (uint32_t)I.m3, rg, (int)sl, lw, base);
+        // decision and the renormalisation scale 1 / sqrt(S_m) on the segment's
+        // first lane, in the vector's precision (self-normalised probabilities
+        // make the scale matter only for the overall norm)
         Real sc = 0;
-        if (lane == 0) {
-          double pd;
+        if (sl == 0 && !dead) {
           if (sizeof(Real) == 8) {
-            pd = (double)(l0 ? s1 : s0) / (double)(s0 + s1);
+            const double pd = (double)(l0 ? s1 : s0) / (double)(s0 + s1);
             m = decide64(U, pd);
+            if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = pd;
           } else {
             const float pf = (float)((l0 ? s1 : s0) / (s0 + s1));
             m = decide32(U, pf);
-            pd = (double)pf;
+            if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = (double)pf;
           }
-          if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = pd;
           sc = sizeof(Real) == 8 ? (Real)(1.0 / sqrt((double)((l0 ^ m) ? s1 : s0))) : (Real)rsqrtf((float)((l0 ^ m) ? s1 : s0));
         }
-        m = __shfl_sync(0xffffffffu, m, 0);
+        m = __shfl_sync(0xffffffffu, m, base);
         const uint32_t lab = l0 ^ m;
-        const Real scale = shfl_r(sc, 0);
+        const Real scale = shfl_r(sc, base);
         if (I.kind == 5) {
           const uint32_t u = insert_bit(z & (half - 1 + (half == 0)), h, lab);
           const uint32_t x = u ^ ((uint32_t)(__popc(u & I.b & ~(1u << h)) & 1) << h);
-          const Real nre = shfl_r(re, (int)(x & 31)), nim = shfl_r(im, (int)(x & 31));
+          const int xs = base + (int)(x & (Wd - 1u));
+          const Real nre = shfl_r(re, xs), nim = shfl_r(im, xs);
           re = z < half ? nre * scale : (Real)0;
           im = z < half ? nim * scale : (Real)0;
         } else {
@@ -739,16 +759,18 @@ __global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) 
           im = z < half ? (lab ? b1im : b0im) * scale : (Real)0;
         }
         --k;
-        if (m && lane == 0) {
+        if (m && sl == 0) {                    // m is 0 on dead segments
           m3b[I.m3 >> 5] |= 1u << (I.m3 & 31);
           atomicOr(reinterpret_cast<unsigned long long*>(A.m3_out) + (uint64_t)I.m3 * A.W + w,
-                   1ull << bitpos);
+                   1ull << (r & 63));
         }
         __syncwarp();
         if (A.det_exo && I.post_grp != kNoGroup) {   // early exit once rejected
-          const bool dead = group_rejects(A.p, A.det_exo, A.W, r, I.post_grp, m3b);
-          __syncwarp();
-          if (dead) break;
+          bool d2 = dead;
+          if (!d2 && sl == 0) d2 = group_rejects(A.p, A.det_exo, A.W, r, I.post_grp, m3b);
+          deadm = __ballot_sync(0xffffffffu, sl == 0 && d2);
+          dead = (deadm >> base) & 1u;
+          if ((deadm & lead_mask) == lead_mask) break;
         }
       }
     }
@@ -776,7 +798,7 @@ __device__ __forceinline__ void cta_instr(const DenseArgs& A, Cplx<Real>* vec, C
                                           const DenseInstrDev& I, uint32_t lam, uint64_t rg, uint64_t r, uint64_t w,
                                           uint64_t bitmask, uint32_t* m3b, double* red, int* bcast, uint32_t tid) {
   const Real sg = lam ? (Real)-1 : (Real)1;
-  const Real c = (Real)I.c, s = (Real)I.s;
+  const Real c = coef_c<Real>(I), s = coef_s<Real>(I);
   if (I.kind == 0) {
     for (uint32_t x = tid; x < n; x += blockDim.x) {
       Cplx<Real> v = vec[x], hi;
@@ -1224,7 +1246,7 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs A) {
       __syncthreads();
       const uint32_t lam = (uint32_t)bcast[0];
       const Real sg = lam ? (Real)-1 : (Real)1;
-      const Real c = (Real)I.c, s = (Real)I.s;
+      const Real c = coef_c<Real>(I), s = coef_s<Real>(I);
       const uint32_t n = 1u << k;
       if (I.kind == 0) {
         for (uint32_t x = tid; x < n; x += blockDim.x) {
@@ -1506,13 +1528,25 @@ size_t dense_warp_smem_bytes(const DevPlan& p, int wpb, size_t vec_bytes, bool v
 
 size_t dense_reg_smem_bytes(const DevPlan& p) {
   const size_t G = p.n_dense;
-  return G * sizeof(DenseInstrDev) + (size_t)kRegWarps * (((G + 31) / 32) + ((p.n_m3 + 31) / 32)) * 4 + 16;
+  return G * sizeof(DenseInstrDev) + (size_t)kRegWarps * (G + 32 * ((p.n_m3 + 31) / 32)) * 4 + 16;
+}
+
+template <typename Real>
+static void launch_dense_reg_t(const DenseArgs& a, int grid, size_t smem, cudaStream_t st) {
+  switch (a.kmax) {
+    case 1: dense_reg_kernel<Real, 1><<<grid, kRegWarps * 32, smem, st>>>(a); break;
+    case 2: dense_reg_kernel<Real, 2><<<grid, kRegWarps * 32, smem, st>>>(a); break;
+    case 3: dense_reg_kernel<Real, 3><<<grid, kRegWarps * 32, smem, st>>>(a); break;
+    case 4: dense_reg_kernel<Real, 4><<<grid, kRegWarps * 32, smem, st>>>(a); break;
+    default: dense_reg_kernel<Real, 5><<<grid, kRegWarps * 32, smem, st>>>(a); break;
+  }
 }
 
 cudaError_t launch_dense_reg(const DenseArgs& a, bool fp64, int grid, cudaStream_t st) {
+  if (a.kmax < 1 || a.kmax > 5) return cudaErrorInvalidValue;
   const size_t smem = dense_reg_smem_bytes(a.p);
-  if (fp64) dense_reg_kernel<double><<<grid, kRegWarps * 32, smem, st>>>(a);
-  else dense_reg_kernel<float><<<grid, kRegWarps * 32, smem, st>>>(a);
+  if (fp64) launch_dense_reg_t<double>(a, grid, smem, st);
+  else launch_dense_reg_t<float>(a, grid, smem, st);
   return cudaGetLastError();
 }
 
@@ -1554,7 +1588,11 @@ cudaError_t set_smem_limits() {
                        (const void*)dense_kernel<float>, (const void*)dense_kernel<double>,
                        (const void*)dense_pc_kernel<float>, (const void*)dense_pc_kernel<double>,
                        (const void*)dense_pc_cta_kernel<float>, (const void*)dense_pc_cta_kernel<double>,
-                       (const void*)dense_reg_kernel<float>, (const void*)dense_reg_kernel<double>,
+                       (const void*)dense_reg_kernel<float, 1>, (const void*)dense_reg_kernel<float, 2>,
+                       (const void*)dense_reg_kernel<float, 3>, (const void*)dense_reg_kernel<float, 4>,
+                       (const void*)dense_reg_kernel<float, 5>, (const void*)dense_reg_kernel<double, 1>,
+                       (const void*)dense_reg_kernel<double, 2>, (const void*)dense_reg_kernel<double, 3>,
+                       (const void*)dense_reg_kernel<double, 4>, (const void*)dense_reg_kernel<double, 5>,
                        (const void*)dense_cta_kernel<float>, (const void*)dense_cta_kernel<double>,
                        (const void*)plain_kernel<float>, (const void*)plain_kernel<double>};
   for (const void* f : fns) {

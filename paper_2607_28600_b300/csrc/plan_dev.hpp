@@ -54,8 +54,23 @@ struct DenseInstrDev {
   uint32_t t;
   uint32_t post_grp;          // active measurement: detector group to check for early
                               // exit after it, or kNoGroup
+  float cf, sf;               // c and s rounded to FP32 (to nearest) on the host: the
+                              // FP32 executors' coefficients, so no lane converts
+                              // from FP64 (a slow pipe on B300) per instruction
   uint32_t pad;
 };
+
+// The rotation coefficients (c, s) of an instruction in the vector's precision.
+template <typename Real>
+__host__ __device__ inline Real coef_c(const DenseInstrDev& I) {
+  if constexpr (sizeof(Real) == 4) return I.cf;
+  else return I.c;
+}
+template <typename Real>
+__host__ __device__ inline Real coef_s(const DenseInstrDev& I) {
+  if constexpr (sizeof(Real) == 4) return I.sf;
+  else return I.s;
+}
 
 constexpr uint32_t kNoGroup = 0xFFFFFFFFu;
 

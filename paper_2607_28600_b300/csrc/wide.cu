@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kWideThreads) wide_rot_kernel(WideArgs A, uint
   const int lg = I.kind == 2 ? I.k - 1 : I.k;          // pairs for ActivePairRot
   const uint64_t total = (uint64_t)A.nb << lg;
   const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
-  const Real c = (Real)I.c, s = (Real)I.s;
+  const Real c = coef_c<Real>(I), s = coef_s<Real>(I);
   const uint8_t* lamg = A.lam + (size_t)g * A.nb;
   Amp<Real>* vbase = reinterpret_cast<Amp<Real>*>(A.vec[A.cur]);
   if (I.kind == 0) {                    // a'_x = c a_x, a'_{x+n} = -i sg s a_x
@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(kWideThreads) wide_fused_rot_kernel(WideArgs A
       const FuseInstr& L = F.ins[q];
       const uint32_t g = F.g0 + q;
       const DenseInstrDev& I = A.p.dense[g];
-      const Real c = (Real)I.c, s = (Real)I.s;
+      const Real c = coef_c<Real>(I), s = coef_s<Real>(I);
       const Real sgs = A.lam[(size_t)g * A.nb + b] ? -s : s;
       const uint32_t po = __popc(L.b_out & off) & 1u;
       if (L.kind == 0) {                              // a'_x = c a_x, a'_{x+new} = -i sg s a_x

@@ -35,8 +35,9 @@ def _run(text, shots, seed, precision, product_components, postselect=0, executo
 
 
 def test_literal_distillation_components_vs_statevector():
-    """16 qubits, k_max = 15: the component workspace (5,530 amplitudes) is in
-    shared memory in FP32 and in a global slot per warp in FP64."""
+    """16 qubits, k_max = 15: the component workspace (5,530 amplitudes) sits in
+    a global slot per warp in both precisions (the placement that keeps more
+    warps resident per SM)."""
     text = distillation_15_to_1(1e-3, "literal")
     shots, seed = 48, 23
     plan, rec64, p64 = _gpu_probs(text, shots, seed, precision=1)
