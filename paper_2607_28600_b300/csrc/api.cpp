@@ -491,7 +491,7 @@ int prepare(symft_plan* P, const symft_sample_args* a, uint64_t* meas, uint64_t*
       if (P->pc_wpb[pi] == 0) {
         int best = 0, bw = 1, bc = 0;
         for (int c = 1; c <= 8 && ws_bytes + m3bytes <= 227 * 1024; ++c) {
-          const size_t sm = dense_warp_smem_bytes(P->dp, c, ws_bytes, true);
+          const size_t sm = dense_pc_smem_bytes(P->dp, c, ws_bytes, true);
           if (sm > 227 * 1024) break;
           int n = 0;
           CUDA_TRY(dense_pc_occupancy(o->fp64, c, sm, &n));
@@ -502,7 +502,7 @@ int prepare(symft_plan* P, const symft_sample_args* a, uint64_t* meas, uint64_t*
           }
         }
         int ng = 0;
-        CUDA_TRY(dense_pc_occupancy(o->fp64, kGlobalWpb, dense_warp_smem_bytes(P->dp, kGlobalWpb, 0, false), &ng));
+        CUDA_TRY(dense_pc_occupancy(o->fp64, kGlobalWpb, dense_pc_smem_bytes(P->dp, kGlobalWpb, 0, false), &ng));
         const bool sm = best > 0 && best >= ng * kGlobalWpb;
         P->pc_smem[pi] = sm ? 1 : 0;
         P->pc_wpb[pi] = sm ? bw : kGlobalWpb;
@@ -510,10 +510,10 @@ int prepare(symft_plan* P, const symft_sample_args* a, uint64_t* meas, uint64_t*
       }
       const bool in_smem = P->pc_smem[pi] != 0;
       int wpb = t.dense_wpb ? t.dense_wpb : P->pc_wpb[pi];
-      while (in_smem && wpb > 1 && dense_warp_smem_bytes(P->dp, wpb, ws_bytes, true) > 227 * 1024) --wpb;
+      while (in_smem && wpb > 1 && dense_pc_smem_bytes(P->dp, wpb, ws_bytes, true) > 227 * 1024) --wpb;
       o->dense_wpb = wpb;
       o->dense_use_smem = in_smem ? 1 : 0;
-      o->dense_smem = dense_warp_smem_bytes(P->dp, wpb, in_smem ? ws_bytes : 0, in_smem);
+      o->dense_smem = dense_pc_smem_bytes(P->dp, wpb, in_smem ? ws_bytes : 0, in_smem);
       int cps = P->pc_cps[pi];
       if (wpb != P->pc_wpb[pi]) CUDA_TRY(dense_pc_occupancy(o->fp64, wpb, o->dense_smem, &cps));
       // resident CTAs times dense_grid_mult / 8 waves: the default, 8, is one

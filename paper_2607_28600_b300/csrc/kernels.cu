@@ -188,11 +188,13 @@ __device__ __forceinline__ void diag_elem(Cplx<Real>* vec, uint32_t x, Cplx<Real
 }
 // ActivePairRot on the pair (x0, x1 = x0 ^ a): coefficient (cr + i ci) on
 // the partner, with its sign (-1)^{b.partner}
+// (pab = parity of a.b: parity(b.x1) = parity(b.x0) xor pab)
 template <typename Real>
 __device__ __forceinline__ void pair_elem(Cplx<Real>* vec, uint32_t x0, uint32_t x1, Cplx<Real> v0, Cplx<Real> v1,
-                                          uint32_t b, Real c, Real cr, Real ci) {
-  const Real s1 = (__popc(x1 & b) & 1) ? (Real)-1 : (Real)1;   // applied to a_{x1} in a'_{x0}
-  const Real s0 = (__popc(x0 & b) & 1) ? (Real)-1 : (Real)1;
+                                          uint32_t b, uint32_t pab, Real c, Real cr, Real ci) {
+  const uint32_t p0 = __popc(x0 & b) & 1;
+  const Real s1 = (p0 ^ pab) ? (Real)-1 : (Real)1;              // applied to a_{x1} in a'_{x0}
+  const Real s0 = p0 ? (Real)-1 : (Real)1;
   Cplx<Real> o0, o1;
   o0.re = c * v0.re + s1 * (cr * v1.re - ci * v1.im);
   o0.im = c * v0.im + s1 * (cr * v1.im + ci * v1.re);
@@ -293,6 +295,7 @@ __device__ __forceinline__ void warp_instr(const DenseArgs& A, Cplx<Real>* vec, 
       cr *= sg * s;
       ci *= sg * s;
       const uint32_t nh = n >> 1;
+      const uint32_t pab = __popc(I.a & I.b) & 1;
       if (kBatch > 1 && nh >= 32 * kBatch) {
         for (uint32_t z0 = lane; z0 < nh; z0 += 32 * kBatch) {
           Cplx<Real> v0[kBatch], v1[kBatch];
@@ -305,13 +308,13 @@ __device__ __forceinline__ void warp_instr(const DenseArgs& A, Cplx<Real>* vec, 
 #pragma unroll
           for (uint32_t j = 0; j < kBatch; ++j) {
             const uint32_t x0 = insert_bit(z0 + 32 * j, p, 0u);
-            pair_elem(vec, x0, x0 ^ I.a, v0[j], v1[j], I.b, c, cr, ci);
+            pair_elem(vec, x0, x0 ^ I.a, v0[j], v1[j], I.b, pab, c, cr, ci);
           }
         }
       } else {
         for (uint32_t z = lane; z < nh; z += 32) {
           const uint32_t x0 = insert_bit(z, p, 0u), x1 = x0 ^ I.a;
-          pair_elem(vec, x0, x1, vec[x0], vec[x1], I.b, c, cr, ci);
+          pair_elem(vec, x0, x1, vec[x0], vec[x1], I.b, pab, c, cr, ci);
         }
       }
       break;
@@ -412,16 +415,25 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
   const uint32_t m3w = (A.p.n_m3 + 31) / 32;
   const uint32_t G = A.p.n_dense;
   const uint32_t bkw = m3w + (G + 31) / 32;     // per-warp words: m3 bits, then sign bits
-  uint32_t* m3bits = reinterpret_cast<uint32_t*>(dsm) + (size_t)wib * bkw;
+  // the instruction stream, staged in shared memory when it is small enough
+  const size_t stb = stage_bytes((size_t)G * sizeof(DenseInstrDev));
+  const DenseInstrDev* ins = A.p.dense;
+  if (stb) {
+    for (uint32_t i = threadIdx.x; i < G * (sizeof(DenseInstrDev) / 4); i += blockDim.x)
+      reinterpret_cast<uint32_t*>(dsm)[i] = reinterpret_cast<const uint32_t*>(A.p.dense)[i];
+    ins = reinterpret_cast<const DenseInstrDev*>(dsm);
+  }
+  uint32_t* m3bits = reinterpret_cast<uint32_t*>(dsm + stb) + (size_t)wib * bkw;
   uint32_t* sgn = m3bits + m3w;
   Cplx<Real>* vec;
   const uint64_t warp_global = (uint64_t)blockIdx.x * wpb + wib;
   if (A.use_smem) {
-    size_t off = ((size_t)wpb * bkw * 4 + 15) & ~(size_t)15;
+    size_t off = stb + (((size_t)wpb * bkw * 4 + 15) & ~(size_t)15);
     vec = reinterpret_cast<Cplx<Real>*>(dsm + off) + (size_t)wib * S;
   } else {
     vec = reinterpret_cast<Cplx<Real>*>(A.gvec) + warp_global * A.gvec_stride;
   }
+  __syncthreads();
 
   for (uint64_t r = warp_global; r < A.shots; r += (uint64_t)gridDim.x * wpb) {
     const uint64_t rg = A.shot0 + r;     // absolute shot index
@@ -433,7 +445,7 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
     for (uint32_t base = 0; base < G; base += 32) {
       const uint32_t g = base + lane;
       bool bit = false;
-      if (g < G) bit = (__ldg(A.signs + (uint64_t)A.p.dense[g].sign_target_col * A.W + w) & bitmask) != 0;
+      if (g < G) bit = (__ldg(A.signs + (uint64_t)ins[g].sign_target_col * A.W + w) & bitmask) != 0;
       const uint32_t bal = __ballot_sync(0xffffffffu, bit);
       if (lane == 0) sgn[base >> 5] = bal;
     }
@@ -449,7 +461,7 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
     if (dead0) continue;
     uint32_t k = 0;
     for (uint32_t g = 0; g < G; ++g) {
-      const DenseInstrDev I = A.p.dense[g];
+      const DenseInstrDev I = ins[g];
       // sign: exogenous bit xor causal residual over m3 bits of this shot
       uint32_t lam = (sgn[g >> 5] >> (g & 31)) & 1u;
       for (uint32_t q = 0; q < I.causal_n; ++q) {
@@ -493,16 +505,31 @@ __global__ void __launch_bounds__(256) dense_pc_kernel(DenseArgs A) {
   const uint32_t m3w = (A.p.n_m3 + 31) / 32;
   const uint32_t G = A.p.n_dense;
   const uint32_t bkw = m3w + (G + 31) / 32;
-  uint32_t* m3bits = reinterpret_cast<uint32_t*>(dsm) + (size_t)wib * bkw;
+  // the instruction stream and the component program, staged in shared
+  // memory when they are small enough
+  const size_t ib = (size_t)G * sizeof(DenseInstrDev);
+  const size_t stb = stage_bytes(ib + (size_t)A.p.n_pc * sizeof(PCOp));
+  const DenseInstrDev* ins = A.p.dense;
+  const PCOp* prog = A.p.pc;
+  if (stb) {
+    for (uint32_t i = threadIdx.x; i < G * (sizeof(DenseInstrDev) / 4); i += blockDim.x)
+      reinterpret_cast<uint32_t*>(dsm)[i] = reinterpret_cast<const uint32_t*>(A.p.dense)[i];
+    for (uint32_t i = threadIdx.x; i < A.p.n_pc * (sizeof(PCOp) / 4); i += blockDim.x)
+      reinterpret_cast<uint32_t*>(dsm + ib)[i] = reinterpret_cast<const uint32_t*>(A.p.pc)[i];
+    ins = reinterpret_cast<const DenseInstrDev*>(dsm);
+    prog = reinterpret_cast<const PCOp*>(dsm + ib);
+  }
+  uint32_t* m3bits = reinterpret_cast<uint32_t*>(dsm + stb) + (size_t)wib * bkw;
   uint32_t* sgn = m3bits + m3w;
   const uint64_t warp_global = (uint64_t)blockIdx.x * wpb + wib;
   Cplx<Real>* ws;
   if (A.use_smem) {
-    const size_t off = ((size_t)wpb * bkw * 4 + 15) & ~(size_t)15;
+    const size_t off = stb + (((size_t)wpb * bkw * 4 + 15) & ~(size_t)15);
     ws = reinterpret_cast<Cplx<Real>*>(dsm + off) + (size_t)wib * A.p.pc_capacity;
   } else {
     ws = reinterpret_cast<Cplx<Real>*>(A.gvec) + warp_global * A.gvec_stride;
   }
+  __syncthreads();
   for (uint64_t r = warp_global; r < A.shots; r += (uint64_t)gridDim.x * wpb) {
     const uint64_t rg = A.shot0 + r;
     const uint64_t w = r >> 6;
@@ -511,7 +538,7 @@ __global__ void __launch_bounds__(256) dense_pc_kernel(DenseArgs A) {
     for (uint32_t base = 0; base < G; base += 32) {
       const uint32_t g = base + lane;
       bool bit = false;
-      if (g < G) bit = (__ldg(A.signs + (uint64_t)A.p.dense[g].sign_target_col * A.W + w) & bitmask) != 0;
+      if (g < G) bit = (__ldg(A.signs + (uint64_t)ins[g].sign_target_col * A.W + w) & bitmask) != 0;
       const uint32_t bal = __ballot_sync(0xffffffffu, bit);
       if (lane == 0) sgn[base >> 5] = bal;
     }
@@ -521,7 +548,7 @@ __global__ void __launch_bounds__(256) dense_pc_kernel(DenseArgs A) {
     __syncwarp();
     if (dead0) continue;
     for (uint32_t q = 0; q < A.p.n_pc; ++q) {
-      const PCOp O = A.p.pc[q];
+      const PCOp O = prog[q];
       if (O.op == PC_MERGE) {
         const uint32_t na = 1u << O.kA, nc = 1u << (O.kA + O.kB);
         const Cplx<Real>* pa = ws + O.offA;
@@ -550,7 +577,7 @@ __global__ void __launch_bounds__(256) dense_pc_kernel(DenseArgs A) {
         __syncwarp();
         continue;
       }
-      DenseInstrDev I = A.p.dense[O.g];
+      DenseInstrDev I = ins[O.g];
       uint32_t lam = (sgn[O.g >> 5] >> (O.g & 31)) & 1u;
       for (uint32_t c = 0; c < I.causal_n; ++c) {
         const uint32_t j = __ldg(A.p.dense_causal + I.causal_off + c);
@@ -1523,7 +1550,14 @@ cudaError_t launch_dense_cta(const DenseArgs& a, bool fp64, int grid, size_t sme
 
 size_t dense_warp_smem_bytes(const DevPlan& p, int wpb, size_t vec_bytes, bool vec_in_smem) {
   const size_t bk = ((size_t)(p.n_m3 + 31) / 32 + (p.n_dense + 31) / 32) * 4;   // per warp
-  return (((size_t)wpb * bk + 15) & ~(size_t)15) + (vec_in_smem ? (size_t)wpb * vec_bytes : 0);
+  return stage_bytes((size_t)p.n_dense * sizeof(DenseInstrDev)) + (((size_t)wpb * bk + 15) & ~(size_t)15) +
+         (vec_in_smem ? (size_t)wpb * vec_bytes : 0);
+}
+
+size_t dense_pc_smem_bytes(const DevPlan& p, int wpb, size_t ws_bytes, bool ws_in_smem) {
+  const size_t bk = ((size_t)(p.n_m3 + 31) / 32 + (p.n_dense + 31) / 32) * 4;   // per warp
+  return stage_bytes((size_t)p.n_dense * sizeof(DenseInstrDev) + (size_t)p.n_pc * sizeof(PCOp)) +
+         (((size_t)wpb * bk + 15) & ~(size_t)15) + (ws_in_smem ? (size_t)wpb * ws_bytes : 0);
 }
 
 size_t dense_reg_smem_bytes(const DevPlan& p) {

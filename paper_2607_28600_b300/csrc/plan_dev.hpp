@@ -74,6 +74,14 @@ __host__ __device__ inline Real coef_s(const DenseInstrDev& I) {
 
 constexpr uint32_t kNoGroup = 0xFFFFFFFFu;
 
+// The warp executors copy the instruction stream (and the product-component
+// program) into shared memory, in front of their per-warp words, when it
+// takes at most kStageBytes; else they read it from the plan in global memory.
+constexpr size_t kStageBytes = 24 * 1024;
+__host__ __device__ inline size_t stage_bytes(size_t program_bytes) {
+  return program_bytes <= kStageBytes ? (program_bytes + 15) & ~(size_t)15 : 0;
+}
+
 // Product-component program (Sec. 6, adaptive product-component
 // representation): one op per component initialisation, Kronecker merge or
 // dense instruction, with the component's place in the per-shot workspace.

@@ -49,6 +49,7 @@ cudaError_t set_smem_limits();
 size_t plain_smem_bytes(const DevPlan& p, uint32_t kmax, bool fp64);
 size_t dense_reg_smem_bytes(const DevPlan& p);
 size_t dense_warp_smem_bytes(const DevPlan& p, int wpb, size_t vec_bytes, bool vec_in_smem);
+size_t dense_pc_smem_bytes(const DevPlan& p, int wpb, size_t ws_bytes, bool ws_in_smem);
 size_t dense_cta_smem_bytes(const DevPlan& p, size_t vec_bytes, bool vec_in_smem);
 cudaError_t launch_dense_cta(const DenseArgs& a, bool fp64, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_dense_reg(const DenseArgs& a, bool fp64, int grid, cudaStream_t st);
