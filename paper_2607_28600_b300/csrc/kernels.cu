@@ -495,9 +495,10 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
 template <typename Real>
 __global__ void __launch_bounds__(256) dense_pc_kernel(DenseArgs A) {
   // warp_instr's batch: a shot's steps are a chain of dependent
-  // shared-memory or L2 round trips, so 8 FP32 elements per lane and step
-  // (measured fastest); FP64 measured no faster batched
-  constexpr uint32_t kPcBatch = sizeof(Real) == 4 ? 8 : 1;
+  // shared-memory or L2 round trips, so 4 FP32 elements per lane and step
+  // (measured fastest: 8 needs 127 registers, which halves the resident
+  // warps); FP64 measured no faster batched
+  constexpr uint32_t kPcBatch = sizeof(Real) == 4 ? 4 : 1;
   extern __shared__ unsigned char dsm[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
