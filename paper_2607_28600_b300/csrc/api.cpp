@@ -685,6 +685,7 @@ int enqueue(symft_plan* P, const symft_sample_args* a, const Prep& o, cudaStream
       wa.det_exo = d.det_exo;
       wa.alive = o.wide_alive;
       wa.lab = o.wide_lab;
+      wa.status = o.status;
       for (uint64_t s0 = 0; s0 < a->shots; s0 += o.wide_nb) {
         wa.shot0 = a->shot_offset + s0;
         wa.r0 = s0;

@@ -239,6 +239,7 @@ struct WideArgs {
   uint8_t* lab;           // [nb] kept branch label
   const uint64_t* det_exo;   // as in DenseArgs (early exit), or null
   uint8_t* alive;         // [nb] 0 once the shot is rejected by postselection
+  int* status;            // set non-zero on a device-side failure (a bounded wait that ran out)
 };
 
 struct PlainArgs {

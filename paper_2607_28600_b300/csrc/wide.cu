@@ -417,6 +417,74 @@ __host__ __device__ __forceinline__ uint32_t deposit_bits(uint32_t v, uint32_t m
   return x;
 }
 
+// One fused window on a tile held in shared memory: the tile of shot b whose
+// outer bits are `off` (element i of the tile is amplitude off + the inner
+// bits of i); rotations that touch coordinates not yet promoted skip those
+// (zero) elements.  Ends with the CTA synchronised.
+template <typename Real>
+__device__ __forceinline__ void apply_window(const WideArgs& A, const WideFuse& F, Amp<Real>* tile, uint32_t b,
+                                             uint32_t off, uint32_t tid) {
+  const uint32_t n = 1u << F.T;
+  for (uint32_t q = 0; q < F.n; ++q) {
+    const FuseInstr& L = F.ins[q];
+    const uint32_t g = F.g0 + q;
+    const DenseInstrDev& I = A.p.dense[g];
+    const Real c = coef_c<Real>(I), s = coef_s<Real>(I);
+    const Real sgs = A.lam[(size_t)g * A.nb + b] ? -s : s;
+    const uint32_t po = __popc(L.b_out & off) & 1u;
+    if (L.kind == 0) {                              // a'_x = c a_x, a'_{x+new} = -i sg s a_x
+      const uint32_t pb = 1u << L.p_loc;
+      for (uint32_t z = tid; z < (n >> 1); z += blockDim.x) {
+        const uint32_t i0 = wide_insert_bit(z, L.p_loc, 0u);
+        if (i0 & L.e_loc) continue;
+        Amp<Real> a = tile[i0], hi;
+        hi.re = sgs * a.im;
+        hi.im = -sgs * a.re;
+        a.re *= c;
+        a.im *= c;
+        tile[i0] = a;
+        tile[i0 | pb] = hi;
+      }
+    } else if (L.kind == 1) {                       // a_x *= c - i sg mu (-1)^{b.x} s
+      const Real mus = I.mu == 0 ? sgs : -sgs;
+      for (uint32_t i = tid; i < n; i += blockDim.x) {
+        if (i & L.e_loc) continue;
+        const Real f = ((__popc(i & L.b_loc) ^ po) & 1u) ? -mus : mus;
+        const Amp<Real> a = tile[i];
+        Amp<Real> r;
+        r.re = c * a.re + f * a.im;
+        r.im = c * a.im - f * a.re;
+        tile[i] = r;
+      }
+    } else {                                        // pairs (x0, x0 ^ a)
+      Real cr, ci;
+      switch (I.mu & 3) {
+        case 0: cr = 0; ci = -1; break;
+        case 1: cr = 1; ci = 0; break;
+        case 2: cr = 0; ci = 1; break;
+        default: cr = -1; ci = 0; break;
+      }
+      cr *= sgs;
+      ci *= sgs;
+      for (uint32_t z = tid; z < (n >> 1); z += blockDim.x) {
+        const uint32_t i0 = wide_insert_bit(z, L.p_loc, 0u), i1 = i0 ^ L.a_loc;
+        if (i0 & L.e_loc) continue;
+        const Amp<Real> v0 = tile[i0], v1 = tile[i1];
+        const Real s1 = ((__popc(i1 & L.b_loc) ^ po) & 1u) ? (Real)-1 : (Real)1;
+        const Real s0 = ((__popc(i0 & L.b_loc) ^ po) & 1u) ? (Real)-1 : (Real)1;
+        Amp<Real> o0, o1;
+        o0.re = c * v0.re + s1 * (cr * v1.re - ci * v1.im);
+        o0.im = c * v0.im + s1 * (cr * v1.im + ci * v1.re);
+        o1.re = c * v1.re + s0 * (cr * v0.re - ci * v0.im);
+        o1.im = c * v1.im + s0 * (cr * v0.im + ci * v0.re);
+        tile[i0] = o0;
+        tile[i1] = o1;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <typename Real>
 __global__ void __launch_bounds__(kWideThreads) wide_fused_rot_kernel(WideArgs A, WideFuse F) {
   extern __shared__ __align__(16) unsigned char fsm[];
@@ -445,67 +513,155 @@ __global__ void __launch_bounds__(kWideThreads) wide_fused_rot_kernel(WideArgs A
       tile[i] = a;
     }
     __syncthreads();
-    for (uint32_t q = 0; q < F.n; ++q) {
-      const FuseInstr& L = F.ins[q];
-      const uint32_t g = F.g0 + q;
-      const DenseInstrDev& I = A.p.dense[g];
-      const Real c = coef_c<Real>(I), s = coef_s<Real>(I);
-      const Real sgs = A.lam[(size_t)g * A.nb + b] ? -s : s;
-      const uint32_t po = __popc(L.b_out & off) & 1u;
-      if (L.kind == 0) {                              // a'_x = c a_x, a'_{x+new} = -i sg s a_x
-        const uint32_t pb = 1u << L.p_loc;
-        for (uint32_t z = tid; z < (n >> 1); z += blockDim.x) {
-          const uint32_t i0 = wide_insert_bit(z, L.p_loc, 0u);
-          if (i0 & L.e_loc) continue;
-          Amp<Real> a = tile[i0], hi;
-          hi.re = sgs * a.im;
-          hi.im = -sgs * a.re;
-          a.re *= c;
-          a.im *= c;
-          tile[i0] = a;
-          tile[i0 | pb] = hi;
-        }
-      } else if (L.kind == 1) {                       // a_x *= c - i sg mu (-1)^{b.x} s
-        const Real mus = I.mu == 0 ? sgs : -sgs;
-        for (uint32_t i = tid; i < n; i += blockDim.x) {
-          if (i & L.e_loc) continue;
-          const Real f = ((__popc(i & L.b_loc) ^ po) & 1u) ? -mus : mus;
-          const Amp<Real> a = tile[i];
-          Amp<Real> r;
-          r.re = c * a.re + f * a.im;
-          r.im = c * a.im - f * a.re;
-          tile[i] = r;
-        }
-      } else {                                        // pairs (x0, x0 ^ a)
-        Real cr, ci;
-        switch (I.mu & 3) {
-          case 0: cr = 0; ci = -1; break;
-          case 1: cr = 1; ci = 0; break;
-          case 2: cr = 0; ci = 1; break;
-          default: cr = -1; ci = 0; break;
-        }
-        cr *= sgs;
-        ci *= sgs;
-        for (uint32_t z = tid; z < (n >> 1); z += blockDim.x) {
-          const uint32_t i0 = wide_insert_bit(z, L.p_loc, 0u), i1 = i0 ^ L.a_loc;
-          if (i0 & L.e_loc) continue;
-          const Amp<Real> v0 = tile[i0], v1 = tile[i1];
-          const Real s1 = ((__popc(i1 & L.b_loc) ^ po) & 1u) ? (Real)-1 : (Real)1;
-          const Real s0 = ((__popc(i0 & L.b_loc) ^ po) & 1u) ? (Real)-1 : (Real)1;
-          Amp<Real> o0, o1;
-          o0.re = c * v0.re + s1 * (cr * v1.re - ci * v1.im);
-          o0.im = c * v0.im + s1 * (cr * v1.im + ci * v1.re);
-          o1.re = c * v1.re + s0 * (cr * v0.re - ci * v0.im);
-          o1.im = c * v1.im + s0 * (cr * v0.im + ci * v0.re);
-          tile[i0] = o0;
-          tile[i1] = o1;
-        }
-      }
-      __syncthreads();
-    }
+    apply_window<Real>(A, F, tile, b, off, tid);
     for (uint32_t i = tid; i < n; i += blockDim.x) v[off + hi_tab[i >> 5] + (i & 31u)] = tile[i];
     __syncthreads();
   }
+}
+
+// ---- bulk asynchronous copies (Blackwell copy engine) ------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t* m, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* m, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(m)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// wait for phase `parity` of m to complete, for at most ~2^32 SM clocks
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(m, parity))
+    if (clock64() - t0 > (1ll << 32)) return false;
+  return true;
+}
+// global -> shared, completing `bytes` on the mbarrier (both addresses 16-byte
+// aligned, bytes a multiple of 16)
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* m) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(m))
+               : "memory");
+}
+// shared -> global in this thread's current bulk group
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// this thread's bulk stores have read their shared-memory sources
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// this thread's bulk stores are complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// order this thread's generic shared-memory accesses before later async-proxy ones
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// The fused window with tiles streamed by the copy engine: a tile is n / 32
+// chunks of 32 consecutive amplitudes (the inner bits include bits 0..4, so a
+// chunk is 256 B in FP32, 512 B in FP64, aligned to its size).  Each CTA walks
+// its tiles with two buffers: while it applies the window to one tile, the
+// next tile's chunks arrive by bulk copies that complete on that buffer's
+// mbarrier, and the previous tile leaves by bulk stores.  A buffer is refilled
+// only after the stores issued from it have read it.  Chunks of coordinates not
+// yet promoted (a whole chunk, since F.kstart >= 5) are zero-filled instead of
+// copied.  A bounded wait that runs out sets *A.status and ends the CTA.
+template <typename Real>
+__global__ void __launch_bounds__(kWideThreads) wide_fused_bulk_kernel(WideArgs A, WideFuse F) {
+  extern __shared__ __align__(128) unsigned char fsm[];
+  const uint32_t n = 1u << F.T;
+  const size_t tb = sizeof(Amp<Real>) << F.T;       // tile bytes
+  auto buf = [&](int s) { return reinterpret_cast<Amp<Real>*>(fsm + (size_t)s * tb); };
+  uint32_t* hi_tab = reinterpret_cast<uint32_t*>(fsm + 2 * tb);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(fsm + 2 * tb + ((size_t)4 << (F.T - 5)));
+  const uint32_t tid = threadIdx.x;
+  const uint32_t nch = n >> 5;                       // chunks per tile
+  constexpr uint32_t cb = 32u * sizeof(Amp<Real>);  // chunk bytes
+  const uint32_t inner_hi = F.inner & ~31u;
+  const uint32_t kst_mask = F.kstart >= 32 ? ~0u : (1u << F.kstart) - 1u;
+  for (uint32_t j = tid; j < nch; j += blockDim.x) hi_tab[j] = deposit_bits(j, inner_hi);
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+  }
+  fence_async_shared();
+  __syncthreads();
+  // chunks of a tile that exist (their inner high bits below k_start): the
+  // same for every tile whose outer bits are below k_start, none otherwise
+  uint32_t nlive = 0;
+  for (uint32_t j = 0; j < nch; ++j) nlive += (hi_tab[j] & ~kst_mask) == 0u;
+  const uint32_t tiles = 1u << (F.kend - F.T);
+  const uint64_t total = (uint64_t)A.nb * tiles;
+  auto next_live = [&](uint64_t t) {
+    while (t < total && !A.alive[t / tiles]) t += gridDim.x;
+    return t;
+  };
+  auto issue_load = [&](uint64_t t, int s) {
+    const uint32_t b = (uint32_t)(t / tiles), o = (uint32_t)(t - (uint64_t)b * tiles);
+    const uint32_t off = deposit_bits(o, F.outer);
+    const Amp<Real>* v = reinterpret_cast<const Amp<Real>*>(A.vec[A.cur]) + (size_t)b * A.stride;
+    const bool outer_live = (off & ~kst_mask) == 0u;
+    if (tid == 0) mbar_arrive_expect(&mbar[s], outer_live ? nlive * cb : 0u);
+    __syncthreads();                                 // the expected bytes precede every copy
+    for (uint32_t j = tid; j < nch; j += blockDim.x) {
+      const uint32_t cs = off + hi_tab[j];
+      Amp<Real>* d = buf(s) + 32 * j;
+      if (outer_live && (hi_tab[j] & ~kst_mask) == 0u) {
+        bulk_load(d, v + cs, cb, &mbar[s]);
+      } else {
+        Amp<Real> z;
+        z.re = (Real)0;
+        z.im = (Real)0;
+        for (uint32_t e = 0; e < 32; ++e) d[e] = z;
+      }
+    }
+  };
+  uint32_t phase = 0u;                               // bit s: parity of buffer s's next phase
+  uint64_t t = next_live(blockIdx.x);
+  if (t < total) issue_load(t, 0);
+  bool failed = false, pending = false;
+  int ps = 0;
+  for (uint32_t it = 0; t < total; ++it) {
+    const int s = it & 1;
+    const uint64_t tn = next_live(t + gridDim.x);
+    if (tn < total) {
+      bulk_wait_read();                              // the stores from buffer s ^ 1 have read it
+      __syncthreads();
+      issue_load(tn, s ^ 1);
+      pending = true;
+      ps = s ^ 1;
+    } else {
+      pending = false;
+    }
+    const bool ok = mbar_wait_bounded(&mbar[s], (phase >> s) & 1u);
+    phase ^= 1u << s;
+    if (__syncthreads_or(!ok)) {                     // also orders the zero fills
+      failed = true;
+      break;
+    }
+    const uint32_t b = (uint32_t)(t / tiles), o = (uint32_t)(t - (uint64_t)b * tiles);
+    const uint32_t off = deposit_bits(o, F.outer);
+    apply_window<Real>(A, F, buf(s), b, off, tid);
+    fence_async_shared();
+    __syncthreads();
+    Amp<Real>* v = reinterpret_cast<Amp<Real>*>(A.vec[A.cur]) + (size_t)b * A.stride;
+    for (uint32_t j = tid; j < nch; j += blockDim.x) bulk_store(v + off + hi_tab[j], buf(s) + 32 * j, cb);
+    bulk_commit();
+    t = tn;
+  }
+  if (failed) {
+    if (tid == 0 && A.status) atomicExch(A.status, 3);
+    if (pending) (void)mbar_wait_bounded(&mbar[ps], (phase >> ps) & 1u);
+  }
+  bulk_wait_all();
 }
 
 // bit positions of mask, gathered: the index of each set bit of x & mask
@@ -598,18 +754,34 @@ static cudaError_t wide_batch_t(WideArgs A, const DenseInstrDev* host_dense, int
       const uint32_t nw = build_window(host_dense, A.p.n_dense, g, T, &F);
       if (nw >= 2 && F.kend >= 5) {
         // one pass over HBM for the whole window
-        const size_t smem = (sizeof(Amp<Real>) << F.T) + ((size_t)4 << (F.T - 5));
         const uint64_t tiles = (uint64_t)A.nb << (F.kend - F.T);
-        const uint64_t cap = (uint64_t)sm_count * 8;
-        const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
         static bool attr_set = false;
+        static int bulk_per_sm = 0;   // resident CTAs per SM at the largest tile
+        const size_t smem_bulk = 2 * (sizeof(Amp<Real>) << F.T) + ((size_t)4 << (F.T - 5)) + 16;
         if (!attr_set) {
+          const size_t smem_max = 2 * (sizeof(Amp<Real>) << T) + ((size_t)4 << (T - 5)) + 16;
           cudaError_t e = cudaFuncSetAttribute((const void*)wide_fused_rot_kernel<Real>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+          if (e == cudaSuccess)
+            e = cudaFuncSetAttribute((const void*)wide_fused_bulk_kernel<Real>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+          if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bulk_per_sm, wide_fused_bulk_kernel<Real>,
+                                                              kWideThreads, smem_max);
           if (e != cudaSuccess) return e;
           attr_set = true;
         }
-        wide_fused_rot_kernel<Real><<<grid, kWideThreads, smem, st>>>(A, F);
+        if (F.kstart >= 5 && bulk_per_sm > 0) {
+          // tiles streamed by bulk copies; one resident wave of CTAs walks them
+          const uint64_t cap = (uint64_t)sm_count * bulk_per_sm;
+          const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
+          wide_fused_bulk_kernel<Real><<<grid, kWideThreads, smem_bulk, st>>>(A, F);
+        } else {
+          const size_t smem = (sizeof(Amp<Real>) << F.T) + ((size_t)4 << (F.T - 5));
+          const uint64_t cap = (uint64_t)sm_count * 8;
+          const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
+          wide_fused_rot_kernel<Real><<<grid, kWideThreads, smem, st>>>(A, F);
+        }
         ++*launches;
         g += nw - 1;
       } else {
