@@ -611,17 +611,16 @@ __global__ void __launch_bounds__(kWideThreads) wide_fused_bulk_kernel(WideArgs 
     const bool outer_live = (off & ~kst_mask) == 0u;
     if (tid == 0) mbar_arrive_expect(&mbar[s], outer_live ? nlive * cb : 0u);
     __syncthreads();                                 // the expected bytes precede every copy
-    for (uint32_t j = tid; j < nch; j += blockDim.x) {
-      const uint32_t cs = off + hi_tab[j];
-      Amp<Real>* d = buf(s) + 32 * j;
-      if (outer_live && (hi_tab[j] & ~kst_mask) == 0u) {
-        bulk_load(d, v + cs, cb, &mbar[s]);
-      } else {
-        Amp<Real> z;
-        z.re = (Real)0;
-        z.im = (Real)0;
-        for (uint32_t e = 0; e < 32; ++e) d[e] = z;
-      }
+    for (uint32_t j = tid; j < nch; j += blockDim.x)
+      if (outer_live && (hi_tab[j] & ~kst_mask) == 0u) bulk_load(buf(s) + 32 * j, v + off + hi_tab[j], cb, &mbar[s]);
+    // chunks that are not copied are zero, written element-strided across the
+    // CTA (consecutive threads, consecutive banks)
+    if (!outer_live || nlive < nch) {
+      Amp<Real> z;
+      z.re = (Real)0;
+      z.im = (Real)0;
+      for (uint32_t i = tid; i < n; i += blockDim.x)
+        if (!outer_live || (hi_tab[i >> 5] & ~kst_mask) != 0u) buf(s)[i] = z;
     }
   };
   uint32_t phase = 0u;                               // bit s: parity of buffer s's next phase
