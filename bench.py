@@ -511,6 +511,8 @@ def measure_mixed_batch(S, torch, dev, stream, steps, warmup, n_circuits=64, tar
         info = pl.refresh_info()
         row = {"k_max": info["k_max"], "executor": info["dense_executor"][0],
                "tuned_ns_per_shot": ns, "shots": shots[plans.index(pl)]}
+        if row["executor"] == "wide":
+            row["wide_tile_bits"] = info["wide_tile_bits"][0]
         if info["k_max"] > 0:
             fl = dense_floor(info, peaks)
             row["dense_floor_ns_per_shot"] = fl["floor_s_per_shot"] * 1e9

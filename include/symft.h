@@ -97,7 +97,10 @@ typedef struct {
                               / a CTA); used when it can run the plan, else the
                               automatic choice; 0 = automatic.  symft_autotune
                               replaces it with its own pick */
-  int reserved[1];
+  int wide_tile_bits;      /* wide executor: amplitudes per fused-window tile
+                              as a power of two, 10..13 (FP32) or 10..12 (FP64;
+                              larger values are clamped); 0 = the default (12 /
+                              11).  symft_autotune replaces it with its own pick */
 } symft_options;
 
 /* Counts of a compiled plan (Sec. 5, sampling complexity). */
@@ -162,6 +165,9 @@ typedef struct {
                                  rotation, merged rotations removed (angle a
                                  multiple of 2 pi), rotations removed as the
                                  branch phase of a later same-body measurement */
+  uint32_t wide_tile_bits[2]; /* wide executor: amplitudes per fused-window
+                                 tile, as a power of two, at FP32 / FP64 (the
+                                 default, or the one symft_autotune chose) */
 } symft_info;
 
 /* One sampling request.  All pointers may be NULL to skip that output. */

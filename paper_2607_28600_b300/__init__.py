@@ -39,7 +39,7 @@ class _Options(ctypes.Structure):
     _fields_ = [("postselect", ctypes.c_int), ("n_post_dets", ctypes.c_uint32),
                  ("post_dets", ctypes.POINTER(ctypes.c_uint32)), ("no_simplify", ctypes.c_int),
                 ("no_product_components", ctypes.c_int), ("executor", ctypes.c_int),
-                ("reserved", ctypes.c_int * 1)]
+                ("wide_tile_bits", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -55,7 +55,8 @@ class _Info(ctypes.Structure):
                 ("dense_executor", ctypes.c_uint32 * 2), ("pc_capacity", ctypes.c_uint32),
                 ("pc_selected", ctypes.c_uint32), ("pc_work", ctypes.c_uint64 * 2),
                 ("sign_model", ctypes.c_double * 3),
-                ("simplified", ctypes.c_uint32 * 3)]
+                ("simplified", ctypes.c_uint32 * 3),
+                ("wide_tile_bits", ctypes.c_uint32 * 2)]
 
 
 class _SampleArgs(ctypes.Structure):
@@ -194,7 +195,8 @@ EXECUTORS = {"auto": 0, "register": 1, "warp": 2, "cta": 3, "wide": 4, "componen
 
 
 def symft_compile(circuit_text: str, postselect: int = POSTSELECT_NONE, post_dets=None,
-                  simplify: bool = True, product_components: bool = True, executor: str = "auto") -> Plan:
+                  simplify: bool = True, product_components: bool = True, executor: str = "auto",
+                  wide_tile_bits: int = 0) -> Plan:
     """Compile circuit text.  postselect=POSTSELECT_LISTED rejects a shot only at
     the detectors whose indices are listed in `post_dets`; simplify=False skips
     the commutation-aware simplification before planning."""
@@ -204,6 +206,7 @@ def symft_compile(circuit_text: str, postselect: int = POSTSELECT_NONE, post_det
     opt.no_simplify = 0 if simplify else 1
     opt.no_product_components = 0 if product_components else 1
     opt.executor = EXECUTORS[executor]
+    opt.wide_tile_bits = int(wide_tile_bits)
     if post_dets is not None:
         dets = [int(d) for d in post_dets]
         arr = (ctypes.c_uint32 * max(1, len(dets)))(*dets)
@@ -218,7 +221,8 @@ def symft_plan_info(plan: Plan) -> dict:
     _check(lib().symft_plan_info(plan.handle, ctypes.byref(info)))
     d = {name: getattr(info, name) for name, _ in _Info._fields_
          if name not in ("n_instr", "tuned_ns_per_shot", "simplified", "wide_amp_traffic", "sign_model",
-                         "dense_executor", "pc_work")}
+                         "dense_executor", "pc_work", "wide_tile_bits")}
+    d["wide_tile_bits"] = [int(info.wide_tile_bits[0]), int(info.wide_tile_bits[1])]
     d["pc_work"] = [int(info.pc_work[0]), int(info.pc_work[1])]
     kinds = {0: "none", 1: "register", 2: "warp", 3: "cta", 4: "wide", 5: "components_warp",
              6: "components_cta"}

@@ -364,6 +364,7 @@ struct Prep {
   int plain_grid = 0;
   // wide executor: batch size and workspace pieces
   uint32_t wide_nb = 0;
+  uint32_t wide_tile_bits = 0;   // 0: the executor's default
   void* wide_vec[2] = {nullptr, nullptr};
   uint32_t* wide_m3b = nullptr;
   uint8_t* wide_lam = nullptr;
@@ -556,6 +557,7 @@ int prepare(symft_plan* P, const symft_sample_args* a, uint64_t* meas, uint64_t*
       // wide executor: batches of shots with their vectors in HBM (two
       // buffers each), instruction by instruction; ~8 GB of vectors
       o->dense_kind = 4;
+      o->wide_tile_bits = static_cast<uint32_t>(t.wide_tile_bits);
       const uint64_t per_shot = 2 * vec_bytes;
       const uint64_t nb = std::min<uint64_t>({a->shots, std::max<uint64_t>(1, (8ull << 30) / per_shot), 65535});
       o->wide_nb = static_cast<uint32_t>(nb);
@@ -692,7 +694,7 @@ int enqueue(symft_plan* P, const symft_sample_args* a, const Prep& o, cudaStream
         wa.nb = static_cast<uint32_t>(std::min<uint64_t>(o.wide_nb, a->shots - s0));
         wa.cur = 0;
         int l = 0;
-        CUDA_TRY(launch_wide_batch(wa, P->dense_host.data(), o.fp64, P->sm_count, st, &l));
+        CUDA_TRY(launch_wide_batch(wa, P->dense_host.data(), o.fp64, P->sm_count, st, &l, o.wide_tile_bits));
         *launches += l;
       }
       --*launches;   // counted once below
@@ -838,6 +840,11 @@ int autotune_impl(symft_plan* P, uint64_t shots, int precision, cudaStream_t st)
     for (int gm : {2, 4, 8, 16, 32}) { Tune c = base; c.dense_grid_mult = gm; cands.push_back(c); }
     for (int wpb : {2, 4, 8}) { Tune c = base; c.dense_wpb = wpb; cands.push_back(c); }
     for (int cm : {1, 2, 4}) { Tune c = base; c.cta_grid_mult = cm; cands.push_back(c); }
+    // the wide executor's fused-window tile (shape of the tiles it streams)
+    if (dense_kind_for(P, h, precision == SYMFT_FP64, base.dense_kind) == 4) {
+      const int hi = precision == SYMFT_FP64 ? static_cast<int>(kWideTileBitsMaxF64) : static_cast<int>(kWideTileBitsMaxF32);
+      for (int tb = static_cast<int>(kWideTileBitsMin); tb <= hi; ++tb) { Tune c = base; c.wide_tile_bits = tb; cands.push_back(c); }
+    }
     for (const Tune& cand : cands) {
       t = cand;
       float ms = 0.0f;
@@ -1014,11 +1021,14 @@ int symft_compile_ex(const char* text, const symft_options* opt, symft_plan** ou
           return set_error(SYMFT_E_ARG, "postselect LISTED: detector " + std::to_string(o.post_dets[i]) +
                                             " out of range (" + std::to_string(c.n_dets) + " detectors)");
     if (o.executor < 0 || o.executor > 6) return set_error(SYMFT_E_ARG, "bad executor preference");
+    if (o.wide_tile_bits != 0 && (o.wide_tile_bits < static_cast<int>(kWideTileBitsMin) || o.wide_tile_bits > 16))
+      return set_error(SYMFT_E_ARG, "wide_tile_bits out of range");
     symft_plan* p = new symft_plan();
     try {
       p->hp = compile_plan(c, o);
       build_blob(p);
       p->tune[0].dense_kind = p->tune[1].dense_kind = o.executor;
+      p->tune[0].wide_tile_bits = p->tune[1].wide_tile_bits = o.wide_tile_bits;
     } catch (...) {
       delete p;
       throw;
@@ -1111,8 +1121,10 @@ int symft_plan_info(const symft_plan* p, symft_info* info) {
     info->sign_model[1] = fires;
     info->sign_model[2] = xor_ops;
   }
-  info->wide_amp_traffic[0] = wide_amp_traffic(p->dense_host.data(), static_cast<uint32_t>(p->dense_host.size()), false);
-  info->wide_amp_traffic[1] = wide_amp_traffic(p->dense_host.data(), static_cast<uint32_t>(p->dense_host.size()), true);
+  info->wide_amp_traffic[0] = wide_amp_traffic(p->dense_host.data(), static_cast<uint32_t>(p->dense_host.size()), false,
+                                                static_cast<uint32_t>(p->tune[0].wide_tile_bits));
+  info->wide_amp_traffic[1] = wide_amp_traffic(p->dense_host.data(), static_cast<uint32_t>(p->dense_host.size()), true,
+                                                static_cast<uint32_t>(p->tune[1].wide_tile_bits));
   info->pc_capacity = h.pc.capacity;
   info->pc_selected = h.pc.use ? 1u : 0u;
   info->pc_work[0] = h.pc.work_pc;
@@ -1120,6 +1132,8 @@ int symft_plan_info(const symft_plan* p, symft_info* info) {
   info->simplified[0] = h.n_fused;
   info->simplified[1] = h.n_cancelled;
   info->simplified[2] = h.n_branch_phase;
+  info->wide_tile_bits[0] = wide_tile_bits_in_use(false, static_cast<uint32_t>(p->tune[0].wide_tile_bits));
+  info->wide_tile_bits[1] = wide_tile_bits_in_use(true, static_cast<uint32_t>(p->tune[1].wide_tile_bits));
   for (int i = 0; i < 2; ++i) {
     info->tuned_ns_per_shot[i] = p->tune[i].tuned ? p->tune[i].best_ms_per_shot * 1e6f : 0.0f;
     info->dense_executor[i] = h.dense.empty() ? 0u

@@ -74,6 +74,9 @@ __host__ __device__ inline Real coef_s(const DenseInstrDev& I) {
 
 constexpr uint32_t kNoGroup = 0xFFFFFFFFu;
 
+// fused-window tile sizes (log2 amplitudes) the wide executor accepts
+constexpr uint32_t kWideTileBitsMin = 10, kWideTileBitsMaxF32 = 13, kWideTileBitsMaxF64 = 12;
+
 // The warp executors copy the instruction stream (and the product-component
 // program) into shared memory, in front of their per-warp words, when it
 // takes at most kStageBytes; else they read it from the plan in global memory.

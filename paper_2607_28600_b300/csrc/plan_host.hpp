@@ -61,10 +61,14 @@ cudaError_t launch_dense_pc_cta(const DenseArgs& a, bool fp64, int grid, size_t 
 cudaError_t launch_plain(const PlainArgs& a, bool fp64, int grid, cudaStream_t st);
 // all dense instructions for one batch of the wide executor (host_dense: the
 // plan's instruction stream in host memory, for the per-instruction launches)
+// (tile_bits: amplitudes per fused-window tile as a power of two, 0 = default)
 cudaError_t launch_wide_batch(const WideArgs& a, const DenseInstrDev* host_dense, bool fp64, int sm_count,
-                              cudaStream_t st, int* launches);
+                              cudaStream_t st, int* launches,
+                              uint32_t tile_bits = 0);
 // amplitudes one shot moves through HBM in the wide executor's passes
-uint64_t wide_amp_traffic(const DenseInstrDev* d, uint32_t G, bool fp64);
+uint64_t wide_amp_traffic(const DenseInstrDev* d, uint32_t G, bool fp64, uint32_t tile_bits = 0);
+// the fused-window tile bits the wide executor uses for a request (0 = default)
+uint32_t wide_tile_bits_in_use(bool fp64, uint32_t tile_bits);
 
 // Launch shapes chosen by symft_autotune (0 = built-in heuristic).
 struct Tune {
@@ -73,6 +77,7 @@ struct Tune {
   int dense_grid_mult = 8;   // register / warp executors: CTAs per SM
   int dense_wpb = 0;         // warp executor: warps (shots) per CTA
   int cta_grid_mult = 2;     // CTA executor with global vectors: CTAs per SM
+  int wide_tile_bits = 0;    // wide executor: fused-window tile of 2^bits amplitudes (0 = default)
   int dense_kind = 0;        // dense executor (1 register, 2 warp, 3 CTA, 4 wide, 5 / 6 product
                              // components on a warp / a CTA; 0 = the cost model's choice)
   float best_ms_per_shot = 0.0f;

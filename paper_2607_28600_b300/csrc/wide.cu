@@ -387,6 +387,16 @@ constexpr int kFuseMax = 48;        // instructions per window
 // tile bits: 2^12 FP32 / 2^11 FP64 amplitudes = 32 KB of shared memory (larger
 // tiles make the pass compute-bound before they save HBM traffic)
 constexpr uint32_t kFuseBitsF32 = 12, kFuseBitsF64 = 11;
+// the tile bits in use: the requested ones clamped to what the kernels take
+// (a 2^T-amplitude tile, two of them in the bulk form, within 200 KB), else
+// the default
+template <typename Real>
+inline uint32_t wide_tile_bits(uint32_t requested) {
+  const uint32_t def = sizeof(Real) == 4 ? kFuseBitsF32 : kFuseBitsF64;
+  const uint32_t hi = sizeof(Real) == 4 ? kWideTileBitsMaxF32 : kWideTileBitsMaxF64;
+  if (requested == 0) return def;
+  return requested < kWideTileBitsMin ? kWideTileBitsMin : (requested > hi ? hi : requested);
+}
 
 struct FuseInstr {
   uint32_t b_out;      // b & outer bits (parity fixed per tile)
@@ -576,12 +586,12 @@ __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy
 // copied.  A bounded wait that runs out sets *A.status and ends the CTA.
 template <typename Real>
 __global__ void __launch_bounds__(kWideThreads) wide_fused_bulk_kernel(WideArgs A, WideFuse F) {
-  extern __shared__ __align__(128) unsigned char fsm[];
+  extern __shared__ __align__(128) unsigned char bsm[];
   const uint32_t n = 1u << F.T;
   const size_t tb = sizeof(Amp<Real>) << F.T;       // tile bytes
-  auto buf = [&](int s) { return reinterpret_cast<Amp<Real>*>(fsm + (size_t)s * tb); };
-  uint32_t* hi_tab = reinterpret_cast<uint32_t*>(fsm + 2 * tb);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(fsm + 2 * tb + ((size_t)4 << (F.T - 5)));
+  auto buf = [&](int s) { return reinterpret_cast<Amp<Real>*>(bsm + (size_t)s * tb); };
+  uint32_t* hi_tab = reinterpret_cast<uint32_t*>(bsm + 2 * tb);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(bsm + 2 * tb + ((size_t)4 << (F.T - 5)));
   const uint32_t tid = threadIdx.x;
   const uint32_t nch = n >> 5;                       // chunks per tile
   constexpr uint32_t cb = 32u * sizeof(Amp<Real>);  // chunk bytes
@@ -740,11 +750,11 @@ static unsigned wide_chunks(uint64_t elems, int sm_count, uint32_t nb) {
 
 template <typename Real>
 static cudaError_t wide_batch_t(WideArgs A, const DenseInstrDev* host_dense, int sm_count, cudaStream_t st,
-                                int* launches) {
+                                int* launches, uint32_t tile_bits) {
   const unsigned nb_blocks = (A.nb + 127) / 128;
   wide_init_kernel<Real><<<nb_blocks, 128, 0, st>>>(A);
   ++*launches;
-  const uint32_t T = sizeof(Real) == 4 ? kFuseBitsF32 : kFuseBitsF64;
+  const uint32_t T = wide_tile_bits<Real>(tile_bits);
   for (uint32_t g = 0; g < A.p.n_dense; ++g) {
     const DenseInstrDev& I = host_dense[g];
     const uint64_t n = 1ull << I.k;
@@ -755,24 +765,27 @@ static cudaError_t wide_batch_t(WideArgs A, const DenseInstrDev* host_dense, int
         // one pass over HBM for the whole window
         const uint64_t tiles = (uint64_t)A.nb << (F.kend - F.T);
         static bool attr_set = false;
-        static int bulk_per_sm = 0;   // resident CTAs per SM at the largest tile
+        static int bulk_per_sm[32] = {};   // resident CTAs per SM by tile bits (at the full tile)
         const size_t smem_bulk = 2 * (sizeof(Amp<Real>) << F.T) + ((size_t)4 << (F.T - 5)) + 16;
         if (!attr_set) {
-          const size_t smem_max = 2 * (sizeof(Amp<Real>) << T) + ((size_t)4 << (T - 5)) + 16;
           cudaError_t e = cudaFuncSetAttribute((const void*)wide_fused_rot_kernel<Real>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
           if (e == cudaSuccess)
             e = cudaFuncSetAttribute((const void*)wide_fused_bulk_kernel<Real>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-          if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bulk_per_sm, wide_fused_bulk_kernel<Real>,
-                                                              kWideThreads, smem_max);
           if (e != cudaSuccess) return e;
           attr_set = true;
         }
-        if (F.kstart >= 5 && bulk_per_sm > 0) {
+        if (bulk_per_sm[T] == 0) {
+          const size_t smem_max = 2 * (sizeof(Amp<Real>) << T) + ((size_t)4 << (T - 5)) + 16;
+          cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bulk_per_sm[T], wide_fused_bulk_kernel<Real>,
+                                                                        kWideThreads, smem_max);
+          if (e != cudaSuccess) return e;
+          if (bulk_per_sm[T] == 0) bulk_per_sm[T] = -1;   // does not fit: thread loads and stores
+        }
+        if (F.kstart >= 5 && bulk_per_sm[T] > 0) {
           // tiles streamed by bulk copies; one resident wave of CTAs walks them
-          const uint64_t cap = (uint64_t)sm_count * bulk_per_sm;
+          const uint64_t cap = (uint64_t)sm_count * bulk_per_sm[T];
           const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
           wide_fused_bulk_kernel<Real><<<grid, kWideThreads, smem_bulk, st>>>(A, F);
         } else {
@@ -812,8 +825,12 @@ static cudaError_t wide_batch_t(WideArgs A, const DenseInstrDev* host_dense, int
 // writes 2^(k+1), a lone diagonal or pair rotation reads and writes 2^k; a
 // measurement reads 2^k for its sums, reads up to 2^k for the compaction and
 // writes 2^(k-1).
-uint64_t wide_amp_traffic(const DenseInstrDev* d, uint32_t G, bool fp64) {
-  const uint32_t T = fp64 ? kFuseBitsF64 : kFuseBitsF32;
+uint32_t wide_tile_bits_in_use(bool fp64, uint32_t tile_bits) {
+  return fp64 ? wide_tile_bits<double>(tile_bits) : wide_tile_bits<float>(tile_bits);
+}
+
+uint64_t wide_amp_traffic(const DenseInstrDev* d, uint32_t G, bool fp64, uint32_t tile_bits) {
+  const uint32_t T = fp64 ? wide_tile_bits<double>(tile_bits) : wide_tile_bits<float>(tile_bits);
   uint64_t amps = 0;
   for (uint32_t g = 0; g < G; ++g) {
     const uint64_t n = 1ull << d[g].k;
@@ -834,9 +851,9 @@ uint64_t wide_amp_traffic(const DenseInstrDev* d, uint32_t G, bool fp64) {
 }
 
 cudaError_t launch_wide_batch(const WideArgs& a, const DenseInstrDev* host_dense, bool fp64, int sm_count,
-                              cudaStream_t st, int* launches) {
-  return fp64 ? wide_batch_t<double>(a, host_dense, sm_count, st, launches)
-              : wide_batch_t<float>(a, host_dense, sm_count, st, launches);
+                              cudaStream_t st, int* launches, uint32_t tile_bits) {
+  return fp64 ? wide_batch_t<double>(a, host_dense, sm_count, st, launches, tile_bits)
+              : wide_batch_t<float>(a, host_dense, sm_count, st, launches, tile_bits);
 }
 
 }  // namespace symft

@@ -291,3 +291,25 @@ def test_plain_form_early_exit_matches_batched(which):
         for a, b in zip(outs[0], other):
             np.testing.assert_array_equal(a, b)
     assert 0.02 < unpack(outs[1][3].view(np.uint64).reshape(1, -1), shots).mean() < 0.99
+
+
+@pytest.mark.parametrize("precision,bits", [(0, (10, 11, 13)), (1, (10, 12))])
+def test_wide_tile_shapes_give_the_same_bits(precision, bits):
+    """The wide executor's fused-window tile (2^bits amplitudes, a tuning
+    parameter) only regroups the same per-amplitude updates into passes: the
+    literal 15-to-1 circuit on the wide executor (k = 15) samples the same
+    records for every tile size."""
+    import paper_2607_28600_b300 as S
+    from paper_2607_28600_b300.workloads import distillation_15_to_1
+    text = distillation_15_to_1(1e-3, "literal")
+    shots, seed = 256, 31
+    outs = []
+    for b in (0,) + tuple(bits):
+        plan = S.symft_compile(text, postselect=1, product_components=False, executor="wide", wide_tile_bits=b)
+        assert plan.info["dense_executor"][precision] == "wide"
+        assert plan.info["wide_tile_bits"][precision] == (b or (12 if precision == 0 else 11))
+        meas, det, obs, disc = S.sample_to_tensors(plan, shots, seed, precision=precision)
+        outs.append([t.cpu().numpy() for t in (meas, det, obs, disc)])
+    for o in outs[1:]:
+        for x, y in zip(outs[0], o):
+            np.testing.assert_array_equal(x, y)
