@@ -153,6 +153,16 @@ void build_blob(symft_plan* P) {
   P->off.m1g = push(blob, h.m1_tgt);
   P->off.tco = push(blob, h.tgt_causal_off);
   P->off.tca = push(blob, h.tgt_causal);
+  {
+    std::vector<uint4> ctg;
+    for (uint32_t i = 0; i + 1 < h.tgt_causal_off.size(); ++i) {
+      const uint32_t b = h.tgt_causal_off[i], e = h.tgt_causal_off[i + 1];
+      if (e > b) ctg.push_back(make_uint4(i, b, e - b, 0u));
+    }
+    P->off.n_ctg = static_cast<uint32_t>(ctg.size());
+    if (ctg.empty()) ctg.push_back(make_uint4(0u, 0u, 0u, 0u));
+    P->off.ctg = push(blob, ctg);
+  }
   P->off.sc = push(blob, h.slot_const);
   // slot -> constant and random-measurement sources (inverse of the m1 lists)
   {
@@ -261,6 +271,8 @@ void bind_plan(const symft_plan* P, unsigned char* base, DevPlan* dptr) {
   d.gat_ovf = reinterpret_cast<const uint32_t*>(at(P->off.gv));
   d.tgt_causal_off = reinterpret_cast<const uint32_t*>(at(P->off.tco));
   d.tgt_causal = reinterpret_cast<const uint32_t*>(at(P->off.tca));
+  d.n_causal_tgt = P->off.n_ctg;
+  d.causal_tgt = reinterpret_cast<const uint4*>(at(P->off.ctg));
   d.n_post_events = static_cast<uint32_t>(h.post_events.size());
   d.post_events = reinterpret_cast<const int32_t*>(at(P->off.pe));
   d.n_dense = static_cast<uint32_t>(h.dense.size());

@@ -1450,15 +1450,17 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs A) {
 
 
 __global__ void finalize_kernel(FinalArgs A) {
+  constexpr uint32_t kEv = 8;   // postselection events whose words are loaded together
   for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < A.W; w += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t pad = ~0ull;
     if (w == A.W - 1 && (A.shots & 63)) pad = (1ull << (A.shots & 63)) - 1;
     if (A.m3) {
-      for (uint32_t i = 0; i < A.p.tgt_sign0; ++i) {
-        uint32_t b = __ldg(A.p.tgt_causal_off + i), e = __ldg(A.p.tgt_causal_off + i + 1);
-        if (b == e) continue;
+      // outputs with causal terms: XOR in the active outcomes they name
+      for (uint32_t t = 0; t < A.p.n_causal_tgt; ++t) {
+        const uint4 it = __ldg(A.p.causal_tgt + t);
         uint64_t acc = 0;
-        for (uint32_t q = b; q < e; ++q) acc ^= A.m3[(uint64_t)__ldg(A.p.tgt_causal + q) * A.W + w];
+        for (uint32_t q = it.y; q < it.y + it.z; ++q) acc ^= A.m3[(uint64_t)__ldg(A.p.tgt_causal + q) * A.W + w];
+        const uint32_t i = it.x;
         uint64_t* col;
         uint64_t idx;
         if (i < A.p.tgt_det0) { col = A.meas; idx = i; }
@@ -1468,17 +1470,33 @@ __global__ void finalize_kernel(FinalArgs A) {
       }
     }
     if (A.p.postselect) {
+      // the walk in circuit order: every record and detector after the first
+      // fired postselected detector is cleared.  Each event is its own
+      // column, so a batch's words are all loaded before any is stored.
       uint64_t cut = 0;
-      for (uint32_t e = 0; e < A.p.n_post_events; ++e) {
-        int32_t ev = __ldg(A.p.post_events + e);
-        if (ev >= 0) {
-          if (A.meas) A.meas[(uint64_t)ev * A.W + w] &= ~cut;
-        } else {
-          const uint32_t code = (uint32_t)(-1 - ev);
-          uint64_t* d = A.det + (uint64_t)(code >> 1) * A.W + w;
-          uint64_t v = *d & ~cut;
-          *d = v;
-          if (code & 1u) cut |= v;
+      for (uint32_t e0 = 0; e0 < A.p.n_post_events; e0 += kEv) {
+        const uint32_t ne = min(kEv, A.p.n_post_events - e0);
+        uint64_t* ptr[kEv];
+        uint64_t val[kEv];
+#pragma unroll
+        for (uint32_t j = 0; j < kEv; ++j) {
+          ptr[j] = nullptr;
+          val[j] = 0;
+          if (j < ne) {
+            const int32_t ev = __ldg(A.p.post_events + e0 + j);
+            if (ev >= 0) ptr[j] = A.meas ? A.meas + (uint64_t)ev * A.W + w : nullptr;
+            else ptr[j] = A.det + (uint64_t)((uint32_t)(-1 - ev) >> 1) * A.W + w;
+            if (ptr[j]) val[j] = *ptr[j];
+          }
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < kEv; ++j) {
+          if (j < ne) {
+            const int32_t ev = __ldg(A.p.post_events + e0 + j);
+            const uint64_t v = val[j] & ~cut;
+            if (ptr[j]) *ptr[j] = v;
+            if (ev < 0 && (((uint32_t)(-1 - ev)) & 1u)) cut |= v;
+          }
         }
       }
       if (A.obs)
@@ -1646,7 +1664,8 @@ cudaError_t launch_plain(const PlainArgs& a, bool fp64, int grid, cudaStream_t s
 }
 
 cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t st) {
-  int threads = 256;
+  // one thread per 64-shot word; small CTAs spread the words over every SM
+  int threads = 64;
   uint64_t blocks = (a.W + threads - 1) / threads;
   if (blocks > 65535) blocks = 65535;
   if (blocks == 0) blocks = 1;

@@ -121,6 +121,10 @@ struct DevPlan {
   uint32_t n_targets, tgt_det0, tgt_obs0, tgt_sign0;
   const uint32_t* tgt_causal_off;
   const uint32_t* tgt_causal;
+  // the outputs with causal terms only: n_causal_tgt items, x = output index,
+  // y = first entry in tgt_causal, z = count
+  uint32_t n_causal_tgt;
+  const uint4* causal_tgt;
   // sign-kernel slots [records][dense signs]
   uint32_t n_slots;
   const uint8_t* slot_const;

@@ -36,6 +36,8 @@ struct BlobOffsets {
   size_t ch, q, ct, t4, qi, qs, pc, m1t, m1o, m1g, tco, tca, sc, li, gi, gv, pe, dn, dc, m3t, sm1, sm1o, pco, pch;
   size_t plc, plo, pls;
   size_t clt, clo;
+  size_t ctg;
+  uint32_t n_ctg = 0;
 };
 
 cudaError_t launch_sign(const SignArgs& a, int grid, cudaStream_t st);
