@@ -541,9 +541,9 @@ int prepare(symft_plan* P, const symft_sample_args* a, uint64_t* meas, uint64_t*
         o->gvec = P->gvec.ptr;
       }
     } else if (dense_kind_for(P, h, o->fp64, t.dense_kind) == 1) {
-      o->dense_kind = 1;   // register-resident: 32 / 2^k_max shots per warp, lane x of a shot's
-                           // segment holds amplitude x
-      const uint64_t per_cta = 8ull * (32u >> h.k_max);
+      o->dense_kind = 1;   // register-resident: 32 / 2^k_max segments per warp, lane x of a
+                           // shot's segment holds amplitude x (in one or two register sets)
+      const uint64_t per_cta = dense_reg_shots_per_cta(h.k_max, o->fp64);
       const uint64_t want = (a->shots + per_cta - 1) / per_cta;
       const uint64_t cap = static_cast<uint64_t>(P->sm_count) * t.dense_grid_mult;
       o->dense_grid = static_cast<int>(std::max<uint64_t>(1, std::min(want, cap)));

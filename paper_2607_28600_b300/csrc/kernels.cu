@@ -625,7 +625,13 @@ __device__ __forceinline__ Real shfl_r(Real v, int src) {
   return __shfl_sync(0xffffffffu, v, src);
 }
 
-template <typename Real, uint32_t kLw>
+// Shots per warp of the register executor: 32 / 2^k_max segments, times the
+// register sets a lane carries (kRegSetsF32 in FP32: every instruction is
+// decoded once for twice the shots, and a lane has independent work per set;
+// one in FP64, whose pipe bounds it either way).
+constexpr uint32_t kRegSetsF32 = 2;
+
+template <typename Real, uint32_t kLw, uint32_t kSets>
 __global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) {
   extern __shared__ __align__(16) unsigned char rsm[];
   const int lane = threadIdx.x & 31;
@@ -634,70 +640,105 @@ __global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) 
   const uint32_t m3w = (A.p.n_m3 + 31) / 32;
   constexpr uint32_t lw = kLw;                       // log2 lanes per shot (= k_max)
   constexpr uint32_t Wd = 1u << lw;
-  constexpr uint32_t S = 32u >> lw;                  // shots per warp
-  const uint32_t seg = (uint32_t)lane >> lw;         // this lane's shot
+  constexpr uint32_t S = 32u >> lw;                  // segments per warp
+  constexpr uint32_t SW = S * kSets;                 // shots per warp (<= 64)
+  const uint32_t seg = (uint32_t)lane >> lw;         // this lane's segment
   const uint32_t sl = (uint32_t)lane & (Wd - 1u);    // its amplitude index
   const int base = (int)(seg << lw);                 // the segment's first lane
   DenseInstrDev* ins = reinterpret_cast<DenseInstrDev*>(rsm);
-  uint32_t* sgw = reinterpret_cast<uint32_t*>(rsm + (size_t)G * sizeof(DenseInstrDev)) + (size_t)warp * (G + 32 * m3w);
-  uint32_t* m3b = sgw + G + (size_t)seg * m3w;       // this shot's active outcomes
+  // per warp: the sign word of each instruction (64 shots), then the active
+  // outcomes of each of its shots
+  uint32_t* wbase = reinterpret_cast<uint32_t*>(rsm + align16((size_t)G * sizeof(DenseInstrDev))) +
+                    (size_t)warp * (2 * G + 64 * m3w);
+  uint64_t* sgw = reinterpret_cast<uint64_t*>(wbase);
+  uint32_t* m3all = wbase + 2 * G;
   for (uint32_t i = threadIdx.x; i < G * (sizeof(DenseInstrDev) / 4); i += blockDim.x)
     reinterpret_cast<uint32_t*>(ins)[i] = reinterpret_cast<const uint32_t*>(A.p.dense)[i];
   __syncthreads();
 
   uint32_t lead_mask = 0u;                           // lane 0 of every segment
   for (uint32_t q = 0; q < S; ++q) lead_mask |= 1u << (q << lw);
-  const uint64_t wstride = (uint64_t)gridDim.x * kRegWarps * S;
-  for (uint64_t r0 = ((uint64_t)blockIdx.x * kRegWarps + warp) * S; r0 < A.shots; r0 += wstride) {
-    const uint64_t r = r0 + seg;                     // request-local shot of this segment
-    const uint64_t rg = A.shot0 + r;                 // absolute shot index
-    const uint64_t w = r >> 6;
-    const uint32_t rb = (uint32_t)(r & 31);          // bit of the shot in its half-word
-    // exogenous sign bits: the 32-shot half-word of each sign column that
-    // holds all of the warp's shots (r0 is a multiple of S <= 32)
-    const uint32_t hw = (uint32_t)(r0 >> 5) & 1u;
+  const uint64_t wstride = (uint64_t)gridDim.x * kRegWarps * SW;
+  for (uint64_t r0 = ((uint64_t)blockIdx.x * kRegWarps + warp) * SW; r0 < A.shots; r0 += wstride) {
+    // set j of this segment holds request-local shot r0 + j S + seg; r0 is a
+    // multiple of SW, which divides 64, so all of the warp's shots share the
+    // 64-shot word r0 / 64
+    const uint64_t w = r0 >> 6;
+    uint64_t r[kSets];
+    uint32_t* m3b[kSets];
+#pragma unroll
+    for (uint32_t j = 0; j < kSets; ++j) {
+      r[j] = r0 + j * S + seg;
+      m3b[j] = m3all + (size_t)(j * S + seg) * m3w;
+    }
     for (uint32_t g = lane; g < G; g += 32)
-      sgw[g] = (uint32_t)(__ldg(A.signs + (uint64_t)ins[g].sign_target_col * A.W + (r0 >> 6)) >> (32 * hw));
-    for (uint32_t i = lane; i < S * m3w; i += 32) sgw[G + i] = 0u;
+      sgw[g] = __ldg(A.signs + (uint64_t)ins[g].sign_target_col * A.W + w);
+    for (uint32_t i = lane; i < SW * m3w; i += 32) m3all[i] = 0u;
     __syncwarp();
-    // segments past the request, or rejected before any active measurement,
-    // need no dense work; they step along masked while others run
-    bool dead = r >= A.shots;
-    if (!dead && sl == 0 && A.det_exo && A.p.post_grp0 == 0) dead = group_rejects(A.p, A.det_exo, A.W, r, 0, m3b);
-    uint32_t deadm = __ballot_sync(0xffffffffu, sl == 0 && dead);
-    dead = (deadm >> base) & 1u;
+    // shots past the request, or rejected before any active measurement, need
+    // no dense work; their sets step along masked while others run
+    bool dead[kSets];
+    uint32_t deadm[kSets];
+    bool all_dead = true;
+#pragma unroll
+    for (uint32_t j = 0; j < kSets; ++j) {
+      dead[j] = r[j] >= A.shots;
+      if (!dead[j] && sl == 0 && A.det_exo && A.p.post_grp0 == 0)
+        dead[j] = group_rejects(A.p, A.det_exo, A.W, r[j], 0, m3b[j]);
+      deadm[j] = __ballot_sync(0xffffffffu, sl == 0 && dead[j]);
+      dead[j] = (deadm[j] >> base) & 1u;
+      all_dead = all_dead && (deadm[j] & lead_mask) == lead_mask;
+    }
     __syncwarp();
-    if ((deadm & lead_mask) == lead_mask) continue;
-    ShotUniforms su;
-    Real re = sl == 0 ? (Real)1 : (Real)0, im = (Real)0;
+    if (all_dead) continue;
+    ShotUniforms su[kSets];
+    Real re[kSets], im[kSets];
+#pragma unroll
+    for (uint32_t j = 0; j < kSets; ++j) {
+      re[j] = sl == 0 ? (Real)1 : (Real)0;
+      im[j] = (Real)0;
+    }
     uint32_t k = 0;
     for (uint32_t g = 0; g < G; ++g) {
       const DenseInstrDev& I = ins[g];
-      uint32_t lam = (sgw[g] >> rb) & 1u;
-      for (uint32_t q = 0; q < I.causal_n; ++q) {
-        const uint32_t j = __ldg(A.p.dense_causal + I.causal_off + q);
-        lam ^= (m3b[j >> 5] >> (j & 31)) & 1u;
+      const uint64_t sw = sgw[g];
+      Real sg[kSets];
+      uint32_t lam[kSets];
+#pragma unroll
+      for (uint32_t j = 0; j < kSets; ++j) {
+        lam[j] = (uint32_t)(sw >> (r[j] & 63)) & 1u;
+        for (uint32_t q = 0; q < I.causal_n; ++q) {
+          const uint32_t jj = __ldg(A.p.dense_causal + I.causal_off + q);
+          lam[j] ^= (m3b[j][jj >> 5] >> (jj & 31)) & 1u;
+        }
+        sg[j] = lam[j] ? (Real)-1 : (Real)1;
       }
-      const Real sg = lam ? (Real)-1 : (Real)1;
       const Real c = coef_c<Real>(I), s = coef_s<Real>(I);
       const uint32_t n = 1u << k;
       if (I.kind == 0) {                       // PromoteRot
         const int src = base + (int)(sl >= n ? sl - n : sl);
-        const Real ore = shfl_r(re, src), oim = shfl_r(im, src);
-        if (sl < n) {
-          re *= c;
-          im *= c;
-        } else if (sl < 2 * n) {
-          re = sg * s * oim;                   // -i sg s alpha
-          im = -sg * s * ore;
+#pragma unroll
+        for (uint32_t j = 0; j < kSets; ++j) {
+          const Real ore = shfl_r(re[j], src), oim = shfl_r(im[j], src);
+          if (sl < n) {
+            re[j] *= c;
+            im[j] *= c;
+          } else if (sl < 2 * n) {
+            re[j] = sg[j] * s * oim;           // -i sg s alpha
+            im[j] = -sg[j] * s * ore;
+          }
         }
         ++k;
       } else if (I.kind == 1) {                // ActiveDiagRot
         const Real mu = I.mu == 0 ? (Real)1 : (Real)-1;
-        const Real f = sg * mu * s * ((__popc(sl & I.b) & 1) ? (Real)-1 : (Real)1);
-        const Real nre = c * re + f * im, nim = c * im - f * re;
-        re = nre;
-        im = nim;
+        const Real par = (__popc(sl & I.b) & 1) ? (Real)-1 : (Real)1;
+#pragma unroll
+        for (uint32_t j = 0; j < kSets; ++j) {
+          const Real f = sg[j] * mu * s * par;
+          const Real nre = c * re[j] + f * im[j], nim = c * im[j] - f * re[j];
+          re[j] = nre;
+          im[j] = nim;
+        }
       } else if (I.kind == 2) {                // ActivePairRot
         Real cr, ci;                           // -i * i^mu
         switch (I.mu & 3) {
@@ -707,98 +748,114 @@ __global__ void __launch_bounds__(kRegWarps * 32) dense_reg_kernel(DenseArgs A) 
           default: cr = -1; ci = 0; break;
         }
         const uint32_t partner = (sl ^ I.a) & (Wd - 1u);
-        const Real pre = shfl_r(re, base + (int)partner), pim = shfl_r(im, base + (int)partner);
-        const Real sp = ((__popc(partner & I.b) & 1) ? (Real)-1 : (Real)1) * sg * s;
-        const Real nre = c * re + sp * (cr * pre - ci * pim), nim = c * im + sp * (cr * pim + ci * pre);
-        if (sl < n) {
-          re = nre;
-          im = nim;
+        const Real ps = (__popc(partner & I.b) & 1) ? (Real)-1 : (Real)1;
+#pragma unroll
+        for (uint32_t j = 0; j < kSets; ++j) {
+          const Real pre = shfl_r(re[j], base + (int)partner), pim = shfl_r(im[j], base + (int)partner);
+          const Real sp = ps * sg[j] * s;
+          const Real nre = c * re[j] + sp * (cr * pre - ci * pim), nim = c * im[j] + sp * (cr * pim + ci * pre);
+          if (sl < n) {
+            re[j] = nre;
+            im[j] = nim;
+          }
         }
       } else {                                 // active measurements
         const int h = I.h;
         const uint32_t half = n >> 1;
         const Real inv_sqrt2 = (Real)0.70710678118654752440;
-        // diag: partition by parity(b.x); pair: beta_z(y) from (u0, u0^a)
-        Real b0re = 0, b0im = 0, b1re = 0, b1im = 0;
         const uint32_t z = sl;
         const uint32_t u0 = insert_bit(z & (half - 1 + (half == 0)), h, 0u);
         Real mcr = 0, mci = 0;
-        Real s0 = 0, s1 = 0;                   // this lane's share (one amplitude)
-        if (I.kind == 5) {
-          if (sl < n) {
-            const Real v = re * re + im * im;
-            if (__popc(sl & I.b) & 1) s1 = v; else s0 = v;
-          }
-        } else {
+        if (I.kind == 6) {
           switch (I.mu & 3) {
             case 0: mcr = 1; mci = 0; break;
             case 1: mcr = 0; mci = -1; break;
             case 2: mcr = -1; mci = 0; break;
             default: mcr = 0; mci = 1; break;
           }
-          const int l0s = base + (int)(u0 & (Wd - 1u)), l1s = base + (int)((u0 ^ I.a) & (Wd - 1u));
-          const Real a0re = shfl_r(re, l0s), a0im = shfl_r(im, l0s);
-          const Real a1re = shfl_r(re, l1s), a1im = shfl_r(im, l1s);
-          const Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
-          const Real tr = sb * (mcr * a1re - mci * a1im), ti = sb * (mcr * a1im + mci * a1re);
-          b0re = (a0re + tr) * inv_sqrt2; b0im = (a0im + ti) * inv_sqrt2;
-          b1re = (a0re - tr) * inv_sqrt2; b1im = (a0im - ti) * inv_sqrt2;
-          if (z < half) {
-            s0 = b0re * b0re + b0im * b0im;
-            s1 = b1re * b1re + b1im * b1im;
-          }
         }
-        // at most 32 terms, summed over the segment in the vector's own precision
-        for (uint32_t o = Wd >> 1; o; o >>= 1) {
-          s0 += __shfl_xor_sync(0xffffffffu, s0, (int)o);
-          s1 += __shfl_xor_sync(0xffffffffu, s1, (int)o);
-        }
-        const uint32_t l0 = I.kind == 5 ? (lam ^ (uint32_t)I.eta) : lam;
-        uint32_t m = 0;
-        const uint64_t U = su.get(A, (uint32_t)I.m3, rg, (int)sl, lw, base);
-        // decision and the renormalisation scale 1 / sqrt(S_m) on the segment's
-        // first lane, in the vector's precision (self-normalised probabilities
-        // make the scale matter only for the overall norm)
-        Real sc = 0;
-        if (sl == 0 && !dead) {
-          if (sizeof(Real) == 8) {
-            const double pd = (double)(l0 ? s1 : s0) / (double)(s0 + s1);
-            m = decide64(U, pd);
-            if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = pd;
+        const int l0s = base + (int)(u0 & (Wd - 1u)), l1s = base + (int)((u0 ^ I.a) & (Wd - 1u));
+        const Real sb = (__popc(I.b & u0) & 1) ? (Real)-1 : (Real)1;
+        const bool podd = __popc(sl & I.b) & 1;
+        bool stop = true;
+#pragma unroll
+        for (uint32_t j = 0; j < kSets; ++j) {
+          // diag: partition by parity(b.x); pair: beta_z(y) from (u0, u0^a)
+          Real b0re = 0, b0im = 0, b1re = 0, b1im = 0;
+          Real s0 = 0, s1 = 0;                 // this lane's share (one amplitude)
+          if (I.kind == 5) {
+            if (sl < n) {
+              const Real v = re[j] * re[j] + im[j] * im[j];
+              if (podd) s1 = v; else s0 = v;
+            }
           } else {
-            const float pf = (float)((l0 ? s1 : s0) / (s0 + s1));
-            m = decide32(U, pf);
-            if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = (double)pf;
+            const Real a0re = shfl_r(re[j], l0s), a0im = shfl_r(im[j], l0s);
+            const Real a1re = shfl_r(re[j], l1s), a1im = shfl_r(im[j], l1s);
+            const Real tr = sb * (mcr * a1re - mci * a1im), ti = sb * (mcr * a1im + mci * a1re);
+            b0re = (a0re + tr) * inv_sqrt2; b0im = (a0im + ti) * inv_sqrt2;
+            b1re = (a0re - tr) * inv_sqrt2; b1im = (a0im - ti) * inv_sqrt2;
+            if (z < half) {
+              s0 = b0re * b0re + b0im * b0im;
+              s1 = b1re * b1re + b1im * b1im;
+            }
           }
-          sc = sizeof(Real) == 8 ? (Real)(1.0 / sqrt((double)((l0 ^ m) ? s1 : s0))) : (Real)rsqrtf((float)((l0 ^ m) ? s1 : s0));
-        }
-        m = __shfl_sync(0xffffffffu, m, base);
-        const uint32_t lab = l0 ^ m;
-        const Real scale = shfl_r(sc, base);
-        if (I.kind == 5) {
-          const uint32_t u = insert_bit(z & (half - 1 + (half == 0)), h, lab);
-          const uint32_t x = u ^ ((uint32_t)(__popc(u & I.b & ~(1u << h)) & 1) << h);
-          const int xs = base + (int)(x & (Wd - 1u));
-          const Real nre = shfl_r(re, xs), nim = shfl_r(im, xs);
-          re = z < half ? nre * scale : (Real)0;
-          im = z < half ? nim * scale : (Real)0;
-        } else {
-          re = z < half ? (lab ? b1re : b0re) * scale : (Real)0;
-          im = z < half ? (lab ? b1im : b0im) * scale : (Real)0;
+          // at most 32 terms, summed over the segment in the vector's own precision
+          for (uint32_t o = Wd >> 1; o; o >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, (int)o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, (int)o);
+          }
+          const uint32_t l0 = I.kind == 5 ? (lam[j] ^ (uint32_t)I.eta) : lam[j];
+          uint32_t m = 0;
+          const uint64_t U = su[j].get(A, (uint32_t)I.m3, A.shot0 + r[j], (int)sl, lw, base);
+          // decision and the renormalisation scale 1 / sqrt(S_m) on the
+          // segment's first lane, in the vector's precision (self-normalised
+          // probabilities make the scale matter only for the overall norm)
+          Real sc = 0;
+          if (sl == 0 && !dead[j]) {
+            if (sizeof(Real) == 8) {
+              const double pd = (double)(l0 ? s1 : s0) / (double)(s0 + s1);
+              m = decide64(U, pd);
+              if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r[j]] = pd;
+            } else {
+              const float pf = (float)((l0 ? s1 : s0) / (s0 + s1));
+              m = decide32(U, pf);
+              if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r[j]] = (double)pf;
+            }
+            sc = sizeof(Real) == 8 ? (Real)(1.0 / sqrt((double)((l0 ^ m) ? s1 : s0)))
+                                   : (Real)rsqrtf((float)((l0 ^ m) ? s1 : s0));
+          }
+          m = __shfl_sync(0xffffffffu, m, base);
+          const uint32_t lab = l0 ^ m;
+          const Real scale = shfl_r(sc, base);
+          if (I.kind == 5) {
+            const uint32_t u = insert_bit(z & (half - 1 + (half == 0)), h, lab);
+            const uint32_t x = u ^ ((uint32_t)(__popc(u & I.b & ~(1u << h)) & 1) << h);
+            const int xs = base + (int)(x & (Wd - 1u));
+            const Real nre = shfl_r(re[j], xs), nim = shfl_r(im[j], xs);
+            re[j] = z < half ? nre * scale : (Real)0;
+            im[j] = z < half ? nim * scale : (Real)0;
+          } else {
+            re[j] = z < half ? (lab ? b1re : b0re) * scale : (Real)0;
+            im[j] = z < half ? (lab ? b1im : b0im) * scale : (Real)0;
+          }
+          if (m && sl == 0) {                  // m is 0 on dead segments
+            m3b[j][I.m3 >> 5] |= 1u << (I.m3 & 31);
+            atomicOr(reinterpret_cast<unsigned long long*>(A.m3_out) + (uint64_t)I.m3 * A.W + w,
+                     1ull << (r[j] & 63));
+          }
         }
         --k;
-        if (m && sl == 0) {                    // m is 0 on dead segments
-          m3b[I.m3 >> 5] |= 1u << (I.m3 & 31);
-          atomicOr(reinterpret_cast<unsigned long long*>(A.m3_out) + (uint64_t)I.m3 * A.W + w,
-                   1ull << (r & 63));
-        }
         __syncwarp();
         if (A.det_exo && I.post_grp != kNoGroup) {   // early exit once rejected
-          bool d2 = dead;
-          if (!d2 && sl == 0) d2 = group_rejects(A.p, A.det_exo, A.W, r, I.post_grp, m3b);
-          deadm = __ballot_sync(0xffffffffu, sl == 0 && d2);
-          dead = (deadm >> base) & 1u;
-          if ((deadm & lead_mask) == lead_mask) break;
+#pragma unroll
+          for (uint32_t j = 0; j < kSets; ++j) {
+            bool d2 = dead[j];
+            if (!d2 && sl == 0) d2 = group_rejects(A.p, A.det_exo, A.W, r[j], I.post_grp, m3b[j]);
+            deadm[j] = __ballot_sync(0xffffffffu, sl == 0 && d2);
+            dead[j] = (deadm[j] >> base) & 1u;
+            stop = stop && (deadm[j] & lead_mask) == lead_mask;
+          }
+          if (stop) break;
         }
       }
     }
@@ -1581,18 +1638,23 @@ size_t dense_pc_smem_bytes(const DevPlan& p, int wpb, size_t ws_bytes, bool ws_i
 
 size_t dense_reg_smem_bytes(const DevPlan& p) {
   const size_t G = p.n_dense;
-  return G * sizeof(DenseInstrDev) + (size_t)kRegWarps * (G + 32 * ((p.n_m3 + 31) / 32)) * 4 + 16;
+  return align16((size_t)G * sizeof(DenseInstrDev)) + (size_t)kRegWarps * (2 * G + 64 * ((p.n_m3 + 31) / 32)) * 4 + 16;
 }
 
 template <typename Real>
 static void launch_dense_reg_t(const DenseArgs& a, int grid, size_t smem, cudaStream_t st) {
+  constexpr uint32_t K = sizeof(Real) == 4 ? kRegSetsF32 : 1;
   switch (a.kmax) {
-    case 1: dense_reg_kernel<Real, 1><<<grid, kRegWarps * 32, smem, st>>>(a); break;
-    case 2: dense_reg_kernel<Real, 2><<<grid, kRegWarps * 32, smem, st>>>(a); break;
-    case 3: dense_reg_kernel<Real, 3><<<grid, kRegWarps * 32, smem, st>>>(a); break;
-    case 4: dense_reg_kernel<Real, 4><<<grid, kRegWarps * 32, smem, st>>>(a); break;
-    default: dense_reg_kernel<Real, 5><<<grid, kRegWarps * 32, smem, st>>>(a); break;
+    case 1: dense_reg_kernel<Real, 1, K><<<grid, kRegWarps * 32, smem, st>>>(a); break;
+    case 2: dense_reg_kernel<Real, 2, K><<<grid, kRegWarps * 32, smem, st>>>(a); break;
+    case 3: dense_reg_kernel<Real, 3, K><<<grid, kRegWarps * 32, smem, st>>>(a); break;
+    case 4: dense_reg_kernel<Real, 4, K><<<grid, kRegWarps * 32, smem, st>>>(a); break;
+    default: dense_reg_kernel<Real, 5, K><<<grid, kRegWarps * 32, smem, st>>>(a); break;
   }
+}
+
+uint32_t dense_reg_shots_per_cta(uint32_t kmax, bool fp64) {
+  return (uint32_t)kRegWarps * (32u >> kmax) * (fp64 ? 1u : kRegSetsF32);
 }
 
 cudaError_t launch_dense_reg(const DenseArgs& a, bool fp64, int grid, cudaStream_t st) {
@@ -1641,11 +1703,13 @@ cudaError_t set_smem_limits() {
                        (const void*)dense_kernel<float>, (const void*)dense_kernel<double>,
                        (const void*)dense_pc_kernel<float>, (const void*)dense_pc_kernel<double>,
                        (const void*)dense_pc_cta_kernel<float>, (const void*)dense_pc_cta_kernel<double>,
-                       (const void*)dense_reg_kernel<float, 1>, (const void*)dense_reg_kernel<float, 2>,
-                       (const void*)dense_reg_kernel<float, 3>, (const void*)dense_reg_kernel<float, 4>,
-                       (const void*)dense_reg_kernel<float, 5>, (const void*)dense_reg_kernel<double, 1>,
-                       (const void*)dense_reg_kernel<double, 2>, (const void*)dense_reg_kernel<double, 3>,
-                       (const void*)dense_reg_kernel<double, 4>, (const void*)dense_reg_kernel<double, 5>,
+                       (const void*)dense_reg_kernel<float, 1, kRegSetsF32>,
+                       (const void*)dense_reg_kernel<float, 2, kRegSetsF32>,
+                       (const void*)dense_reg_kernel<float, 3, kRegSetsF32>,
+                       (const void*)dense_reg_kernel<float, 4, kRegSetsF32>,
+                       (const void*)dense_reg_kernel<float, 5, kRegSetsF32>, (const void*)dense_reg_kernel<double, 1, 1>,
+                       (const void*)dense_reg_kernel<double, 2, 1>, (const void*)dense_reg_kernel<double, 3, 1>,
+                       (const void*)dense_reg_kernel<double, 4, 1>, (const void*)dense_reg_kernel<double, 5, 1>,
                        (const void*)dense_cta_kernel<float>, (const void*)dense_cta_kernel<double>,
                        (const void*)plain_kernel<float>, (const void*)plain_kernel<double>};
   for (const void* f : fns) {

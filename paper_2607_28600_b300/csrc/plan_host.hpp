@@ -55,6 +55,8 @@ size_t dense_pc_smem_bytes(const DevPlan& p, int wpb, size_t ws_bytes, bool ws_i
 size_t dense_cta_smem_bytes(const DevPlan& p, size_t vec_bytes, bool vec_in_smem);
 cudaError_t launch_dense_cta(const DenseArgs& a, bool fp64, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_dense_reg(const DenseArgs& a, bool fp64, int grid, cudaStream_t st);
+// shots one CTA of the register executor holds at a time
+uint32_t dense_reg_shots_per_cta(uint32_t kmax, bool fp64);
 cudaError_t launch_dense_pc(const DenseArgs& a, bool fp64, int warps_per_block, int grid, size_t smem,
                             cudaStream_t st);
 // resident CTAs per SM of the product-component warp executor for a launch shape
