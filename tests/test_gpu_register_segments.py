@@ -70,3 +70,20 @@ def test_segments_match_the_oracle(name):
     np.testing.assert_array_equal(det, o["dets"])
     np.testing.assert_array_equal(obs, o["obs"])
     np.testing.assert_array_equal(disc, o["discard"])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", ["surface_d3_T_k1", "random_k3", "coherent_d3_r1_k4", "cultivation_small_k4"])
+def test_shot_bits_do_not_depend_on_the_warp_layout(name, precision):
+    """A shot's bits are a function of its absolute index alone: one call over
+    N shots equals two calls over the same shots split at a 512-shot offset,
+    although the shots land in other warps, segments and register sets (FP32
+    lanes carry two sets of shots)."""
+    text, _ = CASES[name]
+    shots, seed, cut = 3000 + 13, 17, 512 * 3
+    plan, whole = _run(text, shots, seed, 0, precision, "register")
+    assert plan.info["dense_executor"][precision] == "register"
+    _, first = _run(text, cut, seed, 0, precision, "register")
+    _, second = _run(text, shots - cut, seed, cut, precision, "register")
+    for w, a, b in zip(whole, first, second):
+        np.testing.assert_array_equal(w, np.concatenate([a, b], axis=0))
