@@ -112,6 +112,17 @@ __device__ __forceinline__ uint32_t decide32(uint64_t U, float p0) {
   return U < T ? 0u : 1u;
 }
 
+// the sums over a group of kGW lanes (a whole warp for 32, else the aligned
+// half or quarter that holds this lane)
+template <uint32_t kGW, typename Acc>
+__device__ __forceinline__ void group_sum2(Acc& a, Acc& b) {
+#pragma unroll
+  for (int o = (int)kGW / 2; o; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+}
+
 template <typename Acc>
 __device__ __forceinline__ void warp_sum2(Acc& a, Acc& b) {
 #pragma unroll
@@ -244,41 +255,43 @@ __device__ __forceinline__ Cplx<Real> kept_elem(const Cplx<Real>* vec, const Den
 // measurement's in-place compaction reads every source of a step before any
 // of its writes (a source is never below its destination).  Batching costs
 // registers, so only executors whose occupancy is set by shared memory take it.
-template <typename Real, uint32_t kBatch>
+template <typename Real, uint32_t kBatch, uint32_t kGW = 32>
 __device__ __forceinline__ void warp_instr(const DenseArgs& A, Cplx<Real>* vec, Cplx<Real>* out, uint32_t n,
                                            const DenseInstrDev& I, uint32_t lam, uint64_t r, uint64_t rg, uint64_t w,
-                                           uint64_t bitmask, uint32_t* m3bits, ShotUniforms& su, int lane) {
+                                           uint64_t bitmask, uint32_t* m3bits, ShotUniforms& su, int lane,
+                                           int gbase = 0, bool live = true) {
+  constexpr uint32_t kLgGW = kGW == 32 ? 5 : (kGW == 16 ? 4 : 3);
   const Real sg = lam ? (Real)-1 : (Real)1;
   const Real c = coef_c<Real>(I), s = coef_s<Real>(I);
 
   switch (I.kind) {
     case 0: {  // PromoteRot: a'_{x} = c a_x, a'_{x+2^k} = -i sg s a_x
-      if (kBatch > 1 && n >= 32 * kBatch) {
-        for (uint32_t x0 = lane; x0 < n; x0 += 32 * kBatch) {
+      if (kBatch > 1 && n >= kGW * kBatch) {
+        for (uint32_t x0 = lane; x0 < n; x0 += kGW * kBatch) {
           Cplx<Real> v[kBatch];
 #pragma unroll
-          for (uint32_t j = 0; j < kBatch; ++j) v[j] = vec[x0 + 32 * j];
+          for (uint32_t j = 0; j < kBatch; ++j) v[j] = vec[x0 + kGW * j];
 #pragma unroll
-          for (uint32_t j = 0; j < kBatch; ++j) promote_elem(vec, x0 + 32 * j, n, v[j], sg, s, c);
+          for (uint32_t j = 0; j < kBatch; ++j) promote_elem(vec, x0 + kGW * j, n, v[j], sg, s, c);
         }
       } else {
-        for (uint32_t x = lane; x < n; x += 32) promote_elem(vec, x, n, vec[x], sg, s, c);
+        for (uint32_t x = lane; x < n; x += kGW) promote_elem(vec, x, n, vec[x], sg, s, c);
       }
       break;
     }
     case 1: {  // ActiveDiagRot: a_x *= c - i sg mu (-1)^{b.x} s
       const Real mu = I.mu == 0 ? (Real)1 : (Real)-1;
       const Real sgmus = sg * mu * s;
-      if (kBatch > 1 && n >= 32 * kBatch) {
-        for (uint32_t x0 = lane; x0 < n; x0 += 32 * kBatch) {
+      if (kBatch > 1 && n >= kGW * kBatch) {
+        for (uint32_t x0 = lane; x0 < n; x0 += kGW * kBatch) {
           Cplx<Real> v[kBatch];
 #pragma unroll
-          for (uint32_t j = 0; j < kBatch; ++j) v[j] = vec[x0 + 32 * j];
+          for (uint32_t j = 0; j < kBatch; ++j) v[j] = vec[x0 + kGW * j];
 #pragma unroll
-          for (uint32_t j = 0; j < kBatch; ++j) diag_elem(vec, x0 + 32 * j, v[j], sgmus, I.b, c);
+          for (uint32_t j = 0; j < kBatch; ++j) diag_elem(vec, x0 + kGW * j, v[j], sgmus, I.b, c);
         }
       } else {
-        for (uint32_t x = lane; x < n; x += 32) diag_elem(vec, x, vec[x], sgmus, I.b, c);
+        for (uint32_t x = lane; x < n; x += kGW) diag_elem(vec, x, vec[x], sgmus, I.b, c);
       }
       break;
     }
@@ -296,23 +309,23 @@ __device__ __forceinline__ void warp_instr(const DenseArgs& A, Cplx<Real>* vec, 
       ci *= sg * s;
       const uint32_t nh = n >> 1;
       const uint32_t pab = __popc(I.a & I.b) & 1;
-      if (kBatch > 1 && nh >= 32 * kBatch) {
-        for (uint32_t z0 = lane; z0 < nh; z0 += 32 * kBatch) {
+      if (kBatch > 1 && nh >= kGW * kBatch) {
+        for (uint32_t z0 = lane; z0 < nh; z0 += kGW * kBatch) {
           Cplx<Real> v0[kBatch], v1[kBatch];
 #pragma unroll
           for (uint32_t j = 0; j < kBatch; ++j) {
-            const uint32_t x0 = insert_bit(z0 + 32 * j, p, 0u);
+            const uint32_t x0 = insert_bit(z0 + kGW * j, p, 0u);
             v0[j] = vec[x0];
             v1[j] = vec[x0 ^ I.a];
           }
 #pragma unroll
           for (uint32_t j = 0; j < kBatch; ++j) {
-            const uint32_t x0 = insert_bit(z0 + 32 * j, p, 0u);
+            const uint32_t x0 = insert_bit(z0 + kGW * j, p, 0u);
             pair_elem(vec, x0, x0 ^ I.a, v0[j], v1[j], I.b, pab, c, cr, ci);
           }
         }
       } else {
-        for (uint32_t z = lane; z < nh; z += 32) {
+        for (uint32_t z = lane; z < nh; z += kGW) {
           const uint32_t x0 = insert_bit(z, p, 0u), x1 = x0 ^ I.a;
           pair_elem(vec, x0, x1, vec[x0], vec[x1], I.b, pab, c, cr, ci);
         }
@@ -336,50 +349,50 @@ __device__ __forceinline__ void warp_instr(const DenseArgs& A, Cplx<Real>* vec, 
       Real scale;
       if (sizeof(Real) == 8 || n >= (1u << 14)) {      // FP64 sums
         double S0 = 0.0, S1 = 0.0;
-        branch_sums<Real, double>(vec, I, n, lane, 32, mcr, mci, S0, S1);
-        warp_sum2(S0, S1);
-        const uint64_t U = su.get(A, (uint32_t)I.m3, rg, lane);
-        if (lane == 0) {
+        branch_sums<Real, double>(vec, I, n, lane, kGW, mcr, mci, S0, S1);
+        group_sum2<kGW>(S0, S1);
+        const uint64_t U = su.get(A, (uint32_t)I.m3, rg, lane, kLgGW, gbase);
+        if (lane == 0 && live) {
           const double p0 = (l0 ? S1 : S0) / (S0 + S1);
           m = decide64(U, p0);
           if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = p0;
         }
-        m = __shfl_sync(0xffffffffu, m, 0);
+        m = __shfl_sync(0xffffffffu, m, gbase);
         scale = (Real)(1.0 / sqrt((l0 ^ m) ? S1 : S0));
       } else {                                         // FP32 sums below 2^14 terms
         float S0 = 0.0f, S1 = 0.0f;
-        branch_sums<Real, float>(vec, I, n, lane, 32, mcr, mci, S0, S1);
-        warp_sum2(S0, S1);
-        const uint64_t U = su.get(A, (uint32_t)I.m3, rg, lane);
+        branch_sums<Real, float>(vec, I, n, lane, kGW, mcr, mci, S0, S1);
+        group_sum2<kGW>(S0, S1);
+        const uint64_t U = su.get(A, (uint32_t)I.m3, rg, lane, kLgGW, gbase);
         // the renormalisation scale 1 / sqrt(S_m) in FP32 on one lane: every
         // later branch probability is self-normalised, so the scale only
         // sets the vector's overall norm (an FP64 scale measured 2.4-3x
         // slower on B300, whose FP64 pipe is a small fraction of FP32's)
         float sc = 0.0f;
-        if (lane == 0) {
+        if (lane == 0 && live) {
           const float p0 = (l0 ? S1 : S0) / (S0 + S1);
           m = decide32(U, p0);
           if (A.prob) A.prob[(uint64_t)I.m3 * A.shots + r] = (double)p0;
           sc = rsqrtf((l0 ^ m) ? S1 : S0);
         }
-        m = __shfl_sync(0xffffffffu, m, 0);
-        scale = (Real)__shfl_sync(0xffffffffu, sc, 0);
+        m = __shfl_sync(0xffffffffu, m, gbase);
+        scale = (Real)__shfl_sync(0xffffffffu, sc, gbase);
       }
       const uint32_t lab = l0 ^ m;
       // compaction in increasing z order (in place, sources are never below z)
       const uint32_t half = n >> 1;
-      if (kBatch > 1 && half >= 32 * kBatch) {
-        for (uint32_t z0 = lane; z0 < half; z0 += 32 * kBatch) {
+      if (kBatch > 1 && half >= kGW * kBatch) {
+        for (uint32_t z0 = lane; z0 < half; z0 += kGW * kBatch) {
           Cplx<Real> val[kBatch];
 #pragma unroll
-          for (uint32_t j = 0; j < kBatch; ++j) val[j] = kept_elem(vec, I, z0 + 32 * j, lab, mcr, mci, scale);
+          for (uint32_t j = 0; j < kBatch; ++j) val[j] = kept_elem(vec, I, z0 + kGW * j, lab, mcr, mci, scale);
           __syncwarp();
 #pragma unroll
-          for (uint32_t j = 0; j < kBatch; ++j) out[z0 + 32 * j] = val[j];
+          for (uint32_t j = 0; j < kBatch; ++j) out[z0 + kGW * j] = val[j];
           __syncwarp();
         }
       } else {
-        for (uint32_t z0 = 0; z0 < half; z0 += 32) {
+        for (uint32_t z0 = 0; z0 < half; z0 += kGW) {
           const uint32_t z = z0 + lane;
           Cplx<Real> val;
           val.re = 0;
@@ -405,16 +418,24 @@ __device__ __forceinline__ void warp_instr(const DenseArgs& A, Cplx<Real>* vec, 
   }
 }
 
-template <typename Real>
+template <typename Real, uint32_t kGroups>
 __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
+  // kGroups shots per warp, each on a group of kGW lanes with its own vector:
+  // every instruction is decoded once for all of them
+  constexpr uint32_t kGW = 32 / kGroups;
   extern __shared__ unsigned char dsm[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
+  const uint32_t gid = (uint32_t)lane / kGW;             // this lane's shot in the warp
+  const int gl = lane & (int)(kGW - 1);                  // its lane in the shot's group
+  const int gbase = (int)(gid * kGW);
+  const uint32_t vwpb = (uint32_t)wpb * kGroups;         // shots per CTA
+  const uint32_t vw = (uint32_t)wib * kGroups + gid;     // this shot's slot in the CTA
   const uint32_t S = 1u << A.kmax;
   const uint32_t m3w = (A.p.n_m3 + 31) / 32;
   const uint32_t G = A.p.n_dense;
-  const uint32_t bkw = m3w + (G + 31) / 32;     // per-warp words: m3 bits, then sign bits
+  const uint32_t bkw = m3w + (G + 31) / 32;     // per-shot words: m3 bits, then sign bits
   // the instruction stream, staged in shared memory when it is small enough
   const size_t stb = stage_bytes((size_t)G * sizeof(DenseInstrDev));
   const DenseInstrDev* ins = A.p.dense;
@@ -423,42 +444,55 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
       reinterpret_cast<uint32_t*>(dsm)[i] = reinterpret_cast<const uint32_t*>(A.p.dense)[i];
     ins = reinterpret_cast<const DenseInstrDev*>(dsm);
   }
-  uint32_t* m3bits = reinterpret_cast<uint32_t*>(dsm + stb) + (size_t)wib * bkw;
+  uint32_t* m3bits = reinterpret_cast<uint32_t*>(dsm + stb) + (size_t)vw * bkw;
   uint32_t* sgn = m3bits + m3w;
   Cplx<Real>* vec;
-  const uint64_t warp_global = (uint64_t)blockIdx.x * wpb + wib;
+  const uint64_t slot_global = (uint64_t)blockIdx.x * vwpb + vw;
   if (A.use_smem) {
-    size_t off = stb + (((size_t)wpb * bkw * 4 + 15) & ~(size_t)15);
-    vec = reinterpret_cast<Cplx<Real>*>(dsm + off) + (size_t)wib * S;
+    size_t off = stb + (((size_t)vwpb * bkw * 4 + 15) & ~(size_t)15);
+    vec = reinterpret_cast<Cplx<Real>*>(dsm + off) + (size_t)vw * S;
   } else {
-    vec = reinterpret_cast<Cplx<Real>*>(A.gvec) + warp_global * A.gvec_stride;
+    vec = reinterpret_cast<Cplx<Real>*>(A.gvec) + slot_global * A.gvec_stride;
   }
   __syncthreads();
 
-  for (uint64_t r = warp_global; r < A.shots; r += (uint64_t)gridDim.x * wpb) {
+  for (uint64_t r0 = (uint64_t)blockIdx.x * vwpb + (uint64_t)wib * kGroups; r0 < A.shots;
+       r0 += (uint64_t)gridDim.x * vwpb) {
+    const uint64_t r = r0 + gid;         // request-local shot of this group
+    const bool inreq = r < A.shots;
     const uint64_t rg = A.shot0 + r;     // absolute shot index
     const uint64_t w = r >> 6;
     const uint64_t bitmask = 1ull << (r & 63);
-    for (uint32_t i = lane; i < m3w; i += 32) m3bits[i] = 0u;
-    // the shot's exogenous sign bits, 32 instructions per ballot, fetched
+    for (uint32_t i = gl; i < m3w; i += kGW) m3bits[i] = 0u;
+    // the shot's exogenous sign bits, kGW instructions per ballot, fetched
     // together before the instruction loop
-    for (uint32_t base = 0; base < G; base += 32) {
-      const uint32_t g = base + lane;
+    for (uint32_t base = 0; base < G; base += kGW) {
+      const uint32_t g = base + gl;
       bool bit = false;
-      if (g < G) bit = (__ldg(A.signs + (uint64_t)ins[g].sign_target_col * A.W + w) & bitmask) != 0;
+      if (inreq && g < G) bit = (__ldg(A.signs + (uint64_t)ins[g].sign_target_col * A.W + w) & bitmask) != 0;
       const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-      if (lane == 0) sgn[base >> 5] = bal;
+      if (gl == 0) {
+        if (kGW == 32) {
+          sgn[base >> 5] = bal;
+        } else {
+          const uint32_t part = (bal >> gbase) & ((1u << kGW) - 1u);
+          if ((base & 31) == 0) sgn[base >> 5] = part;
+          else sgn[base >> 5] |= part << (base & 31);
+        }
+      }
     }
     ShotUniforms su;
-    if (lane == 0) {
+    if (gl == 0) {
       vec[0].re = (Real)1;
       vec[0].im = (Real)0;
     }
     __syncwarp();
-    // a shot rejected before any active measurement needs no dense work
-    const bool dead0 = A.det_exo && A.p.post_grp0 == 0 && group_rejects(A.p, A.det_exo, A.W, r, 0, m3bits);
+    // a shot rejected before any active measurement needs no dense work; a
+    // warp runs while any of its shots is live, the others stepping masked
+    bool live = inreq && !(A.det_exo && A.p.post_grp0 == 0 && group_rejects(A.p, A.det_exo, A.W, r, 0, m3bits));
+    uint32_t livem = __ballot_sync(0xffffffffu, live);
     __syncwarp();
-    if (dead0) continue;
+    if (livem == 0) continue;
     uint32_t k = 0;
     for (uint32_t g = 0; g < G; ++g) {
       const DenseInstrDev I = ins[g];
@@ -469,14 +503,15 @@ __global__ void __launch_bounds__(256) dense_kernel(DenseArgs A) {
         lam ^= (m3bits[j >> 5] >> (j & 31)) & 1u;
       }
       const uint32_t n = 1u << k;
-      warp_instr<Real, 1>(A, vec, vec, n, I, lam, r, rg, w, bitmask, m3bits, su, lane);
+      warp_instr<Real, 1, kGW>(A, vec, vec, n, I, lam, r, rg, w, bitmask, m3bits, su, gl, gbase, live);
       if (I.kind == 0) ++k;
       else if (I.kind == 5 || I.kind == 6) --k;
       __syncwarp();
       if (A.det_exo && I.post_grp != kNoGroup) {           // early exit once rejected
-        const bool dead = group_rejects(A.p, A.det_exo, A.W, r, I.post_grp, m3bits);
+        if (live) live = !group_rejects(A.p, A.det_exo, A.W, r, I.post_grp, m3bits);
+        livem = __ballot_sync(0xffffffffu, live);
         __syncwarp();
-        if (dead) break;
+        if (livem == 0) break;
       }
     }
   }
@@ -1608,8 +1643,10 @@ __global__ void count_kernel(CountArgs A) {
 cudaError_t set_smem_limits();
 
 template <typename Real>
-cudaError_t launch_dense_t(const DenseArgs& a, int warps_per_block, int grid, size_t smem, cudaStream_t st) {
-  dense_kernel<Real><<<grid, warps_per_block * 32, smem, st>>>(a);
+cudaError_t launch_dense_t(const DenseArgs& a, int warps_per_block, int grid, size_t smem, cudaStream_t st,
+                           int shots_per_warp) {
+  if (shots_per_warp == 2) dense_kernel<Real, 2><<<grid, warps_per_block * 32, smem, st>>>(a);
+  else dense_kernel<Real, 1><<<grid, warps_per_block * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1684,9 +1721,10 @@ cudaError_t launch_dense_pc_cta(const DenseArgs& a, bool fp64, int grid, size_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_dense(const DenseArgs& a, bool fp64, int warps_per_block, int grid, size_t smem, cudaStream_t st) {
-  return fp64 ? launch_dense_t<double>(a, warps_per_block, grid, smem, st)
-              : launch_dense_t<float>(a, warps_per_block, grid, smem, st);
+cudaError_t launch_dense(const DenseArgs& a, bool fp64, int warps_per_block, int grid, size_t smem, cudaStream_t st,
+                         int shots_per_warp) {
+  return fp64 ? launch_dense_t<double>(a, warps_per_block, grid, smem, st, shots_per_warp)
+              : launch_dense_t<float>(a, warps_per_block, grid, smem, st, shots_per_warp);
 }
 
 size_t plain_smem_bytes(const DevPlan& p, uint32_t kmax, bool fp64) {
@@ -1700,7 +1738,8 @@ cudaError_t set_smem_limits() {
   if (done) return cudaSuccess;
   const int lim = 227 * 1024;
   const void* fns[] = {sign_kernel_fn(),
-                       (const void*)dense_kernel<float>, (const void*)dense_kernel<double>,
+                       (const void*)dense_kernel<float, 1>, (const void*)dense_kernel<double, 1>,
+                       (const void*)dense_kernel<float, 2>, (const void*)dense_kernel<double, 2>,
                        (const void*)dense_pc_kernel<float>, (const void*)dense_pc_kernel<double>,
                        (const void*)dense_pc_cta_kernel<float>, (const void*)dense_pc_cta_kernel<double>,
                        (const void*)dense_reg_kernel<float, 1, kRegSetsF32>,

@@ -43,8 +43,10 @@ struct BlobOffsets {
 cudaError_t launch_sign(const SignArgs& a, int grid, cudaStream_t st);
 size_t sign_smem_bytes(const DevPlan& p);
 cudaError_t sign_occupancy(const DevPlan& p, int* ctas_per_sm);
+// shots_per_warp 2: two shots per warp, each on 16 lanes (the smem size is
+// then that of 2 * warps_per_block shots)
 cudaError_t launch_dense(const DenseArgs& a, bool fp64, int warps_per_block, int grid, size_t smem,
-                         cudaStream_t st);
+                         cudaStream_t st, int shots_per_warp = 1);
 cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t st);
 cudaError_t launch_count(const CountArgs& a, int sm_count, cudaStream_t st);
 cudaError_t set_smem_limits();
