@@ -113,3 +113,33 @@ def test_every_executor_gives_the_same_bits(which):
     for ex, o in outs.items():
         for x, y in zip(outs["warp"], o):
             np.testing.assert_array_equal(x, y, err_msg=ex)
+
+
+def test_random_circuits_every_executor_same_bits():
+    """Random near-Clifford circuits over a range of k_max (seeded), with and
+    without postselection: every dense executor that can run a plan (register
+    with several shots per warp, warp with one or two shots per warp, CTA,
+    wide with its streamed tiles, product components on a warp or a CTA)
+    samples the same FP64 bits, at a shot offset and a ragged shot count."""
+    import paper_2607_28600_b300 as S
+    rng = random.Random(2024)
+    compared = 0
+    for _ in range(10):
+        nq, layers, nrot = rng.randint(6, 16), rng.randint(3, 8), rng.randint(1, 12)
+        text = random_near_clifford(nq, layers, nrot, 5e-3, seed=rng.randint(0, 10**6))
+        post = rng.randint(0, 1)
+        outs = []
+        for ex in ("register", "warp", "cta", "wide", "components_warp", "components_cta"):
+            try:
+                plan = S.symft_compile(text, postselect=post, executor=ex)
+            except S.SymftError:
+                continue
+            if plan.info["k_max"] == 0 or plan.info["dense_executor"][1] != ex:
+                continue
+            m, d, o, disc = S.sample_to_tensors(plan, 1537, 99, shot_offset=512, precision=S.FP64)
+            outs.append((ex, [t.cpu().numpy() for t in (m, d, o, disc)]))
+        for ex, o in outs[1:]:
+            for x, y in zip(outs[0][1], o):
+                np.testing.assert_array_equal(x, y, err_msg=f"{outs[0][0]} vs {ex}")
+            compared += 1
+    assert compared >= 20
