@@ -731,6 +731,11 @@ def main():
         S.symft_sample_ex(plan, shots, 2000 + i, shot_offset=offset, meas_out=hm, det_out=hd,
                           obs_out=ho, out_location=S.OUT_HOST, stream=stream)
     e2e_s = (time.perf_counter() - t0) / max(1, e2e_steps)
+    if world > 1:
+        # the slowest rank sets the whole job's end-to-end time, as for `value`
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
     e2e_val = world * shots / e2e_s if e2e_steps else None
 
     if rank != 0:
