@@ -1,10 +1,13 @@
 // Dense-state, plain-form, finalize and tally kernels (Sec. 5, single-shot
 // algorithm, run for many shots at once).
 //
-//  dense_reg_kernel  k_max <= 5: one warp per shot, lane x holds amplitude x
-//  dense_kernel      one warp per shot, active vector in shared memory
+//  dense_reg_kernel  k_max <= 5: 32 / 2^k_max shots per warp (twice that in
+//                    FP32), lane x of a shot's segment holds amplitude x
+//  dense_kernel      one shot per warp (two on 16-lane groups up to k_max 8),
+//                    active vector in shared memory
+//  dense_pc_kernel   one shot per warp on its product-component workspace
 //  dense_cta_kernel  one CTA per shot, vector in shared memory
-//                    -- all three run PromoteRot, ActiveDiagRot, ActivePairRot,
+//                    -- all of them run PromoteRot, ActiveDiagRot, ActivePairRot,
 //                    ActiveDiagMeas and ActivePairMeas (Sec. 4) on the shot's
 //                    active vector, completing each sign with the causal
 //                    residual of the active outcomes sampled earlier in the shot
@@ -24,7 +27,8 @@ namespace symft {
 const void* sign_kernel_fn();
 
 // ---------------------------------------------------------------------------
-// Dense executor: one warp per shot, active vector in shared or global memory.
+// Dense executor: a warp (or a group of its lanes) per shot, active vector in
+// shared or global memory.
 // ---------------------------------------------------------------------------
 template <typename Real>
 struct Cplx {
