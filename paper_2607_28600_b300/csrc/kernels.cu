@@ -246,13 +246,15 @@ __device__ __forceinline__ Cplx<Real> kept_elem(const Cplx<Real>* vec, const Den
 
 // One dense instruction (Sec. 4: PromoteRot, ActiveDiagRot, ActivePairRot,
 // ActiveDiagMeas, ActivePairMeas) on a vector of n = 2^k amplitudes held by
-// one warp (shared or global memory), with the instruction's sign lam; the
-// masks a, b and the pivot h of I are those of the vector's own bits.  A
-// measurement writes the kept half to out: in place (out == vec) when h is
-// the highest bit of a (pair) or any bit of b (diagonal), else to a disjoint
-// region.
+// a group of kGW lanes (the whole warp, or the half that starts at lane
+// gbase; `lane` is the lane's index in its group), in shared or global
+// memory, with the instruction's sign lam; the masks a, b and the pivot h of
+// I are those of the vector's own bits.  A measurement writes the kept half
+// to out: in place (out == vec) when h is the highest bit of a (pair) or any
+// bit of b (diagonal), else to a disjoint region.  A group whose shot is not
+// live computes along but decides nothing and writes no outcome.
 //
-// kBatch > 1: an instruction over at least 32 kBatch elements (amplitudes,
+// kBatch > 1: an instruction over at least kGW kBatch elements (amplitudes,
 // pairs or kept amplitudes) runs in steps of kBatch elements per lane whose
 // loads are all issued before the step's stores, so their shared-memory
 // latencies overlap; the elements of a step are disjoint, and a
