@@ -1548,23 +1548,37 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs A) {
 
 
 __global__ void finalize_kernel(FinalArgs A) {
-  constexpr uint32_t kEv = 8;   // postselection events whose words are loaded together
+  constexpr uint32_t kEv = 8;   // columns (outputs, postselection events) whose words are loaded together
   for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < A.W; w += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t pad = ~0ull;
     if (w == A.W - 1 && (A.shots & 63)) pad = (1ull << (A.shots & 63)) - 1;
     if (A.m3) {
-      // outputs with causal terms: XOR in the active outcomes they name
-      for (uint32_t t = 0; t < A.p.n_causal_tgt; ++t) {
-        const uint4 it = __ldg(A.p.causal_tgt + t);
-        uint64_t acc = 0;
-        for (uint32_t q = it.y; q < it.y + it.z; ++q) acc ^= A.m3[(uint64_t)__ldg(A.p.tgt_causal + q) * A.W + w];
-        const uint32_t i = it.x;
-        uint64_t* col;
-        uint64_t idx;
-        if (i < A.p.tgt_det0) { col = A.meas; idx = i; }
-        else if (i < A.p.tgt_obs0) { col = A.det; idx = i - A.p.tgt_det0; }
-        else { col = A.obs; idx = i - A.p.tgt_obs0; }
-        if (col) col[idx * A.W + w] ^= acc & pad;
+      // outputs with causal terms: XOR in the active outcomes they name.
+      // Each output is its own column, so a batch's words are all loaded
+      // before any is stored.
+      for (uint32_t t0 = 0; t0 < A.p.n_causal_tgt; t0 += kEv) {
+        const uint32_t nt = min(kEv, A.p.n_causal_tgt - t0);
+        uint64_t* ptr[kEv];
+        uint64_t val[kEv], acc[kEv];
+#pragma unroll
+        for (uint32_t j = 0; j < kEv; ++j) {
+          ptr[j] = nullptr;
+          val[j] = 0;
+          acc[j] = 0;
+          if (j < nt) {
+            const uint4 it = __ldg(A.p.causal_tgt + t0 + j);
+            for (uint32_t q = it.y; q < it.y + it.z; ++q)
+              acc[j] ^= A.m3[(uint64_t)__ldg(A.p.tgt_causal + q) * A.W + w];
+            const uint32_t i = it.x;
+            if (i < A.p.tgt_det0) ptr[j] = A.meas ? A.meas + (uint64_t)i * A.W + w : nullptr;
+            else if (i < A.p.tgt_obs0) ptr[j] = A.det ? A.det + (uint64_t)(i - A.p.tgt_det0) * A.W + w : nullptr;
+            else ptr[j] = A.obs ? A.obs + (uint64_t)(i - A.p.tgt_obs0) * A.W + w : nullptr;
+            if (ptr[j]) val[j] = *ptr[j];
+          }
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < kEv; ++j)
+          if (ptr[j]) *ptr[j] = val[j] ^ (acc[j] & pad);
       }
     }
     if (A.p.postselect) {
