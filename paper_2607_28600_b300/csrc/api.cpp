@@ -170,10 +170,12 @@ void build_blob(symft_plan* P) {
   }
   P->off.sc = push(blob, h.slot_const);
   // slot -> constant and random-measurement sources (inverse of the m1 lists)
+  std::vector<uint32_t> sm1_nsrc(h.n_slots, 0);
   {
     std::vector<std::vector<uint32_t>> src(h.n_slots);
     for (size_t j = 0; j < h.m1_t.size(); ++j)
       for (uint32_t q = h.m1_off[j]; q < h.m1_off[j + 1]; ++q) src[h.m1_tgt[q]].push_back(static_cast<uint32_t>(j));
+    for (uint32_t i = 0; i < h.n_slots; ++i) sm1_nsrc[i] = static_cast<uint32_t>(src[i].size());
     std::vector<uint4> sm1(std::max<size_t>(1, h.n_slots));
     std::vector<uint32_t> ovf;
     for (uint32_t i = 0; i < h.n_slots; ++i) {
@@ -223,6 +225,41 @@ void build_blob(symft_plan* P) {
     }
   }
   if (gat_ovf.empty()) gat_ovf.push_back(0);
+  // slots that do not start at zero
+  {
+    std::vector<uint32_t> nz;
+    for (uint32_t i = 0; i < h.n_slots; ++i)
+      if (h.slot_const[i] || sm1_nsrc[i]) nz.push_back(i);
+    P->off.n_snz = static_cast<uint32_t>(nz.size());
+    if (nz.empty()) nz.push_back(0);
+    P->off.snz = push(blob, nz);
+  }
+  // outputs that equal one slot before the record chains (exo(b) = delta_b ^
+  // exo(a) when a is b's only parent, so exo(a) ^ exo(b) = delta_b), and the rest
+  {
+    std::vector<uint2> dl;
+    std::vector<uint32_t> rest;
+    auto npar = [&](uint32_t r) { return h.par_off[r + 1] - h.par_off[r]; };
+    for (uint32_t j = 0; j < n_gat; ++j) {
+      const uint32_t off = h.gat_off[j], n = h.gat_off[j + 1] - off;
+      int64_t slot = -1;
+      if (n == 1 && npar(h.gat_rec[off]) == 0) {
+        slot = h.gat_rec[off];
+      } else if (n == 2) {
+        const uint32_t a = std::min(h.gat_rec[off], h.gat_rec[off + 1]);
+        const uint32_t b = std::max(h.gat_rec[off], h.gat_rec[off + 1]);
+        if (npar(b) == 1 && h.par[h.par_off[b]] == a) slot = b;
+      }
+      if (slot >= 0) dl.push_back(make_uint2(j, static_cast<uint32_t>(slot)));
+      else rest.push_back(j);
+    }
+    P->off.n_odl = static_cast<uint32_t>(dl.size());
+    P->off.n_ors = static_cast<uint32_t>(rest.size());
+    if (dl.empty()) dl.push_back(make_uint2(0u, 0u));
+    if (rest.empty()) rest.push_back(0);
+    P->off.odl = push(blob, dl);
+    P->off.ors = push(blob, rest);
+  }
   P->off.m3t = push(blob, h.m3_t);
   P->off.pco = push(blob, h.post_chk_off);
   P->off.pch = push(blob, h.post_chk);
@@ -274,6 +311,12 @@ void bind_plan(const symft_plan* P, unsigned char* base, DevPlan* dptr) {
   d.post_grp0 = P->post_grp0;
   d.gat_item = reinterpret_cast<const uint4*>(at(P->off.gi));
   d.gat_ovf = reinterpret_cast<const uint32_t*>(at(P->off.gv));
+  d.n_slot_nz = P->off.n_snz;
+  d.slot_nz = reinterpret_cast<const uint32_t*>(at(P->off.snz));
+  d.n_out_delta = P->off.n_odl;
+  d.n_out_rest = P->off.n_ors;
+  d.out_delta = reinterpret_cast<const uint2*>(at(P->off.odl));
+  d.out_rest = reinterpret_cast<const uint32_t*>(at(P->off.ors));
   d.tgt_causal_off = reinterpret_cast<const uint32_t*>(at(P->off.tco));
   d.tgt_causal = reinterpret_cast<const uint32_t*>(at(P->off.tca));
   d.n_causal_tgt = P->off.n_ctg;

@@ -141,6 +141,16 @@ struct DevPlan {
   // and (y, z) = (offset, count) of a record list in gat_ovf
   const uint4* gat_item;
   const uint32_t* gat_ovf;
+  // slots that do not start at zero (a constant or random-measurement sources)
+  uint32_t n_slot_nz;
+  const uint32_t* slot_nz;
+  // detectors / observables (index j < n_dets + n_obs) that equal one slot as
+  // it stands before the record chains: x = j, y = slot (a record without
+  // parents, or the later record of a two-record gather whose only parent is
+  // the other one); every other output is gathered after the chains
+  uint32_t n_out_delta, n_out_rest;
+  const uint2* out_delta;
+  const uint32_t* out_rest;
   // postselection walk in circuit order: record r as r (>= 0), detector i as
   // -1 - (2 i + p) with p = 1 when detector i is postselected
   uint32_t n_post_events;

@@ -38,6 +38,8 @@ struct BlobOffsets {
   size_t clt, clo;
   size_t ctg;
   uint32_t n_ctg = 0;
+  size_t snz, odl, ors;
+  uint32_t n_snz = 0, n_odl = 0, n_ors = 0;
 };
 
 cudaError_t launch_sign(const SignArgs& a, int grid, cudaStream_t st);

@@ -46,6 +46,52 @@ __device__ __forceinline__ void scatter7(uint32_t* sw, uint4 tg, uint32_t n, uin
 // 128-lane sub-blocks of a noise block; a slot holds one uint4 per sub-block
 constexpr int kSub = kNoiseBlock / 128;
 
+// This thread's 16-byte column pieces in a noise block: sub-block t % kSub of
+// every (blockDim / kSub)-th column, so consecutive threads cover consecutive
+// pieces of one column and the padding masks are per thread.  Full pieces
+// (both words hold only real shots, W even and the array 16-byte aligned, so
+// every piece is too) are one 16-byte store; the request's last piece is
+// masked.
+struct Piece {
+  uint32_t b;          // sub-block
+  uint64_t wa;         // first 64-shot word of the piece
+  bool live, full, hb; // real shots in the piece; unmasked store; second word exists
+  uint64_t m0, m1;     // padding masks of the two words
+  __device__ __forceinline__ void put(uint64_t* d, uint4 v, bool al) const {
+    if (full && al) {
+      *reinterpret_cast<uint4*>(d) = v;
+    } else {
+      d[0] = (((uint64_t)v.y << 32) | v.x) & m0;
+      if (hb) d[1] = (((uint64_t)v.w << 32) | v.z) & m1;
+    }
+  }
+};
+
+__device__ __forceinline__ Piece piece_of(const SignArgs& A, uint64_t sub0, uint32_t nsub) {
+  Piece p;
+  p.b = threadIdx.x % kSub;
+  p.wa = 2 * (sub0 + p.b);
+  p.live = p.b < nsub;
+  p.full = 64 * (p.wa + 2) <= A.shots && (A.W & 1) == 0;
+  const uint64_t la = p.live ? A.shots - 64 * p.wa : 0;   // shots in word wa (>= 1 when live)
+  p.m0 = la < 64 ? (1ull << la) - 1 : ~0ull;
+  p.hb = p.wa + 1 < A.W;
+  const uint64_t lb = p.hb ? A.shots - 64 * (p.wa + 1) : 0;
+  p.m1 = !p.hb ? 0ull : (lb < 64 ? (1ull << lb) - 1 : ~0ull);
+  return p;
+}
+
+// column piece of detector / observable j (null when the caller skipped it)
+__device__ __forceinline__ uint64_t* out_col(const SignArgs& A, const Piece& p, uint32_t j, bool& al) {
+  const uint32_t ND = A.p.n_dets;
+  if (j < ND) {
+    al = (reinterpret_cast<uintptr_t>(A.det) & 15) == 0;
+    return A.det ? A.det + (uint64_t)j * A.W + p.wa : nullptr;
+  }
+  al = (reinterpret_cast<uintptr_t>(A.obs) & 15) == 0;
+  return A.obs ? A.obs + (uint64_t)(j - ND) * A.W + p.wa : nullptr;
+}
+
 struct SignLayout {
   size_t q_off, qs_off, qk_off, c_off, slot_off, qa_off, qb_off, cnt_off, total;
 };
@@ -95,7 +141,7 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
 
   const uint32_t n_groups = (A.p.n_channels + 3) >> 2;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  const uint32_t R = A.p.n_records, DO = A.p.n_dets + A.p.n_obs;
+  const uint32_t R = A.p.n_records;
   uint32_t* sw = reinterpret_cast<uint32_t*>(slots);
 
   for (uint64_t blk = blockIdx.x; blk < A.n_blocks; blk += gridDim.x) {
@@ -108,6 +154,9 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
     //    (still unused) queue area and every slot gathers its own sources;
     //    otherwise the words are scattered into the slots with atomics.
     if ((size_t)A.p.n_m1 * kSub * 16 <= (size_t)kSignWarps * kQueue * 16) {
+      // every slot starts at zero; the slots with a constant or random
+      // sources are then set from their items
+      for (uint32_t i = threadIdx.x; i < NT * kSub; i += blockDim.x) slots[i] = make_uint4(0u, 0u, 0u, 0u);
       uint4* mw = reinterpret_cast<uint4*>(smem_raw + Lay.qa_off);    // [n_m1][kSub]
       for (uint32_t it = threadIdx.x; it < nsub * A.p.n_m1; it += blockDim.x) {
         const uint32_t b = it / A.p.n_m1, j = it - b * A.p.n_m1;
@@ -115,8 +164,9 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
         mw[j * kSub + b] = philox(make_uint4(__ldg(A.p.m1_t + j), (uint32_t)gs, (uint32_t)(gs >> 32), kTagMbit), A.keys);
       }
       __syncthreads();
-      for (uint32_t i = threadIdx.x; i < NT * kSub; i += blockDim.x) {
-        const uint32_t b = i % kSub;
+      for (uint32_t x = threadIdx.x; x < A.p.n_slot_nz * kSub; x += blockDim.x) {
+        const uint32_t b = x % kSub;
+        const uint32_t i = __ldg(A.p.slot_nz + x / kSub) * kSub + b;
         const uint4 e = __ldg(A.p.slot_m1 + i / kSub);
         const uint32_t c = (e.x & 0x8000u) ? ~0u : 0u;
         uint4 v = make_uint4(c, c, c, c);
@@ -308,91 +358,80 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
       }
     }
     __syncthreads();
-    // 4. records: XOR in the parent records level by level (exo_r = delta_r ^ parents)
+    const uint32_t step = blockDim.x / kSub;
+    const uint32_t i0 = threadIdx.x / kSub;
+    // 4. detectors and observables that equal one slot before the chains
+    {
+      const Piece pc = piece_of(A, sub0, nsub);
+      if (pc.live && (A.det || A.obs)) {
+        for (uint32_t x = i0; x < A.p.n_out_delta; x += step) {
+          const uint2 e = __ldg(A.p.out_delta + x);
+          bool al;
+          uint64_t* d = out_col(A, pc, e.x, al);
+          if (d) pc.put(d, slots[(size_t)e.y * kSub + pc.b], al);
+        }
+      }
+    }
+    if (A.p.n_levels) __syncthreads();
+    // 5. records: XOR in the parent records level by level (exo_r = delta_r ^ parents)
     for (uint32_t L = 0; L < A.p.n_levels; ++L) {
       const uint32_t hi = A.lvl[L + 1] * kSub;
       for (uint32_t x = A.lvl[L] * kSub + threadIdx.x; x < hi; x += blockDim.x) {
         const uint4 it = __ldg(A.p.lvl_item + x / kSub);
-        const uint32_t b = x % kSub, np = it.x >> 16;
+        const uint32_t bb = x % kSub, np = it.x >> 16;
         const uint32_t pr[4] = {it.y & 0xFFFFu, it.y >> 16, it.z & 0xFFFFu, it.z >> 16};
-        uint4 acc = slots[(it.x & 0xFFFFu) * kSub + b];
+        uint4 acc = slots[(it.x & 0xFFFFu) * kSub + bb];
 #pragma unroll
         for (uint32_t k = 0; k < 4; ++k) {
           if (k >= np) break;
-          acc = xor4(acc, slots[pr[k] * kSub + b]);
+          acc = xor4(acc, slots[pr[k] * kSub + bb]);
         }
-        slots[(it.x & 0xFFFFu) * kSub + b] = acc;
+        slots[(it.x & 0xFFFFu) * kSub + bb] = acc;
       }
       __syncthreads();
     }
-    // 5. write the columns (records, gathered detectors / observables, dense
-    //    signs): 16-byte pieces, thread t writing sub-block t % kSub of every
-    //    (blockDim / kSub)-th column, so consecutive threads cover consecutive
-    //    pieces of one column and the padding masks are per thread
-    {
-      const uint32_t b = threadIdx.x % kSub;
-      const uint32_t step = blockDim.x / kSub;
-      const uint32_t i0 = threadIdx.x / kSub;
-      const uint64_t wa = 2 * (sub0 + b);                 // first 64-shot word of the piece
-      if (b < nsub) {
-        // full pieces (both words hold only real shots, W even and the array
-        // 16-byte aligned, so every piece is too) are one 16-byte store; the
-        // request's last piece is masked
-        const bool full = 64 * (wa + 2) <= A.shots && (A.W & 1) == 0;
-        const uint64_t la = A.shots - 64 * wa;            // shots in word wa (>= 1)
-        const uint64_t m0 = la < 64 ? (1ull << la) - 1 : ~0ull;
-        const bool hb = wa + 1 < A.W;                     // the piece has a second word
-        const uint64_t lb = hb ? A.shots - 64 * (wa + 1) : 0;
-        const uint64_t m1 = !hb ? 0ull : (lb < 64 ? (1ull << lb) - 1 : ~0ull);
-        auto put = [&](uint64_t* d, uint4 v, bool al) {
-          if (full && al) {
-            *reinterpret_cast<uint4*>(d) = v;
-          } else {
-            d[0] = (((uint64_t)v.y << 32) | v.x) & m0;
-            if (hb) d[1] = (((uint64_t)v.w << 32) | v.z) & m1;
-          }
-        };
-        const uint64_t cstep = (uint64_t)step * A.W;
-        if (A.meas) {
-          uint64_t* d = A.meas + (uint64_t)i0 * A.W + wa;
-          const uint4* sl = slots + (size_t)i0 * kSub + b;
-          const bool al = ((reinterpret_cast<uintptr_t>(A.meas) & 15) == 0);
-          for (uint32_t i = i0; i < R; i += step, d += cstep, sl += (size_t)step * kSub) put(d, *sl, al);
-        }
-        // detectors, then observables: XOR of the gathered records' slots
-        auto gather = [&](uint32_t j) {
-          uint4 v = make_uint4(0u, 0u, 0u, 0u);
-          const uint4 gi = __ldg(A.p.gat_item + j);
-          const uint32_t n = gi.x & 0xFFFFu;
-          if (n == 0xFFFFu) {
-            for (uint32_t q = gi.y; q < gi.y + gi.z; ++q) v = xor4(v, slots[__ldg(A.p.gat_ovf + q) * kSub + b]);
-          } else {
-            const uint32_t f[7] = {gi.x >> 16, gi.y & 0xFFFFu, gi.y >> 16, gi.z & 0xFFFFu, gi.z >> 16,
-                                   gi.w & 0xFFFFu, gi.w >> 16};
+    // 6. write the records, the gathered detectors / observables (XOR of
+    //    records) and the dense signs
+    const Piece pc = piece_of(A, sub0, nsub);
+    const uint32_t b = pc.b;
+    const uint64_t wa = pc.wa;
+    if (pc.live) {
+      const uint64_t cstep = (uint64_t)step * A.W;
+      if (A.meas) {
+        uint64_t* d = A.meas + (uint64_t)i0 * A.W + wa;
+        const uint4* sl = slots + (size_t)i0 * kSub + b;
+        const bool al = ((reinterpret_cast<uintptr_t>(A.meas) & 15) == 0);
+        for (uint32_t i = i0; i < R; i += step, d += cstep, sl += (size_t)step * kSub) pc.put(d, *sl, al);
+      }
+      auto gather = [&](uint32_t j) {
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        const uint4 gi = __ldg(A.p.gat_item + j);
+        const uint32_t n = gi.x & 0xFFFFu;
+        if (n == 0xFFFFu) {
+          for (uint32_t q = gi.y; q < gi.y + gi.z; ++q) v = xor4(v, slots[__ldg(A.p.gat_ovf + q) * kSub + b]);
+        } else {
+          const uint32_t f[7] = {gi.x >> 16, gi.y & 0xFFFFu, gi.y >> 16, gi.z & 0xFFFFu, gi.z >> 16,
+                                 gi.w & 0xFFFFu, gi.w >> 16};
 #pragma unroll
-            for (uint32_t k = 0; k < 7; ++k) {
-              if (k >= n) break;
-              v = xor4(v, slots[f[k] * kSub + b]);
-            }
+          for (uint32_t k = 0; k < 7; ++k) {
+            if (k >= n) break;
+            v = xor4(v, slots[f[k] * kSub + b]);
           }
-          return v;
-        };
-        const uint32_t ND = A.p.n_dets;
-        if (A.det) {
-          uint64_t* d = A.det + (uint64_t)i0 * A.W + wa;
-          const bool al = ((reinterpret_cast<uintptr_t>(A.det) & 15) == 0);
-          for (uint32_t j = i0; j < ND; j += step, d += cstep) put(d, gather(j), al);
         }
-        if (A.obs) {
-          uint64_t* d = A.obs + (uint64_t)i0 * A.W + wa;
-          const bool al = ((reinterpret_cast<uintptr_t>(A.obs) & 15) == 0);
-          for (uint32_t j = i0; j < DO - ND; j += step, d += cstep) put(d, gather(ND + j), al);
+        return v;
+      };
+      if (A.det || A.obs) {
+        for (uint32_t x = i0; x < A.p.n_out_rest; x += step) {
+          const uint32_t j = __ldg(A.p.out_rest + x);
+          bool al;
+          uint64_t* d = out_col(A, pc, j, al);
+          if (d) pc.put(d, gather(j), al);
         }
-        if (A.signs) {
-          uint64_t* d = A.signs + (uint64_t)i0 * A.W + wa;
-          const bool al = ((reinterpret_cast<uintptr_t>(A.signs) & 15) == 0);
-          for (uint32_t g = i0; g < NT - R; g += step, d += cstep) put(d, slots[(size_t)(R + g) * kSub + b], al);
-        }
+      }
+      if (A.signs) {
+        uint64_t* d = A.signs + (uint64_t)i0 * A.W + wa;
+        const bool al = ((reinterpret_cast<uintptr_t>(A.signs) & 15) == 0);
+        for (uint32_t g = i0; g < NT - R; g += step, d += cstep) pc.put(d, slots[(size_t)(R + g) * kSub + b], al);
       }
     }
     __syncthreads();
