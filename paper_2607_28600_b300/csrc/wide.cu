@@ -42,6 +42,37 @@ __device__ __forceinline__ uint32_t wide_insert_bit(uint32_t z, int h, uint32_t 
   return low | (d << h) | ((z >> h) << (h + 1));
 }
 
+// Element updates shared by every rotation pass (lone, fused in shared
+// memory, fused in registers), so all give the same bits.  Pair rotation: v' = c v + s z w, w the partner
+// element, s = -1 when `neg`, z = sg s i^mu is real (mu odd) or imaginary
+// (mu even), so z w takes two products: zr = the non-zero part of z.
+template <typename Real>
+__device__ __forceinline__ Amp<Real> pair_update(Amp<Real> v, Amp<Real> w, Real c, Real zr, bool odd, bool neg) {
+  const Real k = neg ? -zr : zr;
+  const Real pr = odd ? w.re : -w.im;
+  const Real pi = odd ? w.im : w.re;
+  Amp<Real> o;
+  o.re = fma(c, v.re, k * pr);
+  o.im = fma(c, v.im, k * pi);
+  return o;
+}
+
+// the non-zero part of z = sg s i^mu (mu odd: real, even: imaginary)
+template <typename Real>
+__device__ __forceinline__ Real pair_z(int mu, Real sgs) {
+  // i^mu times -i: mu = 0 -> -i, 1 -> 1, 2 -> i, 3 -> -1
+  return (mu & 3) == 0 || (mu & 3) == 3 ? -sgs : sgs;
+}
+
+// Diagonal rotation: a' = (c - i f) a with f = +-mu s
+template <typename Real>
+__device__ __forceinline__ Amp<Real> diag_update(Amp<Real> a, Real c, Real f) {
+  Amp<Real> r;
+  r.re = fma(f, a.im, c * a.re);
+  r.im = fma(-f, a.re, c * a.im);
+  return r;
+}
+
 __device__ __forceinline__ uint64_t wide_meas_U(const PhiloxKeys& K, uint32_t t, uint64_t r) {
   const uint64_t w = r >> 6;
   const uint4 ob = philox(make_uint4(t, (uint32_t)(w >> 1), (uint32_t)(w >> 33), kTagMbit), K);
@@ -122,39 +153,21 @@ __global__ void __launch_bounds__(kWideThreads) wide_rot_kernel(WideArgs A, uint
       if (!A.alive[b]) continue;
       Amp<Real>* v = vbase + (size_t)b * A.stride;
       const Real f = (lamg[b] ? -mus : mus) * ((__popc(x & I.b) & 1) ? (Real)-1 : (Real)1);
-      const Amp<Real> a = v[x];
-      Amp<Real> o;
-      o.re = c * a.re + f * a.im;
-      o.im = c * a.im - f * a.re;
-      v[x] = o;
+      v[x] = diag_update(v[x], c, f);
     }
   } else {                              // pairs (x0, x0 ^ a), coefficient -i mu sg s (-1)^{b.x}
     const int pb = 31 - __clz(I.a);
-    Real cr0, ci0;
-    switch (I.mu & 3) {
-      case 0: cr0 = 0; ci0 = -1; break;
-      case 1: cr0 = 1; ci0 = 0; break;
-      case 2: cr0 = 0; ci0 = 1; break;
-      default: cr0 = -1; ci0 = 0; break;
-    }
+    const bool odd = (I.mu & 1) != 0;
     const uint32_t half_mask = (n >> 1) - 1;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += step) {
       const uint32_t b = (uint32_t)(i >> lg), z = (uint32_t)i & half_mask;
       if (!A.alive[b]) continue;
       Amp<Real>* v = vbase + (size_t)b * A.stride;
-      const Real sgs = lamg[b] ? -s : s;
-      const Real cr = cr0 * sgs, ci = ci0 * sgs;
+      const Real zr = pair_z<Real>(I.mu, lamg[b] ? -s : s);
       const uint32_t x0 = wide_insert_bit(z, pb, 0u), x1 = x0 ^ I.a;
       const Amp<Real> v0 = v[x0], v1 = v[x1];
-      const Real s1 = (__popc(x1 & I.b) & 1) ? (Real)-1 : (Real)1;
-      const Real s0 = (__popc(x0 & I.b) & 1) ? (Real)-1 : (Real)1;
-      Amp<Real> o0, o1;
-      o0.re = c * v0.re + s1 * (cr * v1.re - ci * v1.im);
-      o0.im = c * v0.im + s1 * (cr * v1.im + ci * v1.re);
-      o1.re = c * v1.re + s0 * (cr * v0.re - ci * v0.im);
-      o1.im = c * v1.im + s0 * (cr * v0.im + ci * v0.re);
-      v[x0] = o0;
-      v[x1] = o1;
+      v[x0] = pair_update(v0, v1, c, zr, odd, (__popc(x1 & I.b) & 1) != 0);
+      v[x1] = pair_update(v1, v0, c, zr, odd, (__popc(x0 & I.b) & 1) != 0);
     }
   }
 }
@@ -406,6 +419,15 @@ struct FuseInstr {
   uint8_t p_loc;       // tile bit of the new coordinate (PromoteRot) or of a's pivot (pair)
   uint16_t e_loc;      // tile bits of coordinates not yet promoted: elements with
                        // any of them set do not exist yet (zero) and are skipped
+  uint8_t ra, rb;      // register phases: a (PromoteRot: the new bit) and b
+                       // gathered onto the phase's register bits
+};
+
+// A phase of a window: rotations q0 .. q0 + n - 1 applied in registers on the
+// register bits R (a mask of kRegBits tile bits >= 5), or (R == 0) one
+// rotation applied on the tile in shared memory.
+struct FusePhase {
+  uint16_t q0, n, R, pad;
 };
 
 struct WideFuse {
@@ -414,8 +436,17 @@ struct WideFuse {
   uint32_t outer;          // outer bits: [0, k_start) without the inner bits
   uint32_t T, kstart, kend;
   uint32_t hi_shift;       // 5: inner bits 0..4 are the tile's low bits
+  uint32_t n_ph;           // phases
   FuseInstr ins[kFuseMax];
+  FusePhase ph[kFuseMax];
 };
+
+// register bits of a phase: 2^kRegBits amplitudes per thread (16 FP32 / 8 FP64)
+template <typename Real>
+struct RegBits {
+  static constexpr int M = sizeof(Real) == 4 ? 4 : 3;
+};
+constexpr uint32_t reg_bits(bool fp64) { return fp64 ? 3u : 4u; }
 
 // x with the bits of v placed at the set positions of mask, lowest first
 __host__ __device__ __forceinline__ uint32_t deposit_bits(uint32_t v, uint32_t mask) {
@@ -427,70 +458,250 @@ __host__ __device__ __forceinline__ uint32_t deposit_bits(uint32_t v, uint32_t m
   return x;
 }
 
-// One fused window on a tile held in shared memory: the tile of shot b whose
-// outer bits are `off` (element i of the tile is amplitude off + the inner
-// bits of i); rotations that touch coordinates not yet promoted skip those
-// (zero) elements.  Ends with the CTA synchronised.
+// One rotation of a fused window on the whole tile in shared memory: the
+// tile of shot b whose outer bits are `off` (element i of the tile is
+// amplitude off + the inner bits of i); elements of coordinates not yet
+// promoted are skipped (they are zero).
+template <typename Real>
+__device__ __forceinline__ void apply_rot_smem(const WideArgs& A, const WideFuse& F, Amp<Real>* tile, uint32_t b,
+                                               uint32_t off, uint32_t tid, uint32_t q) {
+  const uint32_t n = 1u << F.T;
+  const FuseInstr& L = F.ins[q];
+  const uint32_t g = F.g0 + q;
+  const DenseInstrDev& I = A.p.dense[g];
+  const Real c = coef_c<Real>(I), s = coef_s<Real>(I);
+  const Real sgs = A.lam[(size_t)g * A.nb + b] ? -s : s;
+  const uint32_t po = __popc(L.b_out & off) & 1u;
+  if (L.kind == 0) {                              // a'_x = c a_x, a'_{x+new} = -i sg s a_x
+    const uint32_t pb = 1u << L.p_loc;
+    for (uint32_t z = tid; z < (n >> 1); z += blockDim.x) {
+      const uint32_t i0 = wide_insert_bit(z, L.p_loc, 0u);
+      if (i0 & L.e_loc) continue;
+      Amp<Real> a = tile[i0], hi;
+      hi.re = sgs * a.im;
+      hi.im = -sgs * a.re;
+      a.re *= c;
+      a.im *= c;
+      tile[i0] = a;
+      tile[i0 | pb] = hi;
+    }
+  } else if (L.kind == 1) {                       // a_x *= c - i sg mu (-1)^{b.x} s
+    const Real mus = I.mu == 0 ? sgs : -sgs;
+    for (uint32_t i = tid; i < n; i += blockDim.x) {
+      if (i & L.e_loc) continue;
+      const Real f = ((__popc(i & L.b_loc) ^ po) & 1u) ? -mus : mus;
+      tile[i] = diag_update(tile[i], c, f);
+    }
+  } else {                                        // pairs (x0, x0 ^ a)
+    const Real zr = pair_z<Real>(I.mu, sgs);
+    const bool odd = (I.mu & 1) != 0;
+    for (uint32_t z = tid; z < (n >> 1); z += blockDim.x) {
+      const uint32_t i0 = wide_insert_bit(z, L.p_loc, 0u), i1 = i0 ^ L.a_loc;
+      if (i0 & L.e_loc) continue;
+      const Amp<Real> v0 = tile[i0], v1 = tile[i1];
+      const bool n1 = ((__popc(i1 & L.b_loc) ^ po) & 1u) != 0u;
+      const bool n0 = ((__popc(i0 & L.b_loc) ^ po) & 1u) != 0u;
+      tile[i0] = pair_update(v0, v1, c, zr, odd, n1);
+      tile[i1] = pair_update(v1, v0, c, zr, odd, n0);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Register phases.  A warp holds 2^(5+M) amplitudes of the tile: lane l and
+// register j hold element base | l | dep(j), where the lanes run over tile bits
+// 0..4 (so every shared-memory access of the warp is 32 consecutive elements),
+// dep(j) places the M bits of j on the phase's register bits R, and base sets
+// the remaining (warp) bits.  A rotation whose pair bits above bit 4 lie in R
+// pairs element x with x ^ a: register j ^ aR of lane l ^ aL, reached by a
+// register copy and, for aL != 0, a shuffle.  Every element takes its new
+// value from itself and its partner with the same formulas as the
+// shared-memory form, so a phase of several rotations costs one load and one
+// store of the tile.
+// ---------------------------------------------------------------------------
+// bit j: parity of j & bR, for the 2^M register indices j
+template <int M>
+__device__ __forceinline__ uint32_t reg_parity_table(uint32_t bR) {
+  constexpr uint32_t pat[4] = {0xAAAAu, 0xCCCCu, 0xF0F0u, 0xFF00u};
+  uint32_t t = 0;
+#pragma unroll
+  for (int k = 0; k < M; ++k)
+    if ((bR >> k) & 1u) t ^= pat[k];
+  return t & ((1u << (1 << M)) - 1u);
+}
+
+template <typename Real>
+__device__ __forceinline__ Amp<Real> shfl_amp(Amp<Real> v, uint32_t lanemask) {
+  Amp<Real> w;
+  w.re = __shfl_xor_sync(0xffffffffu, v.re, lanemask);
+  w.im = __shfl_xor_sync(0xffffffffu, v.im, lanemask);
+  return w;
+}
+
+// pair rotation with register part AR of a and lane part aL; bit j of sg set:
+// the partner of element j has a negative sign
+template <int AR, int M, typename Real>
+__device__ __forceinline__ void reg_pair(Amp<Real>* v, uint32_t aL, Real c, Real zr, bool odd, uint32_t sg) {
+  constexpr int NJ = 1 << M;
+  if constexpr (AR == 0) {
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      const Amp<Real> w = shfl_amp(v[j], aL);
+      v[j] = pair_update(v[j], w, c, zr, odd, (sg >> j) & 1u);
+    }
+  } else {
+    constexpr int P = 31 - __builtin_clz((unsigned)AR);
+#pragma unroll
+    for (int j0 = 0; j0 < NJ; ++j0) {
+      if ((j0 >> P) & 1) continue;
+      const int j1 = j0 ^ AR;
+      Amp<Real> w0 = v[j1], w1 = v[j0];
+      if (aL) {
+        w0 = shfl_amp(w0, aL);
+        w1 = shfl_amp(w1, aL);
+      }
+      const Amp<Real> o0 = pair_update(v[j0], w0, c, zr, odd, (sg >> j0) & 1u);
+      const Amp<Real> o1 = pair_update(v[j1], w1, c, zr, odd, (sg >> j1) & 1u);
+      v[j0] = o0;
+      v[j1] = o1;
+    }
+  }
+}
+
+// PromoteRot with the new coordinate on register bit PR
+template <int PR, int M, typename Real>
+__device__ __forceinline__ void reg_promote(Amp<Real>* v, Real c, Real sgs) {
+  constexpr int NJ = 1 << M;
+#pragma unroll
+  for (int j0 = 0; j0 < NJ; ++j0) {
+    if ((j0 >> PR) & 1) continue;
+    Amp<Real> a = v[j0], hi;
+    hi.re = sgs * a.im;
+    hi.im = -sgs * a.re;
+    a.re *= c;
+    a.im *= c;
+    v[j0] = a;
+    v[j0 | (1 << PR)] = hi;
+  }
+}
+
+template <int M, typename Real>
+__device__ __forceinline__ void reg_pair_dispatch(uint32_t ar, Amp<Real>* v, uint32_t aL, Real c, Real zr, bool odd,
+                                                  uint32_t sg) {
+  switch (ar) {
+#define SYMFT_PAIR_CASE(k) \
+  case k: if constexpr (k < (1 << M)) reg_pair<k, M, Real>(v, aL, c, zr, odd, sg); break;
+    SYMFT_PAIR_CASE(0) SYMFT_PAIR_CASE(1) SYMFT_PAIR_CASE(2) SYMFT_PAIR_CASE(3)
+    SYMFT_PAIR_CASE(4) SYMFT_PAIR_CASE(5) SYMFT_PAIR_CASE(6) SYMFT_PAIR_CASE(7)
+    SYMFT_PAIR_CASE(8) SYMFT_PAIR_CASE(9) SYMFT_PAIR_CASE(10) SYMFT_PAIR_CASE(11)
+    SYMFT_PAIR_CASE(12) SYMFT_PAIR_CASE(13) SYMFT_PAIR_CASE(14) SYMFT_PAIR_CASE(15)
+#undef SYMFT_PAIR_CASE
+    default: break;
+  }
+}
+
+// One register phase of a window on the tile of shot b with outer bits `off`.
+template <typename Real>
+__device__ __forceinline__ void apply_phase_reg(const WideArgs& A, const WideFuse& F, Amp<Real>* tile, uint32_t b,
+                                                uint32_t off, const FusePhase P) {
+  constexpr int M = RegBits<Real>::M;
+  constexpr int NJ = 1 << M;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const uint32_t Wb = ((1u << F.T) - 1u) & ~31u & ~(uint32_t)P.R;
+  uint32_t rb[M];
+  {
+    uint32_t m = P.R;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      rb[k] = m & (~m + 1u);
+      m &= m - 1u;
+    }
+  }
+  auto dep = [&](int j) {
+    uint32_t x = 0;
+#pragma unroll
+    for (int k = 0; k < M; ++k)
+      if ((j >> k) & 1) x |= rb[k];
+    return x;
+  };
+  // elements with a warp bit of a coordinate not yet promoted are zero for
+  // the whole phase (the phase promotes only register or lane bits)
+  const uint32_t e_w = F.ins[P.q0].e_loc & Wb;
+  const uint32_t nsub = 1u << (F.T - 5 - M);
+  for (uint32_t sub = warp; sub < nsub; sub += nwarps) {
+    const uint32_t base = deposit_bits(sub, Wb);
+    if (base & e_w) continue;                       // uniform over the warp
+    const uint32_t x0 = base | lane;
+    Amp<Real> v[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) v[j] = tile[x0 | dep(j)];
+    for (uint32_t q = P.q0; q < (uint32_t)P.q0 + P.n; ++q) {
+      const FuseInstr& L = F.ins[q];
+      const uint32_t g = F.g0 + q;
+      const DenseInstrDev& I = A.p.dense[g];
+      const Real c = coef_c<Real>(I), s = coef_s<Real>(I);
+      const Real sgs = A.lam[(size_t)g * A.nb + b] ? -s : s;
+      // parity of b over the outer and warp bits of the element
+      const uint32_t pw = (__popc(L.b_out & off) ^ __popc(base & L.b_loc)) & 1u;
+      const uint32_t bL = L.b_loc & 31u;
+      const uint32_t tb = reg_parity_table<M>(L.rb);
+      if (L.kind == 0) {
+        if (L.p_loc >= 5) {
+          switch (L.ra) {
+            case 1: reg_promote<0, M, Real>(v, c, sgs); break;
+            case 2: reg_promote<1, M, Real>(v, c, sgs); break;
+            case 4: reg_promote<2, M, Real>(v, c, sgs); break;
+            default: if constexpr (M > 3) reg_promote<3, M, Real>(v, c, sgs); break;
+          }
+        } else {
+          const uint32_t pb = 1u << L.p_loc;
+          const bool upper = (lane & pb) != 0u;
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) {
+            const Amp<Real> w = shfl_amp(v[j], pb);
+            Amp<Real> o;
+            if (upper) {
+              o.re = sgs * w.im;
+              o.im = -sgs * w.re;
+            } else {
+              o.re = v[j].re * c;
+              o.im = v[j].im * c;
+            }
+            v[j] = o;
+          }
+        }
+      } else if (L.kind == 1) {
+        const Real mus = I.mu == 0 ? sgs : -sgs;
+        const uint32_t pt = (pw ^ __popc(lane & bL)) & 1u;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          const Real f = (((tb >> j) ^ pt) & 1u) ? -mus : mus;
+          v[j] = diag_update(v[j], c, f);
+        }
+      } else {
+        const Real zr = pair_z<Real>(I.mu, sgs);
+        const bool odd = (I.mu & 1) != 0;
+        const uint32_t aL = L.a_loc & 31u;
+        // sign of the partner x ^ a of element j: parity of (x ^ a) & b
+        const uint32_t pt = (pw ^ __popc((lane ^ aL) & bL) ^ __popc((uint32_t)L.ra & L.rb)) & 1u;
+        const uint32_t sg = tb ^ (pt ? (1u << NJ) - 1u : 0u);
+        reg_pair_dispatch<M, Real>(L.ra, v, aL, c, zr, odd, sg);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) tile[x0 | dep(j)] = v[j];
+  }
+}
+
+// One fused window on a tile held in shared memory, phase by phase.  Ends with
+// the CTA synchronised.
 template <typename Real>
 __device__ __forceinline__ void apply_window(const WideArgs& A, const WideFuse& F, Amp<Real>* tile, uint32_t b,
                                              uint32_t off, uint32_t tid) {
-  const uint32_t n = 1u << F.T;
-  for (uint32_t q = 0; q < F.n; ++q) {
-    const FuseInstr& L = F.ins[q];
-    const uint32_t g = F.g0 + q;
-    const DenseInstrDev& I = A.p.dense[g];
-    const Real c = coef_c<Real>(I), s = coef_s<Real>(I);
-    const Real sgs = A.lam[(size_t)g * A.nb + b] ? -s : s;
-    const uint32_t po = __popc(L.b_out & off) & 1u;
-    if (L.kind == 0) {                              // a'_x = c a_x, a'_{x+new} = -i sg s a_x
-      const uint32_t pb = 1u << L.p_loc;
-      for (uint32_t z = tid; z < (n >> 1); z += blockDim.x) {
-        const uint32_t i0 = wide_insert_bit(z, L.p_loc, 0u);
-        if (i0 & L.e_loc) continue;
-        Amp<Real> a = tile[i0], hi;
-        hi.re = sgs * a.im;
-        hi.im = -sgs * a.re;
-        a.re *= c;
-        a.im *= c;
-        tile[i0] = a;
-        tile[i0 | pb] = hi;
-      }
-    } else if (L.kind == 1) {                       // a_x *= c - i sg mu (-1)^{b.x} s
-      const Real mus = I.mu == 0 ? sgs : -sgs;
-      for (uint32_t i = tid; i < n; i += blockDim.x) {
-        if (i & L.e_loc) continue;
-        const Real f = ((__popc(i & L.b_loc) ^ po) & 1u) ? -mus : mus;
-        const Amp<Real> a = tile[i];
-        Amp<Real> r;
-        r.re = c * a.re + f * a.im;
-        r.im = c * a.im - f * a.re;
-        tile[i] = r;
-      }
-    } else {                                        // pairs (x0, x0 ^ a)
-      Real cr, ci;
-      switch (I.mu & 3) {
-        case 0: cr = 0; ci = -1; break;
-        case 1: cr = 1; ci = 0; break;
-        case 2: cr = 0; ci = 1; break;
-        default: cr = -1; ci = 0; break;
-      }
-      cr *= sgs;
-      ci *= sgs;
-      for (uint32_t z = tid; z < (n >> 1); z += blockDim.x) {
-        const uint32_t i0 = wide_insert_bit(z, L.p_loc, 0u), i1 = i0 ^ L.a_loc;
-        if (i0 & L.e_loc) continue;
-        const Amp<Real> v0 = tile[i0], v1 = tile[i1];
-        const Real s1 = ((__popc(i1 & L.b_loc) ^ po) & 1u) ? (Real)-1 : (Real)1;
-        const Real s0 = ((__popc(i0 & L.b_loc) ^ po) & 1u) ? (Real)-1 : (Real)1;
-        Amp<Real> o0, o1;
-        o0.re = c * v0.re + s1 * (cr * v1.re - ci * v1.im);
-        o0.im = c * v0.im + s1 * (cr * v1.im + ci * v1.re);
-        o1.re = c * v1.re + s0 * (cr * v0.re - ci * v0.im);
-        o1.im = c * v1.im + s0 * (cr * v0.im + ci * v0.re);
-        tile[i0] = o0;
-        tile[i1] = o1;
-      }
-    }
+  for (uint32_t ph = 0; ph < F.n_ph; ++ph) {
+    const FusePhase P = F.ph[ph];
+    if (P.R == 0) apply_rot_smem<Real>(A, F, tile, b, off, tid, P.q0);
+    else apply_phase_reg<Real>(A, F, tile, b, off, P);
     __syncthreads();
   }
 }
@@ -585,7 +796,7 @@ __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy
 // yet promoted (a whole chunk, since F.kstart >= 5) are zero-filled instead of
 // copied.  A bounded wait that runs out sets *A.status and ends the CTA.
 template <typename Real>
-__global__ void __launch_bounds__(kWideThreads) wide_fused_bulk_kernel(WideArgs A, WideFuse F) {
+__global__ void __launch_bounds__(kWideThreads, 3) wide_fused_bulk_kernel(WideArgs A, WideFuse F) {
   extern __shared__ __align__(128) unsigned char bsm[];
   const uint32_t n = 1u << F.T;
   const size_t tb = sizeof(Amp<Real>) << F.T;       // tile bytes
@@ -683,7 +894,8 @@ static uint32_t gather_bits(uint32_t x, uint32_t mask) {
 
 // Greedy window from instruction g0 (a rotation): consecutive rotations while
 // the inner bits fit in T.  Returns the number of instructions taken.
-static uint32_t build_window(const DenseInstrDev* d, uint32_t G, uint32_t g0, uint32_t T, WideFuse* F) {
+static uint32_t build_window(const DenseInstrDev* d, uint32_t G, uint32_t g0, uint32_t T, WideFuse* F,
+                             uint32_t M) {
   const uint32_t kstart = (uint32_t)d[g0].k;
   uint32_t inner = 0u;
   for (uint32_t j = 0; j < 5; ++j) inner |= 1u << j;
@@ -723,7 +935,52 @@ static uint32_t build_window(const DenseInstrDev* d, uint32_t G, uint32_t g0, ui
     if (I.kind == 0) L.p_loc = (uint8_t)__builtin_popcount(inner & ((1u << I.k) - 1u));
     else if (I.kind == 2) L.p_loc = (uint8_t)(31 - __builtin_clz((uint32_t)L.a_loc));
     L.e_loc = (uint16_t)gather_bits(~((1u << I.k) - 1u), inner);
+    L.ra = L.rb = 0;
   }
+  // phases: consecutive rotations whose tile bits above bit 4 (pair bits, new
+  // bit) fit in M register bits; a rotation that needs more is a phase of its
+  // own in shared memory.  Tiles too small for a warp's 2^(5+M) elements use
+  // shared memory throughout.
+  F->n_ph = 0;
+  const uint32_t tmask = (1u << F->T) - 1u;
+  auto high_need = [&](const FuseInstr& L) -> uint32_t {
+    if (L.kind == 0) return L.p_loc >= 5 ? (1u << L.p_loc) : 0u;
+    if (L.kind == 2) return L.a_loc & ~31u;
+    return 0u;
+  };
+  auto close = [&](uint32_t q0, uint32_t cnt, uint32_t R) {
+    // pad R to M bits with the lowest free tile bits above bit 4
+    for (uint32_t j = 5; j < F->T && (uint32_t)__builtin_popcount(R) < M; ++j)
+      if (!((R >> j) & 1u)) R |= 1u << j;
+    for (uint32_t q = q0; q < q0 + cnt; ++q) {
+      FuseInstr& L = F->ins[q];
+      L.ra = (uint8_t)gather_bits(L.kind == 0 ? high_need(L) : L.a_loc, R);
+      L.rb = (uint8_t)gather_bits(L.b_loc, R);
+    }
+    F->ph[F->n_ph++] = FusePhase{(uint16_t)q0, (uint16_t)cnt, (uint16_t)R, 0};
+  };
+  if (F->T < 5 + M) {
+    for (uint32_t q = 0; q < n; ++q) F->ph[F->n_ph++] = FusePhase{(uint16_t)q, 1, 0, 0};
+    return n;
+  }
+  uint32_t q0 = 0, R = 0;
+  for (uint32_t q = 0; q < n; ++q) {
+    const uint32_t need = high_need(F->ins[q]) & tmask;
+    if ((uint32_t)__builtin_popcount(R | need) <= M) {
+      R |= need;
+      continue;
+    }
+    if (q > q0) close(q0, q - q0, R);
+    if ((uint32_t)__builtin_popcount(need) > M) {
+      F->ph[F->n_ph++] = FusePhase{(uint16_t)q, 1, 0, 0};
+      q0 = q + 1;
+      R = 0;
+    } else {
+      q0 = q;
+      R = need;
+    }
+  }
+  if (n > q0) close(q0, n - q0, R);
   return n;
 }
 
@@ -760,7 +1017,7 @@ static cudaError_t wide_batch_t(WideArgs A, const DenseInstrDev* host_dense, int
     const uint64_t n = 1ull << I.k;
     if (I.kind <= 2) {
       WideFuse F;
-      const uint32_t nw = build_window(host_dense, A.p.n_dense, g, T, &F);
+      const uint32_t nw = build_window(host_dense, A.p.n_dense, g, T, &F, RegBits<Real>::M);
       if (nw >= 2 && F.kend >= 5) {
         // one pass over HBM for the whole window
         const uint64_t tiles = (uint64_t)A.nb << (F.kend - F.T);
@@ -836,7 +1093,7 @@ uint64_t wide_amp_traffic(const DenseInstrDev* d, uint32_t G, bool fp64, uint32_
     const uint64_t n = 1ull << d[g].k;
     if (d[g].kind <= 2) {
       WideFuse F;
-      const uint32_t nw = build_window(d, G, g, T, &F);
+      const uint32_t nw = build_window(d, G, g, T, &F, reg_bits(fp64));
       if (nw >= 2 && F.kend >= 5) {
         amps += (1ull << F.kstart) + (1ull << F.kend);
         g += nw - 1;
