@@ -47,14 +47,32 @@ __device__ __forceinline__ uint32_t wide_insert_bit(uint32_t z, int h, uint32_t 
 // element, s = -1 when `neg`, z = sg s i^mu is real (mu odd) or imaginary
 // (mu even), so z w takes two products: zr = the non-zero part of z.
 template <typename Real>
-__device__ __forceinline__ Amp<Real> pair_update(Amp<Real> v, Amp<Real> w, Real c, Real zr, bool odd, bool neg) {
-  const Real k = neg ? -zr : zr;
+__device__ __forceinline__ Amp<Real> pair_update_k(Amp<Real> v, Amp<Real> w, Real c, Real k, bool odd) {
   const Real pr = odd ? w.re : -w.im;
   const Real pi = odd ? w.im : w.re;
   Amp<Real> o;
   o.re = fma(c, v.re, k * pr);
   o.im = fma(c, v.im, k * pi);
   return o;
+}
+
+// the same with mu's parity known at compile time (no selects)
+template <bool ODD, typename Real>
+__device__ __forceinline__ Amp<Real> pair_update_t(Amp<Real> v, Amp<Real> w, Real c, Real k) {
+  Amp<Real> o;
+  if constexpr (ODD) {
+    o.re = fma(c, v.re, k * w.re);
+    o.im = fma(c, v.im, k * w.im);
+  } else {
+    o.re = fma(c, v.re, k * -w.im);
+    o.im = fma(c, v.im, k * w.re);
+  }
+  return o;
+}
+
+template <typename Real>
+__device__ __forceinline__ Amp<Real> pair_update(Amp<Real> v, Amp<Real> w, Real c, Real zr, bool odd, bool neg) {
+  return pair_update_k(v, w, c, neg ? -zr : zr, odd);
 }
 
 // the non-zero part of z = sg s i^mu (mu odd: real, even: imaginary)
@@ -519,17 +537,6 @@ __device__ __forceinline__ void apply_rot_smem(const WideArgs& A, const WideFuse
 // shared-memory form, so a phase of several rotations costs one load and one
 // store of the tile.
 // ---------------------------------------------------------------------------
-// bit j: parity of j & bR, for the 2^M register indices j
-template <int M>
-__device__ __forceinline__ uint32_t reg_parity_table(uint32_t bR) {
-  constexpr uint32_t pat[4] = {0xAAAAu, 0xCCCCu, 0xF0F0u, 0xFF00u};
-  uint32_t t = 0;
-#pragma unroll
-  for (int k = 0; k < M; ++k)
-    if ((bR >> k) & 1u) t ^= pat[k];
-  return t & ((1u << (1 << M)) - 1u);
-}
-
 template <typename Real>
 __device__ __forceinline__ Amp<Real> shfl_amp(Amp<Real> v, uint32_t lanemask) {
   Amp<Real> w;
@@ -538,39 +545,75 @@ __device__ __forceinline__ Amp<Real> shfl_amp(Amp<Real> v, uint32_t lanemask) {
   return w;
 }
 
-// pair rotation with register part AR of a and lane part aL; bit j of sg set:
-// the partner of element j has a negative sign
-template <int AR, int M, typename Real>
-__device__ __forceinline__ void reg_pair(Amp<Real>* v, uint32_t aL, Real c, Real zr, bool odd, uint32_t sg) {
+// compile-time bit helpers of the register loops
+__host__ __device__ constexpr int ctz_c(int x) { return x & 1 ? 0 : 1 + ctz_c(x >> 1); }
+__host__ __device__ constexpr int msb_c(int x) { return x > 1 ? 1 + msb_c(x >> 1) : 0; }
+__host__ __device__ constexpr int nth_bit_c(int mask, int n) { return n == 0 ? ctz_c(mask) : nth_bit_c(mask & (mask - 1), n - 1); }
+__host__ __device__ constexpr int deposit_c(int v, int mask) {
+  return mask == 0 ? 0 : ((v & 1) ? (mask & -mask) : 0) | deposit_c(v >> 1, mask & (mask - 1));
+}
+
+// k times the sign of chi (+-1): a multiplication in FP32; in FP64 (a slow
+// pipe on B300) an XOR of the sign bit
+__device__ __forceinline__ float mul_sign(float k, float chi) { return k * chi; }
+__device__ __forceinline__ double mul_sign(double k, double chi) {
+  return __longlong_as_double(__double_as_longlong(k) ^ (__double_as_longlong(chi) & (long long)0x8000000000000000ull));
+}
+
+// Pair rotation with register part AR of a and lane part aL.  The partner
+// signs follow a character of the register bits: chi[k] = -1 when bit k of
+// b's register part is set, so walking the register indices in Gray-code
+// order gives every element's coefficient k = +-zr with one (exact)
+// multiplication by +-1; k starts as element 0's, and chiAR relates element
+// j1 = j0 ^ AR to j0.  Step T of the walk is a template argument, so every
+// register index is a compile-time constant.
+template <int AR, int M, int T, bool ODD, typename Real>
+__device__ __forceinline__ void reg_pair_step(Amp<Real> (&v)[1 << M], uint32_t aL, Real c, Real k,
+                                              const Real (&chi)[M], Real chiAR) {
   constexpr int NJ = 1 << M;
   if constexpr (AR == 0) {
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) {
+    if constexpr (T < NJ) {
+      if constexpr (T > 0) k = mul_sign(k, chi[ctz_c(T)]);
+      constexpr int j = T ^ (T >> 1);
       const Amp<Real> w = shfl_amp(v[j], aL);
-      v[j] = pair_update(v[j], w, c, zr, odd, (sg >> j) & 1u);
+      v[j] = pair_update_t<ODD>(v[j], w, c, k);
+      reg_pair_step<AR, M, T + 1, ODD, Real>(v, aL, c, k, chi, chiAR);
     }
   } else {
-    constexpr int P = 31 - __builtin_clz((unsigned)AR);
-#pragma unroll
-    for (int j0 = 0; j0 < NJ; ++j0) {
-      if ((j0 >> P) & 1) continue;
-      const int j1 = j0 ^ AR;
+    if constexpr (T < NJ / 2) {
+      constexpr int FM = (NJ - 1) & ~(1 << msb_c(AR));   // register bits other than a's pivot
+      if constexpr (T > 0) k = mul_sign(k, chi[nth_bit_c(FM, ctz_c(T))]);
+      constexpr int j0 = deposit_c(T ^ (T >> 1), FM);
+      constexpr int j1 = j0 ^ AR;
       Amp<Real> w0 = v[j1], w1 = v[j0];
       if (aL) {
         w0 = shfl_amp(w0, aL);
         w1 = shfl_amp(w1, aL);
       }
-      const Amp<Real> o0 = pair_update(v[j0], w0, c, zr, odd, (sg >> j0) & 1u);
-      const Amp<Real> o1 = pair_update(v[j1], w1, c, zr, odd, (sg >> j1) & 1u);
+      const Amp<Real> o0 = pair_update_t<ODD>(v[j0], w0, c, k);
+      const Amp<Real> o1 = pair_update_t<ODD>(v[j1], w1, c, mul_sign(k, chiAR));
       v[j0] = o0;
       v[j1] = o1;
+      reg_pair_step<AR, M, T + 1, ODD, Real>(v, aL, c, k, chi, chiAR);
     }
+  }
+}
+
+// Diagonal rotation in registers: coefficient f of element 0, the others by
+// the same Gray-code walk
+template <int M, int T, typename Real>
+__device__ __forceinline__ void reg_diag_step(Amp<Real> (&v)[1 << M], Real c, Real f, const Real (&chi)[M]) {
+  if constexpr (T < (1 << M)) {
+    if constexpr (T > 0) f = mul_sign(f, chi[ctz_c(T)]);
+    constexpr int j = T ^ (T >> 1);
+    v[j] = diag_update(v[j], c, f);
+    reg_diag_step<M, T + 1, Real>(v, c, f, chi);
   }
 }
 
 // PromoteRot with the new coordinate on register bit PR
 template <int PR, int M, typename Real>
-__device__ __forceinline__ void reg_promote(Amp<Real>* v, Real c, Real sgs) {
+__device__ __forceinline__ void reg_promote(Amp<Real> (&v)[1 << M], Real c, Real sgs) {
   constexpr int NJ = 1 << M;
 #pragma unroll
   for (int j0 = 0; j0 < NJ; ++j0) {
@@ -586,11 +629,17 @@ __device__ __forceinline__ void reg_promote(Amp<Real>* v, Real c, Real sgs) {
 }
 
 template <int M, typename Real>
-__device__ __forceinline__ void reg_pair_dispatch(uint32_t ar, Amp<Real>* v, uint32_t aL, Real c, Real zr, bool odd,
-                                                  uint32_t sg) {
-  switch (ar) {
-#define SYMFT_PAIR_CASE(k) \
-  case k: if constexpr (k < (1 << M)) reg_pair<k, M, Real>(v, aL, c, zr, odd, sg); break;
+__device__ __forceinline__ void reg_pair_dispatch(uint32_t ar, Amp<Real> (&v)[1 << M], uint32_t aL, Real c, Real k0,
+                                                  const Real (&chi)[M], Real chiAR, bool odd) {
+  // (ar, mu odd) -> one instantiation each
+  switch (ar | (odd ? 16u : 0u)) {
+#define SYMFT_PAIR_CASE(k)                                                                         \
+  case k:                                                                                          \
+    if constexpr (k < (1 << M)) reg_pair_step<k, M, 0, false, Real>(v, aL, c, k0, chi, chiAR);     \
+    break;                                                                                         \
+  case k + 16:                                                                                     \
+    if constexpr (k < (1 << M)) reg_pair_step<k, M, 0, true, Real>(v, aL, c, k0, chi, chiAR);      \
+    break;
     SYMFT_PAIR_CASE(0) SYMFT_PAIR_CASE(1) SYMFT_PAIR_CASE(2) SYMFT_PAIR_CASE(3)
     SYMFT_PAIR_CASE(4) SYMFT_PAIR_CASE(5) SYMFT_PAIR_CASE(6) SYMFT_PAIR_CASE(7)
     SYMFT_PAIR_CASE(8) SYMFT_PAIR_CASE(9) SYMFT_PAIR_CASE(10) SYMFT_PAIR_CASE(11)
@@ -644,7 +693,9 @@ __device__ __forceinline__ void apply_phase_reg(const WideArgs& A, const WideFus
       // parity of b over the outer and warp bits of the element
       const uint32_t pw = (__popc(L.b_out & off) ^ __popc(base & L.b_loc)) & 1u;
       const uint32_t bL = L.b_loc & 31u;
-      const uint32_t tb = reg_parity_table<M>(L.rb);
+      Real chi[M];
+#pragma unroll
+      for (int k = 0; k < M; ++k) chi[k] = ((L.rb >> k) & 1u) ? (Real)-1 : (Real)1;
       if (L.kind == 0) {
         if (L.p_loc >= 5) {
           switch (L.ra) {
@@ -673,19 +724,15 @@ __device__ __forceinline__ void apply_phase_reg(const WideArgs& A, const WideFus
       } else if (L.kind == 1) {
         const Real mus = I.mu == 0 ? sgs : -sgs;
         const uint32_t pt = (pw ^ __popc(lane & bL)) & 1u;
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-          const Real f = (((tb >> j) ^ pt) & 1u) ? -mus : mus;
-          v[j] = diag_update(v[j], c, f);
-        }
+        reg_diag_step<M, 0, Real>(v, c, pt ? -mus : mus, chi);
       } else {
         const Real zr = pair_z<Real>(I.mu, sgs);
         const bool odd = (I.mu & 1) != 0;
         const uint32_t aL = L.a_loc & 31u;
         // sign of the partner x ^ a of element j: parity of (x ^ a) & b
         const uint32_t pt = (pw ^ __popc((lane ^ aL) & bL) ^ __popc((uint32_t)L.ra & L.rb)) & 1u;
-        const uint32_t sg = tb ^ (pt ? (1u << NJ) - 1u : 0u);
-        reg_pair_dispatch<M, Real>(L.ra, v, aL, c, zr, odd, sg);
+        const Real chiAR = (__popc((uint32_t)L.ra & L.rb) & 1u) ? (Real)-1 : (Real)1;
+        reg_pair_dispatch<M, Real>(L.ra, v, aL, c, pt ? -zr : zr, chi, chiAR, odd);
       }
     }
 #pragma unroll
