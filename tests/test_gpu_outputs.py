@@ -313,3 +313,48 @@ def test_wide_tile_shapes_give_the_same_bits(precision, bits):
     for o in outs[1:]:
         for x, y in zip(outs[0], o):
             np.testing.assert_array_equal(x, y)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_wide_register_phases_with_wide_pair_masks_against_the_oracle(precision):
+    """Windows of the wide executor split into register phases; a rotation
+    whose pair bits above the lanes do not fit in the register bits runs on
+    the whole tile in shared memory between two register phases.  A random
+    near-Clifford circuit (18 qubits, 20 rotations on weight-1..4 Paulis,
+    k_max = 17) has such rotations in both precisions (host analysis of its
+    windows: FP32 4 register phases and 2 shared-memory ones, FP64 6 and 2).
+    Four shots on the wide executor, outcome by outcome and every active
+    branch probability against the plain SymFT oracle: FP64 within 1e-9 and
+    equal records; FP32 within 1e-5 up to a shot's first outcome flip."""
+    import paper_2607_28600_b300 as S
+    from oracle import symft as osymft
+    text = random_near_clifford(18, 40, 20, 1e-3, seed=7)
+    plan = S.symft_compile(text, product_components=False, executor="wide")
+    info = plan.info
+    assert info["k_max"] == 17 and info["dense_executor"][precision] == "wide"
+    n, seed = 4, 9
+    meas = torch.zeros((info["n_records"], 1), dtype=torch.int64, device="cuda")
+    prob = torch.zeros((info["n_causal"], n), dtype=torch.float64, device="cuda")
+    S.symft_sample_ex(plan, n, seed, meas_out=meas, precision=precision, prob_out=prob, check=True)
+    torch.cuda.synchronize()
+    recs = unpack(meas.cpu().numpy().view(np.uint64), n)
+    c = oparse(text)
+    act = plan.active_meas()
+    for shot in range(n):
+        log = []
+        o = osymft.sample_shot(osymft.Plan(c), seed, shot, NoiseSampler(c, seed), prob_log=log)
+        want = np.array([o[op.t] for op in c.ops if op.kind == "meas" and op.rec >= 0], dtype=np.uint8)
+        ref = dict(log)
+        got = prob.cpu().numpy()[:, shot]
+        if precision == 1:
+            np.testing.assert_array_equal(recs[shot], want)
+            assert np.abs(got - np.array([ref[t] for t in act])).max() <= 1e-9
+            continue
+        flipped = False
+        for j, t in enumerate(act):
+            assert abs(got[j] - ref[t]) <= 1e-5, (shot, j, got[j], ref[t])
+            if outcome_from(got[j], meas_uniform(seed, t, shot)) != outcome_from(ref[t], meas_uniform(seed, t, shot)):
+                flipped = True
+                break
+        if not flipped:
+            np.testing.assert_array_equal(recs[shot], want)
