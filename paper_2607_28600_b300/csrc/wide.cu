@@ -43,9 +43,11 @@ __device__ __forceinline__ uint32_t wide_insert_bit(uint32_t z, int h, uint32_t 
 }
 
 // Element updates shared by every rotation pass (lone, fused in shared
-// memory, fused in registers), so all give the same bits.  Pair rotation: v' = c v + s z w, w the partner
-// element, s = -1 when `neg`, z = sg s i^mu is real (mu odd) or imaginary
-// (mu even), so z w takes two products: zr = the non-zero part of z.
+// memory, fused in registers), so all give the same bits.  Pair rotation:
+// v' = c v + s z w with w the partner element, s = -1 when `neg` (the
+// partner's (-1)^{b.x}) and z = -i i^mu sg s, which is real for odd mu and
+// imaginary for even mu, so z w takes two products; zr is z's non-zero part
+// (k = s zr) and `odd` selects which part it is.
 template <typename Real>
 __device__ __forceinline__ Amp<Real> pair_update_k(Amp<Real> v, Amp<Real> w, Real c, Real k, bool odd) {
   const Real pr = odd ? w.re : -w.im;
@@ -75,7 +77,7 @@ __device__ __forceinline__ Amp<Real> pair_update(Amp<Real> v, Amp<Real> w, Real 
   return pair_update_k(v, w, c, neg ? -zr : zr, odd);
 }
 
-// the non-zero part of z = sg s i^mu (mu odd: real, even: imaginary)
+// the non-zero part of z = -i i^mu sg s (odd mu: real, even mu: imaginary)
 template <typename Real>
 __device__ __forceinline__ Real pair_z(int mu, Real sgs) {
   // i^mu times -i: mu = 0 -> -i, 1 -> 1, 2 -> i, 3 -> -1
