@@ -197,17 +197,34 @@ void build_blob(symft_plan* P) {
     P->off.sm1 = push(blob, sm1);
     P->off.sm1o = push(blob, ovf);
   }
-  // level items: record and up to four parents, 16 bits each
-  std::vector<uint4> lvl_item(std::max<size_t>(1, h.lvl_rec.size()));
-  for (size_t x = 0; x < h.lvl_rec.size(); ++x) {
-    const uint32_t r = h.lvl_rec[x], p0 = h.par_off[r], np = h.par_off[r + 1] - p0;
-    if (np > 4) throw Error(SYMFT_E_DEVICE, "internal: more than four parent records");
-    uint32_t pp[4] = {0, 0, 0, 0};
-    for (uint32_t q = 0; q < np; ++q) pp[q] = h.par[p0 + q];
-    lvl_item[x] = make_uint4(r | (np << 16), pp[0] | (pp[1] << 16), pp[2] | (pp[3] << 16), 0u);
+  // record chains as paths: from each root that has a child, the chain of
+  // single children (the compile step gives every record at most one parent
+  // and at most one child)
+  {
+    std::vector<int64_t> child(h.n_records, -1);
+    for (uint32_t r = 0; r < h.n_records; ++r) {
+      const uint32_t np = h.par_off[r + 1] - h.par_off[r];
+      if (np > 1) throw Error(SYMFT_E_DEVICE, "internal: a record with more than one parent");
+      if (np == 1) {
+        const uint32_t pa = h.par[h.par_off[r]];
+        if (child[pa] >= 0) throw Error(SYMFT_E_DEVICE, "internal: a record with more than one child");
+        child[pa] = r;
+      }
+    }
+    std::vector<uint2> pdesc;
+    std::vector<uint32_t> prec;
+    for (uint32_t r = 0; r < h.n_records; ++r) {
+      if (h.par_off[r + 1] != h.par_off[r] || child[r] < 0) continue;
+      const uint32_t x = static_cast<uint32_t>(prec.size());
+      for (int64_t q = r; q >= 0; q = child[q]) prec.push_back(static_cast<uint32_t>(q));
+      pdesc.push_back(make_uint2(x, static_cast<uint32_t>(prec.size()) - x));
+    }
+    P->off.n_pth = static_cast<uint32_t>(pdesc.size());
+    if (pdesc.empty()) pdesc.push_back(make_uint2(0u, 0u));
+    if (prec.empty()) prec.push_back(0);
+    P->off.pds = push(blob, pdesc);
+    P->off.prc = push(blob, prec);
   }
-  if (h.lvl_off.size() > static_cast<size_t>(kMaxLevels) + 1)
-    throw Error(SYMFT_E_DEVICE, "internal: record chains deeper than the level limit");
   // detector / observable gathers: up to seven records inline, else a list
   const size_t n_gat = h.gat_off.size() - 1;
   std::vector<uint4> gat_item(std::max<size_t>(1, n_gat));
@@ -263,7 +280,6 @@ void build_blob(symft_plan* P) {
   P->off.m3t = push(blob, h.m3_t);
   P->off.pco = push(blob, h.post_chk_off);
   P->off.pch = push(blob, h.post_chk);
-  P->off.li = push(blob, lvl_item);
   P->off.gi = push(blob, gat_item);
   P->off.gv = push(blob, gat_ovf);
   P->off.pe = push(blob, h.post_events);
@@ -302,8 +318,9 @@ void bind_plan(const symft_plan* P, unsigned char* base, DevPlan* dptr) {
   d.slot_const = reinterpret_cast<const uint8_t*>(at(P->off.sc));
   d.slot_m1 = reinterpret_cast<const uint4*>(at(P->off.sm1));
   d.slot_m1_ovf = reinterpret_cast<const uint32_t*>(at(P->off.sm1o));
-  d.n_levels = h.lvl_off.empty() ? 0 : static_cast<uint32_t>(h.lvl_off.size() - 1);
-  d.lvl_item = reinterpret_cast<const uint4*>(at(P->off.li));
+  d.n_paths = P->off.n_pth;
+  d.path_desc = reinterpret_cast<const uint2*>(at(P->off.pds));
+  d.path_rec = reinterpret_cast<const uint32_t*>(at(P->off.prc));
   d.m3_t = reinterpret_cast<const uint32_t*>(at(P->off.m3t));
   const bool early = h.postselect && !h.post_chk.empty();
   d.post_chk_off = early ? reinterpret_cast<const uint32_t*>(at(P->off.pco)) : nullptr;
@@ -697,7 +714,6 @@ int enqueue(symft_plan* P, const symft_sample_args* a, const Prep& o, cudaStream
     s.p = P->dp;
     s.seed = a->seed;
     s.keys = make_philox_keys(a->seed);
-    set_levels(h, &s);
     s.block0 = a->shot_offset / kNoiseBlock;
     s.n_blocks = o.nblk;
     s.W = W;

@@ -789,7 +789,7 @@ void Compiler::lower(HostPlan& P) {
   }
 
   // ---- exogenous record parts, delta-chained to earlier records ----
-  // The sign kernel evaluates exo_r = const ^ delta_r ^ XOR(parents).  A parent
+  // The sign kernel evaluates exo_r = const ^ delta_r ^ exo(parent).  A parent
   // is taken when it removes enough weighted incidences: a noise component
   // costs work only in the rare blocks where it fires, a random-measurement
   // bit every block, a parent one word-XOR per block.
@@ -821,12 +821,18 @@ void Compiler::lower(HostPlan& P) {
   std::vector<Expr> delta(R);
   std::vector<std::vector<uint32_t>> inv(NS);       // symbol -> records containing it
   constexpr uint64_t kParentGain = 20;
-  constexpr int kMaxParents = 4;
   constexpr size_t kMaxCand = 96;
-  // chains are cut at depth kMaxLevels: the sign kernel resolves records
-  // level by level, one CTA barrier per level
-  constexpr uint32_t kMaxLevel = kMaxLevels;
+  // The chains are paths: a record takes at most one parent, and a record is
+  // the parent of at most one other, so the sign kernel walks each path in one
+  // thread with no barrier between its records.  (More parents, or several
+  // children per parent, remove more incidences -- d=7: 2.61 against 3.31
+  // targets per fired cell -- but the kernel then resolves the records level
+  // by level with a CTA barrier per level, measured slower.)  Paths are cut
+  // after kMaxLevels records.
+  constexpr int kMaxParents = 1;
+  constexpr uint32_t kMaxLevel = kMaxLevels - 1;
   std::vector<uint32_t> level(R, 0);
+  std::vector<uint8_t> has_child(R, 0);
   std::vector<uint32_t> seen_mark(R, 0xFFFFFFFFu);
   for (uint32_t r = 0; r < R; ++r) {
     Expr resid = exo[r];
@@ -839,7 +845,7 @@ void Compiler::lower(HostPlan& P) {
         const auto& lst = inv[sidx];
         for (size_t j = lst.size(); j-- > 0 && cand.size() < kMaxCand;) {
           uint32_t p = lst[j];
-          if (level[p] >= kMaxLevel) continue;
+          if (level[p] >= kMaxLevel || has_child[p]) continue;
           if (seen_mark[p] != r * 8 + it) {
             seen_mark[p] = r * 8 + it;
             cand.push_back(p);
@@ -861,23 +867,16 @@ void Compiler::lower(HostPlan& P) {
       ea_.xor_into(resid, exo[best]);
       cres = best_c;
       parents[r].push_back(static_cast<uint32_t>(best));
+      has_child[best] = 1;
       level[r] = std::max(level[r], level[best] + 1);
     }
     delta[r] = std::move(resid);
     ea_.for_each(exo[r], 0, NS, [&](uint32_t sidx) { inv[sidx].push_back(r); });
   }
-  uint32_t max_level = 0;
-  for (uint32_t r = 0; r < R; ++r) max_level = std::max(max_level, level[r]);
   P.par_off.assign(R + 1, 0);
   for (uint32_t r = 0; r < R; ++r) {
     P.par.insert(P.par.end(), parents[r].begin(), parents[r].end());
     P.par_off[r + 1] = static_cast<uint32_t>(P.par.size());
-  }
-  P.lvl_off.assign(max_level + 1, 0);    // levels 1..max_level
-  for (uint32_t L = 1; L <= max_level; ++L) {
-    for (uint32_t r = 0; r < R; ++r)
-      if (level[r] == L) P.lvl_rec.push_back(r);
-    P.lvl_off[L] = static_cast<uint32_t>(P.lvl_rec.size());
   }
 
   // ---- sign-kernel slots: [records (deltas)][dense signs (exogenous part)] ----

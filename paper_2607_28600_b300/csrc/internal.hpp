@@ -138,11 +138,10 @@ struct HostPlan {
   std::vector<uint32_t> tgt_causal_off, tgt_causal;   // m3 indices per output
 
   // sign-kernel slots: [records][dense signs]; a record slot accumulates
-  // const + delta (noise and random bits) and then XORs in its parent records
+  // const + delta (noise and random bits) and then XORs in its parent record
   uint32_t n_slots = 0;
   std::vector<uint8_t> slot_const;
-  std::vector<uint32_t> par_off, par;        // record -> parent records (CSR)
-  std::vector<uint32_t> lvl_off, lvl_rec;    // records with parents, grouped by level
+  std::vector<uint32_t> par_off, par;        // record -> parent record (CSR, at most one)
   std::vector<uint32_t> gat_off, gat_rec;    // det / obs -> records (CSR)
 
   // plain (per-shot, unpacked) form: full exogenous expression of every output

@@ -150,7 +150,6 @@ extern "C" int symft_sample_noalloc(const symft_plan* plan, uint64_t shots, uint
     s.p = dp;
     s.seed = seed;
     s.keys = make_philox_keys(seed);
-    set_levels(h, &s);
     s.block0 = shot_offset / kNoiseBlock;
     s.n_blocks = nblk;
     s.W = W;

@@ -15,7 +15,7 @@ constexpr uint32_t kTagHead = 1, kTagTail = 2, kTagMbit = 3, kTagMfrac = 4;
 constexpr int kNoiseBlock = 512;
 // shots per packed random-measurement Philox block (two 64-shot words)
 constexpr int kWordPair = 128;
-// levels of the record chains (the compile step cuts chains at this depth)
+// records per chain path at most (the compile step starts a new path there)
 constexpr int kMaxLevels = 16;
 
 struct ChannelDev {        // 16 bytes, one per noise channel
@@ -133,10 +133,12 @@ struct DevPlan {
   // indices, or n = 0x7FFF and (y, z) = (offset, count) of a list in slot_m1_ovf
   const uint4* slot_m1;
   const uint32_t* slot_m1_ovf;
-  // records with parents in level order, one 16-byte item each: x = record |
-  // (parents << 16), y = p0 | p1 << 16, z = p2 | p3 << 16
-  uint32_t n_levels;
-  const uint4* lvl_item;
+  // record chains as paths (every record has at most one parent and at most
+  // one child): path p is path_rec[x .. x + n) with (x, n) = path_desc[p],
+  // n >= 2, each record the parent of the next
+  uint32_t n_paths;
+  const uint2* path_desc;
+  const uint32_t* path_rec;
   // det / obs -> records: f0 = n <= 7 and f1..f(n) = records, or f0 = 0xFFFF
   // and (y, z) = (offset, count) of a record list in gat_ovf
   const uint4* gat_item;
@@ -201,7 +203,6 @@ inline PhiloxKeys make_philox_keys(uint64_t seed) {
 struct SignArgs {
   DevPlan p;
   PhiloxKeys keys;        // round keys of `seed`
-  uint32_t lvl[kMaxLevels + 1];   // level L holds lvl_item[lvl[L] .. lvl[L+1])
   uint64_t seed;
   uint64_t block0;        // global index of the first noise block (kNoiseBlock shots)
   uint64_t n_blocks;      // local noise blocks

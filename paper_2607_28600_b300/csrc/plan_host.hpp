@@ -38,7 +38,8 @@ struct BlobOffsets {
   size_t clt, clo;
   size_t ctg;
   uint32_t n_ctg = 0;
-  size_t snz, odl, ors;
+  size_t snz, odl, ors, pds, prc;
+  uint32_t n_pth = 0;
   uint32_t n_snz = 0, n_odl = 0, n_ors = 0;
 };
 
@@ -118,12 +119,6 @@ struct symft_plan {
 };
 
 namespace symft {
-// Level boundaries of the record chains into the sign kernel's parameters.
-inline void set_levels(const HostPlan& h, SignArgs* s) {
-  for (int L = 0; L <= kMaxLevels; ++L)
-    s->lvl[L] = h.lvl_off.empty() ? 0 : h.lvl_off[std::min<size_t>(L, h.lvl_off.size() - 1)];
-}
-
 // Build the device image of a compiled plan (throws Error on capacity limits).
 void build_blob(symft_plan* P);
 // Point the DevPlan arrays into a copy of the blob at `base` (device address).

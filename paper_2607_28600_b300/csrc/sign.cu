@@ -372,24 +372,20 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
         }
       }
     }
-    if (A.p.n_levels) __syncthreads();
-    // 5. records: XOR in the parent records level by level (exo_r = delta_r ^ parents)
-    for (uint32_t L = 0; L < A.p.n_levels; ++L) {
-      const uint32_t hi = A.lvl[L + 1] * kSub;
-      for (uint32_t x = A.lvl[L] * kSub + threadIdx.x; x < hi; x += blockDim.x) {
-        const uint4 it = __ldg(A.p.lvl_item + x / kSub);
-        const uint32_t bb = x % kSub, np = it.x >> 16;
-        const uint32_t pr[4] = {it.y & 0xFFFFu, it.y >> 16, it.z & 0xFFFFu, it.z >> 16};
-        uint4 acc = slots[(it.x & 0xFFFFu) * kSub + bb];
-#pragma unroll
-        for (uint32_t k = 0; k < 4; ++k) {
-          if (k >= np) break;
-          acc = xor4(acc, slots[pr[k] * kSub + bb]);
-        }
-        slots[(it.x & 0xFFFFu) * kSub + bb] = acc;
+    __syncthreads();
+    // 5. records: each chain path walked by one thread per sub-block, no
+    //    barrier between its records (exo_r = delta_r ^ exo_parent)
+    for (uint32_t x = threadIdx.x; x < A.p.n_paths * kSub; x += blockDim.x) {
+      const uint2 pd = __ldg(A.p.path_desc + x / kSub);
+      const uint32_t bb = x % kSub;
+      uint4 acc = slots[(size_t)__ldg(A.p.path_rec + pd.x) * kSub + bb];
+      for (uint32_t i = 1; i < pd.y; ++i) {
+        uint4* sl = slots + (size_t)__ldg(A.p.path_rec + pd.x + i) * kSub + bb;
+        acc = xor4(acc, *sl);
+        *sl = acc;
       }
-      __syncthreads();
     }
+    __syncthreads();
     // 6. write the records, the gathered detectors / observables (XOR of
     //    records) and the dense signs
     const Piece pc = piece_of(A, sub0, nsub);
