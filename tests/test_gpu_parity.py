@@ -41,6 +41,18 @@ def test_surface_code_bit_exact(d, p, shots):
     np.testing.assert_array_equal(g["obs"], o["obs"])
 
 
+def test_long_memory_chains_cut_into_paths_bit_exact():
+    """A 24-round d=3 memory: each stabilizer's records chain over 24 rounds,
+    longer than the 16 records a chain path may hold, so the compile step
+    starts new paths within a chain.  Every record, detector and observable
+    bit against the tableau oracle."""
+    text = rotated_surface_code_memory(3, 24, 2e-2)
+    _, g, o = _compare(text, 700, seed=5)
+    np.testing.assert_array_equal(g["records"], o["records"])
+    np.testing.assert_array_equal(g["dets"], o["dets"])
+    np.testing.assert_array_equal(g["obs"], o["obs"])
+
+
 @pytest.mark.parametrize("shots", [1, 63, 64, 65, 127, 128, 129, 300])
 def test_ragged_shot_counts(shots):
     text = rotated_surface_code_memory(3, 2, 5e-2)
