@@ -56,6 +56,19 @@ def test_surface_code_plan_counts(d):
     assert info["n_instr"]["RandomMeas"] == d * d - 1
 
 
+@pytest.mark.parametrize("d,rounds", [(3, 24), (3, 40), (11, 11), (13, 13)])
+def test_long_and_large_record_chains_compile(d, rounds):
+    """The compile step turns the record chains into paths (each record at
+    most one parent and one child, at most 16 records per path) and the device
+    image checks both properties; memories whose stabilizer chains are longer
+    than a path (24 and 40 rounds) or large (d = 11, 13) compile with every
+    record of the circuit in the plan."""
+    p = S.symft_compile(rotated_surface_code_memory(d, rounds, 1e-3))
+    info = p.info
+    assert info["n_records"] == (d * d - 1) * rounds + d * d
+    assert info["sign_xor_terms"] > 0
+
+
 @pytest.mark.parametrize("text,code", [
     ("H 0\nFOO 1\n", -2),
     ("H 0\nCX 0\n", -1),
