@@ -211,19 +211,22 @@ void build_blob(symft_plan* P) {
         child[pa] = r;
       }
     }
-    std::vector<uint2> pdesc;
-    std::vector<uint32_t> prec;
+    // 16 fields of 16 bits per path (two 16-byte items), unused ones 0xFFFF
+    std::vector<uint16_t> ids;
     for (uint32_t r = 0; r < h.n_records; ++r) {
       if (h.par_off[r + 1] != h.par_off[r] || child[r] < 0) continue;
-      const uint32_t x = static_cast<uint32_t>(prec.size());
-      for (int64_t q = r; q >= 0; q = child[q]) prec.push_back(static_cast<uint32_t>(q));
-      pdesc.push_back(make_uint2(x, static_cast<uint32_t>(prec.size()) - x));
+      const size_t x = ids.size();
+      ids.resize(x + kMaxLevels, 0xFFFFu);
+      size_t n = 0;
+      for (int64_t q = r; q >= 0; q = child[q], ++n) {
+        if (n == static_cast<size_t>(kMaxLevels) || q >= 0xFFFF)
+          throw Error(SYMFT_E_DEVICE, "internal: a record chain path longer than the path limit");
+        ids[x + n] = static_cast<uint16_t>(q);
+      }
     }
-    P->off.n_pth = static_cast<uint32_t>(pdesc.size());
-    if (pdesc.empty()) pdesc.push_back(make_uint2(0u, 0u));
-    if (prec.empty()) prec.push_back(0);
-    P->off.pds = push(blob, pdesc);
-    P->off.prc = push(blob, prec);
+    P->off.n_pth = static_cast<uint32_t>(ids.size() / kMaxLevels);
+    if (ids.empty()) ids.resize(kMaxLevels, 0xFFFFu);
+    P->off.pid = push(blob, ids);
   }
   // detector / observable gathers: up to seven records inline, else a list
   const size_t n_gat = h.gat_off.size() - 1;
@@ -319,8 +322,7 @@ void bind_plan(const symft_plan* P, unsigned char* base, DevPlan* dptr) {
   d.slot_m1 = reinterpret_cast<const uint4*>(at(P->off.sm1));
   d.slot_m1_ovf = reinterpret_cast<const uint32_t*>(at(P->off.sm1o));
   d.n_paths = P->off.n_pth;
-  d.path_desc = reinterpret_cast<const uint2*>(at(P->off.pds));
-  d.path_rec = reinterpret_cast<const uint32_t*>(at(P->off.prc));
+  d.path_ids = reinterpret_cast<const uint4*>(at(P->off.pid));
   d.m3_t = reinterpret_cast<const uint32_t*>(at(P->off.m3t));
   const bool early = h.postselect && !h.post_chk.empty();
   d.post_chk_off = early ? reinterpret_cast<const uint32_t*>(at(P->off.pco)) : nullptr;

@@ -134,11 +134,11 @@ struct DevPlan {
   const uint4* slot_m1;
   const uint32_t* slot_m1_ovf;
   // record chains as paths (every record has at most one parent and at most
-  // one child): path p is path_rec[x .. x + n) with (x, n) = path_desc[p],
-  // n >= 2, each record the parent of the next
+  // one child): path p is path_ids[2p], path_ids[2p + 1], its 2..kMaxLevels
+  // records as 16-bit fields in order, each the parent of the next, the
+  // unused fields 0xFFFF
   uint32_t n_paths;
-  const uint2* path_desc;
-  const uint32_t* path_rec;
+  const uint4* path_ids;
   // det / obs -> records: f0 = n <= 7 and f1..f(n) = records, or f0 = 0xFFFF
   // and (y, z) = (offset, count) of a record list in gat_ovf
   const uint4* gat_item;

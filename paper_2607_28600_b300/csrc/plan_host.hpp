@@ -38,7 +38,7 @@ struct BlobOffsets {
   size_t clt, clo;
   size_t ctg;
   uint32_t n_ctg = 0;
-  size_t snz, odl, ors, pds, prc;
+  size_t snz, odl, ors, pid;
   uint32_t n_pth = 0;
   uint32_t n_snz = 0, n_odl = 0, n_ors = 0;
 };

@@ -45,6 +45,8 @@ __device__ __forceinline__ void scatter7(uint32_t* sw, uint4 tg, uint32_t n, uin
 
 // 128-lane sub-blocks of a noise block; a slot holds one uint4 per sub-block
 constexpr int kSub = kNoiseBlock / 128;
+// a chain path's record ids are two 16-byte items of eight 32-bit words
+static_assert(kMaxLevels == 16, "the path walk reads 16 record ids per path");
 
 // This thread's 16-byte column pieces in a noise block: sub-block t % kSub of
 // every (blockDim / kSub)-th column, so consecutive threads cover consecutive
@@ -375,12 +377,17 @@ __global__ void __launch_bounds__(kSignWarps * 32, 5) sign_kernel(SignArgs A) {
     __syncthreads();
     // 5. records: each chain path walked by one thread per sub-block, no
     //    barrier between its records (exo_r = delta_r ^ exo_parent)
+    //    The path's record ids (two 16-byte items) are loaded up front.
     for (uint32_t x = threadIdx.x; x < A.p.n_paths * kSub; x += blockDim.x) {
-      const uint2 pd = __ldg(A.p.path_desc + x / kSub);
+      const uint4 w0 = __ldg(A.p.path_ids + 2 * (x / kSub)), w1 = __ldg(A.p.path_ids + 2 * (x / kSub) + 1);
+      const uint32_t f[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
       const uint32_t bb = x % kSub;
-      uint4 acc = slots[(size_t)__ldg(A.p.path_rec + pd.x) * kSub + bb];
-      for (uint32_t i = 1; i < pd.y; ++i) {
-        uint4* sl = slots + (size_t)__ldg(A.p.path_rec + pd.x + i) * kSub + bb;
+      uint4 acc = slots[(size_t)(f[0] & 0xFFFFu) * kSub + bb];
+#pragma unroll
+      for (int i = 1; i < kMaxLevels; ++i) {
+        const uint32_t id = (i & 1) ? (f[i >> 1] >> 16) : (f[i >> 1] & 0xFFFFu);
+        if (id == 0xFFFFu) break;
+        uint4* sl = slots + (size_t)id * kSub + bb;
         acc = xor4(acc, *sl);
         *sl = acc;
       }
