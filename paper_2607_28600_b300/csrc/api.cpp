@@ -220,7 +220,8 @@ void build_blob(symft_plan* P) {
       size_t n = 0;
       for (int64_t q = r; q >= 0; q = child[q], ++n) {
         if (n == static_cast<size_t>(kMaxLevels) || q >= 0xFFFF)
-          throw Error(SYMFT_E_DEVICE, "internal: a record chain path longer than the path limit");
+          throw Error(SYMFT_E_DEVICE, "internal: a record chain path of more than 16 records or a record index "
+                                      "beyond 16 bits");
         ids[x + n] = static_cast<uint16_t>(q);
       }
     }
